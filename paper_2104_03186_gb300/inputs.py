@@ -1,0 +1,227 @@
+"""Seeded synthetic LQT workloads.
+
+This module only draws inputs: dynamics (F_k, c_k, L_k), costs (H_k, r_k, X_k,
+U_k), terminal terms (H_T, r_T, X_T) and the initial state x_0 of the LQT
+problem of Sec. II-B (eq. LQT_problem).  It holds none of the solver's
+arithmetic, so the CUDA path and the FP64 oracle can both be fed from it.
+
+Per-step arrays carry a leading time axis of length T, or of length 1 for a
+matrix that is the same at every step (a step stride of 0 at the C ABI).
+All arrays are float64 and C-contiguous; ``LQTProblem.astype`` casts them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+STEP_FIELDS = ("F", "c", "L", "U", "H", "r", "X")
+
+
+@dataclasses.dataclass
+class LQTProblem:
+    F: np.ndarray            # (1|T, n, n)
+    c: Optional[np.ndarray]  # (1|T, n) or None (= 0)
+    L: np.ndarray            # (1|T, n, m)
+    U: np.ndarray            # (1|T, m, m)
+    H: np.ndarray            # (1|T, p, n)
+    r: Optional[np.ndarray]  # (1|T, p) or None (= 0)
+    X: np.ndarray            # (1|T, p, p)
+    HT: np.ndarray           # (pT, n)
+    rT: Optional[np.ndarray] # (pT,) or None (= 0)
+    XT: np.ndarray           # (pT, pT)
+    x0: np.ndarray           # (n,)
+    T: int
+
+    @property
+    def n(self) -> int:
+        return int(self.F.shape[-1])
+
+    @property
+    def m(self) -> int:
+        return int(self.L.shape[-1])
+
+    @property
+    def p(self) -> int:
+        return int(self.H.shape[-2])
+
+    @property
+    def pT(self) -> int:
+        return int(self.HT.shape[0])
+
+    def time_invariant(self, name: str) -> bool:
+        a = getattr(self, name)
+        return a is None or a.shape[0] == 1
+
+    def astype(self, dtype) -> "LQTProblem":
+        def cast(a):
+            return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+        return dataclasses.replace(
+            self, **{f.name: cast(getattr(self, f.name))
+                     for f in dataclasses.fields(self) if f.name != "T"})
+
+    def rounded_to(self, dtype) -> "LQTProblem":
+        """Round every input to ``dtype`` and back to float64, so that a
+        lower-precision solver and a float64 reference see identical values."""
+        return self.astype(dtype).astype(np.float64)
+
+    def check(self) -> None:
+        n, m, p, T = self.n, self.m, self.p, self.T
+        shapes = {"F": (n, n), "c": (n,), "L": (n, m), "U": (m, m),
+                  "H": (p, n), "r": (p,), "X": (p, p)}
+        for name, tail in shapes.items():
+            a = getattr(self, name)
+            if a is None:
+                continue
+            assert a.shape[1:] == tail, (name, a.shape, tail)
+            assert a.shape[0] in (1, T), (name, a.shape, T)
+        assert self.HT.shape == (self.pT, n)
+        assert self.XT.shape == (self.pT, self.pT)
+        assert self.rT is None or self.rT.shape == (self.pT,)
+        assert self.x0.shape == (n,)
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# 2-D constant-velocity vehicle tracking (the paper's Sec. VI-A model).
+# ---------------------------------------------------------------------------
+
+def vehicle_model(dt: float = 0.1):
+    """F and L of the 2-D constant-velocity model printed in Sec. VI-A:
+    state (p_x, p_y, v_x, v_y), control (a_x, a_y)."""
+    I2 = np.eye(2)
+    Z2 = np.zeros((2, 2))
+    F = np.block([[I2, dt * I2], [Z2, I2]])
+    L = np.vstack([0.5 * dt * dt * I2, dt * I2])
+    return _c(F), _c(L)
+
+
+def vehicle_reference(T: int, rng: np.random.Generator, noise: float = 0.01) -> np.ndarray:
+    """r_k = (sin 0.01k, cos 0.013k) + N(0, noise^2), k = 0..T (row T is r_T)."""
+    k = np.arange(T + 1, dtype=np.float64)
+    r = np.stack([np.sin(0.01 * k), np.cos(0.013 * k)], axis=1)
+    return _c(r + noise * rng.standard_normal(r.shape))
+
+
+def vehicle(T: int, seed: int = 0, dt: float = 0.1, x_weight: float = 1.0,
+            u_weight: float = 0.1, terminal_weight: float = 100.0) -> LQTProblem:
+    """Vehicle tracking workload: nx=4, nu=2, p=2.
+
+    F = [[I, dt I], [0, I]], L = [[dt^2/2 I], [dt I]], c = 0, H = [I 0],
+    X_k = x_weight I, U_k = u_weight I, terminal H_T = [I 0],
+    X_T = terminal_weight I; r_k a sinusoid plus N(0, 0.01^2) noise;
+    x_0 ~ N(0, I).  Time-invariant matrices have a leading axis of 1.
+    """
+    rng = np.random.default_rng(seed)
+    F, L = vehicle_model(dt)
+    H = np.hstack([np.eye(2), np.zeros((2, 2))])
+    r = vehicle_reference(T, rng)
+    x0 = rng.standard_normal(4)
+    return LQTProblem(
+        F=F[None], c=None, L=L[None], U=_c(u_weight * np.eye(2))[None],
+        H=_c(H)[None], r=_c(r[:T]), X=_c(x_weight * np.eye(2))[None],
+        HT=_c(H), rT=_c(r[T]), XT=_c(terminal_weight * np.eye(2)), x0=_c(x0), T=T)
+
+
+def paper_tracking(T: int, seed: int = 0, dt: float = 0.1) -> LQTProblem:
+    """The cost set-up of Sec. VI-A as printed: reference points every 10th step
+    (held in between), X_k = c_k I with c_k = 100 at reference steps and 1e-6
+    otherwise, U = 0.1 I, H_T = I_4, X_T = I_4 and a zero terminal velocity.
+    The reference points themselves are only shown in a figure, so a seeded
+    smooth curve stands in for them."""
+    rng = np.random.default_rng(seed)
+    F, L = vehicle_model(dt)
+    H = np.hstack([np.eye(2), np.zeros((2, 2))])
+    n_pts = T // 10 + 1
+    s = np.linspace(0.0, 2.0 * math.pi, n_pts)
+    pts = np.stack([5.0 * np.cos(s), 5.0 * np.sin(2 * s)], 1) + 0.1 * rng.standard_normal((n_pts, 2))
+    k = np.arange(T)
+    r = pts[k // 10]
+    ck = np.where(k % 10 == 0, 100.0, 1e-6)
+    X = ck[:, None, None] * np.eye(2)[None]
+    rT = np.concatenate([pts[T // 10], np.zeros(2)])
+    x0 = np.array([5.0, 5.0, 0.0, 0.0])
+    return LQTProblem(
+        F=F[None], c=None, L=L[None], U=_c(0.1 * np.eye(2))[None],
+        H=_c(H)[None], r=_c(r), X=_c(X), HT=_c(np.eye(4)), rT=_c(rT),
+        XT=_c(np.eye(4)), x0=_c(x0), T=T)
+
+
+# ---------------------------------------------------------------------------
+# Random problems.
+# ---------------------------------------------------------------------------
+
+def _stable_dynamics(rng, n, count, radius=1.05, spread=0.05):
+    F = np.eye(n)[None] + spread * rng.standard_normal((count, n, n))
+    for i in range(count):
+        rho = np.max(np.abs(np.linalg.eigvals(F[i])))
+        if rho > radius:
+            F[i] *= radius / rho
+    return F
+
+
+def _psd(rng, p, count, rank=None):
+    rank = p if rank is None else rank
+    B = rng.standard_normal((count, p, rank)) / math.sqrt(max(rank, 1))
+    return B @ np.swapaxes(B, 1, 2)
+
+
+def random_problem(n: int, m: int, p: Optional[int] = None, T: int = 16, seed: int = 0,
+                   time_varying: bool = True, with_c: bool = True, pT: Optional[int] = None,
+                   x_rank: Optional[int] = None, u_scale: float = 0.1) -> LQTProblem:
+    """A random time-varying LQT problem with F_k = I + 0.05 N(0,1) (rescaled to
+    spectral radius <= 1.05), L_k ~ N(0, 1/n), X_k = B B^T (PSD, optionally rank
+    deficient), U_k = u_scale I + a random SPD part, r_k ~ N(0, 1),
+    c_k ~ N(0, 0.1^2)."""
+    p = n if p is None else p
+    pT = p if pT is None else pT
+    rng = np.random.default_rng(seed)
+    cnt = T if time_varying else 1
+    F = _stable_dynamics(rng, n, cnt)
+    L = rng.standard_normal((cnt, n, m)) / math.sqrt(n)
+    H = rng.standard_normal((cnt, p, n)) / math.sqrt(n)
+    X = _psd(rng, p, cnt, x_rank)
+    U = u_scale * np.eye(m)[None] + 0.1 * _psd(rng, m, cnt)
+    r = rng.standard_normal((T, p))
+    c = 0.1 * rng.standard_normal((cnt, n)) if with_c else None
+    HT = rng.standard_normal((pT, n)) / math.sqrt(n)
+    XT = _psd(rng, pT, 1)[0]
+    rT = rng.standard_normal(pT)
+    x0 = rng.standard_normal(n)
+    return LQTProblem(F=_c(F), c=None if c is None else _c(c), L=_c(L), U=_c(U), H=_c(H),
+                      r=_c(r), X=_c(X), HT=_c(HT), rT=_c(rT), XT=_c(XT), x0=_c(x0), T=T)
+
+
+def diag_tracking(n: int, T: int, seed: int = 0) -> LQTProblem:
+    """Stable random dynamics with m = n/2, H = I, c = 0, X_k = diag(U[0.5, 2]),
+    terminal X_T drawn the same way, U = 0.1 I, r_k ~ N(0, 1), x_0 ~ N(0, I)."""
+    m = max(n // 2, 1)
+    rng = np.random.default_rng(seed)
+    F = _stable_dynamics(rng, n, T)
+    L = rng.standard_normal((T, n, m)) / math.sqrt(n)
+    X = np.zeros((T, n, n))
+    idx = np.arange(n)
+    X[:, idx, idx] = rng.uniform(0.5, 2.0, (T, n))
+    XT = np.diag(rng.uniform(0.5, 2.0, n))
+    r = rng.standard_normal((T, n))
+    rT = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    return LQTProblem(F=_c(F), c=None, L=_c(L), U=_c(0.1 * np.eye(m))[None],
+                      H=_c(np.eye(n))[None], r=_c(r), X=_c(X), HT=_c(np.eye(n)), rT=_c(rT),
+                      XT=_c(XT), x0=_c(x0), T=T)
+
+
+def scalar_lqr(a: float, b: float, q: float, rho: float, T: int, s_terminal: float,
+               x0: float = 1.0) -> LQTProblem:
+    """Scalar time-invariant regulator: n = m = p = 1, F = a, L = b, H = 1,
+    X = q, U = rho, r = c = 0, terminal weight s_terminal."""
+    one = np.ones((1, 1, 1))
+    return LQTProblem(F=a * one, c=None, L=b * one, U=rho * one, H=one.copy(), r=None,
+                      X=q * one, HT=np.ones((1, 1)), rT=None, XT=np.full((1, 1), s_terminal),
+                      x0=np.array([x0], dtype=np.float64), T=T)
