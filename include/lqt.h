@@ -1,0 +1,184 @@
+/*
+ * lqt.h -- C ABI of the GB300 (sm_103a) temporally parallel LQT solver.
+ *
+ * The library solves the linear quadratic tracking (LQT) problem of
+ * Särkkä & García-Fernández, "Temporal Parallelisation of Dynamic Programming
+ * and Linear Quadratic Control", Sec. II-B, eq. LQT_problem:
+ *
+ *     x_{k+1} = F_k x_k + c_k + L_k u_k,                       k = 0..T-1
+ *     cost    = 1/2 (H_T x_T - r_T)^T X_T (H_T x_T - r_T)
+ *             + sum_k 1/2 (H_k x_k - r_k)^T X_k (H_k x_k - r_k) + 1/2 u_k^T U_k u_k
+ *
+ * with X_k, X_T symmetric positive semi-definite and U_k symmetric positive
+ * definite, and returns the value function V_k(x) = z + 1/2 x^T S_k x - v_k^T x
+ * (eq. V_k_LQT), the feedback gains K_k of the control law eq. Control_LQT, the
+ * optimal states x*_k and the optimal controls u*_k.
+ *
+ * Method (Sec. IV and V-A): per-step elements (A, b, C, eta, J) of eq. lqt_init,
+ * a backward parallel scan with the associative operator of eq. lqt_comb
+ * (Lemma LQT_combination) giving S_k = J_{k,T+1} and v_k = eta_{k,T+1}
+ * (Lemma LQT_assoc), and a forward parallel scan of the closed-loop affine maps
+ * (Lemma LQT_trajectory_combination, Lemma lqt_fwd_init: "Method 1").
+ * Scans are blocked (Sec. V-C): sequential folds over chunks of steps, and
+ * up/down sweeps (Sec. II-C, Alg. 1) over the chunk totals.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major, per-step arrays are time-major and densely packed
+ *     within one step.  A step stride (in elements) of 0 means the same matrix
+ *     at every step.
+ *   - dtype LQT_F32 means every input and output is float, LQT_F64 double.
+ *   - Unless an entry point says otherwise, every pointer is a DEVICE pointer
+ *     owned by the caller; inputs are only read.  The library allocates no
+ *     device memory: scratch space is the caller's workspace.
+ *   - Every pointer must be aligned to its element size; workspace pointers to
+ *     256 bytes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Solves are asynchronous: the return value reports argument
+ *     validation and launch errors only.  Numerical failures found on the
+ *     device are reported by lqt_workspace_status().
+ *   - Entry points are thread-safe except lqt_profile_enable/lqt_profile_read,
+ *     which keep process-wide state.
+ */
+#ifndef LQT_H
+#define LQT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LQT_OK = 0,
+    LQT_EINVAL = 1,       /* invalid argument (sizes, NULL pointer, alignment) */
+    LQT_ENOTSPD = 2,      /* L^T S L + U or U was not positive definite at some step */
+    LQT_ENONFINITE = 3,   /* a non-finite value appeared in the outputs */
+    LQT_ENOMEM = 4,       /* the workspace passed in is smaller than required */
+    LQT_ECUDA = 5,        /* a CUDA runtime call failed */
+    LQT_ETIMEOUT = 6,     /* a bounded device wait ran out */
+    LQT_EUNSUPPORTED = 7, /* no kernel compiled for this (n, m, dtype) */
+    LQT_ESINGULAR = 8     /* I + C J was numerically singular in a combine */
+} lqt_status;
+
+typedef enum { LQT_F32 = 0, LQT_F64 = 1 } lqt_dtype;
+
+/* One per-step input: base pointer and the distance between consecutive steps
+ * in elements (0 = time-invariant). */
+typedef struct {
+    const void *ptr;
+    int64_t step_stride;
+} lqt_in;
+
+/* The problem of eq. LQT_problem with S = 0 (Sec. II-A numbering k = 0..T).
+ *   n = state size nx, m = control size nu, p = rows of H_k, pT = rows of H_T.
+ *   F : n x n,  c : n (ptr may be NULL: c_k = 0),  L : n x m,  U : m x m
+ *   H : p x n,  r : p (ptr may be NULL: r_k = 0),  X : p x p        (k = 0..T-1)
+ *   HT: pT x n, rT: pT (may be NULL), XT: pT x pT                   (terminal)
+ *   x0: n                                                             (initial state)
+ * The stride of a time-varying input must be at least its per-step size. */
+typedef struct {
+    int32_t n, m, p, pT;
+    int64_t T;
+    int32_t dtype; /* lqt_dtype */
+    lqt_in F, c, L, U;
+    lqt_in H, r, X;
+    const void *HT, *rT, *XT;
+    const void *x0;
+} lqt_problem;
+
+/* Outputs (caller-allocated, contiguous, dtype of the problem):
+ *   S: (T+1) x n x n   value-function matrices S_0..S_T   (eq. V_k_LQT)
+ *   v: (T+1) x n       value-function vectors  v_0..v_T
+ *   K: T x m x n       feedback gains K_0..K_{T-1}        (eq. Control_LQT)
+ *   x: (T+1) x n       optimal states x*_0..x*_T          (x*_0 = x0)
+ *   u: T x m           optimal controls u*_0..u*_{T-1}
+ * Output arrays must not overlap each other or any input. */
+typedef struct {
+    void *S, *v, *K, *x, *u;
+} lqt_solution;
+
+/* Solver options.  Pass NULL for the defaults (refine = LQT_REFINE_AUTO).
+ *
+ * refine: mixed-precision iterative refinement of the trajectory.  The optimal
+ *   control u*_k = -K_k x*_k + d_k is often a small difference of large terms
+ *   (tracking a slowly varying reference), so FP32 rounding of S, v and x is
+ *   amplified in u*.  With refinement the solve runs twice: first on the
+ *   problem, then on the same problem shifted by the first trajectory x^
+ *   (x = x^ + xi: r'_k = r_k - H_k x^_k, c'_k = F_k x^_k + c_k - x^_{k+1},
+ *   r'_T = r_T - H_T x^_T, x'_0 = 0), whose residual terms are formed with
+ *   compensated (twice-working-precision) dot products.  The shifted problem
+ *   has small data, so its controls carry no cancellation; it returns
+ *   u* directly and x* = x^ + xi.  S, v and K come from the first solve.
+ *   LQT_REFINE_AUTO refines FP32 solves and not FP64 ones. */
+enum { LQT_REFINE_OFF = 0, LQT_REFINE_ON = 1, LQT_REFINE_AUTO = 2 };
+typedef struct {
+    int32_t refine;
+    int32_t reserved[7]; /* must be 0 */
+} lqt_options;
+
+/* Bytes of device workspace that lqt_solve needs for this problem and these
+ * options (0 on invalid arguments or an unsupported size).  Depends on n, m,
+ * p, pT, T, dtype, the options and the current device's SM count. */
+size_t lqt_workspace_bytes(const lqt_problem *prob, const lqt_options *opts);
+
+/* Temporally parallel LQT solve (Sec. V-A: initialisation, backward scan and
+ * extraction, then the Method-1 forward scan), asynchronous on `stream`.
+ * `workspace` is a device buffer of at least lqt_workspace_bytes(prob) bytes,
+ * 256-byte aligned, used by this call until the stream reaches the end of the
+ * solve; its first bytes hold the device status word read by
+ * lqt_workspace_status().  Between its kernels the solve keeps the
+ * feedforward terms of the control law in the u output.
+ * Returns LQT_EINVAL / LQT_ENOMEM / LQT_EUNSUPPORTED / LQT_ECUDA on failure,
+ * before or while launching; nothing is written in the first three cases. */
+lqt_status lqt_solve(const lqt_problem *prob, const lqt_solution *sol, const lqt_options *opts,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/* Sequential Riccati recursion of Sec. II-B followed by the forward pass of
+ * eq. optimal_trajectory, run on the GPU by one thread per problem (the
+ * sequential baseline).  Same problem, options, outputs and workspace rules
+ * as lqt_solve (lqt_workspace_bytes with the same options suffices). */
+lqt_status lqt_riccati_sequential(const lqt_problem *prob, const lqt_solution *sol,
+                                  const lqt_options *opts, void *workspace,
+                                  size_t workspace_bytes, void *stream);
+
+/* Synchronises `stream` and returns the device status word of the last solve
+ * that used `workspace`: LQT_OK, LQT_ENOTSPD, LQT_ENONFINITE or LQT_ESINGULAR
+ * (LQT_ECUDA if the read itself failed). */
+lqt_status lqt_workspace_status(const void *workspace, void *stream);
+
+/* Host-buffer solve: every pointer in `host_prob` and `host_sol` is a HOST
+ * pointer (pinned memory gives full copy speed).  The inputs are copied into
+ * `device_buffer` (a device buffer of at least lqt_host_solve_bytes(host_prob,
+ * opts) bytes, 256-byte aligned), lqt_solve runs there, and the outputs are copied
+ * back; the call synchronises `stream` and returns the device status of the
+ * solve.  Returns LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED or LQT_ECUDA on
+ * failure. */
+size_t lqt_host_solve_bytes(const lqt_problem *host_prob, const lqt_options *opts);
+lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host_sol,
+                          const lqt_options *opts, void *device_buffer, size_t device_bytes,
+                          void *stream);
+
+/* Static string for a status code (never NULL). */
+const char *lqt_strerror(lqt_status status);
+
+/* Per-kernel timing of lqt_solve.  While enabled, each lqt_solve records CUDA
+ * events on its stream around every kernel it launches.  lqt_profile_read
+ * waits for the last profiled solve and fills up to `max_entries` durations
+ * (milliseconds) and static kernel names; it returns the number of kernels of
+ * that solve (0 if none was profiled, -1 on a CUDA error).  Process-wide state:
+ * not for concurrent use from several threads. */
+lqt_status lqt_profile_enable(int enable);
+int lqt_profile_read(float *ms, const char **names, int max_entries);
+
+/* Launch geometry lqt_solve would use: steps per chunk, threads per tile,
+ * number of tiles, kernels launched per solve (with these options).
+ * Returns LQT_EINVAL / LQT_EUNSUPPORTED / LQT_ECUDA. */
+lqt_status lqt_plan(const lqt_problem *prob, const lqt_options *opts, int32_t *chunk_steps,
+                    int32_t *tile_threads, int32_t *tiles, int32_t *kernels);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQT_H */

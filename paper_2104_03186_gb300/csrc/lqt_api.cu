@@ -1,0 +1,547 @@
+// C ABI of the LQT solver (include/lqt.h): argument validation, launch
+// planning, workspace layout, dispatch to the compiled (dtype, n, m) variants,
+// kernel timing and the host-buffer solve.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "lqt.h"
+#include "lqt_kernels.cuh"
+#include "lqt_launch.cuh"
+#include "lqt_refine.cuh"
+#include "lqt_variants.h"
+
+namespace lqt {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStatusBytes = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int sm_count_current() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        cache[dev] = sms;
+    }
+    return cache[dev];
+}
+
+size_t elem_bytes(int dtype) { return dtype == LQT_F64 ? 8 : 4; }
+
+// Per-instantiation sizes the planner needs.
+struct Variant {
+    int dtype, n, m;
+    int W, TP;
+    int elem, value, affine;  // components of an element, a value, an affine map
+    lqt_status (*solve)(const void* params, const Plan& plan, cudaStream_t s, Prof* prof);
+    lqt_status (*seq)(const void* params, cudaStream_t s);
+};
+
+template <typename R, int N, int M>
+lqt_status solve_thunk(const void* params, const Plan& plan, cudaStream_t s, Prof* prof) {
+    return launch_solve<R, N, M>(*static_cast<const Params<R>*>(params), plan, s, prof);
+}
+
+template <typename R, int N, int M>
+lqt_status seq_thunk(const void* params, cudaStream_t s) {
+    return launch_seq<R, N, M>(*static_cast<const Params<R>*>(params), s);
+}
+
+#define LQT_VARIANT_ROW(R, N, M)                                                                \
+    Variant{sizeof(R) == 8 ? LQT_F64 : LQT_F32, N, M, tile_threads<R, N>(), top_threads(),        \
+            Dims<N>::ELEM, Dims<N>::VALUE, Dims<N>::AFFINE, &solve_thunk<R, N, M>,                \
+            &seq_thunk<R, N, M>},
+
+const Variant kVariants[] = {LQT_VARIANTS(LQT_VARIANT_ROW)};
+
+const Variant* find_variant(int dtype, int n, int m) {
+    for (const Variant& v : kVariants)
+        if (v.dtype == dtype && v.n == n && v.m == m) return &v;
+    return nullptr;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Validates everything that does not depend on a compiled variant.
+lqt_status validate(const lqt_problem* P, const lqt_solution* sol) {
+    if (!P) return LQT_EINVAL;
+    if (P->dtype != LQT_F32 && P->dtype != LQT_F64) return LQT_EINVAL;
+    if (P->n < 1 || P->m < 1 || P->p < 0 || P->pT < 0 || P->T < 0) return LQT_EINVAL;
+    if (P->T > (int64_t(1) << 40)) return LQT_EINVAL;
+    const size_t es = elem_bytes(P->dtype);
+    const int64_t n = P->n, m = P->m, p = P->p, pT = P->pT;
+    struct In {
+        const lqt_in* in;
+        int64_t size;
+        bool optional;
+    } ins[] = {{&P->F, n * n, false}, {&P->c, n, true},     {&P->L, n * m, false},
+               {&P->U, m * m, false}, {&P->H, p * n, p == 0}, {&P->r, p, true},
+               {&P->X, p * p, p == 0}};
+    for (const In& i : ins) {
+        if (!i.in->ptr) {
+            if (!i.optional && P->T > 0) return LQT_EINVAL;
+            continue;
+        }
+        if (!aligned(i.in->ptr, es)) return LQT_EINVAL;
+        if (i.in->step_stride != 0 && i.in->step_stride < i.size) return LQT_EINVAL;
+        if (i.in->step_stride < 0) return LQT_EINVAL;
+    }
+    if (pT > 0 && (!P->HT || !P->XT)) return LQT_EINVAL;
+    if (!P->x0) return LQT_EINVAL;
+    const void* terms[] = {P->HT, P->rT, P->XT, P->x0};
+    for (const void* t : terms)
+        if (t && !aligned(t, es)) return LQT_EINVAL;
+    if (sol) {
+        if (!sol->S || !sol->v || !sol->x) return LQT_EINVAL;
+        if (P->T > 0 && (!sol->K || !sol->u)) return LQT_EINVAL;
+        const void* outs[] = {sol->S, sol->v, sol->K, sol->x, sol->u};
+        for (const void* o : outs)
+            if (o && !aligned(o, 16)) return LQT_EINVAL;
+    }
+    return LQT_OK;
+}
+
+lqt_status resolve_refine(const lqt_problem* P, const lqt_options* o, bool* refine) {
+    int mode = LQT_REFINE_AUTO;
+    if (o) {
+        for (int r : o->reserved)
+            if (r != 0) return LQT_EINVAL;
+        mode = o->refine;
+    }
+    if (mode == LQT_REFINE_AUTO)
+        *refine = P->dtype == LQT_F32;
+    else if (mode == LQT_REFINE_ON || mode == LQT_REFINE_OFF)
+        *refine = mode == LQT_REFINE_ON;
+    else
+        return LQT_EINVAL;
+    if (*refine && P->T > 0 && P->p > 0 && !P->H.ptr) return LQT_EINVAL;
+    return LQT_OK;
+}
+
+lqt_status make_plan(const lqt_problem* P, const Variant& var, Plan* plan) {
+    const int sms = sm_count_current();
+    if (sms <= 0) return LQT_ECUDA;
+    const int64_t W = var.W;
+    const int64_t target = (int64_t)sms * W;
+    int64_t B = (P->T + target - 1) / target;
+    if (B < 1) B = 1;
+    const int64_t tiles = (P->T + W * B - 1) / (W * B);
+    if (B > INT32_MAX || tiles > INT32_MAX) return LQT_EINVAL;
+    plan->B = (int)B;
+    plan->W = (int)W;
+    plan->tiles = (int)tiles;
+    plan->TP = var.TP;
+    return LQT_OK;
+}
+
+struct Layout {
+    size_t tree, tile_agg, tile_carry, ftree, ftile_agg, ftile_x;
+    // refinement pass: shifted references / offsets, zero initial state, state correction
+    size_t rp, rTp, cp, x0p, xi;
+    size_t total;
+};
+
+Layout layout(const Variant& var, const Plan& plan, size_t es, const lqt_problem* P,
+              bool refine) {
+    Layout L;
+    size_t off = kStatusBytes;
+    const size_t t = (size_t)plan.tiles;
+    L.tree = off;
+    off += align_up(t * var.elem * plan.W * es);
+    L.tile_agg = off;
+    off += align_up(t * var.elem * es);
+    L.tile_carry = off;
+    off += align_up(t * var.value * es);
+    L.ftree = off;
+    off += align_up(t * var.affine * plan.W * es);
+    L.ftile_agg = off;
+    off += align_up(t * var.affine * es);
+    L.ftile_x = off;
+    off += align_up(t * var.n * es);
+    L.rp = L.rTp = L.cp = L.x0p = L.xi = 0;
+    if (refine) {
+        const size_t T = (size_t)P->T, n = (size_t)P->n;
+        L.rp = off;
+        off += align_up(T * (size_t)P->p * es);
+        L.rTp = off;
+        off += align_up((size_t)P->pT * es);
+        L.cp = off;
+        off += align_up(T * n * es);
+        L.x0p = off;
+        off += align_up(n * es);
+        L.xi = off;
+        off += align_up((T + 1) * n * es);
+    }
+    L.total = off;
+    return L;
+}
+
+template <typename R>
+void fill_params(Params<R>& K, const lqt_problem* P, const lqt_solution* sol, void* ws,
+                 const Layout* L, const Plan* plan) {
+    memset(&K, 0, sizeof(K));
+    K.n = P->n;
+    K.m = P->m;
+    K.p = P->p;
+    K.pT = P->pT;
+    K.T = P->T;
+    K.F = static_cast<const R*>(P->F.ptr);
+    K.c = static_cast<const R*>(P->c.ptr);
+    K.L = static_cast<const R*>(P->L.ptr);
+    K.U = static_cast<const R*>(P->U.ptr);
+    K.H = static_cast<const R*>(P->H.ptr);
+    K.r = static_cast<const R*>(P->r.ptr);
+    K.X = static_cast<const R*>(P->X.ptr);
+    K.sF = P->F.step_stride;
+    K.sc = P->c.step_stride;
+    K.sL = P->L.step_stride;
+    K.sU = P->U.step_stride;
+    K.sH = P->H.step_stride;
+    K.sr = P->r.step_stride;
+    K.sX = P->X.step_stride;
+    K.HT = static_cast<const R*>(P->HT);
+    K.rT = static_cast<const R*>(P->rT);
+    K.XT = static_cast<const R*>(P->XT);
+    K.x0 = static_cast<const R*>(P->x0);
+    K.S = static_cast<R*>(sol->S);
+    K.v = static_cast<R*>(sol->v);
+    K.K = static_cast<R*>(sol->K);
+    K.x = static_cast<R*>(sol->x);
+    K.u = static_cast<R*>(sol->u);
+    char* base = static_cast<char*>(ws);
+    K.status = reinterpret_cast<int*>(base);
+    if (L) {
+        K.tree = reinterpret_cast<R*>(base + L->tree);
+        K.tile_agg = reinterpret_cast<R*>(base + L->tile_agg);
+        K.tile_carry = reinterpret_cast<R*>(base + L->tile_carry);
+        K.ftree = reinterpret_cast<R*>(base + L->ftree);
+        K.ftile_agg = reinterpret_cast<R*>(base + L->ftile_agg);
+        K.ftile_x = reinterpret_cast<R*>(base + L->ftile_x);
+    }
+    if (plan) {
+        K.B = plan->B;
+        K.tiles = plan->tiles;
+    }
+    K.has_c = P->c.ptr != nullptr;
+    // p == 0 (no stage tracking cost) also takes the precomputed path
+    K.cost_invariant = (P->p == 0) || (P->H.step_stride == 0 && P->X.step_stride == 0);
+    K.out_mask = OUT_ALL;
+}
+
+std::mutex g_prof_mu;
+Prof g_prof;
+
+lqt_status prof_begin(Prof** out) {
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof.enabled) return LQT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LQT_ECUDA;
+    if (g_prof.device != dev) {
+        if (g_prof.device >= 0)
+            for (cudaEvent_t& e : g_prof.ev)
+                if (e) cudaEventDestroy(e), e = nullptr;
+        for (cudaEvent_t& e : g_prof.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return LQT_ECUDA;
+        g_prof.device = dev;
+    }
+    g_prof.count = 0;
+    *out = &g_prof;
+    return LQT_OK;
+}
+
+size_t input_elems(const lqt_in& in, int64_t per_step, int64_t T) {
+    if (!in.ptr || T <= 0) return 0;
+    if (in.step_stride == 0) return (size_t)per_step;
+    return (size_t)((T - 1) * in.step_stride + per_step);
+}
+
+}  // namespace
+}  // namespace lqt
+
+using namespace lqt;
+
+extern "C" {
+
+const char* lqt_strerror(lqt_status s) {
+    switch (s) {
+        case LQT_OK: return "ok";
+        case LQT_EINVAL: return "invalid argument";
+        case LQT_ENOTSPD: return "L^T S L + U (or U) not positive definite";
+        case LQT_ENONFINITE: return "non-finite value in the solution";
+        case LQT_ENOMEM: return "workspace too small";
+        case LQT_ECUDA: return "CUDA runtime error";
+        case LQT_ETIMEOUT: return "bounded device wait ran out";
+        case LQT_EUNSUPPORTED: return "no kernel compiled for this (n, m, dtype)";
+        case LQT_ESINGULAR: return "I + C J numerically singular in a combine";
+    }
+    return "unknown status";
+}
+
+lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* chunk_steps,
+                    int32_t* tile_threads_out, int32_t* tiles, int32_t* kernels) {
+    lqt_status st = validate(prob, nullptr);
+    if (st != LQT_OK) return st;
+    bool refine = false;
+    if ((st = resolve_refine(prob, opts, &refine)) != LQT_OK) return st;
+    const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (!var) return LQT_EUNSUPPORTED;
+    Plan plan;
+    if ((st = make_plan(prob, *var, &plan)) != LQT_OK) return st;
+    if (chunk_steps) *chunk_steps = plan.B;
+    if (tile_threads_out) *tile_threads_out = plan.W;
+    if (tiles) *tiles = plan.tiles;
+    const int per_pass = plan.tiles > 0 ? 5 : 2;
+    if (kernels) *kernels = refine ? 2 * per_pass + 2 : per_pass;
+    return LQT_OK;
+}
+
+size_t lqt_workspace_bytes(const lqt_problem* prob, const lqt_options* opts) {
+    if (validate(prob, nullptr) != LQT_OK) return 0;
+    bool refine = false;
+    if (resolve_refine(prob, opts, &refine) != LQT_OK) return 0;
+    const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (!var) return 0;
+    Plan plan;
+    if (make_plan(prob, *var, &plan) != LQT_OK) return 0;
+    return layout(*var, plan, elem_bytes(prob->dtype), prob, refine).total;
+}
+
+}  // extern "C"
+
+namespace lqt {
+namespace {
+
+template <typename R>
+lqt_status launch_refine_prep(const lqt_problem* P, const lqt_solution* sol, char* base,
+                              const Layout& L, cudaStream_t s, Prof* prof) {
+    const long long T = P->T;
+    const int threads = 256;
+    const long long blocks = (T + 1 + threads - 1) / threads;
+    if (prof) prof_mark(prof, s, "refine_prep");
+    k_refine_prep<R><<<(unsigned)blocks, threads, 0, s>>>(
+        P->n, P->p, P->pT, T, static_cast<const R*>(P->F.ptr), P->F.step_stride,
+        static_cast<const R*>(P->c.ptr), P->c.step_stride, static_cast<const R*>(P->H.ptr),
+        P->H.step_stride, static_cast<const R*>(P->r.ptr), P->r.step_stride,
+        static_cast<const R*>(P->HT), static_cast<const R*>(P->rT),
+        static_cast<const R*>(sol->x), reinterpret_cast<R*>(base + L.rp),
+        reinterpret_cast<R*>(base + L.rTp), reinterpret_cast<R*>(base + L.cp),
+        reinterpret_cast<R*>(base + L.x0p));
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+}
+
+template <typename R>
+lqt_status launch_refine_finish(const lqt_problem* P, const lqt_solution* sol, char* base,
+                                const Layout& L, cudaStream_t s, Prof* prof) {
+    const long long count = (P->T + 1) * (long long)P->n;
+    const int threads = 256;
+    long long blocks = (count + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    if (prof) prof_mark(prof, s, "refine_finish");
+    k_refine_finish<R><<<(unsigned)blocks, threads, 0, s>>>(
+        count, static_cast<R*>(sol->x), reinterpret_cast<const R*>(base + L.xi));
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+}
+
+// One pass of the parallel solve or of the sequential baseline.
+template <typename R>
+lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
+                    void* ws, const Layout& L, const Plan& plan, int out_mask, bool sequential,
+                    cudaStream_t s, Prof* prof) {
+    Params<R> K;
+    fill_params(K, P, sol, ws, &L, &plan);
+    K.out_mask = out_mask;
+    if (sequential) {
+        if (prof) prof_mark(prof, s, "riccati_seq");
+        return var.seq(&K, s);
+    }
+    return var.solve(&K, plan, s, prof);
+}
+
+template <typename R>
+lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
+                     void* ws, const Layout& L, const Plan& plan, bool refine, bool sequential,
+                     cudaStream_t s, Prof* prof) {
+    lqt_status st = run_pass<R>(var, P, sol, ws, L, plan, OUT_ALL, sequential, s, prof);
+    if (st != LQT_OK || !refine || P->T == 0) {
+        if (prof) prof_end(prof, s);
+        return st;
+    }
+    char* base = static_cast<char*>(ws);
+    if ((st = launch_refine_prep<R>(P, sol, base, L, s, prof)) != LQT_OK) return st;
+    // the shifted problem: same matrices, small references and offsets, x'_0 = 0
+    lqt_problem P2 = *P;
+    P2.r.ptr = P->p > 0 ? base + L.rp : nullptr;
+    P2.r.step_stride = P->p;
+    P2.c.ptr = base + L.cp;
+    P2.c.step_stride = P->n;
+    P2.rT = P->pT > 0 ? base + L.rTp : nullptr;
+    P2.x0 = base + L.x0p;
+    // S and K of the shifted problem equal those of the first pass bit for bit
+    // (they do not depend on r or c); the pass reads K back and writes u and xi.
+    lqt_solution sol2 = *sol;
+    sol2.x = base + L.xi;
+    st = run_pass<R>(var, &P2, &sol2, ws, L, plan, 0, sequential, s, prof);
+    if (st != LQT_OK) return st;
+    st = launch_refine_finish<R>(P, sol, base, L, s, prof);
+    if (prof) prof_end(prof, s);
+    return st;
+}
+
+lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const lqt_options* opts,
+                        void* workspace, size_t workspace_bytes, void* stream, bool sequential) {
+    lqt_status st = validate(prob, sol);
+    if (st != LQT_OK) return st;
+    if (!workspace || !aligned(workspace, kAlign)) return LQT_EINVAL;
+    bool refine = false;
+    if ((st = resolve_refine(prob, opts, &refine)) != LQT_OK) return st;
+    if (sequential && prob->p > 64) return LQT_EUNSUPPORTED;
+    const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (!var) return LQT_EUNSUPPORTED;
+    Plan plan;
+    if ((st = make_plan(prob, *var, &plan)) != LQT_OK) return st;
+    const Layout L = layout(*var, plan, elem_bytes(prob->dtype), prob, refine);
+    if (workspace_bytes < L.total) return LQT_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(workspace, 0, sizeof(int), s) != cudaSuccess) return LQT_ECUDA;
+    Prof* prof = nullptr;
+    if ((st = prof_begin(&prof)) != LQT_OK) return st;
+    if (prob->dtype == LQT_F64)
+        return run_solve<double>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof);
+    return run_solve<float>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof);
+}
+
+}  // namespace
+}  // namespace lqt
+
+extern "C" {
+
+lqt_status lqt_solve(const lqt_problem* prob, const lqt_solution* sol, const lqt_options* opts,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+    return solve_common(prob, sol, opts, workspace, workspace_bytes, stream, false);
+}
+
+lqt_status lqt_riccati_sequential(const lqt_problem* prob, const lqt_solution* sol,
+                                  const lqt_options* opts, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    return solve_common(prob, sol, opts, workspace, workspace_bytes, stream, true);
+}
+
+lqt_status lqt_workspace_status(const void* workspace, void* stream) {
+    if (!workspace) return LQT_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    if (cudaMemcpyAsync(&h, workspace, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return LQT_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LQT_ECUDA;
+    return static_cast<lqt_status>(h);
+}
+
+lqt_status lqt_profile_enable(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.enabled = enable != 0;
+    g_prof.count = 0;
+    return LQT_OK;
+}
+
+int lqt_profile_read(float* ms, const char** names, int max_entries) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof.enabled || g_prof.count == 0) return 0;
+    if (cudaEventSynchronize(g_prof.ev[g_prof.count]) != cudaSuccess) return -1;
+    for (int i = 0; i < g_prof.count && i < max_entries; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]) != cudaSuccess) return -1;
+        if (ms) ms[i] = t;
+        if (names) names[i] = g_prof.names[i];
+    }
+    return g_prof.count;
+}
+
+size_t lqt_host_solve_bytes(const lqt_problem* prob, const lqt_options* opts) {
+    if (validate(prob, nullptr) != LQT_OK) return 0;
+    const size_t es = elem_bytes(prob->dtype);
+    const int64_t n = prob->n, m = prob->m, p = prob->p, pT = prob->pT, T = prob->T;
+    size_t total = lqt_workspace_bytes(prob, opts);
+    if (total == 0) return 0;
+    const size_t in_elems[] = {input_elems(prob->F, n * n, T), input_elems(prob->c, n, T),
+                               input_elems(prob->L, n * m, T), input_elems(prob->U, m * m, T),
+                               input_elems(prob->H, p * n, T), input_elems(prob->r, p, T),
+                               input_elems(prob->X, p * p, T)};
+    for (size_t e : in_elems) total += align_up(e * es);
+    total += align_up((size_t)pT * n * es) + align_up((size_t)pT * es) +
+             align_up((size_t)pT * pT * es) + align_up((size_t)n * es);
+    total += align_up((size_t)(T + 1) * n * n * es) + align_up((size_t)(T + 1) * n * es) +
+             align_up((size_t)T * m * n * es) + align_up((size_t)(T + 1) * n * es) +
+             align_up((size_t)T * m * es);
+    return total;
+}
+
+lqt_status lqt_solve_host(const lqt_problem* hp, const lqt_solution* hs, const lqt_options* opts,
+                          void* device_buffer, size_t device_bytes, void* stream) {
+    lqt_status st = validate(hp, hs);
+    if (st != LQT_OK) return st;
+    if (!device_buffer || !aligned(device_buffer, kAlign)) return LQT_EINVAL;
+    const size_t need = lqt_host_solve_bytes(hp, opts);
+    if (need == 0) return find_variant(hp->dtype, hp->n, hp->m) ? LQT_EINVAL : LQT_EUNSUPPORTED;
+    if (device_bytes < need) return LQT_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = elem_bytes(hp->dtype);
+    const int64_t n = hp->n, m = hp->m, p = hp->p, pT = hp->pT, T = hp->T;
+    char* base = static_cast<char*>(device_buffer);
+    const size_t ws_bytes = lqt_workspace_bytes(hp, opts);
+    void* ws = base;
+    size_t off = ws_bytes;
+    auto put = [&](const void* src, size_t elems) -> const void* {
+        if (!src) return nullptr;
+        char* dst = base + off;
+        off += align_up(elems * es);
+        if (elems && cudaMemcpyAsync(dst, src, elems * es, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return reinterpret_cast<const void*>(-1);
+        return dst;
+    };
+    lqt_problem dp = *hp;
+    const void* bad = reinterpret_cast<const void*>(-1);
+    struct Cp {
+        const lqt_in* src;
+        lqt_in* dst;
+        int64_t size;
+    } cps[] = {{&hp->F, &dp.F, n * n}, {&hp->c, &dp.c, n},     {&hp->L, &dp.L, n * m},
+               {&hp->U, &dp.U, m * m}, {&hp->H, &dp.H, p * n}, {&hp->r, &dp.r, p},
+               {&hp->X, &dp.X, p * p}};
+    for (const Cp& c : cps) {
+        c.dst->ptr = put(c.src->ptr, input_elems(*c.src, c.size, T));
+        if (c.dst->ptr == bad) return LQT_ECUDA;
+    }
+    if ((dp.HT = put(hp->HT, (size_t)pT * n)) == bad) return LQT_ECUDA;
+    if ((dp.rT = put(hp->rT, (size_t)pT)) == bad) return LQT_ECUDA;
+    if ((dp.XT = put(hp->XT, (size_t)pT * pT)) == bad) return LQT_ECUDA;
+    if ((dp.x0 = put(hp->x0, (size_t)n)) == bad) return LQT_ECUDA;
+    lqt_solution ds;
+    const size_t sizes[] = {(size_t)(T + 1) * n * n, (size_t)(T + 1) * n, (size_t)T * m * n,
+                            (size_t)(T + 1) * n, (size_t)T * m};
+    void** douts[] = {&ds.S, &ds.v, &ds.K, &ds.x, &ds.u};
+    void* houts[] = {hs->S, hs->v, hs->K, hs->x, hs->u};
+    for (int i = 0; i < 5; ++i) {
+        *douts[i] = base + off;
+        off += align_up(sizes[i] * es);
+    }
+    st = lqt_solve(&dp, &ds, opts, ws, ws_bytes, stream);
+    if (st != LQT_OK) return st;
+    for (int i = 0; i < 5; ++i)
+        if (sizes[i] && houts[i] &&
+            cudaMemcpyAsync(houts[i], *douts[i], sizes[i] * es, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+            return LQT_ECUDA;
+    return lqt_workspace_status(ws, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,7 @@
+// Kernel instantiations: LQT_VARIANTS_F32_SMALL of lqt_variants.h.
+#include "lqt_launch_impl.cuh"
+#include "lqt_variants.h"
+
+namespace lqt {
+LQT_VARIANTS_F32_SMALL(LQT_INSTANTIATE)
+}  // namespace lqt

@@ -1,0 +1,284 @@
+"""Python binding of the C ABI declared in include/lqt.h.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+``liblqt_gb300.so``.  PyTorch is used for device memory and streams.  If the
+library has not been built the import of this module fails loudly; there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblqt_gb300.so")
+
+LQT_OK, LQT_EINVAL, LQT_ENOTSPD, LQT_ENONFINITE, LQT_ENOMEM = 0, 1, 2, 3, 4
+LQT_ECUDA, LQT_ETIMEOUT, LQT_EUNSUPPORTED, LQT_ESINGULAR = 5, 6, 7, 8
+LQT_F32, LQT_F64 = 0, 1
+
+STEP_FIELDS = ("F", "c", "L", "U", "H", "r", "X")
+TERMINAL_FIELDS = ("HT", "rT", "XT", "x0")
+OUTPUT_FIELDS = ("S", "v", "K", "x", "u")
+
+
+class lqt_in(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("step_stride", ctypes.c_int64)]
+
+
+class lqt_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("pT", ctypes.c_int32), ("T", ctypes.c_int64), ("dtype", ctypes.c_int32)] + \
+               [(f, lqt_in) for f in STEP_FIELDS] + \
+               [(f, ctypes.c_void_p) for f in TERMINAL_FIELDS]
+
+
+class lqt_solution(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in OUTPUT_FIELDS]
+
+
+LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO = 0, 1, 2
+
+
+class lqt_options(ctypes.Structure):
+    _fields_ = [("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+def options(refine: int = LQT_REFINE_AUTO) -> lqt_options:
+    o = lqt_options()
+    o.refine = refine
+    return o
+
+
+def _opts(o):
+    if o is None:
+        return None
+    if isinstance(o, int):
+        o = options(o)
+    return ctypes.byref(o)
+
+
+class LQTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, lqt_strerror(status), status))
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblqt_gb300.so is not built (run paper_2104_03186_gb300.build.build()); "
+                          "the LQT solver has no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, S = ctypes.POINTER(lqt_problem), ctypes.POINTER(lqt_solution)
+    O = ctypes.POINTER(lqt_options)
+    vp, sz, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    sig = {
+        "lqt_workspace_bytes": (sz, [P, O]),
+        "lqt_solve": (st, [P, S, O, vp, sz, vp]),
+        "lqt_riccati_sequential": (st, [P, S, O, vp, sz, vp]),
+        "lqt_workspace_status": (st, [vp, vp]),
+        "lqt_host_solve_bytes": (sz, [P, O]),
+        "lqt_solve_host": (st, [P, S, O, vp, sz, vp]),
+        "lqt_strerror": (ctypes.c_char_p, [st]),
+        "lqt_profile_enable": (st, [ctypes.c_int]),
+        "lqt_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
+        "lqt_plan": (st, [P, O] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling
+# ---------------------------------------------------------------------------
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+class Problem:
+    """An LQT problem whose arrays are torch tensors (device or pinned host) or
+    numpy arrays (host), plus the lqt_problem struct that points at them."""
+
+    def __init__(self, n, m, p, pT, T, dtype, arrays: Dict[str, object]):
+        self.n, self.m, self.p, self.pT, self.T = n, m, p, pT, T
+        self.dtype = dtype
+        self.arrays = arrays
+        s = lqt_problem()
+        s.n, s.m, s.p, s.pT, s.T, s.dtype = n, m, p, pT, T, dtype
+        for f in STEP_FIELDS:
+            a = arrays.get(f)
+            if a is None:
+                setattr(s, f, lqt_in(None, 0))
+            else:
+                per_step = int(np.prod(a.shape[1:]))
+                setattr(s, f, lqt_in(_ptr(a), 0 if a.shape[0] == 1 else per_step))
+        for f in TERMINAL_FIELDS:
+            setattr(s, f, _ptr(arrays.get(f)))
+        self.struct = s
+
+    @classmethod
+    def from_inputs(cls, prob, dtype=np.float32, device="cuda", pin: bool = False):
+        """Copy a problem of paper_2104_03186_gb300.inputs (float64 numpy) to torch
+        tensors of `dtype` on `device` (or to pinned host memory with pin=True)."""
+        import torch
+
+        tdt = torch.float32 if np.dtype(dtype) == np.float32 else torch.float64
+        arrays = {}
+        for f in STEP_FIELDS + TERMINAL_FIELDS:
+            a = getattr(prob, f)
+            if a is None:
+                continue
+            t = torch.from_numpy(np.ascontiguousarray(a)).to(tdt)
+            arrays[f] = t.pin_memory() if pin else t.to(device)
+        code = LQT_F32 if tdt == torch.float32 else LQT_F64
+        return cls(prob.n, prob.m, prob.p, prob.pT, prob.T, code, arrays)
+
+    def allocate_outputs(self, device="cuda", pin: bool = False):
+        import torch
+
+        tdt = torch.float32 if self.dtype == LQT_F32 else torch.float64
+        n, m, T = self.n, self.m, self.T
+        shapes = {"S": (T + 1, n, n), "v": (T + 1, n), "K": (T, m, n), "x": (T + 1, n),
+                  "u": (T, m)}
+        if pin:
+            return {k: torch.empty(s, dtype=tdt).pin_memory() for k, s in shapes.items()}
+        return {k: torch.empty(s, dtype=tdt, device=device) for k, s in shapes.items()}
+
+
+def solution_struct(out: Dict[str, object]) -> lqt_solution:
+    s = lqt_solution()
+    for f in OUTPUT_FIELDS:
+        setattr(s, f, _ptr(out[f]) if out[f].numel() > 0 else None)
+    return s
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one function each
+# ---------------------------------------------------------------------------
+
+def lqt_strerror(status: int) -> str:
+    return _lib.lqt_strerror(int(status)).decode()
+
+
+def lqt_workspace_bytes(prob: Problem, opts=None) -> int:
+    return int(_lib.lqt_workspace_bytes(ctypes.byref(prob.struct), _opts(opts)))
+
+
+def lqt_plan(prob: Problem, opts=None):
+    vals = [ctypes.c_int32() for _ in range(4)]
+    st = _lib.lqt_plan(ctypes.byref(prob.struct), _opts(opts), *[ctypes.byref(v) for v in vals])
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_plan")
+    return dict(chunk_steps=vals[0].value, tile_threads=vals[1].value, tiles=vals[2].value,
+                kernels=vals[3].value)
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def lqt_solve(prob: Problem, out: Dict[str, object], workspace, stream=None, opts=None) -> None:
+    sol = solution_struct(out)
+    st = _lib.lqt_solve(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
+                        _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve")
+
+
+def lqt_riccati_sequential(prob: Problem, out: Dict[str, object], workspace, stream=None,
+                           opts=None) -> None:
+    sol = solution_struct(out)
+    st = _lib.lqt_riccati_sequential(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
+                                     _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_riccati_sequential")
+
+
+def lqt_workspace_status(workspace, stream=None) -> int:
+    return int(_lib.lqt_workspace_status(_ptr(workspace), _stream_handle(stream)))
+
+
+def lqt_host_solve_bytes(prob: Problem, opts=None) -> int:
+    return int(_lib.lqt_host_solve_bytes(ctypes.byref(prob.struct), _opts(opts)))
+
+
+def lqt_solve_host(prob: Problem, out: Dict[str, object], device_buffer, stream=None,
+                   opts=None) -> int:
+    """Host-pointer solve; returns the device status (raises on launch errors)."""
+    sol = solution_struct(out)
+    st = _lib.lqt_solve_host(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
+                             _ptr(device_buffer), _nbytes(device_buffer), _stream_handle(stream))
+    if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):
+        raise LQTError(st, "lqt_solve_host")
+    return int(st)
+
+
+def lqt_profile_enable(enable: bool) -> None:
+    _lib.lqt_profile_enable(1 if enable else 0)
+
+
+def lqt_profile_read(max_entries: int = 16):
+    ms = (ctypes.c_float * max_entries)()
+    names = (ctypes.c_char_p * max_entries)()
+    k = _lib.lqt_profile_read(ms, names, max_entries)
+    if k < 0:
+        raise LQTError(LQT_ECUDA, "lqt_profile_read")
+    return [(names[i].decode(), float(ms[i])) for i in range(min(k, max_entries))]
+
+
+# ---------------------------------------------------------------------------
+# convenience: allocate with torch, call the C ABI
+# ---------------------------------------------------------------------------
+
+def workspace_for(prob: Problem, device="cuda", opts=None):
+    import torch
+
+    nbytes = lqt_workspace_bytes(prob, opts)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def solve(prob: Problem, stream=None, check: bool = True, workspace=None, sequential=False,
+          opts=None):
+    """Allocate outputs (and a workspace) with torch and run lqt_solve (or the
+    sequential baseline).  With check=True the stream is synchronised and a
+    non-OK device status raises LQTError."""
+    out = prob.allocate_outputs()
+    ws = workspace if workspace is not None else workspace_for(prob, opts=opts)
+    if sequential:
+        lqt_riccati_sequential(prob, out, ws, stream, opts)
+    else:
+        lqt_solve(prob, out, ws, stream, opts)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return out

@@ -1,0 +1,103 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares
+(CPU only: no compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_03186_gb300 import build
+
+    build.build()
+    from paper_2104_03186_gb300 import lqt
+
+    return lqt
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lqt_\w+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_api():
+    names = _declared_functions()
+    for required in ("lqt_solve", "lqt_workspace_bytes", "lqt_workspace_status",
+                     "lqt_riccati_sequential", "lqt_solve_host", "lqt_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_strerror_covers_all_codes(lib):
+    for code in range(9):
+        assert lib.lqt_strerror(code) not in ("", "unknown status")
+    assert lib.lqt_strerror(99) == "unknown status"
+
+
+def _host_problem(lib, **over):
+    from paper_2104_03186_gb300 import inputs
+
+    p = inputs.vehicle(16)
+    arr = {f: np.ascontiguousarray(getattr(p, f), dtype=np.float32)
+           for f in lib.STEP_FIELDS + lib.TERMINAL_FIELDS if getattr(p, f) is not None}
+    arr.update(over)
+    return lib.Problem(p.n, p.m, p.p, p.pT, p.T, lib.LQT_F32, arr), arr
+
+
+def test_invalid_arguments_rejected_before_any_device_work(lib):
+    so = lib.library()
+    P, arr = _host_problem(lib)
+    out = {k: np.zeros(s, np.float32) for k, s in
+           {"S": (17, 4, 4), "v": (17, 4), "K": (16, 2, 4), "x": (17, 4), "u": (16, 2)}.items()}
+    sol = lib.lqt_solution(*[o.ctypes.data for o in out.values()])
+    # NULL problem / solution / workspace
+    assert so.lqt_solve(None, ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    assert so.lqt_solve(ctypes.byref(P.struct), None, None, None, 0, None) == lib.LQT_EINVAL
+    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    # bad sizes
+    bad = lib.lqt_problem.from_buffer_copy(P.struct)
+    bad.n = 0
+    assert so.lqt_solve(ctypes.byref(bad), ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    bad = lib.lqt_problem.from_buffer_copy(P.struct)
+    bad.T = -1
+    assert so.lqt_solve(ctypes.byref(bad), ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    # a time-varying stride shorter than one step
+    bad = lib.lqt_problem.from_buffer_copy(P.struct)
+    bad.r.step_stride = 1
+    assert so.lqt_solve(ctypes.byref(bad), ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    # missing required input
+    bad = lib.lqt_problem.from_buffer_copy(P.struct)
+    bad.F.ptr = None
+    assert so.lqt_solve(ctypes.byref(bad), ctypes.byref(sol), None, None, 0, None) == lib.LQT_EINVAL
+    # misaligned output
+    sol2 = lib.lqt_solution.from_buffer_copy(sol)
+    sol2.S = out["S"].ctypes.data + 4
+    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol2), None, None, 0, None) == lib.LQT_EINVAL
+    # bad options
+    opts = lib.options(5)
+    fake_ws = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced: options fail first
+    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
+                        1 << 30, None) == lib.LQT_EINVAL
+    opts = lib.options(lib.LQT_REFINE_ON)
+    opts.reserved[3] = 1
+    assert so.lqt_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(opts)) == 0
+    # unsupported size reports 0 workspace
+    bad = lib.lqt_problem.from_buffer_copy(P.struct)
+    bad.dtype = 7
+    assert so.lqt_workspace_bytes(ctypes.byref(bad), None) == 0
