@@ -1,0 +1,473 @@
+"""Benchmark: LQT time-steps/s of the temporally parallel solve on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (one "step" = one full solve, Sec. V-A: elements, backward scan,
+gains, forward scan, x* and u*): the 2-D constant-velocity vehicle tracking
+problem, nx = 4, nu = 2, T = 10^6, FP32 with mixed-precision refinement
+(the path that meets the 1e-5 error bound on every output).  Inputs are
+resident in HBM; L2 is flushed (256 MiB write) before every timed step.
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs one independent
+problem per GPU (weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (sequential Riccati) on the
+host cores for the same metric; it is a deliberately slow baseline.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LQT steps/s: parallel scan vs sequential Riccati, 1 GB300, ≤1e-5 err; p99 ms"
+UNIT = "time-steps/s"
+T_HEADLINE = 1_000_000
+SWEEP_T = (100, 1000, 10_000, 100_000, 1_000_000)
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32)
+
+# Algorithmic work per time step of the k_bwd_down kernel (first pass), the
+# kernel with the largest share of the solve: one Riccati step with gains,
+# the closed-loop chunk map, reading r_k and writing S_k, v_k, K_k.
+# Flops for n = 4, m = 2, p = 2 counted from the kernel's arithmetic.
+BWD_DOWN_BYTES_PER_STEP = {"in_r": 2 * 4, "out_S": 16 * 4, "out_v": 4 * 4, "out_K": 8 * 4}
+BWD_DOWN_FLOPS_PER_STEP = 2 * (32 + 12 + 64 + 32 + 40 + 6 + 24 + 32 + 8 + 8 + 16 + 8 + 64 + 16)
+
+
+def workload_config(T):
+    return {
+        "workload": "2-D constant-velocity vehicle tracking, nx=4, nu=2, p=2, T=%d, single "
+                    "problem per GPU" % T,
+        "model": "F=[[I,0.1I],[0,I]], L=[[0.005I],[0.1I]], c=0, H=[I 0], X_k=I, U_k=0.1I, "
+                 "X_T=100I; r_k=(sin 0.01k, cos 0.013k)+N(0,0.01^2), x0~N(0,I)",
+        "T": T, "nx": 4, "nu": 2,
+        "precision": "fp32 scan + mixed-precision refinement (shifted re-solve)",
+        "l2": "flushed before every timed step (256 MiB write)",
+        "inputs": "device-resident",
+    }
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# --------------------------------------------------------------------------
+# host-side helpers (covered by CPU tests)
+# --------------------------------------------------------------------------
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(total_units: float, seconds: float) -> float:
+    return total_units / seconds if seconds > 0 else float("nan")
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
+
+
+def parse_clocks(csv_text: str):
+    """Median SM clock under load, max SM clock and active throttle reasons from
+    `nvidia-smi --query-gpu=index,clocks.sm,clocks.max.sm,power.draw,
+    clocks_event_reasons.active,...hw_slowdown,...hw_thermal_slowdown,
+    ...sw_thermal_slowdown,...sw_power_cap --format=csv` samples."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in csv_text.strip().splitlines():
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9 or not parts[1].split()[0].replace(".", "").isdigit():
+            continue
+        try:
+            sm.append(float(parts[1].split()[0]))
+            smax.append(float(parts[2].split()[0]))
+        except ValueError:
+            continue
+        for name, flag in zip(names, parts[5:9]):
+            if flag.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return None
+    loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+    return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)),
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def result(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        with open(self.path) as f:
+            return parse_clocks(f.read())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on host cores
+# --------------------------------------------------------------------------
+
+def oracle_throughput(T: int, min_seconds: float, max_reps: int = 50):
+    """Time the FP64 oracle (sequential Riccati + forward pass, one core) on the
+    vehicle workload; returns (steps/s, reps, seconds, sample description)."""
+    import oracle
+    from paper_2104_03186_gb300 import inputs
+
+    prob = inputs.vehicle(T, seed=0).rounded_to(np.float32)
+    oracle.riccati(prob, keep_kv_kc=False)  # build/load outside the timing
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.riccati(prob, keep_kv_kc=False)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    return T * reps / el, reps, el, "vehicle T=%d, %d full solves (%.1f s), 1 thread" % (
+        T, reps, el)
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2104_03186_gb300 import inputs
+
+    T = T_HEADLINE
+    prob = inputs.vehicle(T, seed=0).rounded_to(np.float32)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.riccati(prob, keep_kv_kc=False)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = throughput(T * len(times), total)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(T),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "vehicle T=%d, one full FP64 solve per step, 1 thread, %s" % (
+                             T, cpu_model())},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p99_ms": 1e3 * percentile(times, 99), "p50_ms": 1e3 * percentile(times, 50),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def _time_solves(fn, reps, flush, stream):
+    """Per-call device time (ms) with CUDA events on `stream`, L2 flushed before each."""
+    import torch
+
+    out = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = _env_rank()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    T = T_HEADLINE
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    prob = inputs.vehicle(T, seed=rank).rounded_to(np.float32)
+    P = lqt.Problem.from_inputs(prob, dtype=np.float32)
+    out = P.allocate_outputs()
+    opts = lqt.LQT_REFINE_ON
+    ws = lqt.workspace_for(P, opts=opts)
+    plan = lqt.lqt_plan(P, opts)
+
+    def step():
+        lqt.lqt_solve(P, out, ws, stream, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = lqt.lqt_workspace_status(ws, stream)
+    if st != lqt.LQT_OK:
+        raise lqt.LQTError(st, "warm-up solve")
+
+    # accuracy of this exact configuration against the FP64 oracle (untimed)
+    errors = None
+    cpu = None
+    if rank == 0:
+        import oracle
+
+        t0 = time.perf_counter()
+        ref = oracle.riccati(prob, keep_kv_kc=False)
+        oracle_s = time.perf_counter() - t0
+        got = {k: v.double().cpu().numpy() for k, v in out.items()}
+        errors = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                  for k in ("S", "v", "K", "x", "u")}
+        del ref, got
+
+    # ---- timed region: K solves, per-step events, per-kernel events --------
+    lqt.lqt_profile_enable(True)
+    kern = {}
+    times = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            times += _time_solves(step, 1, flush, stream)
+            for i, (name, ms) in enumerate(lqt.lqt_profile_read()):
+                kern.setdefault((i, name), []).append(ms)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    lqt.lqt_profile_enable(False)
+    clocks = clk.result()
+    st = lqt.lqt_workspace_status(ws, stream)
+    if st != lqt.LQT_OK:
+        raise lqt.LQTError(st, "timed solve")
+    total_s = max_over_ranks(sum(times) / 1e3, world)
+    value = throughput(world * T * args.steps, total_s)
+
+    # ---- end to end through the host-buffer entry point ---------------------
+    Ph = lqt.Problem.from_inputs(prob, dtype=np.float32, pin=True)
+    out_h = Ph.allocate_outputs(pin=True)
+    dev_buf = torch.empty(lqt.lqt_host_solve_bytes(Ph, opts), dtype=torch.uint8, device="cuda")
+    h2d = sum(int(t.numel() * t.element_size()) for t in Ph.arrays.values())
+    d2h = sum(int(t.numel() * t.element_size()) for t in out_h.values())
+    lqt.lqt_solve_host(Ph, out_h, dev_buf, stream, opts)
+    e2e_times = []
+    for _ in range(max(3, min(args.steps, 10))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stt = lqt.lqt_solve_host(Ph, out_h, dev_buf, stream, opts)
+        e2e_times.append(time.perf_counter() - t0)
+        if stt != lqt.LQT_OK:
+            raise lqt.LQTError(stt, "host solve")
+    e2e_s = max_over_ranks(float(np.median(e2e_times)), world)
+    del dev_buf, out_h, Ph
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- per-kernel times and the roofline of the dominant kernel ---------
+    # launch order: pass 1 (5 kernels), refine_prep, pass 2 (5 kernels), refine_finish
+    per_kernel = {}
+    for (i, name), v in sorted(kern.items()):
+        key = name + (".refine" if 6 <= i <= 10 else "")
+        per_kernel[key] = float(np.mean(v))
+    dom = max(per_kernel, key=per_kernel.get)
+    bwd_ms = per_kernel["bwd_down"]
+    alg_bytes = sum(BWD_DOWN_BYTES_PER_STEP.values()) * T
+    alg_flops = BWD_DOWN_FLOPS_PER_STEP * T
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    hbm_time = alg_bytes / (hbm_peak * 1e9)
+    alu_time = alg_flops / (fp32_peak * 1e12)
+    if hbm_time >= alu_time:
+        achieved = alg_bytes / (bwd_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        achieved = alg_flops / (bwd_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock"}
+    roof.update({
+        "kernel": "k_bwd_down (first pass)",
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "algorithmic_flops_per_launch": alg_flops,
+        "per_unit": "per time step: %d B (r in; S, v, K out), %d flop" % (
+            sum(BWD_DOWN_BYTES_PER_STEP.values()), BWD_DOWN_FLOPS_PER_STEP),
+        "launch_ms": bwd_ms,
+        "traffic": TRAFFIC_BWD_DOWN,
+        "dominant_kernel_by_time": dom,
+    })
+
+    # ---- T sweep: parallel vs sequential Riccati on this GPU ---------------
+    sweep = []
+    if not args.no_sweep:
+        for Ts in SWEEP_T:
+            ps = inputs.vehicle(Ts, seed=0).rounded_to(np.float32)
+            Pq = lqt.Problem.from_inputs(ps, dtype=np.float32)
+            o2 = Pq.allocate_outputs()
+            w2 = lqt.workspace_for(Pq, opts=opts)
+            par = lambda: lqt.lqt_solve(Pq, o2, w2, stream, opts)  # noqa: E731
+            seq = lambda: lqt.lqt_riccati_sequential(Pq, o2, w2, stream, opts)  # noqa: E731
+            for _ in range(3):
+                par()
+            tp = _time_solves(par, 20 if Ts < T_HEADLINE else 10, flush, stream)
+            seq()
+            ts = _time_solves(seq, 3 if Ts <= 100_000 else 1, flush, stream)
+            sweep.append({"T": Ts, "parallel_steps_per_s": Ts / (np.median(tp) * 1e-3),
+                          "parallel_p50_ms": percentile(tp, 50), "parallel_p99_ms": percentile(tp, 99),
+                          "sequential_steps_per_s": Ts / (np.median(ts) * 1e-3),
+                          "sequential_ms": float(np.median(ts)),
+                          "speedup": float(np.median(ts) / np.median(tp))})
+            del o2, w2, Pq
+
+    # ---- CPU baseline (oracle on the host) ---------------------------------
+    cpu_v, reps, el, sample = oracle_throughput(T, 10.0, max_reps=20)
+    cpu = {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": sample + ", " + cpu_model()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "p50_ms": percentile(times, 50), "p99_ms": percentile(times, 99),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(T),
+        "error_vs_fp64_oracle": errors,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms": 1e3 * e2e_s,
+                "entry_point": "lqt_solve_host (pinned host buffers, copies inside)"},
+        "clocks": clocks,
+        "gpu_launches": plan["kernels"] * args.steps,
+        "kernels_ms": per_kernel,
+        "plan": plan,
+        "sweep": sweep,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
+# (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
+# None when the kernel has changed since the counters were taken.
+TRAFFIC_BWD_DOWN = 131.4e6
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the T sweep")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="profiling mode: run --warmup + this many solves of --T and exit "
+                         "(no JSON line; for ncu captures)")
+    ap.add_argument("--T", type=int, default=T_HEADLINE, help="horizon of --profile-solves")
+    ap.add_argument("--refine", type=int, default=1, help="refinement in --profile-solves")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.profile_solves > 0:
+        return run_profile_solves(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+def run_profile_solves(args):
+    """A bare loop of solves on the vehicle workload, for ncu captures."""
+    import torch
+
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    P = lqt.Problem.from_inputs(inputs.vehicle(args.T, seed=0).rounded_to(np.float32))
+    out = P.allocate_outputs()
+    ws = lqt.workspace_for(P, opts=args.refine)
+    for _ in range(args.warmup + args.profile_solves):
+        lqt.lqt_solve(P, out, ws, None, args.refine)
+    torch.cuda.synchronize()
+    st = lqt.lqt_workspace_status(ws)
+    print("profile solves done: T=%d refine=%d status=%d plan=%s" % (
+        args.T, args.refine, st, lqt.lqt_plan(P, args.refine)))
+    return 0 if st == lqt.LQT_OK else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())
