@@ -159,6 +159,36 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
                           const lqt_options *opts, void *device_buffer, size_t device_bytes,
                           void *stream);
 
+/* Solve without any caller-provided workspace.
+ *
+ * There is no counterpart to this entry point in the paper.  It exists for
+ * callers that cannot allocate device memory for a workspace: for example a
+ * real-time control loop that forbids allocation once it has started, or a
+ * host framework that owns the device allocator and has no way to hand this
+ * library a buffer.  It runs exactly lqt_solve, but its scratch space is one
+ * fixed array of LQT_STATIC_SCRATCH_BYTES compiled into the library: every GPU
+ * that loads the library holds that array until the process exits.
+ *
+ *   - Inputs and outputs are still the caller's device buffers, as for
+ *     lqt_solve.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ *   - Problems whose lqt_workspace_bytes(prob, opts) exceeds
+ *     LQT_STATIC_SCRATCH_BYTES are rejected with LQT_ENOMEM before anything is
+ *     launched.  At n = 4, p = 2 on a 152-SM GPU that is T above about 4e5
+ *     with refinement; without refinement the need stays near 20 MB for any T
+ *     (the launch plan keeps about one tile per SM).
+ *   - The first call on a device looks up the array's device address for that
+ *     device (the device must be current).  Make that first call before any
+ *     stream capture.  A failed look-up returns LQT_ECUDA.
+ *   - All calls share the one array, and it keeps the last call's contents.
+ *     Calls whose work overlaps on the GPU (different streams, or several host
+ *     threads) race on it and give wrong results: serialise them.
+ *   - The call waits for `stream` to finish the solve and returns the device
+ *     status of that solve (LQT_OK, LQT_ENOTSPD, LQT_ENONFINITE or
+ *     LQT_ESINGULAR), or the argument and launch errors of lqt_solve. */
+#define LQT_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+lqt_status lqt_solve_static(const lqt_problem *prob, const lqt_solution *sol,
+                            const lqt_options *opts, void *stream);
+
 /* Static string for a status code (never NULL). */
 const char *lqt_strerror(lqt_status status);
 

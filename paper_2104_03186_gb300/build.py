@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 
-SOURCES = ["lqt_api.cu", "lqt_inst_f32_small.cu", "lqt_inst_f32_n4.cu", "lqt_inst_f64.cu"]
+SOURCES = ["lqt_api.cu", "lqt_inst_f32_small.cu", "lqt_inst_f32_n4.cu", "lqt_inst_f64.cu",
+           "lqt_static.cu"]
 
 
 def nvcc() -> str:

@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "lqt_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float),
                                             ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
         "lqt_plan": (st, [P, O] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+        "lqt_solve_static": (st, [P, S, O, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +238,23 @@ def lqt_solve_host(prob: Problem, out: Dict[str, object], device_buffer, stream=
                              _ptr(device_buffer), _nbytes(device_buffer), _stream_handle(stream))
     if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):
         raise LQTError(st, "lqt_solve_host")
+    return int(st)
+
+
+LQT_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def lqt_solve_static(prob: Problem, out: Dict[str, object], stream=None, opts=None) -> int:
+    """lqt_solve with the library's built-in scratch array instead of a workspace,
+    for callers that cannot allocate device memory.  Waits for the stream and
+    returns the device status of the solve; raises on argument, size
+    (LQT_ENOMEM: the problem needs more than LQT_STATIC_SCRATCH_BYTES) and
+    launch errors.  Calls that overlap on the GPU share the array and race."""
+    sol = solution_struct(out)
+    st = _lib.lqt_solve_static(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
+                               _stream_handle(stream))
+    if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):
+        raise LQTError(st, "lqt_solve_static")
     return int(st)
 
 
