@@ -331,11 +331,8 @@ def run_ours(args):
         return 0
 
     # ---- per-kernel times and the roofline of the dominant kernel ---------
-    # launch order: pass 1 (5 kernels), refine_prep, pass 2 (5 kernels), refine_finish
-    per_kernel = {}
-    for (i, name), v in sorted(kern.items()):
-        key = name + (".refine" if 6 <= i <= 10 else "")
-        per_kernel[key] = float(np.mean(v))
+    # launch order: pass 1 (5 kernels), then pass 2 (the same five, ".refine")
+    per_kernel = {name: float(np.mean(v)) for (i, name), v in sorted(kern.items())}
     dom = max(per_kernel, key=per_kernel.get)
     bwd_ms = per_kernel["bwd_down"]
     alg_bytes = sum(BWD_DOWN_BYTES_PER_STEP.values()) * T

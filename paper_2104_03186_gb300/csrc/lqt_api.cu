@@ -57,7 +57,7 @@ lqt_status seq_thunk(const void* params, cudaStream_t s) {
 }
 
 #define LQT_VARIANT_ROW(R, N, M)                                                                \
-    Variant{sizeof(R) == 8 ? LQT_F64 : LQT_F32, N, M, tile_threads<R, N>(), top_threads(),        \
+    Variant{sizeof(R) == 8 ? LQT_F64 : LQT_F32, N, M, tile_threads<R, N, M>(), top_threads(),        \
             Dims<N>::ELEM, Dims<N>::VALUE, Dims<N>::AFFINE, &solve_thunk<R, N, M>,                \
             &seq_thunk<R, N, M>},
 
@@ -143,10 +143,14 @@ lqt_status make_plan(const lqt_problem* P, const Variant& var, Plan* plan) {
     return LQT_OK;
 }
 
+// Step stride of the shifted references r' (padded to 4 when p <= 4 so that the
+// rollout can store them through its warp staging rows).
+int refine_r_stride(int p) { return p <= kRStage ? kRStage : p; }
+
 struct Layout {
     size_t tree, tile_agg, tile_carry, ftree, ftile_agg, ftile_x;
-    // refinement pass: shifted references / offsets, zero initial state, state correction
-    size_t rp, rTp, cp, x0p, xi;
+    // refinement: shifted references and offsets, zero initial state
+    size_t rp, rTp, cp, x0p;
     size_t total;
 };
 
@@ -167,19 +171,17 @@ Layout layout(const Variant& var, const Plan& plan, size_t es, const lqt_problem
     off += align_up(t * var.affine * es);
     L.ftile_x = off;
     off += align_up(t * var.n * es);
-    L.rp = L.rTp = L.cp = L.x0p = L.xi = 0;
+    L.rp = L.rTp = L.cp = L.x0p = 0;
     if (refine) {
         const size_t T = (size_t)P->T, n = (size_t)P->n;
         L.rp = off;
-        off += align_up(T * (size_t)P->p * es);
+        off += align_up(T * (size_t)refine_r_stride(P->p) * es);
         L.rTp = off;
         off += align_up((size_t)P->pT * es);
         L.cp = off;
         off += align_up(T * n * es);
         L.x0p = off;
         off += align_up(n * es);
-        L.xi = off;
-        off += align_up((T + 1) * n * es);
     }
     L.total = off;
     return L;
@@ -226,6 +228,12 @@ void fill_params(Params<R>& K, const lqt_problem* P, const lqt_solution* sol, vo
         K.ftree = reinterpret_cast<R*>(base + L->ftree);
         K.ftile_agg = reinterpret_cast<R*>(base + L->ftile_agg);
         K.ftile_x = reinterpret_cast<R*>(base + L->ftile_x);
+        if (L->rp | L->rTp | L->cp | L->x0p) {
+            K.rp = reinterpret_cast<R*>(base + L->rp);
+            K.rTp = reinterpret_cast<R*>(base + L->rTp);
+            K.cp = reinterpret_cast<R*>(base + L->cp);
+            K.x0p = reinterpret_cast<R*>(base + L->x0p);
+        }
     }
     if (plan) {
         K.B = plan->B;
@@ -234,6 +242,9 @@ void fill_params(Params<R>& K, const lqt_problem* P, const lqt_solution* sol, vo
     K.has_c = P->c.ptr != nullptr;
     // p == 0 (no stage tracking cost) also takes the precomputed path
     K.cost_invariant = (P->p == 0) || (P->H.step_stride == 0 && P->X.step_stride == 0);
+    K.dyn_invariant =
+        P->F.step_stride == 0 && P->L.step_stride == 0 && P->U.step_stride == 0 ? 1 : 0;
+    K.c_invariant = (P->c.ptr == nullptr || P->c.step_stride == 0) ? 1 : 0;
     K.out_mask = OUT_ALL;
 }
 
@@ -301,7 +312,7 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
     if (tile_threads_out) *tile_threads_out = plan.W;
     if (tiles) *tiles = plan.tiles;
     const int per_pass = plan.tiles > 0 ? 5 : 2;
-    if (kernels) *kernels = refine ? 2 * per_pass + 2 : per_pass;
+    if (kernels) *kernels = (refine && prob->T > 0) ? 2 * per_pass : per_pass;
     return LQT_OK;
 }
 
@@ -321,47 +332,18 @@ size_t lqt_workspace_bytes(const lqt_problem* prob, const lqt_options* opts) {
 namespace lqt {
 namespace {
 
-template <typename R>
-lqt_status launch_refine_prep(const lqt_problem* P, const lqt_solution* sol, char* base,
-                              const Layout& L, cudaStream_t s, Prof* prof) {
-    const long long T = P->T;
-    const int threads = 256;
-    const long long blocks = (T + 1 + threads - 1) / threads;
-    if (prof) prof_mark(prof, s, "refine_prep");
-    k_refine_prep<R><<<(unsigned)blocks, threads, 0, s>>>(
-        P->n, P->p, P->pT, T, static_cast<const R*>(P->F.ptr), P->F.step_stride,
-        static_cast<const R*>(P->c.ptr), P->c.step_stride, static_cast<const R*>(P->H.ptr),
-        P->H.step_stride, static_cast<const R*>(P->r.ptr), P->r.step_stride,
-        static_cast<const R*>(P->HT), static_cast<const R*>(P->rT),
-        static_cast<const R*>(sol->x), reinterpret_cast<R*>(base + L.rp),
-        reinterpret_cast<R*>(base + L.rTp), reinterpret_cast<R*>(base + L.cp),
-        reinterpret_cast<R*>(base + L.x0p));
-    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
-}
-
-template <typename R>
-lqt_status launch_refine_finish(const lqt_problem* P, const lqt_solution* sol, char* base,
-                                const Layout& L, cudaStream_t s, Prof* prof) {
-    const long long count = (P->T + 1) * (long long)P->n;
-    const int threads = 256;
-    long long blocks = (count + threads - 1) / threads;
-    if (blocks > 4096) blocks = 4096;
-    if (prof) prof_mark(prof, s, "refine_finish");
-    k_refine_finish<R><<<(unsigned)blocks, threads, 0, s>>>(
-        count, static_cast<R*>(sol->x), reinterpret_cast<const R*>(base + L.xi));
-    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
-}
-
 // One pass of the parallel solve or of the sequential baseline.
 template <typename R>
 lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
-                    void* ws, const Layout& L, const Plan& plan, int out_mask, bool sequential,
-                    cudaStream_t s, Prof* prof) {
+                    void* ws, const Layout& L, const Plan& plan, int out_mask, int refine_emit,
+                    int refine_add, bool sequential, cudaStream_t s, Prof* prof) {
     Params<R> K;
     fill_params(K, P, sol, ws, &L, &plan);
     K.out_mask = out_mask;
+    K.refine_emit = refine_emit;
+    K.refine_add = refine_add;
     if (sequential) {
-        if (prof) prof_mark(prof, s, "riccati_seq");
+        if (prof) prof_mark(prof, s, refine_add ? "riccati_seq.refine" : "riccati_seq");
         return var.seq(&K, s);
     }
     return var.solve(&K, plan, s, prof);
@@ -371,28 +353,28 @@ template <typename R>
 lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
                      void* ws, const Layout& L, const Plan& plan, bool refine, bool sequential,
                      cudaStream_t s, Prof* prof) {
-    lqt_status st = run_pass<R>(var, P, sol, ws, L, plan, OUT_ALL, sequential, s, prof);
-    if (st != LQT_OK || !refine || P->T == 0) {
+    refine = refine && P->T > 0;
+    // pass 1: the problem; when refining it also writes the shifted data
+    lqt_status st = run_pass<R>(var, P, sol, ws, L, plan, OUT_ALL, refine ? 1 : 0, 0, sequential,
+                                s, prof);
+    if (st != LQT_OK || !refine) {
         if (prof) prof_end(prof, s);
         return st;
     }
+    // pass 2: the problem shifted by the first trajectory, x = x^ + xi, with
+    // the same matrices, small references and offsets, and x'_0 = 0.  Its S
+    // and K equal those of pass 1 bit for bit (they do not depend on r or c):
+    // the pass does not write S, v, K again, reads K back, writes u* and adds
+    // xi into x.
     char* base = static_cast<char*>(ws);
-    if ((st = launch_refine_prep<R>(P, sol, base, L, s, prof)) != LQT_OK) return st;
-    // the shifted problem: same matrices, small references and offsets, x'_0 = 0
     lqt_problem P2 = *P;
     P2.r.ptr = P->p > 0 ? base + L.rp : nullptr;
-    P2.r.step_stride = P->p;
+    P2.r.step_stride = refine_r_stride(P->p);
     P2.c.ptr = base + L.cp;
     P2.c.step_stride = P->n;
     P2.rT = P->pT > 0 ? base + L.rTp : nullptr;
     P2.x0 = base + L.x0p;
-    // S and K of the shifted problem equal those of the first pass bit for bit
-    // (they do not depend on r or c); the pass reads K back and writes u and xi.
-    lqt_solution sol2 = *sol;
-    sol2.x = base + L.xi;
-    st = run_pass<R>(var, &P2, &sol2, ws, L, plan, 0, sequential, s, prof);
-    if (st != LQT_OK) return st;
-    st = launch_refine_finish<R>(P, sol, base, L, s, prof);
+    st = run_pass<R>(var, &P2, sol, ws, L, plan, 0, 0, 1, sequential, s, prof);
     if (prof) prof_end(prof, s);
     return st;
 }

@@ -7,23 +7,32 @@
 // totals across the grid (one CTA).  Launch order on one stream:
 //
 //   bwd_up    a_k built on the fly (eq. lqt_init), chunk fold P <- a_k (x) P
-//             (eq. lqt_comb), in-tile up-sweep; writes the tile tree and total.
+//             (eq. lqt_comb), in-tile up-sweep; bulk-stores the tile tree.
 //   bwd_top   suffix scan of tile totals; the carry into each tile is a value
 //             (0, 0, 0, v, S) (Lemma LQT_assoc); writes S_T, v_T.
-//   bwd_down  in-tile down-sweep of value carries; per chunk a Riccati re-fold
-//             from its carry (S_k = J_{k,T+1}, v_k = eta_{k,T+1}) with the
-//             gains of eq. Control_LQT fused; writes S, v, K and the
-//             feedforward into u; builds the chunk's closed-loop affine map
-//             (Sec. IV-C, Method 1) and the in-tile forward up-sweep.
+//   bwd_down  bulk-loads the tile tree, in-tile down-sweep of value carries;
+//             per chunk a Riccati re-fold from its carry (S_k = J_{k,T+1},
+//             v_k = eta_{k,T+1}) with the gains of eq. Control_LQT fused;
+//             writes S, v, K and the feedforward (into u) through warp
+//             staging; builds the chunk's closed-loop affine map (Sec. IV-C,
+//             Method 1) and the in-tile forward up-sweep.
 //   fwd_top   prefix scan of tile affine maps from x_0 (Lemma lqt_fwd_init).
 //   fwd_down  in-tile down-sweep of states; per chunk the rollout
-//             u*_k = -K_k x*_k + d_k, x*_{k+1} = F_k x*_k + c_k + L_k u*_k.
+//             u*_k = -K_k x*_k + d_k, x*_{k+1} = F_k x*_k + c_k + L_k u*_k,
+//             and, when refining, the shifted data of the second pass (first
+//             pass) or x* = x^ + xi (second pass).
+//
+// Per-step records move between HBM and registers through per-warp shared
+// memory rows (WarpRows), so that global accesses are coalesced although each
+// thread walks its own chunk.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "lqt_dense.cuh"
+#include "lqt_refine.cuh"
+#include "lqt_tma.cuh"
 
 namespace lqt {
 
@@ -31,8 +40,13 @@ enum : int {
     ST_OK = 0,
     ST_NOTSPD = 2,
     ST_NONFINITE = 3,
+    ST_TIMEOUT = 6,
     ST_SINGULAR = 8,
 };
+
+enum : int { OUT_S = 1, OUT_V = 2, OUT_K = 4, OUT_ALL = 7 };
+
+constexpr int kStageG = 2;  // steps per warp-staged group
 
 template <typename R>
 struct Params {
@@ -50,79 +64,127 @@ struct Params {
     R* ftree;       // [tiles][AFFINE][W] in-tile forward up-sweep (right-anchored)
     R* ftile_agg;   // [tiles][AFFINE]
     R* ftile_x;     // [tiles][N]         state at the start of each tile
+    // refinement (see lqt_refine.cuh): shifted data written by the first pass
+    R *rp, *cp, *rTp, *x0p;
     int B;          // steps per chunk
     int tiles;
     int has_c;
     int cost_invariant;  // H and X time-invariant: H^T X and H^T X H precomputed
+    int dyn_invariant;   // F, L, U time-invariant: kept in shared memory
+    int c_invariant;     // c time-invariant (or absent): kept in shared memory
     int out_mask;        // OUT_S | OUT_V | OUT_K: which of S, v, K this pass writes
+    int refine_emit;     // first pass of a refined solve: write r', c', r'_T, x'_0
+    int refine_add;      // second pass: x <- x + xi instead of x <- xi
 };
-
-enum : int { OUT_S = 1, OUT_V = 2, OUT_K = 4, OUT_ALL = 7 };
 
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (code != ST_OK) atomicCAS(status, 0, code);
 }
 
-// Shared-memory cost terms when H, X are time-invariant:
-//   sHX[a * N + i] = (H^T X)[i][a]   (p x N)
-//   sQ[sym(i, j)]  = (H^T X H)[i][j]
-template <typename R, int N>
-__device__ __forceinline__ void cost_prologue(const Params<R>& P, R* sQ, R* sHX) {
-    if (!P.cost_invariant) return;
+__host__ __device__ inline int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Shared-memory model area (floats of R), same layout in every kernel:
+//   F[N*N] L[N*M] U[M*M] c[N] Q[SYM] HX[p*N] H[p*N]
+template <int N, int M>
+struct ModelLayout {
+    static constexpr int OF = 0, OL = N * N, OU = OL + N * M, OC = OU + M * M,
+                         OQ = OC + N, OHX = OQ + Dims<N>::SYM;
+    __host__ __device__ static constexpr int OH(int p) { return OHX + p * N; }
+    __host__ __device__ static constexpr int size(int p) { return OHX + 2 * p * N; }
+};
+
+// Fill the model area from the time-invariant inputs (each part only when its
+// stride is 0).  Ends with __syncthreads.
+template <typename R, int N, int M>
+__device__ __forceinline__ void model_prologue(const Params<R>& P, R* sm) {
+    using ML = ModelLayout<N, M>;
     const int p = P.p;
-    for (int e = threadIdx.x; e < p * N; e += blockDim.x) {
-        const int a = e / N, i = e % N;
-        R t = R(0);
-        for (int b = 0; b < p; ++b) t += P.H[b * N + i] * P.X[b * p + a];
-        sHX[e] = t;
+    if (P.dyn_invariant) {
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) sm[ML::OF + e] = P.F[e];
+        for (int e = threadIdx.x; e < N * M; e += blockDim.x) sm[ML::OL + e] = P.L[e];
+        for (int e = threadIdx.x; e < M * M; e += blockDim.x) sm[ML::OU + e] = P.U[e];
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int i = e / N, j = e % N;
-        if (i > j) continue;
-        R t = R(0);
-        for (int a = 0; a < p; ++a) t += sHX[a * N + i] * P.H[a * N + j];
-        sQ[sym<N>(i, j)] = t;
+    if (P.c_invariant)
+        for (int e = threadIdx.x; e < N; e += blockDim.x) sm[ML::OC + e] = P.has_c ? P.c[e] : R(0);
+    if (P.cost_invariant) {
+        R* sHX = sm + ML::OHX;
+        R* sH = sm + ML::OH(p);
+        for (int e = threadIdx.x; e < p * N; e += blockDim.x) {
+            const int a = e / N, i = e % N;
+            R t = R(0);
+            for (int b = 0; b < p; ++b) t += P.H[b * N + i] * P.X[b * p + a];
+            sHX[e] = t;
+            sH[e] = P.H[e];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const int i = e / N, j = e % N;
+            if (i > j) continue;
+            R t = R(0);
+            for (int a = 0; a < p; ++a) t += sHX[a * N + i] * P.H[a * N + j];
+            sm[ML::OQ + sym<N>(i, j)] = t;
+        }
     }
     __syncthreads();
 }
 
-// Step k of the model: F, c, L, U and the cost element Q = H^T X H, q = H^T X r.
+// Step k of the model: F, c, L, U and the cost element Q = H^T X H, q = H^T X r,
+// from the shared model area where the input is time-invariant.
 template <typename R, int N, int M>
-__device__ __forceinline__ void load_step(const Params<R>& P, long long k, const R* sQ,
-                                          const R* sHX, Step<R, N, M>& st) {
-    const R* F = P.F + k * P.sF;
-    const R* L = P.L + k * P.sL;
-    const R* U = P.U + k * P.sU;
+__device__ __forceinline__ void load_step(const Params<R>& P, long long k, const R* sm,
+                                          const R* r_staged, Step<R, N, M>& st) {
+    using ML = ModelLayout<N, M>;
+    if (P.dyn_invariant) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+        for (int i = 0; i < N; ++i) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) st.F[i][j] = __ldg(F + i * N + j);
+            for (int j = 0; j < N; ++j) st.F[i][j] = sm[ML::OF + i * N + j];
 #pragma unroll
-        for (int a = 0; a < M; ++a) st.L[i][a] = __ldg(L + i * M + a);
+            for (int a = 0; a < M; ++a) st.L[i][a] = sm[ML::OL + i * M + a];
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) st.U[a][b] = sm[ML::OU + a * M + b];
+    } else {
+        const R* F = P.F + k * P.sF;
+        const R* L = P.L + k * P.sL;
+        const R* U = P.U + k * P.sU;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) st.F[i][j] = __ldg(F + i * N + j);
+#pragma unroll
+            for (int a = 0; a < M; ++a) st.L[i][a] = __ldg(L + i * M + a);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) st.U[a][b] = __ldg(U + a * M + b);
     }
+    if (P.c_invariant) {
 #pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int b = 0; b < M; ++b) st.U[a][b] = __ldg(U + a * M + b);
-    if (P.has_c) {
+        for (int i = 0; i < N; ++i) st.c[i] = sm[ML::OC + i];
+    } else {
         const R* c = P.c + k * P.sc;
 #pragma unroll
         for (int i = 0; i < N; ++i) st.c[i] = __ldg(c + i);
-    } else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) st.c[i] = R(0);
     }
     const int p = P.p;
     const R* r = P.r ? P.r + k * P.sr : nullptr;
     if (P.cost_invariant) {
+        const R* sHX = sm + ML::OHX;
 #pragma unroll
-        for (int k2 = 0; k2 < Dims<N>::SYM; ++k2) st.Q[k2] = sQ[k2];
+        for (int k2 = 0; k2 < Dims<N>::SYM; ++k2) st.Q[k2] = sm[ML::OQ + k2];
 #pragma unroll
         for (int i = 0; i < N; ++i) st.q[i] = R(0);
         if (r) {
             for (int a = 0; a < p; ++a) {
-                const R ra = __ldg(r + a);
+                const R ra = r_staged ? r_staged[a] : __ldg(r + a);
 #pragma unroll
                 for (int i = 0; i < N; ++i) st.q[i] += sHX[a * N + i] * ra;
             }
@@ -209,57 +271,188 @@ __device__ __forceinline__ void load_row(const R* src, R* vals) {
     }
 }
 
-template <typename R, int N>
-__host__ __device__ constexpr size_t cost_smem_elems(int p) {
-    return (size_t)Dims<N>::SYM + (size_t)p * N;
+// Chunk geometry of a tile.
+struct TileGeo {
+    long long T;
+    long long chunk0;  // first chunk of the tile
+    int B;
+    __device__ void chunk(int c, long long& s, long long& e) const {
+        s = (chunk0 + c) * (long long)B;
+        e = s + B < T ? s + B : T;
+        if (s > T) s = T;
+    }
+    // chunks of this tile that hold at least one step
+    __device__ int live(int W) const {
+        const long long first = chunk0 * (long long)B;
+        if (first >= T) return 0;
+        const long long n = (T - first + B - 1) / B;
+        return n < W ? (int)n : W;
+    }
+};
+
+// Backward group g of a chunk [s, e): steps [lo, hi), processed hi-1 .. lo.
+__device__ __forceinline__ void bwd_group(long long s, long long e, int g, long long& lo,
+                                          int& cnt) {
+    const long long hi = e - (long long)g * kStageG;
+    lo = hi - kStageG > s ? hi - kStageG : s;
+    cnt = hi > lo ? (int)(hi - lo) : 0;
+}
+
+// Forward group g of a chunk [s, e): steps [lo, lo + cnt).
+__device__ __forceinline__ void fwd_group(long long s, long long e, int g, long long& lo,
+                                          int& cnt) {
+    lo = s + (long long)g * kStageG;
+    const long long hi = lo + kStageG < e ? lo + kStageG : e;
+    cnt = hi > lo ? (int)(hi - lo) : 0;
+}
+
+// Per-thread prefetch of the references r_k of one staged group ahead
+// (p <= kRStage; two buffers of kStageG steps each).
+constexpr int kRStage = 4;
+constexpr int kRBuf = 2 * kStageG * kRStage;  // floats per thread
+
+template <typename R>
+__device__ __forceinline__ bool r_stageable(const Params<R>& P) {
+    return P.r != nullptr && P.p <= kRStage;
+}
+
+// Issue the copies of r for steps [lo, lo + cnt) into buf (slot jj at jj * kRStage)
+// and commit them as one group (an empty group when nothing is staged).
+template <typename R>
+__device__ __forceinline__ void r_prefetch(const Params<R>& P, R* buf, long long lo, int cnt) {
+    if (r_stageable(P))
+        for (int jj = 0; jj < cnt; ++jj)
+            for (int a = 0; a < P.p; ++a)
+                cp_async<sizeof(R)>(buf + jj * kRStage + a, P.r + (lo + jj) * P.sr + a);
+    cp_async_commit();
+}
+
+// Dynamic shared memory of the per-tile kernels: a 16-byte head holding the
+// mbarrier, then the big area, then the per-thread r buffers, then the model
+// area.
+constexpr int kSmemHead = 16;
+
+template <typename R, int N, int M, int W>
+struct Smem {
+    static constexpr int NW = W / 32;
+    // bwd_down staging row per lane: S, v, K, d of kStageG steps
+    static constexpr int DS = 0, DV = DS + round4(kStageG * N * N),
+                         DK = DV + round4(kStageG * N), DD = DK + round4(kStageG * M * N),
+                         DROW = DD + round4(kStageG * M);
+    // fwd_down staging row per lane: two input buffers (K, d, x^) and the
+    // outputs (x, u, c', r' padded to 4 per step)
+    static constexpr int FIK = 0, FID = FIK + round4(kStageG * M * N),
+                         FIX = FID + round4(kStageG * M), FIN = FIX + round4(kStageG * N);
+    static constexpr int FX = 2 * FIN, FU = FX + round4(kStageG * N),
+                         FC = FU + round4(kStageG * M), FR = FC + round4(kStageG * N),
+                         FROW = FR + kStageG * 4;
+    static constexpr int UP_BIG = Dims<N>::ELEM * W;
+    static constexpr int DOWN_BIG_A = (Dims<N>::ELEM + Dims<N>::VALUE) * W;
+    static constexpr int DOWN_BIG_B = NW * 32 * DROW;
+    static constexpr int DOWN_BIG = DOWN_BIG_A > DOWN_BIG_B ? DOWN_BIG_A : DOWN_BIG_B;
+    static constexpr int FDOWN_BIG_A = (Dims<N>::AFFINE + N) * W;
+    static constexpr int FDOWN_BIG_B = NW * 32 * FROW;
+    static constexpr int FDOWN_BIG = FDOWN_BIG_A > FDOWN_BIG_B ? FDOWN_BIG_A : FDOWN_BIG_B;
+    static constexpr int RBUF = W * kRBuf;
+    static size_t bytes(int big, int p) {
+        return kSmemHead + (size_t)(big + RBUF + ModelLayout<N, M>::size(p)) * sizeof(R);
+    }
+};
+
+// Threads per tile (one CTA): 512 in FP32 (256 in FP64) unless the largest
+// per-tile shared-memory layout would exceed the opt-in limit (227 KB), then
+// half.  The in-tile trees hold W elements; W is a power of two.
+template <typename R, int N, int M, int W>
+constexpr size_t tile_smem_bytes_max() {
+    using SM = Smem<R, N, M, W>;
+    constexpr int big = SM::DOWN_BIG > SM::FDOWN_BIG ? SM::DOWN_BIG : SM::FDOWN_BIG;
+    // model area with p up to 2N
+    return kSmemHead + (size_t)(big + SM::RBUF + ModelLayout<N, M>::size(2 * N)) * sizeof(R);
+}
+
+template <typename R, int N, int M>
+constexpr int tile_threads() {
+    constexpr int w = sizeof(R) == 4 ? 512 : 256;
+    return tile_smem_bytes_max<R, N, M, w>() <= 227 * 1024 ? w : w / 2;
 }
 
 // ===========================================================================
 // bwd_up: chunk fold + in-tile up-sweep (left-anchored: after level d, slot
 // i = j * 2^{d+1} holds the total of chunks [i, i + 2^{d+1}); slot i + 2^d
-// keeps the total of [i + 2^d, i + 2^{d+1}) for the down-sweep).
+// keeps the total of [i + 2^d, i + 2^{d+1}) for the down-sweep).  Only the
+// chunks that hold steps are swept (the rest are neutral).
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
+    using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw);           // [ELEM][W]
-    R* sQ = tree + (size_t)Dims<N>::ELEM * W;
-    R* sHX = sQ + Dims<N>::SYM;
-    cost_prologue<R, N>(P, sQ, sHX);
+    R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][W]
+    R* sm = tree + SM::UP_BIG + SM::RBUF;
+    model_prologue<R, N, M>(P, sm);
 
     const int tid = threadIdx.x;
-    const long long chunk = (long long)blockIdx.x * W + tid;
-    const long long s = chunk * P.B;
-    const long long e = min(s + (long long)P.B, P.T);
+    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    const int Weff = next_pow2(geo.live(W));
+    long long s, e;
+    geo.chunk(tid, s, e);
     Elem<R, N> acc;
     set_neutral(acc);
     bool ok = true;
     for (long long k = e - 1; k >= s; --k) {
         Step<R, N, M> st;
-        load_step<R, N, M>(P, k, sQ, sHX, st);
+        load_step<R, N, M>(P, k, sm, nullptr, st);
         ok &= fold_step<R, N, M>(st, P.has_c != 0, acc);
     }
     store_elem(acc, ElemView<R, N>{tree + tid, W});
     __syncthreads();
     bool ok2 = true;
 #pragma unroll 1
-    for (int h = 1; h < W; h <<= 1) {
+    for (int h = 1; h < Weff; h <<= 1) {
         const int i = tid * 2 * h;
-        if (i < W)
+        if (i < Weff)
             ok2 &= combine_view<R, N>(ElemView<R, N>{tree + i, W}, ElemView<R, N>{tree + i + h, W},
                                       ElemView<R, N>{tree + i, W});
         __syncthreads();
     }
-    R* g = P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W;
-    for (int k = tid; k < Dims<N>::ELEM * W; k += W) g[k] = tree[k];
     if (tid < Dims<N>::ELEM) P.tile_agg[(size_t)blockIdx.x * Dims<N>::ELEM + tid] = tree[tid * W];
+    cta_bulk_store(P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W, tree,
+                   (uint32_t)(Dims<N>::ELEM * W * sizeof(R)));
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!ok2) set_status(P.status, ST_SINGULAR);
 }
 
+// Terminal value S_T = H_T^T X_T H_T, v_T = H_T^T X_T r_T.
+template <typename R, int N>
+__device__ __forceinline__ void terminal_value(const Params<R>& P, Value<R, N>& z) {
+    const int pT = P.pT;
+#pragma unroll
+    for (int k = 0; k < Dims<N>::SYM; ++k) z.S[k] = R(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) z.v[i] = R(0);
+    for (int a = 0; a < pT; ++a) {
+        R y[N];
+        R xr = R(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) y[j] = R(0);
+        for (int b = 0; b < pT; ++b) {
+            const R xab = P.XT[a * pT + b];
+#pragma unroll
+            for (int j = 0; j < N; ++j) y[j] += xab * P.HT[b * N + j];
+            if (P.rT) xr += xab * P.rT[b];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const R h = P.HT[a * N + i];
+            z.v[i] += h * xr;
+#pragma unroll
+            for (int j = i; j < N; ++j) z.S[sym<N>(i, j)] += h * y[j];
+        }
+    }
+}
+
 // ===========================================================================
 // bwd_top: one CTA of TP threads.  Thread t folds tiles [t g, (t+1) g)
-// (g = ceil(tiles / TP)), the CTA sweeps the TP partial totals, and the value
+// (g = ceil(tiles / TP)), the CTA sweeps the partial totals, and the value
 // carries flow back from the terminal value (S_T, v_T) of Lemma LQT_assoc.
 // ===========================================================================
 template <typename R, int N, int TP>
@@ -269,20 +462,22 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     R* carry = tree + (size_t)Dims<N>::ELEM * TP;        // [VALUE][TP]
     const int tid = threadIdx.x;
     const int tiles = P.tiles;
-    const int g = (tiles + TP - 1) / TP;
+    const int g = tiles > 0 ? (tiles + TP - 1) / TP : 1;
+    const int used = tiles > 0 ? (tiles + g - 1) / g : 1;
+    const int Teff = next_pow2(used);
     const int t0 = min(tid * g, tiles), t1 = min(t0 + g, tiles);
     bool ok = true;
 
-    // thread partial: tile totals t0..t1-1 folded right to left, in shared
-    // memory slot tid (neutral when the range is empty)
+    // thread partial: tile totals t0..t1-1 folded right to left (neutral if empty)
     {
         ElemView<R, N> mine{tree + tid, TP};
         if (t1 > t0) {
             const R* src = P.tile_agg + (size_t)(t1 - 1) * Dims<N>::ELEM;
             for (int k = 0; k < Dims<N>::ELEM; ++k) mine.p[k * TP] = src[k];
-            // fold further tiles in from the left, through the carry area as scratch
-            R* scratch = carry + tid;  // VALUE >= ... not enough room: use a second pass below
-            (void)scratch;
+            for (int t = t1 - 2; t >= t0; --t)
+                ok &= combine_view<R, N>(
+                    ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1}, mine,
+                    mine);
         } else {
             Elem<R, N> e;
             set_neutral(e);
@@ -290,51 +485,17 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
         }
     }
     __syncthreads();
-    // g > 1: fold the remaining tiles of this thread into its slot, one at a
-    // time, staging the left operand in global tile_agg (read-only) directly.
-    if (g > 1) {
-        for (int t = t1 - 2; t >= t0; --t) {
-            ok &= combine_view<R, N>(
-                ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1},
-                ElemView<R, N>{tree + tid, TP}, ElemView<R, N>{tree + tid, TP});
-        }
-    }
-    __syncthreads();
 #pragma unroll 1
-    for (int h = 1; h < TP; h <<= 1) {
+    for (int h = 1; h < Teff; h <<= 1) {
         const int i = tid * 2 * h;
-        if (i < TP)
+        if (i < Teff)
             ok &= combine_view<R, N>(ElemView<R, N>{tree + i, TP}, ElemView<R, N>{tree + i + h, TP},
                                      ElemView<R, N>{tree + i, TP});
         __syncthreads();
     }
-    // terminal value: S_T = H_T^T X_T H_T, v_T = H_T^T X_T r_T
     if (tid == 0) {
-        const int pT = P.pT;
         Value<R, N> z;
-#pragma unroll
-        for (int k = 0; k < Dims<N>::SYM; ++k) z.S[k] = R(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) z.v[i] = R(0);
-        for (int a = 0; a < pT; ++a) {
-            R y[N];
-            R xr = R(0);
-#pragma unroll
-            for (int j = 0; j < N; ++j) y[j] = R(0);
-            for (int b = 0; b < pT; ++b) {
-                const R xab = P.XT[a * pT + b];
-#pragma unroll
-                for (int j = 0; j < N; ++j) y[j] += xab * P.HT[b * N + j];
-                if (P.rT) xr += xab * P.rT[b];
-            }
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const R h = P.HT[a * N + i];
-                z.v[i] += h * xr;
-#pragma unroll
-                for (int j = i; j < N; ++j) z.S[sym<N>(i, j)] += h * y[j];
-            }
-        }
+        terminal_value<R, N>(P, z);
         store_value(z, ValueView<R, N>{carry, TP});
         R* ST = P.S + (size_t)P.T * N * N;
 #pragma unroll
@@ -348,9 +509,9 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     }
     __syncthreads();
 #pragma unroll 1
-    for (int h = TP / 2; h >= 1; h >>= 1) {
+    for (int h = Teff / 2; h >= 1; h >>= 1) {
         const int i = tid * 2 * h;
-        if (i < TP) {
+        if (i < Teff) {
             Value<R, N> c;
             load_value(c, ValueView<R, N>{carry + i, TP});
             store_value(c, ValueView<R, N>{carry + i + h, TP});
@@ -379,25 +540,39 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
+    using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw);               // [ELEM][W]
-    R* carry = tree + (size_t)Dims<N>::ELEM * W;            // [VALUE][W]
-    R* sQ = carry + (size_t)Dims<N>::VALUE * W;
-    R* sHX = sQ + Dims<N>::SYM;
-    R* ftree = tree;  // [AFFINE][W], reuses the element tree once it is consumed
-    cost_prologue<R, N>(P, sQ, sHX);
-
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
+    R* tree = big;                                       // [ELEM][W]
+    R* carry = big + (size_t)Dims<N>::ELEM * W;          // [VALUE][W]
+    R* rbuf = big + SM::DOWN_BIG + threadIdx.x * kRBuf;
+    R* sm = big + SM::DOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
-    const R* g = P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W;
-    for (int k = tid; k < Dims<N>::ELEM * W; k += W) tree[k] = g[k];
+    if (tid == 0) mbar_init(bar, 1);
+    long long s, e;
+    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    geo.chunk(tid, s, e);
+    {
+        long long lo;
+        int cnt;
+        bwd_group(s, e, 0, lo, cnt);
+        r_prefetch(P, rbuf, lo, cnt);
+    }
+    model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
+
+    uint32_t phase = 0;
+    const bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W,
+                                       (uint32_t)(Dims<N>::ELEM * W * sizeof(R)), bar, phase);
+    const int Weff = next_pow2(geo.live(W));
     if (tid < Dims<N>::VALUE)
         carry[tid * W] = P.tile_carry[(size_t)blockIdx.x * Dims<N>::VALUE + tid];
     __syncthreads();
     bool ok_sing = true;
 #pragma unroll 1
-    for (int h = W / 2; h >= 1; h >>= 1) {
+    for (int h = Weff / 2; h >= 1; h >>= 1) {
         const int i = tid * 2 * h;
-        if (i < W) {
+        if (i < Weff) {
             Value<R, N> c;
             load_value(c, ValueView<R, N>{carry + i, W});
             store_value(c, ValueView<R, N>{carry + i + h, W});
@@ -408,11 +583,13 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     }
     Value<R, N> val;
     load_value(val, ValueView<R, N>{carry + tid, W});
-    __syncthreads();  // tree and carry slots are reused below
+    __syncthreads();  // the big area becomes the warp staging rows
 
-    const long long chunk = (long long)blockIdx.x * W + tid;
-    const long long s = chunk * P.B;
-    const long long e = min(s + (long long)P.B, P.T);
+    const int lane = tid & 31, warp = tid >> 5;
+    R* rows = big + (size_t)warp * 32 * SM::DROW;
+    R* myrow = rows + lane * SM::DROW;
+    const long long tbase = geo.chunk0 * P.B;  // first step of the tile
+    const bool staged = r_stageable(P);
     R Phi[N][N], gam[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -421,55 +598,82 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
         gam[i] = R(0);
     }
     bool ok = true, finite = true;
-    for (long long k = e - 1; k >= s; --k) {
-        Step<R, N, M> st;
-        load_step<R, N, M>(P, k, sQ, sHX, st);
-        R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
-        ok &= riccati_step<R, N, M>(st, P.has_c != 0, val.S, val.v, K, d, Ft, ct, Rc, Rinv);
-        // outputs at step k
-        R Sk[N * N];
+    const int groups = (P.B + kStageG - 1) / kStageG;
+    for (int g = 0; g < groups; ++g) {
+        if (g + 1 < groups) {
+            long long lo1;
+            int cnt1;
+            bwd_group(s, e, g + 1, lo1, cnt1);
+            r_prefetch(P, rbuf + ((g + 1) & 1) * kStageG * kRStage, lo1, cnt1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        long long lo;
+        int cnt;
+        bwd_group(s, e, g, lo, cnt);
+        const R* rg = rbuf + (g & 1) * kStageG * kRStage;
+        for (int jj = cnt - 1; jj >= 0; --jj) {
+            const long long k = lo + jj;
+            Step<R, N, M> st;
+            load_step<R, N, M>(P, k, sm, staged ? rg + jj * kRStage : nullptr, st);
+            R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
+            ok &= riccati_step<R, N, M>(st, P.has_c != 0, val.S, val.v, K, d, Ft, ct, Rc, Rinv);
+            // records of step k into this lane's staging row
+            R rec[N * N];
 #pragma unroll
-        for (int i = 0; i < N; ++i)
+            for (int i = 0; i < N; ++i)
 #pragma unroll
-            for (int j = 0; j < N; ++j) Sk[i * N + j] = val.S[sym<N>(i, j)];
-        if (P.out_mask & OUT_S) store_row<R, N * N>(P.S + (size_t)k * N * N, Sk);
-        if (P.out_mask & OUT_V) store_row<R, N>(P.v + (size_t)k * N, val.v);
-        if (P.out_mask & OUT_K) {
+                for (int j = 0; j < N; ++j) rec[i * N + j] = val.S[sym<N>(i, j)];
+            store_row<R, N * N>(myrow + SM::DS + jj * N * N, rec);
+            store_row<R, N>(myrow + SM::DV + jj * N, val.v);
             R Kk[M * N];
 #pragma unroll
             for (int a = 0; a < M; ++a)
 #pragma unroll
                 for (int j = 0; j < N; ++j) Kk[a * N + j] = K[a][j];
-            store_row<R, M * N>(P.K + (size_t)k * M * N, Kk);
-        }
-        store_row<R, M>(P.u + (size_t)k * M, d);
+            store_row<R, M * N>(myrow + SM::DK + jj * M * N, Kk);
+            store_row<R, M>(myrow + SM::DD + jj * M, d);
 #pragma unroll
-        for (int i = 0; i < N; ++i) finite = finite && isfinite(val.v[i]) && isfinite(Sk[i * N + i]);
-        // chunk map: x_e = Phi x_{k} + gam after adding step k
+            for (int i = 0; i < N; ++i) finite = finite && isfinite(val.v[i]) && isfinite(rec[i * N + i]);
+            // chunk map: x_e = Phi x_k + gam after adding step k
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            R t = gam[i];
+            for (int i = 0; i < N; ++i) {
+                R t = gam[i];
 #pragma unroll
-            for (int j = 0; j < N; ++j) t += Phi[i][j] * ct[j];
-            gam[i] = t;
-        }
-        R Pn[N][N];
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                R t = R(0);
-#pragma unroll
-                for (int l = 0; l < N; ++l) t += Phi[i][l] * Ft[l][j];
-                Pn[i][j] = t;
+                for (int j = 0; j < N; ++j) t += Phi[i][j] * ct[j];
+                gam[i] = t;
             }
+            R Pn[N][N];
 #pragma unroll
-        for (int i = 0; i < N; ++i)
+            for (int i = 0; i < N; ++i)
 #pragma unroll
-            for (int j = 0; j < N; ++j) Phi[i][j] = Pn[i][j];
+                for (int j = 0; j < N; ++j) {
+                    R t = R(0);
+#pragma unroll
+                    for (int l = 0; l < N; ++l) t += Phi[i][l] * Ft[l][j];
+                    Pn[i][j] = t;
+                }
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int j = 0; j < N; ++j) Phi[i][j] = Pn[i][j];
+        }
+        __syncwarp();
+        const int lrel = (int)(lo - tbase);
+        if (P.out_mask & OUT_S)
+            WarpRows<R, N * N, kStageG>::store(P.S, tbase, rows + SM::DS, SM::DROW, lrel, cnt);
+        if (P.out_mask & OUT_V)
+            WarpRows<R, N, kStageG>::store(P.v, tbase, rows + SM::DV, SM::DROW, lrel, cnt);
+        if (P.out_mask & OUT_K)
+            WarpRows<R, M * N, kStageG>::store(P.K, tbase, rows + SM::DK, SM::DROW, lrel, cnt);
+        WarpRows<R, M, kStageG>::store(P.u, tbase, rows + SM::DD, SM::DROW, lrel, cnt);
+        __syncwarp();
     }
+    __syncthreads();  // the big area becomes the forward tree
     // forward up-sweep (right-anchored): after level d, slot j = i + 2^{d+1} - 1
     // holds the composite of chunks [i, i + 2^{d+1}); slot i + 2^d - 1 keeps [i, i + 2^d)
+    R* ftree = big;  // [AFFINE][W]
     {
         AffineView<R, N> mine{ftree + tid, W};
 #pragma unroll
@@ -481,20 +685,21 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     }
     __syncthreads();
 #pragma unroll 1
-    for (int h = 1; h < W; h <<= 1) {
+    for (int h = 1; h < Weff; h <<= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
-        if (j < W)
+        if (j < Weff)
             affine_compose_view<R, N>(AffineView<R, N>{ftree + j - h, W}, AffineView<R, N>{ftree + j, W},
                                       AffineView<R, N>{ftree + j, W});
         __syncthreads();
     }
-    R* fg = P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W;
-    for (int k = tid; k < Dims<N>::AFFINE * W; k += W) fg[k] = ftree[k];
     if (tid < Dims<N>::AFFINE)
-        P.ftile_agg[(size_t)blockIdx.x * Dims<N>::AFFINE + tid] = ftree[tid * W + W - 1];
+        P.ftile_agg[(size_t)blockIdx.x * Dims<N>::AFFINE + tid] = ftree[tid * W + Weff - 1];
+    cta_bulk_store(P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W, ftree,
+                   (uint32_t)(Dims<N>::AFFINE * W * sizeof(R)));
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!finite) set_status(P.status, ST_NONFINITE);
     if (!ok_sing) set_status(P.status, ST_SINGULAR);
+    if (!ok_load) set_status(P.status, ST_TIMEOUT);
 }
 
 // ===========================================================================
@@ -508,7 +713,9 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
     R* xs = tree + (size_t)Dims<N>::AFFINE * TP;   // [N][TP]
     const int tid = threadIdx.x;
     const int tiles = P.tiles;
-    const int g = (tiles + TP - 1) / TP;
+    const int g = tiles > 0 ? (tiles + TP - 1) / TP : 1;
+    const int used = tiles > 0 ? (tiles + g - 1) / g : 1;
+    const int Teff = next_pow2(used);
     const int t0 = min(tid * g, tiles), t1 = min(t0 + g, tiles);
     {
         AffineView<R, N> mine{tree + tid, TP};
@@ -524,9 +731,9 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
     }
     __syncthreads();
 #pragma unroll 1
-    for (int h = 1; h < TP; h <<= 1) {
+    for (int h = 1; h < Teff; h <<= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
-        if (j < TP)
+        if (j < Teff)
             affine_compose_view<R, N>(AffineView<R, N>{tree + j - h, TP}, AffineView<R, N>{tree + j, TP},
                                       AffineView<R, N>{tree + j, TP});
         __syncthreads();
@@ -535,15 +742,15 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const R x0 = P.x0[i];
-            xs[i * TP + TP - 1] = x0;
-            P.x[i] = x0;
+            xs[i * TP + Teff - 1] = x0;
+            if (!P.refine_add) P.x[i] = x0;  // second pass: x*_0 = x^_0 + 0 stays
         }
     }
     __syncthreads();
 #pragma unroll 1
-    for (int h = TP / 2; h >= 1; h >>= 1) {
+    for (int h = Teff / 2; h >= 1; h >>= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
-        if (j < TP) {
+        if (j < Teff) {
             R xv[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) xv[i] = xs[i * TP + j];
@@ -569,21 +776,34 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
 
 // ===========================================================================
 // fwd_down: in-tile down-sweep of states and the per-chunk rollout.
+// First refined pass: also r'_k = r_k - H_k x^_k, c'_k = F_k x^_k + c_k - x^_{k+1}
+// (compensated), r'_T and x'_0.  Second pass: x*_{k+1} = x^_{k+1} + xi_{k+1}.
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
+    using SM = Smem<R, N, M, W>;
+    using ML = ModelLayout<N, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* ftree = reinterpret_cast<R*>(smem_raw);      // [AFFINE][W]
-    R* xs = ftree + (size_t)Dims<N>::AFFINE * W;    // [N][W]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
+    R* ftree = big;                                      // [AFFINE][W]
+    R* xs = big + (size_t)Dims<N>::AFFINE * W;           // [N][W]
+    R* sm = big + SM::FDOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
-    const R* fg = P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W;
-    for (int k = tid; k < Dims<N>::AFFINE * W; k += W) ftree[k] = fg[k];
-    if (tid < N) xs[tid * W + W - 1] = P.ftile_x[(size_t)blockIdx.x * N + tid];
+    if (tid == 0) mbar_init(bar, 1);
+    model_prologue<R, N, M>(P, sm);
+
+    uint32_t phase = 0;
+    const bool ok_load = cta_bulk_load(ftree, P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W,
+                                       (uint32_t)(Dims<N>::AFFINE * W * sizeof(R)), bar, phase);
+    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    const int Weff = next_pow2(geo.live(W));
+    if (tid < N) xs[tid * W + Weff - 1] = P.ftile_x[(size_t)blockIdx.x * N + tid];
     __syncthreads();
 #pragma unroll 1
-    for (int h = W / 2; h >= 1; h >>= 1) {
+    for (int h = Weff / 2; h >= 1; h >>= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
-        if (j < W) {
+        if (j < Weff) {
             R xv[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) xv[i] = xs[i * W + j];
@@ -595,41 +815,181 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
         }
         __syncthreads();
     }
-    R x[N];
+    // The chunk stores its own start state (the tree value) and the states of
+    // its steps; the state after its last step is the next chunk's start (or,
+    // for the last chunk, its own x_T).  Stored states and the shifted data of
+    // the refinement are then consistent to the last bit.
+    R x[N], xnext[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) x[i] = xs[i * W + tid];
-    const long long chunk = (long long)blockIdx.x * W + tid;
-    const long long s = chunk * P.B;
-    const long long e = min(s + (long long)P.B, P.T);
-    for (long long k = s; k < e; ++k) {
-        R Kk[M * N], d[M];
-        load_row<R, M * N>(P.K + (size_t)k * M * N, Kk);
-        load_row<R, M>(P.u + (size_t)k * M, d);
-        const R* F = P.F + k * P.sF;
-        const R* L = P.L + k * P.sL;
-        R uk[M];
+    for (int i = 0; i < N; ++i) {
+        x[i] = xs[i * W + tid];
+        xnext[i] = tid + 1 < W ? xs[i * W + tid + 1] : R(0);
+    }
+    if (tid == W - 1 && blockIdx.x + 1 < (unsigned)P.tiles) {
 #pragma unroll
-        for (int a = 0; a < M; ++a) {
-            R t = d[a];
-#pragma unroll
-            for (int j = 0; j < N; ++j) t -= Kk[a * N + j] * x[j];
-            uk[a] = t;
-        }
-        R xn[N];
+        for (int i = 0; i < N; ++i) xnext[i] = P.ftile_x[(size_t)(blockIdx.x + 1) * N + i];
+    }
+    __syncthreads();  // the big area becomes the warp staging rows
+
+    const int lane = tid & 31, warp = tid >> 5;
+    R* rows = big + (size_t)warp * 32 * SM::FROW;
+    R* myrow = rows + lane * SM::FROW;
+    long long s, e;
+    geo.chunk(tid, s, e);
+    const long long tbase = geo.chunk0 * P.B;
+    const int p = P.p;
+    const R* sHm = sm + ML::OH(p);
+    const int groups = (P.B + kStageG - 1) / kStageG;
+    const bool stage_rp = P.refine_emit && p <= kRStage;  // r' kept with 4 floats per step
+    // a time-invariant F, L stays in registers for the whole chunk
+    R Fr[N][N], Lr[N][M];
+    if (P.dyn_invariant) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            R t = P.has_c ? __ldg(P.c + k * P.sc + i) : R(0);
 #pragma unroll
-            for (int j = 0; j < N; ++j) t += __ldg(F + i * N + j) * x[j];
+            for (int j = 0; j < N; ++j) Fr[i][j] = sm[ML::OF + i * N + j];
 #pragma unroll
-            for (int a = 0; a < M; ++a) t += __ldg(L + i * M + a) * uk[a];
-            xn[i] = t;
+            for (int a = 0; a < M; ++a) Lr[i][a] = sm[ML::OL + i * M + a];
         }
-        store_row<R, M>(P.u + (size_t)k * M, uk);
-        store_row<R, N>(P.x + (size_t)(k + 1) * N, xn);
-#pragma unroll
-        for (int i = 0; i < N; ++i) x[i] = xn[i];
     }
+    // inputs of group g into input buffer (g & 1); one cp.async group per call
+    auto prefetch = [&](int g) {
+        long long lo;
+        int cnt;
+        fwd_group(s, e, g, lo, cnt);
+        const int lrel = (int)(lo - tbase);
+        R* in = rows + (g & 1) * SM::FIN;
+        WarpRows<R, M * N, kStageG>::load_async(P.K, tbase, in + SM::FIK, SM::FROW, lrel, cnt);
+        WarpRows<R, M, kStageG>::load_async(P.u, tbase, in + SM::FID, SM::FROW, lrel, cnt);
+        if (P.refine_add)
+            WarpRows<R, N, kStageG>::load_async(P.x, tbase, in + SM::FIX, SM::FROW, lrel, cnt);
+        cp_async_commit();
+    };
+    prefetch(0);
+    for (int g = 0; g < groups; ++g) {
+        if (g + 1 < groups) {
+            prefetch(g + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        long long lo;
+        int cnt;
+        fwd_group(s, e, g, lo, cnt);
+        const int lrel = (int)(lo - tbase);
+        const R* in = myrow + (g & 1) * SM::FIN;
+        for (int jj = 0; jj < cnt; ++jj) {
+            const long long k = lo + jj;
+            R Kk[M * N], d[M];
+            load_row<R, M * N>(in + SM::FIK + jj * M * N, Kk);
+            load_row<R, M>(in + SM::FID + jj * M, d);
+            if (!P.dyn_invariant) {
+                const R* Fg = P.F + k * P.sF;
+                const R* Lg = P.L + k * P.sL;
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) Fr[i][j] = __ldg(Fg + i * N + j);
+#pragma unroll
+                    for (int a = 0; a < M; ++a) Lr[i][a] = __ldg(Lg + i * M + a);
+                }
+            }
+            const R* c = P.has_c ? (P.c_invariant ? sm + ML::OC : P.c + k * P.sc) : nullptr;
+            R uk[M];
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                R t = d[a];
+#pragma unroll
+                for (int j = 0; j < N; ++j) t -= Kk[a * N + j] * x[j];
+                uk[a] = t;
+            }
+            R xn[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                R t = c ? c[i] : R(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) t += Fr[i][j] * x[j];
+#pragma unroll
+                for (int a = 0; a < M; ++a) t += Lr[i][a] * uk[a];
+                xn[i] = t;
+            }
+            const bool last_step = (k == e - 1);
+            if (last_step && e < P.T) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) xn[i] = xnext[i];
+            }
+            if (P.refine_emit) {
+                // shifted data of the second pass, each a compensated dot product
+                const R* rk = P.r ? P.r + k * P.sr : nullptr;
+                const R* Hk = P.cost_invariant ? sHm : P.H + k * P.sH;
+                R* rrow = myrow + SM::FR + jj * kRStage;
+                for (int a = 0; a < p; ++a) {
+                    Dot2<R> acc(rk ? rk[a] : R(0));
+#pragma unroll
+                    for (int j = 0; j < N; ++j) acc.add_prod(-Hk[a * N + j], x[j]);
+                    if (stage_rp)
+                        rrow[a] = acc.value();
+                    else
+                        P.rp[k * p + a] = acc.value();
+                }
+                if (stage_rp)
+                    for (int a = p; a < kRStage; ++a) rrow[a] = R(0);
+                R cpk[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    Dot2<R> acc(c ? c[i] : R(0));
+#pragma unroll
+                    for (int j = 0; j < N; ++j) acc.add_prod(Fr[i][j], x[j]);
+                    acc.add(-xn[i]);
+                    cpk[i] = acc.value();
+                }
+                store_row<R, N>(myrow + SM::FC + jj * N, cpk);
+            }
+            store_row<R, M>(myrow + SM::FU + jj * M, uk);
+            // the state record of step k is x_k
+            if (P.refine_add) {
+                R xh[N], xo[N];
+                load_row<R, N>(in + SM::FIX + jj * N, xh);
+#pragma unroll
+                for (int i = 0; i < N; ++i) xo[i] = add_rn(xh[i], x[i]);
+                store_row<R, N>(myrow + SM::FX + jj * N, xo);
+            } else {
+                store_row<R, N>(myrow + SM::FX + jj * N, x);
+            }
+            if (k == P.T - 1) {
+                // x_T, and the terminal reference of the shifted problem
+                R* xT = P.x + (size_t)P.T * N;
+                if (P.refine_add) {
+#pragma unroll
+                    for (int i = 0; i < N; ++i) xT[i] = add_rn(xT[i], xn[i]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < N; ++i) xT[i] = xn[i];
+                }
+                if (P.refine_emit)
+                    for (int a = 0; a < P.pT; ++a) {
+                        Dot2<R> acc(P.rT ? P.rT[a] : R(0));
+#pragma unroll
+                        for (int j = 0; j < N; ++j) acc.add_prod(-P.HT[a * N + j], xn[j]);
+                        P.rTp[a] = acc.value();
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = xn[i];
+        }
+        __syncwarp();
+        WarpRows<R, N, kStageG>::store(P.x, tbase, rows + SM::FX, SM::FROW, lrel, cnt);
+        WarpRows<R, M, kStageG>::store(P.u, tbase, rows + SM::FU, SM::FROW, lrel, cnt);
+        if (P.refine_emit) {
+            WarpRows<R, N, kStageG>::store(P.cp, tbase, rows + SM::FC, SM::FROW, lrel, cnt);
+            if (stage_rp)
+                WarpRows<R, kRStage, kStageG>::store(P.rp, tbase, rows + SM::FR, SM::FROW, lrel, cnt);
+        }
+        __syncwarp();
+    }
+    if (P.refine_emit && blockIdx.x == 0 && tid < N) P.x0p[tid] = R(0);
+    if (!ok_load) set_status(P.status, ST_TIMEOUT);
 }
 
 // ===========================================================================
@@ -639,53 +999,12 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
 // ===========================================================================
 template <typename R, int N, int M>
 __global__ void __launch_bounds__(32, 1) k_riccati_seq(const Params<R> P) {
-    __shared__ R sQ[Dims<N>::SYM];
-    __shared__ R sHX[64 * N];
-    if (threadIdx.x == 0 && P.cost_invariant) {
-        // H^T X and H^T X H (p <= 64 here; the host checks)
-        const int p = P.p;
-        for (int a = 0; a < p; ++a)
-            for (int i = 0; i < N; ++i) {
-                R t = R(0);
-                for (int b = 0; b < p; ++b) t += P.H[b * N + i] * P.X[b * p + a];
-                sHX[a * N + i] = t;
-            }
-        for (int i = 0; i < N; ++i)
-            for (int j = i; j < N; ++j) {
-                R t = R(0);
-                for (int a = 0; a < p; ++a) t += sHX[a * N + i] * P.H[a * N + j];
-                sQ[sym<N>(i, j)] = t;
-            }
-    }
-    __syncthreads();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    model_prologue<R, N, M>(P, sm);
     if (threadIdx.x != 0) return;
     Value<R, N> val;
-    {
-        const int pT = P.pT;
-#pragma unroll
-        for (int k = 0; k < Dims<N>::SYM; ++k) val.S[k] = R(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) val.v[i] = R(0);
-        for (int a = 0; a < pT; ++a) {
-            R y[N];
-            R xr = R(0);
-#pragma unroll
-            for (int j = 0; j < N; ++j) y[j] = R(0);
-            for (int b = 0; b < pT; ++b) {
-                const R xab = P.XT[a * pT + b];
-#pragma unroll
-                for (int j = 0; j < N; ++j) y[j] += xab * P.HT[b * N + j];
-                if (P.rT) xr += xab * P.rT[b];
-            }
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const R h = P.HT[a * N + i];
-                val.v[i] += h * xr;
-#pragma unroll
-                for (int j = i; j < N; ++j) val.S[sym<N>(i, j)] += h * y[j];
-            }
-        }
-    }
+    terminal_value<R, N>(P, val);
     bool ok = true;
     {
         R* ST = P.S + (size_t)P.T * N * N;
@@ -700,7 +1019,7 @@ __global__ void __launch_bounds__(32, 1) k_riccati_seq(const Params<R> P) {
     }
     for (long long k = P.T - 1; k >= 0; --k) {
         Step<R, N, M> st;
-        load_step<R, N, M>(P, k, sQ, sHX, st);
+        load_step<R, N, M>(P, k, sm, nullptr, st);
         R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
         ok &= riccati_step<R, N, M>(st, P.has_c != 0, val.S, val.v, K, d, Ft, ct, Rc, Rinv);
 #pragma unroll
@@ -723,11 +1042,15 @@ __global__ void __launch_bounds__(32, 1) k_riccati_seq(const Params<R> P) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         x[i] = P.x0[i];
-        P.x[i] = x[i];
+        if (!P.refine_add) P.x[i] = x[i];
     }
+    using ML = ModelLayout<N, M>;
+    const int p = P.p;
+    const R* sHm = sm + ML::OH(p);
     for (long long k = 0; k < P.T; ++k) {
-        const R* F = P.F + k * P.sF;
-        const R* L = P.L + k * P.sL;
+        const R* F = P.dyn_invariant ? sm + ML::OF : P.F + k * P.sF;
+        const R* L = P.dyn_invariant ? sm + ML::OL : P.L + k * P.sL;
+        const R* c = P.has_c ? (P.c_invariant ? sm + ML::OC : P.c + k * P.sc) : nullptr;
         R uk[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) {
@@ -739,20 +1062,49 @@ __global__ void __launch_bounds__(32, 1) k_riccati_seq(const Params<R> P) {
         R xn[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            R t = P.has_c ? P.c[k * P.sc + i] : R(0);
+            R t = c ? c[i] : R(0);
 #pragma unroll
             for (int j = 0; j < N; ++j) t += F[i * N + j] * x[j];
 #pragma unroll
             for (int a = 0; a < M; ++a) t += L[i * M + a] * uk[a];
             xn[i] = t;
         }
+        if (P.refine_emit) {
+            const R* rk = P.r ? P.r + k * P.sr : nullptr;
+            const R* Hk = P.cost_invariant ? sHm : P.H + k * P.sH;
+            const int rps = p <= kRStage ? kRStage : p;
+            for (int a = 0; a < p; ++a) {
+                Dot2<R> acc(rk ? rk[a] : R(0));
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc.add_prod(-Hk[a * N + j], x[j]);
+                P.rp[k * rps + a] = acc.value();
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                Dot2<R> acc(c ? c[i] : R(0));
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc.add_prod(F[i * N + j], x[j]);
+                acc.add(-xn[i]);
+                P.cp[k * N + i] = acc.value();
+            }
+        }
 #pragma unroll
         for (int a = 0; a < M; ++a) P.u[(size_t)k * M + a] = uk[a];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            P.x[(size_t)(k + 1) * N + i] = xn[i];
+            P.x[(size_t)(k + 1) * N + i] = P.refine_add ? add_rn(P.x[(size_t)(k + 1) * N + i], xn[i]) : xn[i];
             x[i] = xn[i];
         }
+    }
+    if (P.refine_emit) {
+        for (int a = 0; a < P.pT; ++a) {
+            Dot2<R> acc(P.rT ? P.rT[a] : R(0));
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc.add_prod(-P.HT[a * N + j], x[j]);
+            P.rTp[a] = acc.value();
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) P.x0p[i] = R(0);
     }
     if (!ok) set_status(P.status, ST_NOTSPD);
 }

@@ -11,13 +11,6 @@ namespace lqt {
 template <typename R>
 struct Params;
 
-// Threads per tile (one CTA) for state size N and scalar type R.  The in-tile
-// trees hold W elements in shared memory; W is a power of two.
-template <typename R, int N>
-constexpr int tile_threads() {
-    return sizeof(R) == 4 ? 512 : 256;
-}
-
 // Threads of the single-CTA top-level scans.
 constexpr int top_threads() { return 256; }
 

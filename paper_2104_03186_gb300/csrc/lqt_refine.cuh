@@ -1,4 +1,4 @@
-// Kernels of the mixed-precision refinement pass (lqt_options.refine).
+// Compensated arithmetic of the mixed-precision refinement (lqt_options.refine).
 //
 // After a first solve with trajectory x^, the problem is shifted to
 // x = x^ + xi (Sec. II-B problem with the same F, L, U, H, X):
@@ -9,7 +9,9 @@
 // numbers, so they are formed with error-free transformations -- Knuth's
 // TwoSum and the FMA form of Dekker's TwoProduct -- accumulated as in the
 // compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci.
-// Comput. 26(6), 2005), i.e. as if in twice the working precision.
+// Comput. 26(6), 2005), i.e. as if in twice the working precision.  The
+// first pass's rollout (k_fwd_down) forms the shifted data; the second pass's
+// rollout adds xi to x^.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -54,52 +56,5 @@ struct Dot2 {
     }
     __device__ R value() const { return add_rn(s, c); }
 };
-
-// One thread per step k in [0, T]; thread T forms the terminal reference.
-// Writes r' (T x p), rT' (pT), c' (T x n) and x'_0 = 0 (n).
-template <typename R>
-__global__ void k_refine_prep(int n, int p, int pT, long long T, const R* __restrict__ F,
-                              long long sF, const R* __restrict__ c, long long sc,
-                              const R* __restrict__ H, long long sH, const R* __restrict__ r,
-                              long long sr, const R* __restrict__ HT, const R* __restrict__ rT,
-                              const R* __restrict__ xh, R* __restrict__ rp, R* __restrict__ rTp,
-                              R* __restrict__ cp, R* __restrict__ x0p) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > T) return;
-    const R* x = xh + k * n;
-    if (k == T) {
-        for (int a = 0; a < pT; ++a) {
-            Dot2<R> acc(rT ? rT[a] : R(0));
-            for (int j = 0; j < n; ++j) acc.add_prod(-HT[a * n + j], x[j]);
-            rTp[a] = acc.value();
-        }
-        for (int i = 0; i < n; ++i) x0p[i] = R(0);
-        return;
-    }
-    const R* Hk = H + k * sH;
-    const R* rk = r ? r + k * sr : nullptr;
-    for (int a = 0; a < p; ++a) {
-        Dot2<R> acc(rk ? rk[a] : R(0));
-        for (int j = 0; j < n; ++j) acc.add_prod(-Hk[a * n + j], x[j]);
-        rp[k * p + a] = acc.value();
-    }
-    const R* Fk = F + k * sF;
-    const R* ck = c ? c + k * sc : nullptr;
-    const R* xn = x + n;
-    for (int i = 0; i < n; ++i) {
-        Dot2<R> acc(ck ? ck[i] : R(0));
-        for (int j = 0; j < n; ++j) acc.add_prod(Fk[i * n + j], x[j]);
-        acc.add(-xn[i]);
-        cp[k * n + i] = acc.value();
-    }
-}
-
-// x <- x^ + xi over all (T+1) n entries.
-template <typename R>
-__global__ void k_refine_finish(long long count, R* __restrict__ x, const R* __restrict__ xi) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x)
-        x[i] = add_rn(x[i], xi[i]);
-}
 
 }  // namespace lqt
