@@ -129,7 +129,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv",
-                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -290,16 +290,16 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for _ in range(args.steps):
-            times += _time_solves(step, 1, flush, stream)
-            for i, (name, ms) in enumerate(lqt.lqt_profile_read()):
-                kern.setdefault((i, name), []).append(ms)
-        torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.__enter__()  # sampled through the timed steps, the T sweep and the batch
+    for _ in range(args.steps):
+        times += _time_solves(step, 1, flush, stream)
+        for i, (name, ms) in enumerate(lqt.lqt_profile_read()):
+            kern.setdefault((i, name), []).append(ms)
+    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     lqt.lqt_profile_enable(False)
-    clocks = clk.result()
     st = lqt.lqt_workspace_status(ws, stream)
     if st != lqt.LQT_OK:
         raise lqt.LQTError(st, "timed solve")
@@ -390,6 +390,12 @@ def run_ours(args):
                           "speedup": float(np.median(ts) / np.median(tp))})
             del o2, w2, Pq
 
+    # ---- ragged batch: 4096 problems, one persistent launch per (n, m) ----
+    batch = None if args.no_batch else run_batch(args, stream, flush)
+
+    clk.__exit__(None, None, None)
+    clocks = clk.result()
+
     # ---- CPU baseline (oracle on the host) ---------------------------------
     cpu_v, reps, el, sample = oracle_throughput(T, 10.0, max_reps=20)
     cpu = {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -412,12 +418,83 @@ def run_ours(args):
         "kernels_ms": per_kernel,
         "plan": plan,
         "sweep": sweep,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def gen_batch(count: int, seed: int):
+    """The ragged batch of inputs.ragged_batch, drawn on a thread pool (numpy's
+    LAPACK eigenvalue loops release the GIL), rounded to FP32."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2104_03186_gb300 import inputs
+
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray((4, 8, 16)), size=count)
+    Ts = rng.integers(64, 4096 + 1, size=count)
+
+    def one(i):
+        return inputs.diag_tracking(int(ns[i]), T=int(Ts[i]),
+                                    seed=int(seed) * 1_000_003 + i).astype(np.float32)
+
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, range(count)))
+
+
+def run_batch(args, stream, flush):
+    """Ragged batch (4096 problems, n in {4, 8, 16}, m = n/2, T in U[64, 4096],
+    time-varying F_k, L_k, X_k): total time-steps/s of lqt_solve_batched, with
+    the FP64 oracle on sampled problems."""
+    import torch
+
+    import oracle
+    from paper_2104_03186_gb300 import lqt
+
+    t0 = time.perf_counter()
+    probs = gen_batch(args.batch_count, 7)
+    gen_s = time.perf_counter() - t0
+    Ps = [lqt.Problem.from_inputs(p, dtype=np.float32) for p in probs]
+    outs = [P.allocate_outputs() for P in Ps]
+    ws = torch.empty(lqt.lqt_batch_workspace_bytes(len(Ps)), dtype=torch.uint8, device="cuda")
+    steps = sum(p.T for p in probs)
+
+    def run():
+        lqt.lqt_solve_batched(Ps, outs, ws, stream)
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    st = lqt.lqt_workspace_status(ws, stream)
+    times = _time_solves(run, 5, flush, stream)
+    med = float(np.median(times))
+    # accuracy on sampled problems of each size
+    errs = {}
+    rng = np.random.default_rng(0)
+    for n in (4, 8, 16):
+        idx = [i for i, p in enumerate(probs) if p.n == n]
+        for i in rng.choice(idx, size=min(2, len(idx)), replace=False):
+            pr = probs[int(i)].astype(np.float64)
+            ref = oracle.riccati(pr, keep_kv_kc=False)
+            got = {k: v.double().cpu().numpy() for k, v in outs[int(i)].items()}
+            e = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                 for k in ("S", "v", "K", "x", "u")}
+            for k, v in e.items():
+                errs[k] = max(errs.get(k, 0.0), v)
+    by_n = {int(n): int(sum(p.T for p in probs if p.n == n)) for n in (4, 8, 16)}
+    return {"workload": "%d problems, n in {4,8,16} uniform, m=n/2, T uniform in [64,4096], "
+                        "time-varying F_k (I+0.05N(0,1), spectral radius <= 1.05), L_k~N(0,1/n), "
+                        "X_k=diag(U[0.5,2]), U=0.1I, r_k~N(0,1), H=I; FP32, no refinement"
+                        % len(probs),
+            "time_steps": int(steps), "steps_by_n": by_n,
+            "value": steps / (med * 1e-3), "unit": UNIT, "ms_p50": med,
+            "ms_p99": percentile(times, 99), "status": int(st),
+            "max_error_vs_fp64_oracle_sampled": errs, "launches": 3,
+            "generation_s": gen_s}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
@@ -433,6 +510,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-sweep", action="store_true", help="skip the T sweep")
+    ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
+    ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling mode: run --warmup + this many solves of --T and exit "
                          "(no JSON line; for ncu captures)")

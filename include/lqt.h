@@ -159,6 +159,30 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
                           const lqt_options *opts, void *device_buffer, size_t device_bytes,
                           void *stream);
 
+/* Ragged batch of independent problems (any mix of T and of the compiled
+ * batch sizes (n, m) in {(4,2), (8,4), (16,8)}; FP32; p <= 2n), solved by one
+ * persistent launch per (n, m) present.  Each problem runs the temporally
+ * parallel solve of lqt_solve (Sec. V-A, Method 1) inside one CTA: its steps
+ * are cut into chunks, one group of n lanes per chunk, and the chunk totals
+ * are swept in shared memory (Alg. 1).  CTAs take problems from a work queue.
+ *   items: HOST array of `count` descriptors; each holds device pointers to a
+ *          problem's inputs and outputs, with the layouts of lqt_problem and
+ *          lqt_solution.  The array may be reused when the call returns.
+ *   workspace: device buffer of at least lqt_batch_workspace_bytes(count)
+ *          bytes, 256-byte aligned; its first bytes hold the status word read
+ *          by lqt_workspace_status().
+ * No refinement is applied (problems whose controls cancel, see lqt_options,
+ * should use lqt_solve).  Asynchronous on `stream`; returns LQT_EINVAL,
+ * LQT_EUNSUPPORTED, LQT_ENOMEM or LQT_ECUDA on argument or launch errors. */
+typedef struct {
+    lqt_problem problem;
+    lqt_solution solution;
+} lqt_batch_item;
+
+size_t lqt_batch_workspace_bytes(int32_t count);
+lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
 /* Solve without any caller-provided workspace.
  *
  * There is no counterpart to this entry point in the paper.  It exists for

@@ -1,0 +1,176 @@
+// C ABI of the ragged batch (include/lqt.h: lqt_solve_batched): descriptor
+// packing, grouping by (n, m), one persistent launch per group.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lqt.h"
+#include "lqt_batch.cuh"
+
+namespace lqt {
+namespace {
+
+constexpr size_t kAlignB = 256;
+size_t up(size_t x) { return (x + kAlignB - 1) / kAlignB * kAlignB; }
+
+struct BatchVariant {
+    int n, m;
+    void (*launch)(const BatchDesc* d, int count, int* ticket, int* status, cudaStream_t s,
+                   cudaError_t* err);
+};
+
+template <int N, int M, int NG>
+void launch_batch(const BatchDesc* d, int count, int* ticket, int* status, cudaStream_t s,
+                  cudaError_t* err) {
+    using Lay = batch::Layout<N, M, NG>;
+    static bool attr[64];
+    int dev = 0;
+    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return;
+    const size_t smem = Lay::bytes();
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if ((*err = cudaFuncSetAttribute(batch::k_batch<N, M, NG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem)) != cudaSuccess)
+            return;
+        attr[dev] = true;
+    }
+    int sms = 0, per_sm = 0;
+    if ((*err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return;
+    if ((*err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch::k_batch<N, M, NG>,
+                                                              Lay::THREADS, smem)) != cudaSuccess)
+        return;
+    const int grid = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
+    batch::k_batch<N, M, NG><<<grid, Lay::THREADS, smem, s>>>(d, count, ticket, status);
+    *err = cudaGetLastError();
+}
+
+const BatchVariant kBatchVariants[] = {
+    {4, 2, &launch_batch<4, 2, 64>},
+    {8, 4, &launch_batch<8, 4, 32>},
+    {16, 8, &launch_batch<16, 8, 8>},
+};
+constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
+
+int batch_variant(int n, int m) {
+    for (int i = 0; i < kNumBatchVariants; ++i)
+        if (kBatchVariants[i].n == n && kBatchVariants[i].m == m) return i;
+    return -1;
+}
+
+bool is_aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+lqt_status check_item(const lqt_batch_item& it) {
+    const lqt_problem& P = it.problem;
+    const lqt_solution& S = it.solution;
+    if (P.dtype != LQT_F32) return LQT_EUNSUPPORTED;
+    if (P.T < 0 || P.p < 1 || P.pT < 0 || P.p > 2 * P.n) return LQT_EINVAL;
+    if (batch_variant(P.n, P.m) < 0) return LQT_EUNSUPPORTED;
+    if (P.T > 0 && (!P.F.ptr || !P.L.ptr || !P.U.ptr || !P.H.ptr || !P.X.ptr)) return LQT_EINVAL;
+    if (!P.x0 || (P.pT > 0 && (!P.HT || !P.XT))) return LQT_EINVAL;
+    if (!S.S || !S.v || !S.x || (P.T > 0 && (!S.K || !S.u))) return LQT_EINVAL;
+    const int64_t n = P.n, m = P.m, p = P.p;
+    const struct {
+        const lqt_in* in;
+        int64_t size;
+    } ins[] = {{&P.F, n * n}, {&P.c, n},     {&P.L, n * m}, {&P.U, m * m},
+               {&P.H, p * n}, {&P.r, p},     {&P.X, p * p}};
+    for (const auto& i : ins) {
+        if (!i.in->ptr) continue;
+        if (!is_aligned(i.in->ptr, 4)) return LQT_EINVAL;
+        if (i.in->step_stride < 0 || (i.in->step_stride != 0 && i.in->step_stride < i.size))
+            return LQT_EINVAL;
+    }
+    return LQT_OK;
+}
+
+BatchDesc to_desc(const lqt_batch_item& it) {
+    const lqt_problem& P = it.problem;
+    const lqt_solution& S = it.solution;
+    BatchDesc d;
+    memset(&d, 0, sizeof(d));
+    d.n = P.n;
+    d.m = P.m;
+    d.p = P.p;
+    d.pT = P.pT;
+    d.T = P.T;
+    d.F = static_cast<const float*>(P.F.ptr);
+    d.sF = P.F.step_stride;
+    d.c = static_cast<const float*>(P.c.ptr);
+    d.sc = P.c.step_stride;
+    d.L = static_cast<const float*>(P.L.ptr);
+    d.sL = P.L.step_stride;
+    d.U = static_cast<const float*>(P.U.ptr);
+    d.sU = P.U.step_stride;
+    d.H = static_cast<const float*>(P.H.ptr);
+    d.sH = P.H.step_stride;
+    d.r = static_cast<const float*>(P.r.ptr);
+    d.sr = P.r.step_stride;
+    d.X = static_cast<const float*>(P.X.ptr);
+    d.sX = P.X.step_stride;
+    d.HT = static_cast<const float*>(P.HT);
+    d.rT = static_cast<const float*>(P.rT);
+    d.XT = static_cast<const float*>(P.XT);
+    d.x0 = static_cast<const float*>(P.x0);
+    d.S = static_cast<float*>(S.S);
+    d.v = static_cast<float*>(S.v);
+    d.K = static_cast<float*>(S.K);
+    d.x = static_cast<float*>(S.x);
+    d.u = static_cast<float*>(S.u);
+    return d;
+}
+
+}  // namespace
+}  // namespace lqt
+
+using namespace lqt;
+
+extern "C" size_t lqt_batch_workspace_bytes(int32_t count) {
+    if (count < 0) return 0;
+    return up(256) + up(64 * sizeof(int)) + up((size_t)count * sizeof(BatchDesc));
+}
+
+extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t count,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
+    if (count < 0 || (count > 0 && !items)) return LQT_EINVAL;
+    if (!workspace || !is_aligned(workspace, kAlignB)) return LQT_EINVAL;
+    if (workspace_bytes < lqt_batch_workspace_bytes(count)) return LQT_ENOMEM;
+    for (int i = 0; i < count; ++i) {
+        const lqt_status st = check_item(items[i]);
+        if (st != LQT_OK) return st;
+    }
+    // descriptors grouped by (n, m)
+    std::vector<BatchDesc> descs;
+    descs.reserve(count);
+    int offset[kNumBatchVariants + 1] = {0};
+    for (int v = 0; v < kNumBatchVariants; ++v) {
+        offset[v] = (int)descs.size();
+        for (int i = 0; i < count; ++i)
+            if (batch_variant(items[i].problem.n, items[i].problem.m) == v)
+                descs.push_back(to_desc(items[i]));
+    }
+    offset[kNumBatchVariants] = (int)descs.size();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(workspace);
+    int* status = reinterpret_cast<int*>(base);
+    int* tickets = reinterpret_cast<int*>(base + up(256));
+    BatchDesc* d_desc = reinterpret_cast<BatchDesc*>(base + up(256) + up(64 * sizeof(int)));
+    if (cudaMemsetAsync(base, 0, up(256) + up(64 * sizeof(int)), s) != cudaSuccess)
+        return LQT_ECUDA;
+    if (count == 0) return LQT_OK;
+    // pageable source: the runtime stages the copy before the call returns
+    if (cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(BatchDesc),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return LQT_ECUDA;
+    for (int v = 0; v < kNumBatchVariants; ++v) {
+        const int c = offset[v + 1] - offset[v];
+        if (c == 0) continue;
+        cudaError_t err = cudaSuccess;
+        kBatchVariants[v].launch(d_desc + offset[v], c, tickets + v, status, s, &err);
+        if (err != cudaSuccess) return LQT_ECUDA;
+    }
+    return LQT_OK;
+}

@@ -1,0 +1,375 @@
+// Lane-group dense algebra for the LQT operators at larger state sizes.
+//
+// A group of LG = N lanes (N a power of two, N <= 32) owns one element; lane r
+// of the group owns row r of every N-row matrix, and the matrices live in
+// shared memory (row-major, leading dimension given).  Products are row
+// products: lane r reads its row of the left factor and the whole right
+// factor (broadcast reads).  Phases that read what other lanes wrote are
+// separated by a group sync.  The formulas are those of lqt_dense.cuh:
+// eq. lqt_comb for the operator, the Riccati step of Sec. II-B with the gains
+// of eq. Control_LQT, and the affine maps of Sec. IV-C.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lqt {
+namespace lanes {
+
+template <int LG>
+struct Group {
+    int lr;         // lane within the group = owned row
+    unsigned mask;  // lanes of the group within the warp
+    __device__ Group() {
+        const int lane = threadIdx.x & 31;
+        lr = lane % LG;
+        const int g = lane / LG;
+        mask = LG == 32 ? 0xffffffffu : (((1u << LG) - 1u) << (g * LG));
+    }
+    __device__ void sync() const { __syncwarp(mask); }
+};
+
+// out[lr][0..C) = X[lr][0..K) * Y (K x C), for rows lr < ROWS
+template <int ROWS, int K, int C>
+__device__ __forceinline__ void row_mul(float* out, int ldo, const float* X, int ldx,
+                                        const float* Y, int ldy, int lr) {
+    if (lr >= ROWS) return;
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float xk = X[lr * ldx + k];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] += xk * Y[k * ldy + c];
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[lr * ldo + c] = acc[c];
+}
+
+// out[lr][0..C) = X[0..K)[lr]^T-row, i.e. (X^T Y)[lr], X stored K x ROWS
+template <int ROWS, int K, int C>
+__device__ __forceinline__ void row_mul_tn(float* out, int ldo, const float* X, int ldx,
+                                           const float* Y, int ldy, int lr) {
+    if (lr >= ROWS) return;
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float xk = X[k * ldx + lr];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] += xk * Y[k * ldy + c];
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[lr * ldo + c] = acc[c];
+}
+
+// Gauss-Jordan elimination with partial pivoting on [Mx | Bx] (R x R, R x NR),
+// rows owned by lanes lr < R.  On return Bx holds Mx^{-1} Bx.  Returns false
+// for a zero or non-finite pivot (every lane returns the same value).
+template <int LG, int R, int NR>
+__device__ bool solve_gj(float* Mx, int ldm, float* Bx, int ldb, const Group<LG>& g,
+                         float* pivinfo /* 1 float per group */) {
+    bool ok = true;
+    const int lr = g.lr;
+    for (int k = 0; k < R; ++k) {
+        // every lane finds the pivot row redundantly
+        int piv = k;
+        float best = fabsf(Mx[k * ldm + k]);
+        for (int i = k + 1; i < R; ++i) {
+            const float a = fabsf(Mx[i * ldm + k]);
+            if (a > best) { best = a; piv = i; }
+        }
+        ok = ok && (best > 0.f) && isfinite(best);
+        g.sync();
+        if (piv != k) {
+            // swap rows k and piv, columns spread over the lanes
+            for (int j = lr; j < R + NR; j += LG) {
+                float* a = j < R ? &Mx[k * ldm + j] : &Bx[k * ldb + (j - R)];
+                float* b = j < R ? &Mx[piv * ldm + j] : &Bx[piv * ldb + (j - R)];
+                const float t = *a;
+                *a = *b;
+                *b = t;
+            }
+        }
+        g.sync();
+        const float inv = __frcp_rn(Mx[k * ldm + k]);
+        float f = 0.f;
+        if (lr < R && lr != k) f = Mx[lr * ldm + k] * inv;
+        g.sync();
+        if (lr < R && lr != k) {
+#pragma unroll 4
+            for (int j = k + 1; j < R; ++j) Mx[lr * ldm + j] -= f * Mx[k * ldm + j];
+#pragma unroll 4
+            for (int j = 0; j < NR; ++j) Bx[lr * ldb + j] -= f * Bx[k * ldb + j];
+        }
+        g.sync();
+    }
+    if (lr < R) {
+        const float inv = __frcp_rn(Mx[lr * ldm + lr]);
+#pragma unroll 4
+        for (int j = 0; j < NR; ++j) Bx[lr * ldb + j] *= inv;
+    }
+    g.sync();
+    (void)pivinfo;
+    return ok;
+}
+
+// Full element in shared memory: A[N][N], b[N], C[N][N], eta[N], J[N][N].
+template <int N>
+struct LElem {
+    static constexpr int OA = 0, OB = N * N, OC = N * N + N, OE = 2 * N * N + N,
+                         OJ = 2 * N * N + 2 * N, SIZE = 3 * N * N + 2 * N;
+};
+
+template <int N>
+struct LValue {  // S[N][N], v[N]
+    static constexpr int OS = 0, OV = N * N, SIZE = N * N + N;
+};
+
+template <int N>
+struct LAffine {  // F[N][N], c[N]
+    static constexpr int OF = 0, OC = N * N, SIZE = N * N + N;
+};
+
+// Scratch a group needs for combine (floats).
+template <int N>
+constexpr int combine_scratch() {
+    return N * N /*Mx*/ + N * (2 * N + 1) /*Bx*/ + N /*w*/ + N * N /*JX or T3*/ + LElem<N>::SIZE;
+}
+
+template <int LG, int N>
+__device__ void set_neutral(float* e, const Group<LG>& g) {
+    const int r = g.lr;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        e[LElem<N>::OA + r * N + j] = r == j ? 1.f : 0.f;
+        e[LElem<N>::OC + r * N + j] = 0.f;
+        e[LElem<N>::OJ + r * N + j] = 0.f;
+    }
+    e[LElem<N>::OB + r] = 0.f;
+    e[LElem<N>::OE + r] = 0.f;
+    g.sync();
+}
+
+// out = e1 (x) e2 (eq. lqt_comb).  out may alias e1 or e2.
+template <int LG, int N>
+__device__ bool combine(const float* e1, const float* e2, float* out, float* scr,
+                        const Group<LG>& g) {
+    using E = LElem<N>;
+    constexpr int NR = 2 * N + 1;
+    float* Mx = scr;
+    float* Bx = Mx + N * N;
+    float* w = Bx + N * NR;
+    float* T = w + N;
+    float* O = T + N * N;  // result staged here, copied to out at the end
+    const int r = g.lr;
+    // Mx = I + C1 J2 ; Bx = [A1 | b1 + C1 eta2 | C1]
+    {
+        float acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = r == j ? 1.f : 0.f;
+        float be = e1[E::OB + r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float ck = e1[E::OC + r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += ck * e2[E::OJ + k * N + j];
+            be += ck * e2[E::OE + k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Mx[r * N + j] = acc[j];
+            Bx[r * NR + j] = e1[E::OA + r * N + j];
+            Bx[r * NR + N + 1 + j] = e1[E::OC + r * N + j];
+        }
+        Bx[r * NR + N] = be;
+        // w = eta2 - J2 b1
+        float t = e2[E::OE + r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t -= e2[E::OJ + r * N + k] * e1[E::OB + k];
+        w[r] = t;
+    }
+    g.sync();
+    const bool ok = solve_gj<LG, N, NR>(Mx, N, Bx, NR, g, nullptr);
+    // eta = X1^T w + eta1 ; JX = J2 X1 (into T)
+    {
+        float t = e1[E::OE + r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t += Bx[k * NR + r] * w[k];
+        O[E::OE + r] = t;
+    }
+    row_mul<N, N, N>(T, N, e2 + E::OJ, N, Bx, NR, r);
+    g.sync();
+    // J = A1^T JX + J1
+    {
+        float acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = e1[E::OJ + r * N + j];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float a = e1[E::OA + k * N + r];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[E::OJ + r * N + j] = acc[j];
+    }
+    g.sync();
+    // A = A2 X1 ; b = A2 x2 + b2 ; T = A2 X3
+    {
+        float aa[N], tt[N];
+        float bb = e2[E::OB + r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) aa[j] = tt[j] = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float a2 = e2[E::OA + r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                aa[j] += a2 * Bx[k * NR + j];
+                tt[j] += a2 * Bx[k * NR + N + 1 + j];
+            }
+            bb += a2 * Bx[k * NR + N];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            O[E::OA + r * N + j] = aa[j];
+            T[r * N + j] = tt[j];
+        }
+        O[E::OB + r] = bb;
+    }
+    g.sync();
+    // C = T A2^T + C2
+    {
+        float acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = e2[E::OC + r * N + j];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float t = T[r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += t * e2[E::OA + j * N + k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[E::OC + r * N + j] = acc[j];
+    }
+    g.sync();
+    // symmetrise C and J while copying out
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        out[E::OA + r * N + j] = O[E::OA + r * N + j];
+        out[E::OC + r * N + j] = 0.5f * (O[E::OC + r * N + j] + O[E::OC + j * N + r]);
+        out[E::OJ + r * N + j] = 0.5f * (O[E::OJ + r * N + j] + O[E::OJ + j * N + r]);
+    }
+    out[E::OB + r] = O[E::OB + r];
+    out[E::OE + r] = O[E::OE + r];
+    g.sync();
+    return ok;
+}
+
+// value (S, v) <- P (x) (0, 0, 0, v, S)
+template <int LG, int N>
+__device__ bool value_apply(const float* P, float* val, float* scr, const Group<LG>& g) {
+    using E = LElem<N>;
+    using V = LValue<N>;
+    float* Mx = scr;
+    float* X = Mx + N * N;
+    float* T = X + N * N;
+    float* e = T + N * N;
+    float* O = e + N;
+    const int r = g.lr;
+    {
+        float acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = r == j ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float ck = P[E::OC + r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += ck * val[V::OS + k * N + j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Mx[r * N + j] = acc[j];
+            X[r * N + j] = P[E::OA + r * N + j];
+        }
+        float t = val[V::OV + r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t -= val[V::OS + r * N + k] * P[E::OB + k];
+        e[r] = t;
+    }
+    g.sync();
+    const bool ok = solve_gj<LG, N, N>(Mx, N, X, N, g, nullptr);
+    // T = S X1 ; v' = X1^T e + eta
+    row_mul<N, N, N>(T, N, val + V::OS, N, X, N, r);
+    {
+        float t = P[E::OE + r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t += X[k * N + r] * e[k];
+        O[V::OV + r] = t;
+    }
+    g.sync();
+    // S' = A^T T + J
+    {
+        float acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = P[E::OJ + r * N + j];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float a = P[E::OA + k * N + r];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[V::OS + r * N + j] = acc[j];
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        val[V::OS + r * N + j] = 0.5f * (O[V::OS + r * N + j] + O[V::OS + j * N + r]);
+    val[V::OV + r] = O[V::OV + r];
+    g.sync();
+    return ok;
+}
+
+// f2 after f1: (F2 F1, F2 c1 + c2) into out (may alias f1 or f2)
+template <int LG, int N>
+__device__ void affine_compose(const float* f1, const float* f2, float* out, float* scr,
+                               const Group<LG>& g) {
+    using A = LAffine<N>;
+    const int r = g.lr;
+    float acc[N];
+    float c = f2[A::OC + r];
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const float a = f2[A::OF + r * N + k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] += a * f1[A::OF + k * N + j];
+        c += a * f1[A::OC + k];
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j) out[A::OF + r * N + j] = acc[j];
+    out[A::OC + r] = c;
+    g.sync();
+    (void)scr;
+}
+
+// x <- F x + c for x in shared memory
+template <int LG, int N>
+__device__ void affine_apply(const float* f, float* x, const Group<LG>& g) {
+    using A = LAffine<N>;
+    const int r = g.lr;
+    float t = f[A::OC + r];
+#pragma unroll
+    for (int k = 0; k < N; ++k) t += f[A::OF + r * N + k] * x[k];
+    g.sync();
+    x[r] = t;
+    g.sync();
+}
+
+}  // namespace lanes
+}  // namespace lqt

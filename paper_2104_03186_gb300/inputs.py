@@ -159,11 +159,9 @@ def paper_tracking(T: int, seed: int = 0, dt: float = 0.1) -> LQTProblem:
 
 def _stable_dynamics(rng, n, count, radius=1.05, spread=0.05):
     F = np.eye(n)[None] + spread * rng.standard_normal((count, n, n))
-    for i in range(count):
-        rho = np.max(np.abs(np.linalg.eigvals(F[i])))
-        if rho > radius:
-            F[i] *= radius / rho
-    return F
+    rho = np.abs(np.linalg.eigvals(F)).max(axis=-1)
+    scale = np.where(rho > radius, radius / rho, 1.0)
+    return F * scale[:, None, None]
 
 
 def _psd(rng, p, count, rank=None):
@@ -225,3 +223,15 @@ def scalar_lqr(a: float, b: float, q: float, rho: float, T: int, s_terminal: flo
     return LQTProblem(F=a * one, c=None, L=b * one, U=rho * one, H=one.copy(), r=None,
                       X=q * one, HT=np.ones((1, 1)), rT=None, XT=np.full((1, 1), s_terminal),
                       x0=np.array([x0], dtype=np.float64), T=T)
+
+
+def ragged_batch(count: int = 4096, seed: int = 0, sizes=(4, 8, 16), t_min: int = 64,
+                 t_max: int = 4096):
+    """A ragged batch of `count` diagonal-tracking problems (see diag_tracking):
+    n uniform in `sizes`, m = n/2, T uniform in [t_min, t_max], problem i drawn
+    with seed (seed, i)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=count)
+    Ts = rng.integers(t_min, t_max + 1, size=count)
+    return [diag_tracking(int(n), T=int(T), seed=int(seed) * 1_000_003 + i)
+            for i, (n, T) in enumerate(zip(ns, Ts))]

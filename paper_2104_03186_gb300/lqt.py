@@ -40,6 +40,10 @@ class lqt_solution(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in OUTPUT_FIELDS]
 
 
+class lqt_batch_item(ctypes.Structure):
+    _fields_ = [("problem", lqt_problem), ("solution", lqt_solution)]
+
+
 LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO = 0, 1, 2
 
 
@@ -88,6 +92,8 @@ def _load() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
         "lqt_plan": (st, [P, O] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "lqt_solve_static": (st, [P, S, O, vp]),
+        "lqt_batch_workspace_bytes": (sz, [ctypes.c_int32]),
+        "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +245,39 @@ def lqt_solve_host(prob: Problem, out: Dict[str, object], device_buffer, stream=
     if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):
         raise LQTError(st, "lqt_solve_host")
     return int(st)
+
+
+def lqt_batch_workspace_bytes(count: int) -> int:
+    return int(_lib.lqt_batch_workspace_bytes(int(count)))
+
+
+def lqt_solve_batched(problems, outputs, workspace, stream=None) -> None:
+    """Solve a ragged batch: problems[i] (Problem, device tensors) into
+    outputs[i] (dict of device tensors).  Asynchronous; read the device status
+    with lqt_workspace_status(workspace)."""
+    count = len(problems)
+    arr = (lqt_batch_item * max(count, 1))()
+    for i, (P, out) in enumerate(zip(problems, outputs)):
+        arr[i].problem = P.struct
+        arr[i].solution = solution_struct(out)
+    st = _lib.lqt_solve_batched(arr, count, _ptr(workspace), _nbytes(workspace),
+                                _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_batched")
+
+
+def solve_batched(problems, stream=None, check: bool = True):
+    """Allocate outputs and a workspace with torch and run lqt_solve_batched."""
+    import torch
+
+    outs = [P.allocate_outputs() for P in problems]
+    ws = torch.empty(lqt_batch_workspace_bytes(len(problems)), dtype=torch.uint8, device="cuda")
+    lqt_solve_batched(problems, outs, ws, stream)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return outs
 
 
 LQT_STATIC_SCRATCH_BYTES = 32 << 20
