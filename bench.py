@@ -393,6 +393,9 @@ def run_ours(args):
     # ---- ragged batch: 4096 problems, one persistent launch per (n, m) ----
     batch = None if args.no_batch else run_batch(args, stream, flush)
 
+    # ---- serving: Poisson request streams through the continuous batcher ----
+    serving = None if args.no_serve else run_serving(args)
+
     clk.__exit__(None, None, None)
     clocks = clk.result()
 
@@ -419,6 +422,7 @@ def run_ours(args):
         "plan": plan,
         "sweep": sweep,
         "batch": batch,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -497,6 +501,31 @@ def run_batch(args, stream, flush):
             "generation_s": gen_s}
 
 
+def run_serving(args):
+    """20000-request Poisson streams at 2k..50k requests/s: n in {4,8,16,32},
+    m = n/2, T log-uniform in [32, 2048], 30% warm starts (receding horizon
+    from the previous request's device-resident state), admission by a device
+    memory budget of 8 GiB, up to 4 batches in flight."""
+    from paper_2104_03186_gb300 import serve
+
+    pool = serve.ModelPool((4, 8, 16, 32), steps=4096, seed=11)
+    warm = serve.make_requests(200, rate=20000.0, seed=99)
+    serve.Server(pool, memory_budget=8 << 30).run(warm)  # warm-up
+    out = []
+    for rate in (2000, 5000, 10000, 20000, 50000):
+        reqs = serve.make_requests(args.serve_requests, rate=float(rate), seed=rate)
+        _, summ = serve.Server(pool, memory_budget=8 << 30, streams=4).run(reqs)
+        summ["arrival_rate_per_s"] = rate
+        summ["time_steps_per_s"] = summ["time_steps"] / (args.serve_requests / rate) \
+            if summ["solves_per_s"] >= rate * 0.98 else None
+        out.append(summ)
+    return {"workload": "Poisson stream of %d LQT requests per rate; n in {4,8,16,32}, m=n/2, "
+                        "T log-uniform in [32,2048], time-varying device-resident models "
+                        "(diag tracking), fresh reference and x0 per request, 30%% warm starts "
+                        "with shifted horizon; 8 GiB admission budget; FP32" % args.serve_requests,
+            "rates": out}
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
 # (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
 # None when the kernel has changed since the counters were taken.
@@ -512,6 +541,8 @@ def main(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the T sweep")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling mode: run --warmup + this many solves of --T and exit "
                          "(no JSON line; for ncu captures)")

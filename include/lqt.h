@@ -160,7 +160,7 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
                           void *stream);
 
 /* Ragged batch of independent problems (any mix of T and of the compiled
- * batch sizes (n, m) in {(4,2), (8,4), (16,8)}; FP32; p <= 2n), solved by one
+ * batch sizes (n, m) in {(4,2), (8,4), (16,8), (32,16)}; FP32; p <= 2n), solved by one
  * persistent launch per (n, m) present.  Each problem runs the temporally
  * parallel solve of lqt_solve (Sec. V-A, Method 1) inside one CTA: its steps
  * are cut into chunks, one group of n lanes per chunk, and the chunk totals

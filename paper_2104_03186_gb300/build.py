@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 
 SOURCES = ["lqt_api.cu", "lqt_inst_f32_small.cu", "lqt_inst_f32_n4.cu", "lqt_inst_f64.cu",
-           "lqt_static.cu", "lqt_batch.cu"]
+           "lqt_static.cu", "lqt_batch.cu", "lqt_batch32.cu"]
 
 
 def nvcc() -> str:

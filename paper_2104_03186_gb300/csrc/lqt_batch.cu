@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "lqt.h"
-#include "lqt_batch.cuh"
+#include "lqt_batch_launch.cuh"
 
 namespace lqt {
 namespace {
@@ -22,36 +22,17 @@ struct BatchVariant {
                    cudaError_t* err);
 };
 
-template <int N, int M, int NG>
-void launch_batch(const BatchDesc* d, int count, int* ticket, int* status, cudaStream_t s,
-                  cudaError_t* err) {
-    using Lay = batch::Layout<N, M, NG>;
-    static bool attr[64];
-    int dev = 0;
-    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return;
-    const size_t smem = Lay::bytes();
-    if (dev >= 0 && dev < 64 && !attr[dev]) {
-        if ((*err = cudaFuncSetAttribute(batch::k_batch<N, M, NG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem)) != cudaSuccess)
-            return;
-        attr[dev] = true;
-    }
-    int sms = 0, per_sm = 0;
-    if ((*err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return;
-    if ((*err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch::k_batch<N, M, NG>,
-                                                              Lay::THREADS, smem)) != cudaSuccess)
-        return;
-    const int grid = std::max(1, std::min(count, sms * std::max(per_sm, 1)));
-    batch::k_batch<N, M, NG><<<grid, Lay::THREADS, smem, s>>>(d, count, ticket, status);
-    *err = cudaGetLastError();
-}
+}  // namespace
+// n = 32 is compiled in its own translation unit (lqt_batch32.cu)
+extern template void launch_batch<32, 16, 2>(const BatchDesc*, int, int*, int*, cudaStream_t,
+                                             cudaError_t*);
+namespace {
 
 const BatchVariant kBatchVariants[] = {
     {4, 2, &launch_batch<4, 2, 64>},
     {8, 4, &launch_batch<8, 4, 32>},
     {16, 8, &launch_batch<16, 8, 8>},
+    {32, 16, &launch_batch<32, 16, 2>},
 };
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
