@@ -396,6 +396,9 @@ def run_ours(args):
     # ---- serving: Poisson request streams through the continuous batcher ----
     serving = None if args.no_serve else run_serving(args)
 
+    # ---- precision study (n = 32) -------------------------------------------
+    precision = None if args.no_precision else run_precision(args, stream, flush)
+
     clk.__exit__(None, None, None)
     clocks = clk.result()
 
@@ -423,6 +426,7 @@ def run_ours(args):
         "sweep": sweep,
         "batch": batch,
         "serving": serving,
+        "precision_study": precision,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -526,6 +530,78 @@ def run_serving(args):
             "rates": out}
 
 
+def chain_flops_per_step(n: int, m: int, p: int) -> dict:
+    """Algorithmic flops per time step of the chunked lane-group pipeline,
+    counted from its arithmetic (multiply-add = 2 flops): the step model
+    (X H, H^T X H, H^T X r), the low-rank fold of the step into the chunk total
+    (fold_step), the Riccati step with gains and the chunk map (re-fold), and
+    the rollout."""
+    nr = 2 * n + 1
+    model = 2 * (p * p * n + p * n * n + p * p + p * n)
+    fold = 2 * (2 * n * n * n + 2 * n * n * m + 2 * n * n          # J2 F, J2 L, w; A2 F, A2 L, A2 c
+                + m * n * m + m * n * n + m * n + n * n * n      # G, Z, L^T w; F^T J2 F
+                + m * m * (m + nr)                               # Gauss-Jordan on [G | rhs]
+                + n * m * n + n * m + n * m * n + m * n * n + m * n + n * n)  # A, b, C, J, eta
+    riccati = 2 * (n * n * m + n * n * n + n * n + m * n * m + m * n * n + m * n
+                   + m * m * (m + n + 1) + 2 * n * m * n + n * m + n * n * n + n * n)
+    chunk_map = 2 * (n * n * n + n * n)
+    roll = 2 * (m * n + n * n + n * m)
+    return {"model": 2 * model, "fold": fold, "riccati": riccati, "chunk_map": chunk_map,
+            "rollout": roll, "total": 2 * model + fold + riccati + chunk_map + roll}
+
+
+def run_precision(args, stream, flush):
+    """Precision study (n = 32, m = 16, p = 32, cond(X_k) = 1e6, U = 1e-3 I,
+    F_k = 0.99 Haar + rank-2): errors of S, v, K, x*, u* against the FP64
+    oracle for the plain FP32 scan, FP32 with FP64 tree levels and one
+    refinement pass, the FP64 scan and the sequential Riccati recursion on the
+    GPU, with their device times.  All forms solve the same FP32-representable
+    inputs."""
+    import oracle
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    T = args.precision_T
+    t0 = time.perf_counter()
+    prob = inputs.precision_study(T=T, seed=0).rounded_to(np.float32)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref = oracle.riccati(prob, keep_kv_kc=False)
+    oracle_s = time.perf_counter() - t0
+    forms = [("fp32_scan", np.float32, 0, False), ("fp32_fp64tree_refined", np.float32, 1, False),
+             ("fp64_scan", np.float64, 0, False), ("fp32_sequential_riccati", np.float32, 0, True),
+             ("fp32_sequential_riccati_refined", np.float32, 1, True)]
+    flops = chain_flops_per_step(prob.n, prob.m, prob.p)
+    out = {}
+    for name, dt, refine, seq in forms:
+        P = lqt.Problem.from_inputs(prob, dtype=dt)
+        o = P.allocate_outputs()
+        ws = lqt.workspace_for(P, opts=refine)
+        call = (lambda: lqt.lqt_riccati_sequential(P, o, ws, stream, refine)) if seq else \
+            (lambda: lqt.lqt_solve(P, o, ws, stream, refine))
+        call()
+        st = lqt.lqt_workspace_status(ws, stream)
+        reps = 1 if seq else 5
+        times = _time_solves(call, reps, flush, stream)
+        got = {k: v.double().cpu().numpy() for k, v in o.items()}
+        errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                for k in ("S", "v", "K", "x", "u")}
+        med = float(np.median(times))
+        e = {"status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3),
+             "error_vs_fp64_oracle": errs, "plan": lqt.lqt_plan(P, refine) if not seq else None}
+        if not seq and not refine:
+            e["achieved_tflops"] = flops["total"] * T / (med * 1e-3) / 1e12
+        out[name] = e
+        del o, ws, P
+    par = out["fp32_fp64tree_refined"]["ms"]
+    for k in ("fp32_sequential_riccati", "fp32_sequential_riccati_refined"):
+        out[k]["speedup_of_refined_scan"] = out[k]["ms"] / par
+    return {"workload": "precision study: n=32, m=16, p=32, T=%d; F_k=0.99 Haar + 0.01 rank-2, "
+                        "X_k=V diag(10^U[-6,0]) V^T with cond 1e6, L_k~N(0,1/n), U=1e-3 I, "
+                        "H=I, c=0, r_k~N(0,1); inputs rounded to FP32" % T,
+            "forms": out, "flops_per_step": flops, "generation_s": gen_s,
+            "oracle_s": oracle_s}
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
 # (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
 # None when the kernel has changed since the counters were taken.
@@ -543,6 +619,8 @@ def main(argv=None):
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--no-precision", action="store_true", help="skip the n = 32 precision study")
+    ap.add_argument("--precision-T", type=int, default=65536)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling mode: run --warmup + this many solves of --T and exit "
                          "(no JSON line; for ncu captures)")

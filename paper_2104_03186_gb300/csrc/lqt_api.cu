@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "lqt.h"
+#include "lqt_chain_api.h"
 #include "lqt_kernels.cuh"
 #include "lqt_launch.cuh"
 #include "lqt_refine.cuh"
@@ -305,7 +306,19 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
     bool refine = false;
     if ((st = resolve_refine(prob, opts, &refine)) != LQT_OK) return st;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (!var) return LQT_EUNSUPPORTED;
+    if (!var) {
+        if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
+        int NC = 0, nk = 0;
+        long long B = 0;
+        if ((st = chain_workspace(prob, refine, false, nullptr, &NC, &B, &nk)) != LQT_OK)
+            return st;
+        if (B > INT32_MAX) return LQT_EINVAL;
+        if (chunk_steps) *chunk_steps = (int32_t)B;
+        if (tile_threads_out) *tile_threads_out = prob->n;
+        if (tiles) *tiles = NC;
+        if (kernels) *kernels = nk;
+        return LQT_OK;
+    }
     Plan plan;
     if ((st = make_plan(prob, *var, &plan)) != LQT_OK) return st;
     if (chunk_steps) *chunk_steps = plan.B;
@@ -321,7 +334,13 @@ size_t lqt_workspace_bytes(const lqt_problem* prob, const lqt_options* opts) {
     bool refine = false;
     if (resolve_refine(prob, opts, &refine) != LQT_OK) return 0;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (!var) return 0;
+    if (!var) {
+        size_t bytes = 0;
+        if (!chain_supported(prob->dtype, prob->n, prob->m) ||
+            chain_workspace(prob, refine, false, &bytes, nullptr, nullptr, nullptr) != LQT_OK)
+            return 0;
+        return bytes;
+    }
     Plan plan;
     if (make_plan(prob, *var, &plan) != LQT_OK) return 0;
     return layout(*var, plan, elem_bytes(prob->dtype), prob, refine).total;
@@ -388,7 +407,20 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     if ((st = resolve_refine(prob, opts, &refine)) != LQT_OK) return st;
     if (sequential && prob->p > 64) return LQT_EUNSUPPORTED;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (!var) return LQT_EUNSUPPORTED;
+    if (!var) {
+        // lane-group sizes: the chunked pipeline (one chunk when sequential)
+        if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
+        size_t need = 0;
+        if ((st = chain_workspace(prob, refine, sequential, &need, nullptr, nullptr, nullptr)) !=
+            LQT_OK)
+            return st;
+        if (workspace_bytes < need) return LQT_ENOMEM;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (cudaMemsetAsync(workspace, 0, sizeof(int), s) != cudaSuccess) return LQT_ECUDA;
+        Prof* prof = nullptr;
+        if ((st = prof_begin(&prof)) != LQT_OK) return st;
+        return chain_solve(prob, sol, refine, sequential, workspace, workspace_bytes, s, prof);
+    }
     Plan plan;
     if ((st = make_plan(prob, *var, &plan)) != LQT_OK) return st;
     const Layout L = layout(*var, plan, elem_bytes(prob->dtype), prob, refine);
@@ -473,7 +505,10 @@ lqt_status lqt_solve_host(const lqt_problem* hp, const lqt_solution* hs, const l
     if (st != LQT_OK) return st;
     if (!device_buffer || !aligned(device_buffer, kAlign)) return LQT_EINVAL;
     const size_t need = lqt_host_solve_bytes(hp, opts);
-    if (need == 0) return find_variant(hp->dtype, hp->n, hp->m) ? LQT_EINVAL : LQT_EUNSUPPORTED;
+    if (need == 0)
+        return find_variant(hp->dtype, hp->n, hp->m) || chain_supported(hp->dtype, hp->n, hp->m)
+                   ? LQT_EINVAL
+                   : LQT_EUNSUPPORTED;
     if (device_bytes < need) return LQT_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t es = elem_bytes(hp->dtype);

@@ -5,7 +5,7 @@
 // are cut into NG chunks, one lane group of N lanes per chunk (lane r owns
 // row r; lanes.cuh).  Per problem:
 //   1. chunk folds P <- a_k (x) P with the elements of eq. lqt_init and the
-//      operator of eq. lqt_comb,
+//      operator of eq. lqt_comb in its low-rank single-step form (fold_step),
 //   2. an up-sweep of the NG chunk totals (Alg. 1) in shared memory,
 //   3. the terminal value (Lemma LQT_assoc) and a down-sweep of value
 //      carries,
@@ -19,19 +19,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "lqt_lanes.cuh"
+#include "lqt_lane_step.cuh"
 
 namespace lqt {
-
-// One problem of a batch, as the kernel sees it (FP32, device pointers).
-struct BatchDesc {
-    int n, m, p, pT;
-    long long T;
-    const float *F, *c, *L, *U, *H, *r, *X;
-    long long sF, sc, sL, sU, sH, sr, sX;
-    const float *HT, *rT, *XT, *x0;
-    float *S, *v, *K, *x, *u;
-};
 
 namespace batch {
 
@@ -39,17 +29,18 @@ using namespace lanes;
 
 template <int N, int M, int NG>
 struct Layout {
+    using SL = StepLayout<N, M>;
     static constexpr int LG = N;
     static constexpr int THREADS = NG * LG;
-    static constexpr int PMAX = 2 * N;  // largest p (rows of H) this path takes
-    // per-group scratch: the step element, L, U, cost helper Y = X H, and the
+    // per-group buffer: the step (element-shaped, with L, U and X H), then the
     // operator scratch
     static constexpr int G_STEP = 0;
-    static constexpr int G_L = LElem<N>::SIZE;
-    static constexpr int G_U = G_L + N * M;
-    static constexpr int G_Y = G_U + M * M;
-    static constexpr int G_SCR = G_Y + PMAX * N + PMAX;
-    static constexpr int G_SIZE = G_SCR + combine_scratch<N>();
+    static constexpr int G_SCR = SL::SIZE;
+    static constexpr int SCR = combine_scratch<N>() > riccati_scratch<N, M>() + M * (N + 1) +
+                                                           LAffine<N>::SIZE
+                                   ? combine_scratch<N>()
+                                   : riccati_scratch<N, M>() + M * (N + 1) + LAffine<N>::SIZE;
+    static constexpr int G_SIZE = G_SCR + SCR;
     // CTA: tree of chunk totals, value carries, affine maps, chunk start states
     static constexpr int TREE = 0;
     static constexpr int CARRY = TREE + NG * LElem<N>::SIZE;
@@ -59,198 +50,8 @@ struct Layout {
     static constexpr int TICKET = GROUPS + NG * G_SIZE;  // 1 int
     static constexpr int TOTAL = TICKET + 4;
     static size_t bytes() { return (size_t)TOTAL * sizeof(float); }
+    static_assert(fold_scratch<N, M>() <= SCR, "fold scratch");
 };
-
-// Step k of problem D into the group's step element (A = F, b = c,
-// C = L U^{-1} L^T, eta = H^T X r, J = H^T X H) plus L and U.
-template <int N, int M, int NG>
-__device__ void load_step(const BatchDesc& D, long long k, float* gs, const Group<N>& g, bool& ok) {
-    using Lay = Layout<N, M, NG>;
-    using E = LElem<N>;
-    float* e = gs + Lay::G_STEP;
-    float* L = gs + Lay::G_L;
-    float* U = gs + Lay::G_U;
-    float* Y = gs + Lay::G_Y;        // p x N: X H
-    float* xr = Y + Lay::PMAX * N;   // p: X r
-    float* scr = gs + Lay::G_SCR;
-    const int r = g.lr;
-    const int p = D.p;
-    const float* F = D.F + k * D.sF;
-    const float* Lk = D.L + k * D.sL;
-    const float* Uk = D.U + k * D.sU;
-    const float* H = D.H + k * D.sH;
-    const float* X = D.X + k * D.sX;
-    const float* rk = D.r ? D.r + k * D.sr : nullptr;
-#pragma unroll
-    for (int j = 0; j < N; ++j) e[E::OA + r * N + j] = __ldg(F + r * N + j);
-#pragma unroll
-    for (int a = 0; a < M; ++a) L[r * M + a] = __ldg(Lk + r * M + a);
-    if (r < M) {
-#pragma unroll
-        for (int b = 0; b < M; ++b) U[r * M + b] = __ldg(Uk + r * M + b);
-    }
-    e[E::OB + r] = D.c ? __ldg(D.c + k * D.sc + r) : 0.f;
-    // Y = X H and X r, rows spread over the lanes
-    for (int a = r; a < p; a += N) {
-        float acc[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = 0.f;
-        float t = 0.f;
-        for (int b = 0; b < p; ++b) {
-            const float xab = __ldg(X + a * p + b);
-#pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += xab * __ldg(H + b * N + j);
-            if (rk) t += xab * __ldg(rk + b);
-        }
-#pragma unroll
-        for (int j = 0; j < N; ++j) Y[a * N + j] = acc[j];
-        xr[a] = t;
-    }
-    g.sync();
-    // J = H^T Y, eta = H^T (X r)
-    {
-        float acc[N];
-        float t = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = 0.f;
-        for (int a = 0; a < p; ++a) {
-            const float h = __ldg(H + a * N + r);
-#pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += h * Y[a * N + j];
-            t += h * xr[a];
-        }
-#pragma unroll
-        for (int j = 0; j < N; ++j) e[E::OJ + r * N + j] = acc[j];
-        e[E::OE + r] = t;
-    }
-    // C = L U^{-1} L^T: solve U Z = L^T (M x M, N right-hand sides)
-    float* Um = scr;
-    float* Z = Um + M * M;
-    if (r < M) {
-#pragma unroll
-        for (int b = 0; b < M; ++b) Um[r * M + b] = U[r * M + b];
-#pragma unroll
-        for (int j = 0; j < N; ++j) Z[r * N + j] = L[j * M + r];
-    }
-    g.sync();
-    ok &= solve_gj<N, M, N>(Um, M, Z, N, g, nullptr);
-    row_mul<N, M, N>(e + E::OC, N, L, M, Z, N, r);
-    g.sync();
-}
-
-// One Riccati step on the value (S, v) of the group (Sec. II-B), writing the
-// gains into Kd ([K | d], M x (N + 1)) and the closed loop into Ft (F - L K,
-// c + L d).  Uses the step element's F (A part), c (b part), Q (J part) and
-// q (eta part), and L, U.
-template <int N, int M, int NG>
-__device__ bool riccati(float* val, const float* gs, float* Kd, float* Ft, float* scr,
-                        const Group<N>& g) {
-    using Lay = Layout<N, M, NG>;
-    using E = LElem<N>;
-    using V = LValue<N>;
-    const float* e = gs + Lay::G_STEP;
-    const float* F = e + E::OA;
-    const float* c = e + E::OB;
-    const float* Q = e + E::OJ;
-    const float* q = e + E::OE;
-    const float* L = gs + Lay::G_L;
-    const float* U = gs + Lay::G_U;
-    const float* S = val + V::OS;
-    const float* v = val + V::OV;
-    float* SL = scr;            // N x M
-    float* SF = SL + N * M;     // N x N  (later S Ft)
-    float* G = SF + N * N;      // M x M
-    float* ev = G + M * M;      // N
-    float* O = ev + N;          // N x N + N
-    const int r = g.lr;
-    row_mul<N, N, M>(SL, M, S, N, L, M, r);
-    row_mul<N, N, N>(SF, N, S, N, F, N, r);
-    {
-        float t = v[r];
-#pragma unroll
-        for (int k = 0; k < N; ++k) t -= S[r * N + k] * c[k];
-        ev[r] = t;
-    }
-    g.sync();
-    if (r < M) {
-        // G = U + L^T S L ; [L^T S F | L^T (v - S c)]
-        float gg[M], pp[N];
-        float w = 0.f;
-#pragma unroll
-        for (int b = 0; b < M; ++b) gg[b] = U[r * M + b];
-#pragma unroll
-        for (int j = 0; j < N; ++j) pp[j] = 0.f;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const float lk = L[k * M + r];
-            const float sk = SL[k * M + r];
-#pragma unroll
-            for (int b = 0; b < M; ++b) gg[b] += lk * SL[k * M + b];
-#pragma unroll
-            for (int j = 0; j < N; ++j) pp[j] += sk * F[k * N + j];
-            w += lk * ev[k];
-        }
-#pragma unroll
-        for (int b = 0; b < M; ++b) G[r * M + b] = gg[b];
-#pragma unroll
-        for (int j = 0; j < N; ++j) Kd[r * (N + 1) + j] = pp[j];
-        Kd[r * (N + 1) + N] = w;
-    }
-    g.sync();
-    const bool ok = solve_gj<N, M, N + 1>(G, M, Kd, N + 1, g, nullptr);
-    // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
-    {
-        float ft[N], sft[N];
-        float ct = c[r];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            ft[j] = F[r * N + j];
-            sft[j] = SF[r * N + j];
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-            const float la = L[r * M + a];
-            const float sa = SL[r * M + a];
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                ft[j] -= la * Kd[a * (N + 1) + j];
-                sft[j] -= sa * Kd[a * (N + 1) + j];
-            }
-            ct += la * Kd[a * (N + 1) + N];
-        }
-        g.sync();
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            Ft[LAffine<N>::OF + r * N + j] = ft[j];
-            SF[r * N + j] = sft[j];
-        }
-        Ft[LAffine<N>::OC + r] = ct;
-    }
-    g.sync();
-    // S <- F^T (S Ft) + Q ; v <- Ft^T (v - S c) + q
-    {
-        float acc[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = Q[r * N + j];
-        float t = q[r];
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const float fk = F[k * N + r];
-#pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * N + j];
-            t += Ft[LAffine<N>::OF + k * N + r] * ev[k];
-        }
-#pragma unroll
-        for (int j = 0; j < N; ++j) O[r * N + j] = acc[j];
-        O[N * N + r] = t;
-    }
-    g.sync();
-#pragma unroll
-    for (int j = 0; j < N; ++j) val[V::OS + r * N + j] = 0.5f * (O[r * N + j] + O[j * N + r]);
-    val[V::OV + r] = O[N * N + r];
-    g.sync();
-    return ok;
-}
 
 template <int N, int M, int NG>
 __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ items, int count,
@@ -291,8 +92,8 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
         float* P = tree + gi * E::SIZE;
         set_neutral<N, N>(P, g);
         for (long long k = e - 1; k >= s; --k) {
-            load_step<N, M, NG>(D, k, gs, g, ok);
-            ok &= combine<N, N>(gs + Lay::G_STEP, P, P, scr, g);
+            load_step<float, N, M, false>(D, k, gs, scr, g, ok);
+            ok &= fold_step<float, N, M>(P, gs + Lay::G_STEP, scr, g);
         }
         __syncthreads();
         // 2. up-sweep (left-anchored)
@@ -346,11 +147,11 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
         for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = r == j ? 1.f : 0.f;
         Phi[A::OC + r] = 0.f;
         g.sync();
-        float* Kd = scr + 2 * N * N + 2 * N * M + 2 * M * M + 4 * N;  // beyond riccati's scratch
+        float* Kd = scr + riccati_scratch<N, M>();
         float* Ft = Kd + M * (N + 1);
         for (long long k = e - 1; k >= s; --k) {
-            load_step<N, M, NG>(D, k, gs, g, ok);
-            ok &= riccati<N, M, NG>(val, gs, Kd, Ft, scr, g);
+            load_step<float, N, M, false>(D, k, gs, scr, g, ok);
+            ok &= riccati<float, N, M>(val, gs, Kd, Ft, scr, g);
 #pragma unroll
             for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * N + j];
             D.v[k * N + r] = val[V::OV + r];

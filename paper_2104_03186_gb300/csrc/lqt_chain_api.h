@@ -1,0 +1,84 @@
+// Internal interface between the C ABI (lqt_api.cu, lqt_chain.cu) and the
+// compiled variants of the chunked single-problem pipeline (lqt_chain.cuh).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lqt.h"
+#include "lqt_lane_step.cuh"
+#include "lqt_launch.cuh"
+
+namespace lqt {
+
+// One solve as the launcher sees it: the problem, its outputs and the
+// workspace regions, all device pointers.
+struct ChainCall {
+    const lqt_problem* problem;
+    const lqt_solution* solution;
+    int NC;       // chunks (power of two)
+    long long B;  // steps per chunk
+    bool refine, sequential;
+    int* status;
+    void *E, *V, *FE, *X;          // tree elements, carries, affine maps, start states (RT)
+    void *rp, *cp, *rTp, *x0p;     // shifted data of the refinement pass (R)
+};
+
+struct ChainVariant {
+    int dtype, n, m;
+    int mixed;         // FP32 chunk work with FP64 tree levels
+    int rsize, rtsize; // bytes of R and RT
+    lqt_status (*run)(const ChainCall& call, cudaStream_t s, Prof* prof);
+    const void* (*fold_kernel)();
+    size_t (*fold_smem)();
+    int (*fold_groups)();
+};
+
+// Variants compiled in lqt_chain_n8.cu, lqt_chain_n16.cu and lqt_chain_n32.cu.
+const ChainVariant* chain_variants_n8(int* count);
+const ChainVariant* chain_variants_n16(int* count);
+const ChainVariant* chain_variants_n32(int* count);
+
+template <typename R>
+DescT<R> make_desc(const lqt_problem* P, const lqt_solution* S) {
+    DescT<R> d;
+    d.n = P->n;
+    d.m = P->m;
+    d.p = P->p;
+    d.pT = P->pT;
+    d.T = P->T;
+    d.F = static_cast<const R*>(P->F.ptr);
+    d.sF = P->F.step_stride;
+    d.c = static_cast<const R*>(P->c.ptr);
+    d.sc = P->c.step_stride;
+    d.L = static_cast<const R*>(P->L.ptr);
+    d.sL = P->L.step_stride;
+    d.U = static_cast<const R*>(P->U.ptr);
+    d.sU = P->U.step_stride;
+    d.H = static_cast<const R*>(P->H.ptr);
+    d.sH = P->H.step_stride;
+    d.r = static_cast<const R*>(P->r.ptr);
+    d.sr = P->r.step_stride;
+    d.X = static_cast<const R*>(P->X.ptr);
+    d.sX = P->X.step_stride;
+    d.HT = static_cast<const R*>(P->HT);
+    d.rT = static_cast<const R*>(P->rT);
+    d.XT = static_cast<const R*>(P->XT);
+    d.x0 = static_cast<const R*>(P->x0);
+    d.S = static_cast<R*>(S->S);
+    d.v = static_cast<R*>(S->v);
+    d.K = static_cast<R*>(S->K);
+    d.x = static_cast<R*>(S->x);
+    d.u = static_cast<R*>(S->u);
+    return d;
+}
+
+// Chain path entry points used by the C ABI (lqt_chain.cu).
+bool chain_supported(int dtype, int n, int m);
+lqt_status chain_workspace(const lqt_problem* P, bool refine, bool sequential, size_t* bytes,
+                           int* NC, long long* B, int* kernels);
+lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine,
+                       bool sequential, void* ws, size_t ws_bytes, cudaStream_t s, Prof* prof);
+
+}  // namespace lqt

@@ -1,0 +1,443 @@
+// Per-step lane-group routines shared by the batched kernel (lqt_batch.cuh)
+// and the chunked single-problem pipeline (lqt_chain.cuh), in the arithmetic
+// type R:
+//   * load_step: the model of step k in shared memory, with the element terms
+//     of eq. lqt_init (A = F_k, b = c_k, eta = H^T X r, J = H^T X H and, when
+//     asked for, C = L U^{-1} L^T),
+//   * riccati:   one step of the Riccati recursion of Sec. II-B with the gains
+//     of eq. Control_LQT,
+//   * fold_step: P <- a_k (x) P, eq. lqt_comb with a step element as the left
+//     operand, in its low-rank form (C_k = L U^{-1} L^T has rank m, so the
+//     n x n solve with I + C_k J_P reduces to one m x m solve with
+//     G = U + L^T J_P L by the Woodbury identity).
+// Lane r of the group (N lanes) owns row r of every N-row matrix.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lqt_lanes.cuh"
+
+namespace lqt {
+
+// One problem as the lane kernels see it (device pointers of type R).
+template <typename R>
+struct DescT {
+    int n, m, p, pT;
+    long long T;
+    const R *F, *c, *L, *U, *H, *r, *X;
+    long long sF, sc, sL, sU, sH, sr, sX;
+    const R *HT, *rT, *XT, *x0;
+    R *S, *v, *K, *x, *u;
+};
+using BatchDesc = DescT<float>;
+
+namespace lanes {
+
+// Group buffer of one step's model: an element-shaped block E (A = F_k,
+// b = c_k, C, eta, J), then L_k, U_k and the scratch Y = X H, X r.
+template <int N, int M>
+struct StepLayout {
+    static constexpr int PMAX = 2 * N;  // largest p (rows of H) the lane path takes
+    static constexpr int E = 0;
+    static constexpr int L = LElem<N>::SIZE;
+    static constexpr int U = L + N * M;
+    static constexpr int Y = U + M * M;
+    static constexpr int SIZE = Y + PMAX * N + PMAX;
+};
+
+// Scratch of load_step with the C term (M x M copy of U and M x N right sides).
+template <int N, int M>
+constexpr int load_scratch() {
+    return M * M + M * N;
+}
+
+// Step k of D into the step buffer sb.  WITH_C also forms C = L U^{-1} L^T
+// (the general combine needs it; fold_step and riccati do not).
+template <typename R, int N, int M, bool WITH_C>
+__device__ void load_step(const DescT<R>& D, long long k, R* sb, R* scr, const Group<N>& g,
+                          bool& ok) {
+    using SL = StepLayout<N, M>;
+    using E = LElem<N>;
+    R* e = sb + SL::E;
+    R* L = sb + SL::L;
+    R* U = sb + SL::U;
+    R* Y = sb + SL::Y;        // p x N: X H
+    R* xr = Y + SL::PMAX * N;  // p: X r
+    const int r = g.lr;
+    const int p = D.p;
+    const R* F = D.F + k * D.sF;
+    const R* Lk = D.L + k * D.sL;
+    const R* Uk = D.U + k * D.sU;
+    const R* H = D.H + k * D.sH;
+    const R* X = D.X + k * D.sX;
+    const R* rk = D.r ? D.r + k * D.sr : nullptr;
+#pragma unroll
+    for (int j = 0; j < N; ++j) e[E::OA + r * N + j] = __ldg(F + r * N + j);
+#pragma unroll
+    for (int a = 0; a < M; ++a) L[r * M + a] = __ldg(Lk + r * M + a);
+    if (r < M) {
+#pragma unroll
+        for (int b = 0; b < M; ++b) U[r * M + b] = __ldg(Uk + r * M + b);
+    }
+    e[E::OB + r] = D.c ? __ldg(D.c + k * D.sc + r) : R(0);
+    // Y = X H and X r, rows spread over the lanes
+    for (int a = r; a < p; a += N) {
+        R acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = R(0);
+        R t = R(0);
+        for (int b = 0; b < p; ++b) {
+            const R xab = __ldg(X + a * p + b);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += xab * __ldg(H + b * N + j);
+            if (rk) t += xab * __ldg(rk + b);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) Y[a * N + j] = acc[j];
+        xr[a] = t;
+    }
+    g.sync();
+    // J = H^T Y, eta = H^T (X r)
+    {
+        R acc[N];
+        R t = R(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = R(0);
+        for (int a = 0; a < p; ++a) {
+            const R h = __ldg(H + a * N + r);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += h * Y[a * N + j];
+            t += h * xr[a];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) e[E::OJ + r * N + j] = acc[j];
+        e[E::OE + r] = t;
+    }
+    if (WITH_C) {
+        // C = L U^{-1} L^T: solve U Z = L^T (M x M, N right-hand sides)
+        R* Um = scr;
+        R* Z = Um + M * M;
+        if (r < M) {
+#pragma unroll
+            for (int b = 0; b < M; ++b) Um[r * M + b] = U[r * M + b];
+#pragma unroll
+            for (int j = 0; j < N; ++j) Z[r * N + j] = L[j * M + r];
+        }
+        g.sync();
+        ok &= solve_gj<N, M, N>(Um, M, Z, N, g);
+        row_mul<N, M, N>(e + E::OC, N, L, M, Z, N, r);
+    }
+    g.sync();
+}
+
+// Scratch of riccati (elements of R), excluding the caller's Kd and Ft.
+template <int N, int M>
+constexpr int riccati_scratch() {
+    return N * M + N * N + M * M + N + N * N + N;
+}
+
+// One Riccati step on the value (S, v) in val (Sec. II-B): writes the gains
+// into Kd ([K | d], M x (N + 1), with u = d - K x) and the closed loop into Ft
+// (LAffine: F - L K, c + L d), and replaces val by (S_k, v_k).
+template <typename R, int N, int M>
+__device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N>& g) {
+    using SLay = StepLayout<N, M>;
+    using E = LElem<N>;
+    using V = LValue<N>;
+    const R* e = sb + SLay::E;
+    const R* F = e + E::OA;
+    const R* c = e + E::OB;
+    const R* Q = e + E::OJ;
+    const R* q = e + E::OE;
+    const R* L = sb + SLay::L;
+    const R* U = sb + SLay::U;
+    const R* S = val + V::OS;
+    const R* v = val + V::OV;
+    R* SL = scr;            // N x M
+    R* SF = SL + N * M;     // N x N  (later S Ft)
+    R* G = SF + N * N;      // M x M
+    R* ev = G + M * M;      // N
+    R* O = ev + N;          // N x N + N
+    const int r = g.lr;
+    row_mul<N, N, M>(SL, M, S, N, L, M, r);
+    row_mul<N, N, N>(SF, N, S, N, F, N, r);
+    {
+        R t = v[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t -= S[r * N + k] * c[k];
+        ev[r] = t;
+    }
+    g.sync();
+    if (r < M) {
+        // G = U + L^T S L ; [L^T S F | L^T (v - S c)]
+        R gg[M], pp[N];
+        R w = R(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) gg[b] = U[r * M + b];
+#pragma unroll
+        for (int j = 0; j < N; ++j) pp[j] = R(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const R lk = L[k * M + r];
+            const R sk = SL[k * M + r];
+#pragma unroll
+            for (int b = 0; b < M; ++b) gg[b] += lk * SL[k * M + b];
+#pragma unroll
+            for (int j = 0; j < N; ++j) pp[j] += sk * F[k * N + j];
+            w += lk * ev[k];
+        }
+#pragma unroll
+        for (int b = 0; b < M; ++b) G[r * M + b] = gg[b];
+#pragma unroll
+        for (int j = 0; j < N; ++j) Kd[r * (N + 1) + j] = pp[j];
+        Kd[r * (N + 1) + N] = w;
+    }
+    g.sync();
+    const bool ok = solve_gj<N, M, N + 1>(G, M, Kd, N + 1, g);
+    // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
+    {
+        R ft[N], sft[N];
+        R ct = c[r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            ft[j] = F[r * N + j];
+            sft[j] = SF[r * N + j];
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const R la = L[r * M + a];
+            const R sa = SL[r * M + a];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                ft[j] -= la * Kd[a * (N + 1) + j];
+                sft[j] -= sa * Kd[a * (N + 1) + j];
+            }
+            ct += la * Kd[a * (N + 1) + N];
+        }
+        g.sync();
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Ft[LAffine<N>::OF + r * N + j] = ft[j];
+            SF[r * N + j] = sft[j];
+        }
+        Ft[LAffine<N>::OC + r] = ct;
+    }
+    g.sync();
+    // S <- F^T (S Ft) + Q ; v <- Ft^T (v - S c) + q
+    {
+        R acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = Q[r * N + j];
+        R t = q[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const R fk = F[k * N + r];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * N + j];
+            t += Ft[LAffine<N>::OF + k * N + r] * ev[k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[r * N + j] = acc[j];
+        O[N * N + r] = t;
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j) val[V::OS + r * N + j] = R(0.5) * (O[r * N + j] + O[j * N + r]);
+    val[V::OV + r] = O[N * N + r];
+    g.sync();
+    return ok;
+}
+
+// Scratch of fold_step (elements of R).
+template <int N, int M>
+constexpr int fold_scratch() {
+    return 2 * N * N /*JF | A2F, later the staged C and J*/ + N * N /*F^T J2 F*/ +
+           3 * N * M /*P2, JL, Z*/ + 2 * N /*w, A2 c*/ + M * M /*G*/ + M * (2 * N + 1) /*rhs*/;
+}
+
+// P <- a_k (x) P (eq. lqt_comb, a_k = (F, c, L U^{-1} L^T, H^T X r, H^T X H)
+// from the step buffer).  With C_k = L W L^T, W = U^{-1}, and
+// G = U + L^T J2 L:  (I + C_k J2)^{-1} = I - L G^{-1} L^T J2, and
+// (I + C_k J2)^{-1} C_k = L G^{-1} L^T.  Writing Z = L^T J2 F, w = eta2 - J2 c,
+// P2 = A2 L and [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]:
+//   A   = A2 F - P2 Zt              b   = A2 c + P2 om + b2
+//   C   = C2 + P2 Pt                J   = J1 + F^T J2 F - Z^T Zt
+//   eta = eta1 + F^T w - Z^T om
+// Returns false if G is numerically singular.
+template <typename R, int N, int M>
+__device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
+    using SLay = StepLayout<N, M>;
+    using E = LElem<N>;
+    constexpr int NR = 2 * N + 1;
+    const R* e1 = sb + SLay::E;
+    const R* F = e1 + E::OA;
+    const R* c = e1 + E::OB;
+    const R* L = sb + SLay::L;
+    const R* U = sb + SLay::U;
+    R* JF = scr;             // N x N
+    R* A2F = JF + N * N;     // N x N
+    R* FJF = A2F + N * N;    // N x N
+    R* P2 = FJF + N * N;     // N x M
+    R* JL = P2 + N * M;      // N x M
+    R* Z = JL + N * M;       // M x N
+    R* w = Z + M * N;        // N
+    R* A2c = w + N;          // N
+    R* G = A2c + N;          // M x M
+    R* rhs = G + M * M;      // M x NR
+    R* O = JF;               // staged C and J (2 N x N), after JF and A2F are consumed
+    const int r = g.lr;
+    // 1. JF = J2 F, JL = J2 L, w = eta2 - J2 c (row r of J2)
+    {
+        R jf[N], jl[M];
+        R t = P[E::OE + r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) jf[j] = R(0);
+#pragma unroll
+        for (int a = 0; a < M; ++a) jl[a] = R(0);
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            const R jk = P[E::OJ + r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) jf[j] += jk * F[k * N + j];
+#pragma unroll
+            for (int a = 0; a < M; ++a) jl[a] += jk * L[k * M + a];
+            t -= jk * c[k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) JF[r * N + j] = jf[j];
+#pragma unroll
+        for (int a = 0; a < M; ++a) JL[r * M + a] = jl[a];
+        w[r] = t;
+    }
+    //    A2F = A2 F, P2 = A2 L (also into the right sides, transposed), A2 c
+    {
+        R af[N], pl[M];
+        R t = R(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) af[j] = R(0);
+#pragma unroll
+        for (int a = 0; a < M; ++a) pl[a] = R(0);
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            const R ak = P[E::OA + r * N + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) af[j] += ak * F[k * N + j];
+#pragma unroll
+            for (int a = 0; a < M; ++a) pl[a] += ak * L[k * M + a];
+            t += ak * c[k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) A2F[r * N + j] = af[j];
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            P2[r * M + a] = pl[a];
+            rhs[a * NR + N + 1 + r] = pl[a];
+        }
+        A2c[r] = t;
+    }
+    g.sync();
+    // 2. G = U + L^T JL, Z = L^T JF, L^T w (lanes a < M); F^T JF (all lanes)
+    if (r < M) {
+        R gg[M], zz[N];
+        R t = R(0);
+#pragma unroll
+        for (int b = 0; b < M; ++b) gg[b] = U[r * M + b];
+#pragma unroll
+        for (int j = 0; j < N; ++j) zz[j] = R(0);
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            const R lk = L[k * M + r];
+#pragma unroll
+            for (int b = 0; b < M; ++b) gg[b] += lk * JL[k * M + b];
+#pragma unroll
+            for (int j = 0; j < N; ++j) zz[j] += lk * JF[k * N + j];
+            t += lk * w[k];
+        }
+#pragma unroll
+        for (int b = 0; b < M; ++b) G[r * M + b] = gg[b];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Z[r * N + j] = zz[j];
+            rhs[r * NR + j] = zz[j];
+        }
+        rhs[r * NR + N] = t;
+    }
+    {
+        R acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = R(0);
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            const R fk = F[k * N + r];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += fk * JF[k * N + j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) FJF[r * N + j] = acc[j];
+    }
+    g.sync();
+    // 3. [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]
+    const bool ok = solve_gj<N, M, NR>(G, M, rhs, NR, g);
+    // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (in place: A2 is not read again)
+    {
+        R aa[N];
+        R t = A2c[r] + P[E::OB + r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) aa[j] = A2F[r * N + j];
+#pragma unroll 4
+        for (int a = 0; a < M; ++a) {
+            const R pa = P2[r * M + a];
+#pragma unroll
+            for (int j = 0; j < N; ++j) aa[j] -= pa * rhs[a * NR + j];
+            t += pa * rhs[a * NR + N];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) P[E::OA + r * N + j] = aa[j];
+        P[E::OB + r] = t;
+    }
+    g.sync();
+    //    C = C2 + P2 Pt and J = J1 + F^T J2 F - Z^T Zt staged in O;
+    //    eta = eta1 + F^T w - Z^T om in place
+    {
+        R cc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) cc[j] = P[E::OC + r * N + j];
+#pragma unroll 4
+        for (int a = 0; a < M; ++a) {
+            const R pa = P2[r * M + a];
+#pragma unroll
+            for (int j = 0; j < N; ++j) cc[j] += pa * rhs[a * NR + N + 1 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[r * N + j] = cc[j];
+    }
+    {
+        R jj[N];
+        R t = e1[E::OE + r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) jj[j] = e1[E::OJ + r * N + j] + FJF[r * N + j];
+#pragma unroll 4
+        for (int a = 0; a < M; ++a) {
+            const R za = Z[a * N + r];
+#pragma unroll
+            for (int j = 0; j < N; ++j) jj[j] -= za * rhs[a * NR + j];
+            t -= za * rhs[a * NR + N];
+        }
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) t += F[k * N + r] * w[k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) O[N * N + r * N + j] = jj[j];
+        P[E::OE + r] = t;
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        P[E::OC + r * N + j] = R(0.5) * (O[r * N + j] + O[j * N + r]);
+        P[E::OJ + r * N + j] = R(0.5) * (O[N * N + r * N + j] + O[N * N + j * N + r]);
+    }
+    g.sync();
+    return ok;
+}
+
+}  // namespace lanes
+}  // namespace lqt

@@ -1,4 +1,5 @@
-// Lane-group dense algebra for the LQT operators at larger state sizes.
+// Lane-group dense algebra for the LQT operators at larger state sizes, in
+// the arithmetic type R (float or double).
 //
 // A group of LG = N lanes (N a power of two, N <= 32) owns one element; lane r
 // of the group owns row r of every N-row matrix, and the matrices live in
@@ -28,17 +29,21 @@ struct Group {
     __device__ void sync() const { __syncwarp(mask); }
 };
 
+// IEEE round-to-nearest reciprocal in the arithmetic type
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
 // out[lr][0..C) = X[lr][0..K) * Y (K x C), for rows lr < ROWS
-template <int ROWS, int K, int C>
-__device__ __forceinline__ void row_mul(float* out, int ldo, const float* X, int ldx,
-                                        const float* Y, int ldy, int lr) {
+template <int ROWS, int K, int C, typename R>
+__device__ __forceinline__ void row_mul(R* out, int ldo, const R* X, int ldx, const R* Y, int ldy,
+                                        int lr) {
     if (lr >= ROWS) return;
-    float acc[C];
+    R acc[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+    for (int c = 0; c < C; ++c) acc[c] = R(0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float xk = X[lr * ldx + k];
+        const R xk = X[lr * ldx + k];
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] += xk * Y[k * ldy + c];
     }
@@ -47,16 +52,16 @@ __device__ __forceinline__ void row_mul(float* out, int ldo, const float* X, int
 }
 
 // out[lr][0..C) = X[0..K)[lr]^T-row, i.e. (X^T Y)[lr], X stored K x ROWS
-template <int ROWS, int K, int C>
-__device__ __forceinline__ void row_mul_tn(float* out, int ldo, const float* X, int ldx,
-                                           const float* Y, int ldy, int lr) {
+template <int ROWS, int K, int C, typename R>
+__device__ __forceinline__ void row_mul_tn(R* out, int ldo, const R* X, int ldx, const R* Y,
+                                           int ldy, int lr) {
     if (lr >= ROWS) return;
-    float acc[C];
+    R acc[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.f;
+    for (int c = 0; c < C; ++c) acc[c] = R(0);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float xk = X[k * ldx + lr];
+        const R xk = X[k * ldx + lr];
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] += xk * Y[k * ldy + c];
     }
@@ -67,34 +72,33 @@ __device__ __forceinline__ void row_mul_tn(float* out, int ldo, const float* X, 
 // Gauss-Jordan elimination with partial pivoting on [Mx | Bx] (R x R, R x NR),
 // rows owned by lanes lr < R.  On return Bx holds Mx^{-1} Bx.  Returns false
 // for a zero or non-finite pivot (every lane returns the same value).
-template <int LG, int R, int NR>
-__device__ bool solve_gj(float* Mx, int ldm, float* Bx, int ldb, const Group<LG>& g,
-                         float* pivinfo /* 1 float per group */) {
+template <int LG, int R, int NR, typename T>
+__device__ bool solve_gj(T* Mx, int ldm, T* Bx, int ldb, const Group<LG>& g) {
     bool ok = true;
     const int lr = g.lr;
     for (int k = 0; k < R; ++k) {
         // every lane finds the pivot row redundantly
         int piv = k;
-        float best = fabsf(Mx[k * ldm + k]);
+        T best = fabs(Mx[k * ldm + k]);
         for (int i = k + 1; i < R; ++i) {
-            const float a = fabsf(Mx[i * ldm + k]);
+            const T a = fabs(Mx[i * ldm + k]);
             if (a > best) { best = a; piv = i; }
         }
-        ok = ok && (best > 0.f) && isfinite(best);
+        ok = ok && (best > T(0)) && isfinite(best);
         g.sync();
         if (piv != k) {
             // swap rows k and piv, columns spread over the lanes
             for (int j = lr; j < R + NR; j += LG) {
-                float* a = j < R ? &Mx[k * ldm + j] : &Bx[k * ldb + (j - R)];
-                float* b = j < R ? &Mx[piv * ldm + j] : &Bx[piv * ldb + (j - R)];
-                const float t = *a;
+                T* a = j < R ? &Mx[k * ldm + j] : &Bx[k * ldb + (j - R)];
+                T* b = j < R ? &Mx[piv * ldm + j] : &Bx[piv * ldb + (j - R)];
+                const T t = *a;
                 *a = *b;
                 *b = t;
             }
         }
         g.sync();
-        const float inv = __frcp_rn(Mx[k * ldm + k]);
-        float f = 0.f;
+        const T inv = rcp(Mx[k * ldm + k]);
+        T f = T(0);
         if (lr < R && lr != k) f = Mx[lr * ldm + k] * inv;
         g.sync();
         if (lr < R && lr != k) {
@@ -106,12 +110,11 @@ __device__ bool solve_gj(float* Mx, int ldm, float* Bx, int ldb, const Group<LG>
         g.sync();
     }
     if (lr < R) {
-        const float inv = __frcp_rn(Mx[lr * ldm + lr]);
+        const T inv = rcp(Mx[lr * ldm + lr]);
 #pragma unroll 4
         for (int j = 0; j < NR; ++j) Bx[lr * ldb + j] *= inv;
     }
     g.sync();
-    (void)pivinfo;
     return ok;
 }
 
@@ -132,47 +135,47 @@ struct LAffine {  // F[N][N], c[N]
     static constexpr int OF = 0, OC = N * N, SIZE = N * N + N;
 };
 
-// Scratch a group needs for combine (floats).
+// Scratch a group needs for combine (elements of the arithmetic type).
 template <int N>
 constexpr int combine_scratch() {
     return N * N /*Mx*/ + N * (2 * N + 1) /*Bx*/ + N /*w*/ + N * N /*JX or T3*/ + LElem<N>::SIZE;
 }
 
-template <int LG, int N>
-__device__ void set_neutral(float* e, const Group<LG>& g) {
+template <int LG, int N, typename R>
+__device__ void set_neutral(R* e, const Group<LG>& g) {
     const int r = g.lr;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        e[LElem<N>::OA + r * N + j] = r == j ? 1.f : 0.f;
-        e[LElem<N>::OC + r * N + j] = 0.f;
-        e[LElem<N>::OJ + r * N + j] = 0.f;
+        e[LElem<N>::OA + r * N + j] = r == j ? R(1) : R(0);
+        e[LElem<N>::OC + r * N + j] = R(0);
+        e[LElem<N>::OJ + r * N + j] = R(0);
     }
-    e[LElem<N>::OB + r] = 0.f;
-    e[LElem<N>::OE + r] = 0.f;
+    e[LElem<N>::OB + r] = R(0);
+    e[LElem<N>::OE + r] = R(0);
     g.sync();
 }
 
 // out = e1 (x) e2 (eq. lqt_comb).  out may alias e1 or e2.
-template <int LG, int N>
-__device__ bool combine(const float* e1, const float* e2, float* out, float* scr,
+template <int LG, int N, typename R>
+__device__ bool combine(const R* e1, const R* e2, R* out, R* scr,
                         const Group<LG>& g) {
     using E = LElem<N>;
     constexpr int NR = 2 * N + 1;
-    float* Mx = scr;
-    float* Bx = Mx + N * N;
-    float* w = Bx + N * NR;
-    float* T = w + N;
-    float* O = T + N * N;  // result staged here, copied to out at the end
+    R* Mx = scr;
+    R* Bx = Mx + N * N;
+    R* w = Bx + N * NR;
+    R* T = w + N;
+    R* O = T + N * N;  // result staged here, copied to out at the end
     const int r = g.lr;
     // Mx = I + C1 J2 ; Bx = [A1 | b1 + C1 eta2 | C1]
     {
-        float acc[N];
+        R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = r == j ? 1.f : 0.f;
-        float be = e1[E::OB + r];
+        for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
+        R be = e1[E::OB + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float ck = e1[E::OC + r * N + k];
+            const R ck = e1[E::OC + r * N + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += ck * e2[E::OJ + k * N + j];
             be += ck * e2[E::OE + k];
@@ -185,16 +188,16 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
         }
         Bx[r * NR + N] = be;
         // w = eta2 - J2 b1
-        float t = e2[E::OE + r];
+        R t = e2[E::OE + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) t -= e2[E::OJ + r * N + k] * e1[E::OB + k];
         w[r] = t;
     }
     g.sync();
-    const bool ok = solve_gj<LG, N, NR>(Mx, N, Bx, NR, g, nullptr);
+    const bool ok = solve_gj<LG, N, NR>(Mx, N, Bx, NR, g);
     // eta = X1^T w + eta1 ; JX = J2 X1 (into T)
     {
-        float t = e1[E::OE + r];
+        R t = e1[E::OE + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) t += Bx[k * NR + r] * w[k];
         O[E::OE + r] = t;
@@ -203,12 +206,12 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
     g.sync();
     // J = A1^T JX + J1
     {
-        float acc[N];
+        R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = e1[E::OJ + r * N + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float a = e1[E::OA + k * N + r];
+            const R a = e1[E::OA + k * N + r];
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
         }
@@ -218,13 +221,13 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
     g.sync();
     // A = A2 X1 ; b = A2 x2 + b2 ; T = A2 X3
     {
-        float aa[N], tt[N];
-        float bb = e2[E::OB + r];
+        R aa[N], tt[N];
+        R bb = e2[E::OB + r];
 #pragma unroll
-        for (int j = 0; j < N; ++j) aa[j] = tt[j] = 0.f;
+        for (int j = 0; j < N; ++j) aa[j] = tt[j] = R(0);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float a2 = e2[E::OA + r * N + k];
+            const R a2 = e2[E::OA + r * N + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 aa[j] += a2 * Bx[k * NR + j];
@@ -242,12 +245,12 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
     g.sync();
     // C = T A2^T + C2
     {
-        float acc[N];
+        R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = e2[E::OC + r * N + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float t = T[r * N + k];
+            const R t = T[r * N + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += t * e2[E::OA + j * N + k];
         }
@@ -259,8 +262,8 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         out[E::OA + r * N + j] = O[E::OA + r * N + j];
-        out[E::OC + r * N + j] = 0.5f * (O[E::OC + r * N + j] + O[E::OC + j * N + r]);
-        out[E::OJ + r * N + j] = 0.5f * (O[E::OJ + r * N + j] + O[E::OJ + j * N + r]);
+        out[E::OC + r * N + j] = R(0.5) * (O[E::OC + r * N + j] + O[E::OC + j * N + r]);
+        out[E::OJ + r * N + j] = R(0.5) * (O[E::OJ + r * N + j] + O[E::OJ + j * N + r]);
     }
     out[E::OB + r] = O[E::OB + r];
     out[E::OE + r] = O[E::OE + r];
@@ -269,23 +272,23 @@ __device__ bool combine(const float* e1, const float* e2, float* out, float* scr
 }
 
 // value (S, v) <- P (x) (0, 0, 0, v, S)
-template <int LG, int N>
-__device__ bool value_apply(const float* P, float* val, float* scr, const Group<LG>& g) {
+template <int LG, int N, typename R>
+__device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
     using E = LElem<N>;
     using V = LValue<N>;
-    float* Mx = scr;
-    float* X = Mx + N * N;
-    float* T = X + N * N;
-    float* e = T + N * N;
-    float* O = e + N;
+    R* Mx = scr;
+    R* X = Mx + N * N;
+    R* T = X + N * N;
+    R* e = T + N * N;
+    R* O = e + N;
     const int r = g.lr;
     {
-        float acc[N];
+        R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = r == j ? 1.f : 0.f;
+        for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float ck = P[E::OC + r * N + k];
+            const R ck = P[E::OC + r * N + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += ck * val[V::OS + k * N + j];
         }
@@ -294,17 +297,17 @@ __device__ bool value_apply(const float* P, float* val, float* scr, const Group<
             Mx[r * N + j] = acc[j];
             X[r * N + j] = P[E::OA + r * N + j];
         }
-        float t = val[V::OV + r];
+        R t = val[V::OV + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) t -= val[V::OS + r * N + k] * P[E::OB + k];
         e[r] = t;
     }
     g.sync();
-    const bool ok = solve_gj<LG, N, N>(Mx, N, X, N, g, nullptr);
+    const bool ok = solve_gj<LG, N, N>(Mx, N, X, N, g);
     // T = S X1 ; v' = X1^T e + eta
     row_mul<N, N, N>(T, N, val + V::OS, N, X, N, r);
     {
-        float t = P[E::OE + r];
+        R t = P[E::OE + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) t += X[k * N + r] * e[k];
         O[V::OV + r] = t;
@@ -312,12 +315,12 @@ __device__ bool value_apply(const float* P, float* val, float* scr, const Group<
     g.sync();
     // S' = A^T T + J
     {
-        float acc[N];
+        R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = P[E::OJ + r * N + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const float a = P[E::OA + k * N + r];
+            const R a = P[E::OA + k * N + r];
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
         }
@@ -327,25 +330,25 @@ __device__ bool value_apply(const float* P, float* val, float* scr, const Group<
     g.sync();
 #pragma unroll
     for (int j = 0; j < N; ++j)
-        val[V::OS + r * N + j] = 0.5f * (O[V::OS + r * N + j] + O[V::OS + j * N + r]);
+        val[V::OS + r * N + j] = R(0.5) * (O[V::OS + r * N + j] + O[V::OS + j * N + r]);
     val[V::OV + r] = O[V::OV + r];
     g.sync();
     return ok;
 }
 
 // f2 after f1: (F2 F1, F2 c1 + c2) into out (may alias f1 or f2)
-template <int LG, int N>
-__device__ void affine_compose(const float* f1, const float* f2, float* out, float* scr,
+template <int LG, int N, typename R>
+__device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr,
                                const Group<LG>& g) {
     using A = LAffine<N>;
     const int r = g.lr;
-    float acc[N];
-    float c = f2[A::OC + r];
+    R acc[N];
+    R c = f2[A::OC + r];
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc[j] = 0.f;
+    for (int j = 0; j < N; ++j) acc[j] = R(0);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const float a = f2[A::OF + r * N + k];
+        const R a = f2[A::OF + r * N + k];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] += a * f1[A::OF + k * N + j];
         c += a * f1[A::OC + k];
@@ -359,11 +362,11 @@ __device__ void affine_compose(const float* f1, const float* f2, float* out, flo
 }
 
 // x <- F x + c for x in shared memory
-template <int LG, int N>
-__device__ void affine_apply(const float* f, float* x, const Group<LG>& g) {
+template <int LG, int N, typename R>
+__device__ void affine_apply(const R* f, R* x, const Group<LG>& g) {
     using A = LAffine<N>;
     const int r = g.lr;
-    float t = f[A::OC + r];
+    R t = f[A::OC + r];
 #pragma unroll
     for (int k = 0; k < N; ++k) t += f[A::OF + r * N + k] * x[k];
     g.sync();

@@ -235,3 +235,51 @@ def ragged_batch(count: int = 4096, seed: int = 0, sizes=(4, 8, 16), t_min: int 
     Ts = rng.integers(t_min, t_max + 1, size=count)
     return [diag_tracking(int(n), T=int(T), seed=int(seed) * 1_000_003 + i)
             for i, (n, T) in enumerate(zip(ns, Ts))]
+
+
+# ---------------------------------------------------------------------------
+# Precision study (n = 32, m = 16, ill-conditioned costs).
+# ---------------------------------------------------------------------------
+
+def _haar(rng, n, count):
+    """Haar-distributed orthogonal matrices: QR of a Gaussian matrix with the
+    signs of R's diagonal moved into Q (Mezzadri, Notices AMS 54(5), 2007)."""
+    Z = rng.standard_normal((count, n, n))
+    Q, R = np.linalg.qr(Z)
+    d = np.sign(np.diagonal(R, axis1=1, axis2=2))
+    d[d == 0] = 1.0
+    return Q * d[:, None, :]
+
+
+def _cond_spd(rng, n, count, cond):
+    """V diag(lam) V^T with V Haar and log10(lam) uniform on [-log10(cond), 0],
+    then stretched affinely in log10 so that max/min = cond exactly."""
+    V = _haar(rng, n, count)
+    e = rng.uniform(-math.log10(cond), 0.0, size=(count, n))
+    lo, hi = e.min(axis=1, keepdims=True), e.max(axis=1, keepdims=True)
+    e = -math.log10(cond) + math.log10(cond) * (e - lo) / np.maximum(hi - lo, 1e-300)
+    lam = 10.0 ** e
+    X = (V * lam[:, None, :]) @ np.swapaxes(V, 1, 2)
+    return 0.5 * (X + np.swapaxes(X, 1, 2))
+
+
+def precision_study(T: int = 65536, seed: int = 0, n: int = 32, m: int = 16,
+                    cond: float = 1e6, perturb: float = 0.01) -> LQTProblem:
+    """F_k = 0.99 Q_k + perturb (u v^T + w z^T) with Q_k Haar orthogonal and
+    u, v, w, z ~ N(0, 1/n); X_k = V diag(lam) V^T with cond(X_k) = cond and
+    log-uniform eigenvalues; L_k ~ N(0, 1/n), U = 1e-3 I, H = I (p = n),
+    c = 0, r_k ~ N(0, 1).  Terminal: H_T = I, X_T drawn like X_k,
+    r_T ~ N(0, 1); x_0 ~ N(0, I)."""
+    rng = np.random.default_rng(seed)
+    Q = _haar(rng, n, T)
+    u, v, w, z = (rng.standard_normal((T, n)) / math.sqrt(n) for _ in range(4))
+    F = 0.99 * Q + perturb * (u[:, :, None] * v[:, None, :] + w[:, :, None] * z[:, None, :])
+    X = _cond_spd(rng, n, T, cond)
+    L = rng.standard_normal((T, n, m)) / math.sqrt(n)
+    r = rng.standard_normal((T, n))
+    XT = _cond_spd(rng, n, 1, cond)[0]
+    rT = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    return LQTProblem(F=_c(F), c=None, L=_c(L), U=_c(1e-3 * np.eye(m))[None],
+                      H=_c(np.eye(n))[None], r=_c(r), X=_c(X), HT=_c(np.eye(n)), rT=_c(rT),
+                      XT=_c(XT), x0=_c(x0), T=T)

@@ -266,6 +266,20 @@ def lqt_solve_batched(problems, outputs, workspace, stream=None) -> None:
         raise LQTError(st, "lqt_solve_batched")
 
 
+# numpy mirror of lqt_batch_item, for building descriptor arrays column-wise
+BATCH_ITEM = np.dtype(lqt_batch_item)
+
+
+def lqt_solve_batched_array(items: np.ndarray, workspace, stream=None) -> None:
+    """lqt_solve_batched over a C-contiguous numpy array of BATCH_ITEM."""
+    if items.dtype != BATCH_ITEM or not items.flags.c_contiguous:
+        raise LQTError(LQT_EINVAL, "items must be a contiguous BATCH_ITEM array")
+    st = _lib.lqt_solve_batched(items.ctypes.data_as(ctypes.POINTER(lqt_batch_item)), len(items),
+                                _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_batched")
+
+
 def solve_batched(problems, stream=None, check: bool = True):
     """Allocate outputs and a workspace with torch and run lqt_solve_batched."""
     import torch

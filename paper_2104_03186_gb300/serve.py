@@ -84,7 +84,9 @@ class ModelPool:
 
 
 def out_bytes(n: int, m: int, T: int) -> int:
-    return 4 * ((T + 1) * n * n + (T + 1) * n + T * m * n + (T + 1) * n + T * m)
+    """Device bytes a request holds while admitted: S, v, K and x (its u goes to
+    the stream's staging buffer)."""
+    return 4 * ((T + 1) * n * n + (T + 1) * n + T * m * n + (T + 1) * n)
 
 
 def make_requests(count: int, rate: float, seed: int = 0, sizes=(4, 8, 16, 32),
@@ -116,37 +118,64 @@ def make_requests(count: int, rate: float, seed: int = 0, sizes=(4, 8, 16, 32),
     return reqs
 
 
+class _Slot:
+    """One stream with its staging buffers, reused batch after batch: pinned
+    host and device buffers for the packed references and initial states, a
+    device buffer the kernels write u* into, its pinned host copy, the batch
+    workspace and the descriptor array."""
+
+    def __init__(self):
+        import torch
+
+        self.stream = torch.cuda.Stream()
+        self.cap_in = self.cap_u = self.cap_items = 0
+        self.ensure(1 << 22, 1 << 21, 1024)
+
+    def ensure(self, in_elems: int, u_elems: int, count: int):
+        import torch
+
+        if in_elems > self.cap_in:
+            self.cap_in = max(in_elems, 2 * self.cap_in)
+            self.h_in = torch.empty(self.cap_in, dtype=torch.float32).pin_memory()
+            self.d_in = torch.empty(self.cap_in, dtype=torch.float32, device="cuda")
+            self.h_in_np = self.h_in.numpy()
+        if u_elems > self.cap_u:
+            self.cap_u = max(u_elems, 2 * self.cap_u)
+            self.h_u = torch.empty(self.cap_u, dtype=torch.float32).pin_memory()
+            self.d_u = torch.empty(self.cap_u, dtype=torch.float32, device="cuda")
+            self.h_u_np = self.h_u.numpy()
+        if count > self.cap_items:
+            self.cap_items = max(count, 2 * self.cap_items)
+            self.items = np.zeros(self.cap_items, dtype=lqt.BATCH_ITEM)
+            self.ws = torch.empty(lqt.lqt_batch_workspace_bytes(self.cap_items),
+                                  dtype=torch.uint8, device="cuda")
+
+
 class Server:
     def __init__(self, pool: ModelPool, memory_budget: int = 4 << 30, streams: int = 4,
                  max_batch: int = 1024):
-        import torch
-
         self.pool = pool
         self.budget = memory_budget
-        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.slots = [_Slot() for _ in range(streams)]
         self.max_batch = max_batch
         self.mem = 0
         self.peak_mem = 0
+        self.batches = 0
+        self.launches = 0
 
     def _alloc(self, req: Request):
         import torch
 
-        n = req.n
-        m = self.pool.models[n][0].m
-        T = req.T
-        req.out = {"S": torch.empty((T + 1, n, n), device="cuda"),
-                   "v": torch.empty((T + 1, n), device="cuda"),
-                   "K": torch.empty((T, m, n), device="cuda"),
-                   "x": torch.empty((T + 1, n), device="cuda"),
-                   "u": torch.empty((T, m), device="cuda")}
-        self.mem += out_bytes(n, m, T)
+        m = self.pool.models[req.n][0].m
+        nb = out_bytes(req.n, m, req.T)
+        req.out = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
+        self.mem += nb
         self.peak_mem = max(self.peak_mem, self.mem)
 
-    def _release(self, req: Request, keep: bool = False):
+    def _release(self, req: Request):
         """Free a finished request's outputs once no warm request still needs them."""
-        if req.out is not None and req.refs == 0 and not math.isnan(req.done) and not keep:
-            n = req.n
-            self.mem -= out_bytes(n, self.pool.models[n][0].m, req.T)
+        if req.out is not None and req.refs == 0 and not math.isnan(req.done):
+            self.mem -= out_bytes(req.n, self.pool.models[req.n][0].m, req.T)
             req.out = None
 
     def run(self, reqs: List[Request], realtime: bool = True):
@@ -160,55 +189,63 @@ class Server:
             if q.warm_of >= 0:
                 byid[q.warm_of].refs += 1
         queue = deque(sorted(reqs, key=lambda r: r.arrival))
+        ready: deque = deque()    # warm requests whose predecessor has finished
+        parked: Dict[int, List[Request]] = {}  # predecessor rid -> warm requests
         admitted: List[Request] = []
-        inflight = []  # (stream, event, batch, host u buffer, device staging)
-        free = list(self.streams)
+        inflight = []  # (slot, event, batch, u offsets)
+        free = list(self.slots)
         done = 0
         t0 = time.perf_counter()
         while done < len(reqs):
             now = time.perf_counter() - t0 if realtime else math.inf
-            # admission by device-memory budget, first come first served
-            while queue and queue[0].arrival <= now:
-                q = queue[0]
+            # admission by device-memory budget, first come first served; a warm
+            # request waits (parked) until the request it continues has finished
+            blocked = False
+            while not blocked and (ready or (queue and queue[0].arrival <= now)):
+                src = ready if ready else queue
+                q = src[0]
+                if q.warm_of >= 0 and math.isnan(byid[q.warm_of].done):
+                    src.popleft()
+                    parked.setdefault(q.warm_of, []).append(q)
+                    continue
                 need = out_bytes(q.n, self.pool.models[q.n][0].m, q.T)
                 if self.mem + need > self.budget and (admitted or inflight):
+                    blocked = True
                     break
-                if q.warm_of >= 0 and math.isnan(byid[q.warm_of].done):
-                    break  # continues a request that has not finished yet
-                queue.popleft()
+                src.popleft()
                 self._alloc(q)
                 admitted.append(q)
             # launch a batch on a free stream
             if admitted and free:
                 batch, admitted = admitted[: self.max_batch], admitted[self.max_batch:]
-                st = free.pop()
-                inflight.append(self._launch(batch, st, byid))
+                inflight.append(self._launch(batch, free.pop(), byid))
             # completions
             still = []
             for item in inflight:
-                st, ev, batch, hu, stage = item
-                if ev.query():
-                    tdone = time.perf_counter() - t0
-                    off = 0
-                    for q in batch:
-                        mt = q.T * self.pool.models[q.n][0].m
-                        q.u = hu[off: off + mt].numpy().reshape(q.T, -1).copy()
-                        off += mt
-                        q.done = tdone
-                        done += 1
-                        if q.warm_of >= 0:
-                            prior = byid[q.warm_of]
-                            prior.refs -= 1
-                            self._release(prior)
-                        self._release(q)  # kept while warm requests still need it
-                    free.append(st)
-                else:
+                slot, ev, batch, uoff = item
+                if not ev.query():
                     still.append(item)
+                    continue
+                tdone = time.perf_counter() - t0
+                hu = slot.h_u_np
+                for q, off in zip(batch, uoff):
+                    mt = q.T * self.pool.models[q.n][0].m
+                    q.u = hu[off: off + mt].reshape(q.T, -1).copy()
+                    q.done = tdone
+                    done += 1
+                    if q.warm_of >= 0:
+                        prior = byid[q.warm_of]
+                        prior.refs -= 1
+                        self._release(prior)
+                    self._release(q)  # kept while warm requests still need it
+                    if q.rid in parked:
+                        ready.extend(parked.pop(q.rid))
+                free.append(slot)
             inflight = still
-            if not inflight and not admitted and queue and realtime:
+            if not inflight and not admitted and not ready and queue and realtime:
                 wait = queue[0].arrival - (time.perf_counter() - t0)
                 if wait > 0:
-                    time.sleep(min(wait, 1e-3))
+                    time.sleep(min(wait, 1e-4))
         torch.cuda.synchronize()
         lat = np.array([q.done - q.arrival for q in reqs])
         span = max(q.done for q in reqs) - min(q.arrival for q in reqs)
@@ -217,45 +254,82 @@ class Server:
                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
                      "mean_ms": float(lat.mean() * 1e3), "peak_device_bytes": self.peak_mem,
                      "time_steps": int(sum(q.T for q in reqs)),
-                     "warm_requests": int(sum(q.warm_of >= 0 for q in reqs))}
+                     "warm_requests": int(sum(q.warm_of >= 0 for q in reqs)),
+                     "batches": self.batches, "mean_batch": len(reqs) / max(self.batches, 1)}
 
-    def _launch(self, batch: List[Request], st, byid):
+    def _launch(self, batch: List[Request], slot: _Slot, byid):
         import torch
 
-        # one host-to-device copy of every reference (r_0..r_T) and cold x_0
-        sizes = [q.r.size + (q.n if q.warm_of < 0 else 0) for q in batch]
-        total = int(sum(sizes))
-        host = torch.empty(total, dtype=torch.float32).pin_memory()
-        hv = host.numpy()
-        off = 0
-        for q, sz in zip(batch, sizes):
-            hv[off: off + q.r.size] = q.r.ravel()
+        pool = self.pool
+        k = len(batch)
+        # packed layout of the host-to-device copy: per request r_0..r_T then x_0 (cold)
+        in_sizes = [q.r.size + (q.n if q.warm_of < 0 else 0) for q in batch]
+        u_sizes = [q.T * pool.models[q.n][0].m for q in batch]
+        in_off = np.concatenate([[0], np.cumsum(in_sizes)]).astype(np.int64)
+        u_off = np.concatenate([[0], np.cumsum(u_sizes)]).astype(np.int64)
+        slot.ensure(int(in_off[-1]), int(u_off[-1]), k)
+        hv = slot.h_in_np
+        for q, a in zip(batch, in_off[:-1]):
+            a = int(a)
+            hv[a: a + q.r.size] = q.r.ravel()
             if q.warm_of < 0:
-                hv[off + q.r.size: off + sz] = q.x0
-            off += sz
+                hv[a + q.r.size: a + q.r.size + q.n] = q.x0
+        # descriptors, column by column
+        ns = np.fromiter((q.n for q in batch), np.int64, k)
+        Ts = np.fromiter((q.T for q in batch), np.int64, k)
+        offs = np.fromiter((q.offset for q in batch), np.int64, k)
+        outp = np.fromiter((q.out.data_ptr() for q in batch), np.uint64, k)
+        x0p = np.empty(k, np.uint64)
+        din = np.uint64(slot.d_in.data_ptr())
+        for i, q in enumerate(batch):
+            if q.warm_of < 0:
+                x0p[i] = din + np.uint64(4 * (int(in_off[i]) + q.r.size))
+            else:
+                prior = byid[q.warm_of]
+                m0 = pool.models[prior.n][0].m
+                xbase = 4 * ((prior.T + 1) * prior.n * prior.n + (prior.T + 1) * prior.n
+                             + prior.T * m0 * prior.n)
+                x0p[i] = np.uint64(prior.out.data_ptr() + xbase + 4 * q.shift * q.n)
+        ms = np.empty(k, np.int64)
+        base = {f: np.empty(k, np.uint64) for f in ("F", "L", "U", "H", "X", "HT", "XT")}
+        for n, (pr, dev) in pool.models.items():
+            sel = ns == n
+            if not sel.any():
+                continue
+            ms[sel] = pr.m
+            for f in base:
+                base[f][sel] = dev[f].data_ptr()
+        it = slot.items[:k]
+        P, S = it["problem"], it["solution"]
+        P["n"], P["m"], P["p"], P["pT"], P["T"], P["dtype"] = ns, ms, ns, ns, Ts, lqt.LQT_F32
+        n2 = (ns * ns).astype(np.uint64)
+        nm = (ns * ms).astype(np.uint64)
+        o = offs.astype(np.uint64)
+        P["F"]["ptr"], P["F"]["step_stride"] = base["F"] + o * n2 * np.uint64(4), ns * ns
+        P["L"]["ptr"], P["L"]["step_stride"] = base["L"] + o * nm * np.uint64(4), ns * ms
+        P["X"]["ptr"], P["X"]["step_stride"] = base["X"] + o * n2 * np.uint64(4), ns * ns
+        P["U"]["ptr"], P["U"]["step_stride"] = base["U"], 0
+        P["H"]["ptr"], P["H"]["step_stride"] = base["H"], 0
+        P["c"]["ptr"], P["c"]["step_stride"] = 0, 0
+        rp = din + in_off[:-1].astype(np.uint64) * np.uint64(4)
+        P["r"]["ptr"], P["r"]["step_stride"] = rp, ns
+        P["HT"], P["XT"] = base["HT"], base["XT"]
+        P["rT"] = rp + Ts.astype(np.uint64) * ns.astype(np.uint64) * np.uint64(4)
+        P["x0"] = x0p
+        Tu, nu = Ts.astype(np.uint64), ns.astype(np.uint64)
+        S["S"] = outp
+        S["v"] = outp + np.uint64(4) * (Tu + 1) * nu * nu
+        S["K"] = S["v"] + np.uint64(4) * (Tu + 1) * nu
+        S["x"] = S["K"] + np.uint64(4) * Tu * nm
+        S["u"] = np.uint64(slot.d_u.data_ptr()) + u_off[:-1].astype(np.uint64) * np.uint64(4)
+        st = slot.stream
         with torch.cuda.stream(st):
-            dev = host.to("cuda", non_blocking=True)
-            probs, outs = [], []
-            off = 0
-            for q, sz in zip(batch, sizes):
-                n = q.n
-                p = self.pool.models[n][0].p
-                rptr = dev.data_ptr() + off * 4
-                rT = rptr + q.T * p * 4
-                if q.warm_of < 0:
-                    x0 = dev.data_ptr() + (off + q.r.size) * 4
-                else:
-                    prior = byid[q.warm_of]
-                    x0 = prior.out["x"].data_ptr() + q.shift * n * 4
-                probs.append(self.pool.problem(n, q.offset, q.T, rptr, x0, rT))
-                outs.append(q.out)
-                off += sz
-            ws = torch.empty(lqt.lqt_batch_workspace_bytes(len(batch)), dtype=torch.uint8,
-                             device="cuda")
-            lqt.lqt_solve_batched(probs, outs, ws, st)
-            ucat = torch.cat([q.out["u"].reshape(-1) for q in batch])
-            hu = torch.empty(ucat.numel(), dtype=torch.float32).pin_memory()
-            hu.copy_(ucat, non_blocking=True)
+            slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
+            lqt.lqt_solve_batched_array(it, slot.ws, st)
+            nu_el = int(u_off[-1])
+            slot.h_u[:nu_el].copy_(slot.d_u[:nu_el], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return (st, ev, batch, hu, (host, dev, ws))
+        self.batches += 1
+        self.launches += len(set(ns.tolist()))
+        return (slot, ev, batch, [int(a) for a in u_off[:-1]])

@@ -1,0 +1,91 @@
+"""Single problems at the lane-group sizes (n = 8, 16, 32) through lqt_solve:
+the chunked pipeline (chunk folds, one launch per tree level, re-fold,
+forward scan, rollout) against the FP64 oracle, in FP32, FP32 with FP64 tree
+levels and refinement, and FP64; its one-chunk form through
+lqt_riccati_sequential; and the precision-study workload."""
+import numpy as np
+import pytest
+
+from gpu_util import FP32_TOL, FP64_TOL, compare, gpu_solve, oracle_solve
+from paper_2104_03186_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(8, 4), (16, 8), (32, 16)]
+
+
+def _rand(n, m, T, seed, **kw):
+    return inputs.random_problem(n, m, T=T, seed=seed, **kw)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("T", [1, 5, 333, 2000])
+@pytest.mark.parametrize("refine", [0, 1])
+def test_chain_fp32_matches_oracle(n, m, T, refine):
+    prob = _rand(n, m, T, seed=n * 1000 + T).rounded_to(np.float32)
+    compare(gpu_solve(prob, refine=refine), oracle_solve(prob), FP32_TOL)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("T", [1, 333, 2000])
+def test_chain_fp64_matches_oracle(n, m, T):
+    prob = _rand(n, m, T, seed=7 + n + T)
+    compare(gpu_solve(prob, dtype=np.float64), oracle_solve(prob), FP64_TOL)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+def test_chain_sequential_matches_oracle(n, m):
+    prob = _rand(n, m, 300, seed=3 + n).rounded_to(np.float32)
+    compare(gpu_solve(prob, sequential=True, refine=1), oracle_solve(prob), FP32_TOL)
+    prob64 = _rand(n, m, 300, seed=4 + n)
+    compare(gpu_solve(prob64, dtype=np.float64, sequential=True), oracle_solve(prob64), FP64_TOL)
+
+
+@pytest.mark.parametrize("n,m,kw", [
+    (8, 4, dict(p=4, pT=1)),                 # p < n, one terminal row
+    (8, 4, dict(p=16, pT=16)),               # p = 2n
+    (16, 8, dict(with_c=False, pT=0)),       # no offsets, no terminal cost
+    (16, 8, dict(time_varying=False)),       # step stride 0 for every matrix
+    (32, 16, dict(p=8, x_rank=3)),           # rank-deficient X_k
+])
+def test_chain_shapes(n, m, kw):
+    prob = _rand(n, m, 777, seed=11, **kw).rounded_to(np.float32)
+    compare(gpu_solve(prob), oracle_solve(prob), FP32_TOL)
+    prob64 = _rand(n, m, 777, seed=12, **kw)
+    compare(gpu_solve(prob64, dtype=np.float64), oracle_solve(prob64), FP64_TOL)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+def test_chain_zero_horizon(n, m):
+    prob = _rand(n, m, 4, seed=1).rounded_to(np.float32)
+    prob.T = 0
+    for f in ("F", "c", "L", "U", "H", "r", "X"):
+        a = getattr(prob, f)
+        if a is not None and a.shape[0] > 1:
+            setattr(prob, f, a[:0])
+    g = gpu_solve(prob)
+    o = oracle_solve(prob)
+    compare(g, o, FP32_TOL, names=("S", "v", "x"))
+
+
+def test_chain_plan_spans_levels():
+    """The planner cuts a long problem into a power-of-two number of chunks."""
+    from paper_2104_03186_gb300 import lqt
+
+    for n, m in SIZES:
+        P = lqt.Problem.from_inputs(_rand(n, m, 5000, seed=0).rounded_to(np.float32))
+        plan = lqt.lqt_plan(P, 0)
+        nc, B = plan["tiles"], plan["chunk_steps"]
+        assert nc >= 2 and nc & (nc - 1) == 0
+        assert B * nc >= 5000 and B >= 4
+
+
+@pytest.mark.parametrize("T", [4096])
+def test_precision_study_small(T):
+    """The precision-study workload (n = 32, cond(X_k) = 1e6, U = 1e-3 I) at a
+    short horizon: FP64 within 1e-11 and the mixed form within 1e-5."""
+    prob = inputs.precision_study(T=T, seed=1)
+    o64 = oracle_solve(prob)
+    compare(gpu_solve(prob, dtype=np.float64), o64, FP64_TOL)
+    p32 = prob.rounded_to(np.float32)
+    compare(gpu_solve(p32, refine=1), oracle_solve(p32), FP32_TOL)
