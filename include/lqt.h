@@ -100,18 +100,32 @@ typedef struct {
 
 /* Solver options.  Pass NULL for the defaults (refine = LQT_REFINE_AUTO).
  *
- * refine: mixed-precision iterative refinement of the trajectory.  The optimal
- *   control u*_k = -K_k x*_k + d_k is often a small difference of large terms
+ * refine: mixed-precision iterative refinement.  The optimal control
+ *   u*_k = -K_k x*_k + d_k is often a small difference of large terms
  *   (tracking a slowly varying reference), so FP32 rounding of S, v and x is
- *   amplified in u*.  With refinement the solve runs twice: first on the
- *   problem, then on the same problem shifted by the first trajectory x^
- *   (x = x^ + xi: r'_k = r_k - H_k x^_k, c'_k = F_k x^_k + c_k - x^_{k+1},
- *   r'_T = r_T - H_T x^_T, x'_0 = 0), whose residual terms are formed with
- *   compensated (twice-working-precision) dot products.  The shifted problem
- *   has small data, so its controls carry no cancellation; it returns
- *   u* directly and x* = x^ + xi.  S, v and K come from the first solve.
- *   LQT_REFINE_AUTO refines FP32 solves and not FP64 ones. */
-enum { LQT_REFINE_OFF = 0, LQT_REFINE_ON = 1, LQT_REFINE_AUTO = 2 };
+ *   amplified in u*; ill-conditioned costs amplify it in every output.
+ *   n <= 4 (LQT_REFINE_ON and LQT_REFINE_FULL alike): the solve runs twice,
+ *   first on the problem, then on the same problem shifted by the first
+ *   trajectory x^ (x = x^ + xi: r'_k = r_k - H_k x^_k,
+ *   c'_k = F_k x^_k + c_k - x^_{k+1}, r'_T = r_T - H_T x^_T, x'_0 = 0), whose
+ *   residual terms are formed with compensated (twice-working-precision) dot
+ *   products; it returns u* directly and x* = x^ + xi.  S, v, K come from
+ *   the first solve.
+ *   n = 8, 16, 32 (FP32 problems): LQT_REFINE_ON takes one step of iterative
+ *   refinement of the KKT system of the QP: the residuals of the dynamics and
+ *   of the optimality
+ *   conditions in x and u at the first solve (x^, u^, lambda^_k =
+ *   S_k x^_k - v_k) are formed in FP64, a second solve of the correction
+ *   problem (same matrices, linear state terms, offsets) gives (dx, du), and
+ *   x* = x^ + dx, u* = u^ + du.  LQT_REFINE_FULL also runs the tree levels
+ *   above the chunks in FP64 and takes one Newton step of the Riccati
+ *   recursion for S, v and K: the residuals
+ *   R_k = Ric_k(S^_{k+1}) - S^_k are formed in FP64, the linear recursion
+ *   dS_k = Phi_k^T dS_{k+1} Phi_k + R_k (closed loop Phi_k) is solved by the
+ *   same scan, and K_k is recomputed in FP64 from S^ + dS.  FP64 arithmetic is
+ *   slow on this GPU, so FULL costs several times ON.
+ *   LQT_REFINE_AUTO = LQT_REFINE_ON for FP32 solves, OFF for FP64 ones. */
+enum { LQT_REFINE_OFF = 0, LQT_REFINE_ON = 1, LQT_REFINE_AUTO = 2, LQT_REFINE_FULL = 3 };
 typedef struct {
     int32_t refine;
     int32_t reserved[7]; /* must be 0 */
@@ -160,17 +174,24 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
                           void *stream);
 
 /* Ragged batch of independent problems (any mix of T and of the compiled
- * batch sizes (n, m) in {(4,2), (8,4), (16,8), (32,16)}; FP32; p <= 2n), solved by one
- * persistent launch per (n, m) present.  Each problem runs the temporally
- * parallel solve of lqt_solve (Sec. V-A, Method 1) inside one CTA: its steps
- * are cut into chunks, one group of n lanes per chunk, and the chunk totals
- * are swept in shared memory (Alg. 1).  CTAs take problems from a work queue.
+ * batch sizes (n, m) in {(4,2), (8,4), (16,8), (32,16)}; FP32; p, pT <= 2n),
+ * each solved by the temporally parallel method of lqt_solve (Sec. V-A,
+ * Method 1; chunked as in Sec. V-C):
+ *   n = 4:  one persistent launch; each problem runs inside one CTA, its steps
+ *           cut into chunks (one group of 4 lanes per chunk) whose totals are
+ *           swept in shared memory (Alg. 1); CTAs take problems from a work
+ *           queue.
+ *   n >= 8: the chunked pipeline of lqt_solve with all problems of one size
+ *           in each of its launches: every problem's steps are cut into a
+ *           power-of-two number of chunks of at most about 128 steps, and
+ *           one launch per tree level sweeps the chunk results of all of them.
  *   items: HOST array of `count` descriptors; each holds device pointers to a
  *          problem's inputs and outputs, with the layouts of lqt_problem and
  *          lqt_solution.  The array may be reused when the call returns.
- *   workspace: device buffer of at least lqt_batch_workspace_bytes(count)
- *          bytes, 256-byte aligned; its first bytes hold the status word read
- *          by lqt_workspace_status().
+ *   workspace: device buffer of at least lqt_batch_workspace_bytes(items,
+ *          count) bytes (0 means an invalid or unsupported item), 256-byte
+ *          aligned; its first bytes hold the status word read by
+ *          lqt_workspace_status().  The size depends on the problems' n and T.
  * No refinement is applied (problems whose controls cancel, see lqt_options,
  * should use lqt_solve).  Asynchronous on `stream`; returns LQT_EINVAL,
  * LQT_EUNSUPPORTED, LQT_ENOMEM or LQT_ECUDA on argument or launch errors. */
@@ -179,7 +200,7 @@ typedef struct {
     lqt_solution solution;
 } lqt_batch_item;
 
-size_t lqt_batch_workspace_bytes(int32_t count);
+size_t lqt_batch_workspace_bytes(const lqt_batch_item *items, int32_t count);
 lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *workspace,
                              size_t workspace_bytes, void *stream);
 

@@ -18,13 +18,14 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblqt_gb300.so")
+PEAKS_LIB = os.path.join(PKG, "libpeaks_gb300.so")  # FMA-peak microbenchmark (bench only)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 
 SOURCES = ["lqt_api.cu", "lqt_inst_f32_small.cu", "lqt_inst_f32_n4.cu", "lqt_inst_f64.cu",
-           "lqt_static.cu", "lqt_batch.cu", "lqt_batch32.cu", "lqt_chain.cu", "lqt_chain_n8.cu",
+           "lqt_static.cu", "lqt_batch.cu", "lqt_chain.cu", "lqt_chain_n8.cu",
            "lqt_chain_n16.cu", "lqt_chain_n32.cu"]
 
 
@@ -58,8 +59,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, res.stdout, res.stderr))
         return obj, res.stderr
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        results = list(ex.map(compile_one, SOURCES + ["lqt_peaks.cu"]))
+    peaks_obj = results.pop()[0]
+    cmd = [exe, *ARCH, "-shared", "-o", PEAKS_LIB, peaks_obj, "-cudart", "static"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
     if verbose or ptxas_verbose:
         for obj, log in results:
             sys.stderr.write(log)

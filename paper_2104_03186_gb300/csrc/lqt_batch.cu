@@ -1,5 +1,7 @@
-// C ABI of the ragged batch (include/lqt.h: lqt_solve_batched): descriptor
-// packing, grouping by (n, m), one persistent launch per group.
+// C ABI of the ragged batch (include/lqt.h: lqt_solve_batched): grouping by
+// (n, m); n = 4 problems go to one persistent launch of the one-CTA-per-problem
+// kernel (lqt_batch.cuh), the lane-group sizes to the chunked pipeline
+// (lqt_chain.cuh) with all problems of a size in each of its launches.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -9,6 +11,7 @@
 
 #include "lqt.h"
 #include "lqt_batch_launch.cuh"
+#include "lqt_chain_api.h"
 
 namespace lqt {
 namespace {
@@ -22,17 +25,8 @@ struct BatchVariant {
                    cudaError_t* err);
 };
 
-}  // namespace
-// n = 32 is compiled in its own translation unit (lqt_batch32.cu)
-extern template void launch_batch<32, 16, 2>(const BatchDesc*, int, int*, int*, cudaStream_t,
-                                             cudaError_t*);
-namespace {
-
 const BatchVariant kBatchVariants[] = {
     {4, 2, &launch_batch<4, 2, 64>},
-    {8, 4, &launch_batch<8, 4, 32>},
-    {16, 8, &launch_batch<16, 8, 8>},
-    {32, 16, &launch_batch<32, 16, 2>},
 };
 constexpr int kNumBatchVariants = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
@@ -49,7 +43,9 @@ lqt_status check_item(const lqt_batch_item& it) {
     const lqt_solution& S = it.solution;
     if (P.dtype != LQT_F32) return LQT_EUNSUPPORTED;
     if (P.T < 0 || P.p < 1 || P.pT < 0 || P.p > 2 * P.n) return LQT_EINVAL;
-    if (batch_variant(P.n, P.m) < 0) return LQT_EUNSUPPORTED;
+    const bool lanes = chain_supported(LQT_F32, P.n, P.m);
+    if (batch_variant(P.n, P.m) < 0 && !lanes) return LQT_EUNSUPPORTED;
+    if (lanes && P.pT > 2 * P.n) return LQT_EUNSUPPORTED;
     if (P.T > 0 && (!P.F.ptr || !P.L.ptr || !P.U.ptr || !P.H.ptr || !P.X.ptr)) return LQT_EINVAL;
     if (!P.x0 || (P.pT > 0 && (!P.HT || !P.XT))) return LQT_EINVAL;
     if (!S.S || !S.v || !S.x || (P.T > 0 && (!S.K || !S.u))) return LQT_EINVAL;
@@ -109,21 +105,52 @@ BatchDesc to_desc(const lqt_batch_item& it) {
 
 using namespace lqt;
 
-extern "C" size_t lqt_batch_workspace_bytes(int32_t count) {
-    if (count < 0) return 0;
+// Problems of the chunked pipeline, grouped by (n, m): indices into items.
+static std::vector<std::vector<int>> lane_groups(const lqt_batch_item* items, int32_t count) {
+    std::vector<std::vector<int>> groups;
+    std::vector<std::pair<int, int>> keys;
+    for (int i = 0; i < count; ++i) {
+        const lqt_problem& P = items[i].problem;
+        if (batch_variant(P.n, P.m) >= 0) continue;
+        size_t g = 0;
+        while (g < keys.size() && keys[g] != std::make_pair(P.n, P.m)) ++g;
+        if (g == keys.size()) {
+            keys.emplace_back(P.n, P.m);
+            groups.emplace_back();
+        }
+        groups[g].push_back(i);
+    }
+    return groups;
+}
+
+static size_t head_bytes(int32_t count) {
     return up(256) + up(64 * sizeof(int)) + up((size_t)count * sizeof(BatchDesc));
+}
+
+extern "C" size_t lqt_batch_workspace_bytes(const lqt_batch_item* items, int32_t count) {
+    if (count < 0 || (count > 0 && !items)) return 0;
+    size_t lane = 0;
+    for (int i = 0; i < count; ++i)
+        if (check_item(items[i]) != LQT_OK) return 0;
+    for (const std::vector<int>& g : lane_groups(items, count)) {
+        size_t b = 0;
+        if (chain_batch_workspace(items, g.data(), (int)g.size(), &b) != LQT_OK) return 0;
+        lane = std::max(lane, b);  // the groups run one after another on the stream
+    }
+    return head_bytes(count) + up(lane);
 }
 
 extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t count,
                                         void* workspace, size_t workspace_bytes, void* stream) {
     if (count < 0 || (count > 0 && !items)) return LQT_EINVAL;
     if (!workspace || !is_aligned(workspace, kAlignB)) return LQT_EINVAL;
-    if (workspace_bytes < lqt_batch_workspace_bytes(count)) return LQT_ENOMEM;
     for (int i = 0; i < count; ++i) {
         const lqt_status st = check_item(items[i]);
         if (st != LQT_OK) return st;
     }
-    // descriptors grouped by (n, m)
+    const size_t need = lqt_batch_workspace_bytes(items, count);
+    if (need == 0 || workspace_bytes < need) return LQT_ENOMEM;
+    // descriptors of the one-CTA-per-problem kernel, grouped by (n, m)
     std::vector<BatchDesc> descs;
     descs.reserve(count);
     int offset[kNumBatchVariants + 1] = {0};
@@ -142,16 +169,25 @@ extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t cou
     if (cudaMemsetAsync(base, 0, up(256) + up(64 * sizeof(int)), s) != cudaSuccess)
         return LQT_ECUDA;
     if (count == 0) return LQT_OK;
-    // pageable source: the runtime stages the copy before the call returns
-    if (cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(BatchDesc),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return LQT_ECUDA;
-    for (int v = 0; v < kNumBatchVariants; ++v) {
-        const int c = offset[v + 1] - offset[v];
-        if (c == 0) continue;
-        cudaError_t err = cudaSuccess;
-        kBatchVariants[v].launch(d_desc + offset[v], c, tickets + v, status, s, &err);
-        if (err != cudaSuccess) return LQT_ECUDA;
+    if (!descs.empty()) {
+        // pageable source: the runtime stages the copy before the call returns
+        if (cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(BatchDesc),
+                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return LQT_ECUDA;
+        for (int v = 0; v < kNumBatchVariants; ++v) {
+            const int c = offset[v + 1] - offset[v];
+            if (c == 0) continue;
+            cudaError_t err = cudaSuccess;
+            kBatchVariants[v].launch(d_desc + offset[v], c, tickets + v, status, s, &err);
+            if (err != cudaSuccess) return LQT_ECUDA;
+        }
+    }
+    char* lane_ws = base + head_bytes(count);
+    const size_t lane_bytes = workspace_bytes - head_bytes(count);
+    for (const std::vector<int>& g : lane_groups(items, count)) {
+        const lqt_status st =
+            chain_batch_solve(items, g.data(), (int)g.size(), lane_ws, lane_bytes, status, s);
+        if (st != LQT_OK) return st;
     }
     return LQT_OK;
 }

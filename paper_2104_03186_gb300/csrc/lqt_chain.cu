@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "lqt_chain_api.h"
 
 namespace lqt {
@@ -48,39 +51,6 @@ lqt_status fold_slots(const ChainVariant& v, long long* slots) {
     return LQT_OK;
 }
 
-struct ChainLayout {
-    size_t E, V, FE, X, rp, cp, rTp, x0p, total;
-};
-
-ChainLayout chain_layout(const ChainVariant& v, const lqt_problem* P, int NC, bool refine) {
-    const size_t n = (size_t)P->n, rt = (size_t)v.rtsize, r = (size_t)v.rsize;
-    const size_t nc = (size_t)NC;
-    ChainLayout L;
-    size_t off = kStatusC;
-    L.E = off;
-    off += up_c(nc * (3 * n * n + 2 * n) * rt);
-    L.V = off;
-    off += up_c(nc * (n * n + n) * rt);
-    L.FE = off;
-    off += up_c(nc * (n * n + n) * rt);
-    L.X = off;
-    off += up_c(nc * n * rt);
-    L.rp = L.cp = L.rTp = L.x0p = 0;
-    if (refine) {
-        const size_t T = (size_t)P->T;
-        L.rp = off;
-        off += up_c(T * (size_t)P->p * r);
-        L.cp = off;
-        off += up_c(T * n * r);
-        L.rTp = off;
-        off += up_c((size_t)P->pT * r);
-        L.x0p = off;
-        off += up_c(n * r);
-    }
-    L.total = off;
-    return L;
-}
-
 lqt_status geometry(const ChainVariant& v, const lqt_problem* P, bool sequential, int* NC,
                     long long* B) {
     const long long T = P->T;
@@ -108,61 +78,113 @@ int levels(int NC) {
     return l;
 }
 
+// Chunk geometry of a batch of one variant: a chunk length B* from the
+// total work over the resident fold groups, clamped to [kMinChunk,
+// kMaxBatchChunk] so that no problem's latency grows with the batch; each
+// problem takes the largest power-of-two chunk count with chunks of at least
+// B* steps.  Problems sorted by decreasing chunk count.
+constexpr long long kMaxBatchChunk = 64;
+
+lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, const int* idx,
+                          int count, std::vector<ChainProblem>* out) {
+    long long slots = 0;
+    const lqt_status st = fold_slots(v, &slots);
+    if (st != LQT_OK) return st;
+    long long total = 0;
+    for (int i = 0; i < count; ++i) total += items[idx[i]].problem.T;
+    long long Bt = (total + slots - 1) / (slots > 0 ? slots : 1);
+    if (Bt < kMinChunk) Bt = kMinChunk;
+    if (Bt > kMaxBatchChunk) Bt = kMaxBatchChunk;
+    out->resize((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const lqt_batch_item& it = items[idx[i]];
+        const long long T = it.problem.T;
+        long long nc = 1;
+        while (nc * 2 * Bt <= T && nc < (1LL << 20)) nc *= 2;
+        ChainProblem& cp = (*out)[(size_t)i];
+        cp.problem = &it.problem;
+        cp.solution = &it.solution;
+        cp.NC = (int)nc;
+        cp.B = T > 0 ? (T + nc - 1) / nc : 1;
+    }
+    std::stable_sort(out->begin(), out->end(),
+                     [](const ChainProblem& a, const ChainProblem& b) { return a.NC > b.NC; });
+    return LQT_OK;
+}
+
 }  // namespace
 
 bool chain_supported(int dtype, int n, int m) { return find_chain(dtype, n, m, false) != nullptr; }
 
-lqt_status chain_workspace(const lqt_problem* P, bool refine, bool sequential, size_t* bytes,
-                           int* NC, long long* B, int* kernels) {
-    if (P->p > 2 * P->n) return LQT_EUNSUPPORTED;
-    const bool mixed = refine && P->dtype == LQT_F32;
+lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
+                           size_t* bytes, int* NC, long long* B, int* kernels) {
+    if (P->p > 2 * P->n || P->pT > 2 * P->n) return LQT_EUNSUPPORTED;
+    // FP64 tree levels with the FULL refinement (the Newton step); FP32 otherwise
+    const bool mixed = refine && newton && P->dtype == LQT_F32;
     const ChainVariant* v = find_chain(P->dtype, P->n, P->m, mixed);
     if (!v) return LQT_EUNSUPPORTED;
     int nc = 1;
     long long b = 1;
     const lqt_status st = geometry(*v, P, sequential, &nc, &b);
     if (st != LQT_OK) return st;
-    if (bytes) *bytes = chain_layout(*v, P, nc, refine).total;
+    ChainProblem cp{P, nullptr, nc, b};
+    const bool rf = refine && P->T > 0;
+    if (bytes) *bytes = v->workspace(&cp, 1, rf, rf && newton);
     if (NC) *NC = nc;
     if (B) *B = b;
     if (kernels) {
         const int l = levels(nc);
         const int per_pass = sequential ? 3 : 4 + 4 * l;
-        *kernels = (refine && P->T > 0) ? 2 * per_pass + 1 : per_pass;
+        const int bwd = sequential ? 2 : 3 + 2 * l;
+        int k = 1 + per_pass;  // the item upload, the solve
+        if (rf) k += 1 + 1 + per_pass;  // item upload, KKT residuals, correction solve
+        if (rf && newton) k += 2 + bwd + 2;  // constants, residuals, dS/dv scan, gains, add
+        *kernels = k;
     }
     return LQT_OK;
 }
 
-lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine,
+lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine, bool newton,
                        bool sequential, void* ws, size_t ws_bytes, cudaStream_t s, Prof* prof) {
-    if (P->p > 2 * P->n) return LQT_EUNSUPPORTED;
-    const bool mixed = refine && P->dtype == LQT_F32;
+    if (P->p > 2 * P->n || P->pT > 2 * P->n) return LQT_EUNSUPPORTED;
+    const bool mixed = refine && newton && P->dtype == LQT_F32;
     const ChainVariant* v = find_chain(P->dtype, P->n, P->m, mixed);
     if (!v) return LQT_EUNSUPPORTED;
     int NC = 1;
     long long B = 1;
-    lqt_status st = geometry(*v, P, sequential, &NC, &B);
+    const lqt_status st = geometry(*v, P, sequential, &NC, &B);
     if (st != LQT_OK) return st;
-    const ChainLayout L = chain_layout(*v, P, NC, refine);
-    if (ws_bytes < L.total) return LQT_ENOMEM;
-    char* base = static_cast<char*>(ws);
-    ChainCall call;
-    call.problem = P;
-    call.solution = sol;
-    call.NC = NC;
-    call.B = B;
-    call.refine = refine;
-    call.sequential = sequential;
-    call.status = reinterpret_cast<int*>(base);
-    call.E = base + L.E;
-    call.V = base + L.V;
-    call.FE = base + L.FE;
-    call.X = base + L.X;
-    call.rp = refine ? base + L.rp : nullptr;
-    call.cp = refine ? base + L.cp : nullptr;
-    call.rTp = refine ? base + L.rTp : nullptr;
-    call.x0p = refine ? base + L.x0p : nullptr;
+    ChainProblem cp{P, sol, NC, B};
+    const bool rf = refine && P->T > 0;
+    ChainCall call{&cp, 1, rf, rf && newton, sequential, ws, ws_bytes, nullptr};
     return v->run(call, s, prof);
+}
+
+lqt_status chain_batch_workspace(const lqt_batch_item* items, const int* idx, int count,
+                                 size_t* bytes) {
+    *bytes = 0;
+    if (count <= 0) return LQT_OK;
+    const lqt_problem& P0 = items[idx[0]].problem;
+    const ChainVariant* v = find_chain(LQT_F32, P0.n, P0.m, false);
+    if (!v) return LQT_EUNSUPPORTED;
+    std::vector<ChainProblem> probs;
+    const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
+    if (st != LQT_OK) return st;
+    *bytes = v->workspace(probs.data(), count, false, false);
+    return LQT_OK;
+}
+
+lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int count, void* ws,
+                             size_t ws_bytes, int* status, cudaStream_t s) {
+    if (count <= 0) return LQT_OK;
+    const lqt_problem& P0 = items[idx[0]].problem;
+    const ChainVariant* v = find_chain(LQT_F32, P0.n, P0.m, false);
+    if (!v) return LQT_EUNSUPPORTED;
+    std::vector<ChainProblem> probs;
+    const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
+    if (st != LQT_OK) return st;
+    ChainCall call{probs.data(), count, false, false, false, ws, ws_bytes, status};
+    return v->run(call, s, nullptr);
 }
 
 }  // namespace lqt

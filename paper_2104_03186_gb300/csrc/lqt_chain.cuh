@@ -1,9 +1,14 @@
-// Chunked single-problem pipeline for the lane-group sizes (n = 8, 16, 32).
+// Chunked pipeline for the lane-group sizes (n = 8, 16, 32): one problem
+// (lqt_solve) or a ragged batch of problems of one (n, m) (lqt_solve_batched).
 //
-// The T steps are cut into NC chunks (NC a power of two) of B steps; one lane
-// group of N lanes (lane r owns row r) works on one chunk at a time, and the
-// scans over the NC chunk results run level by level, one launch per level,
-// with the chunk results in global memory.  Per pass:
+// Problem i's T_i steps are cut into NC_i chunks (NC_i a power of two) of B_i
+// steps; one lane group of N lanes (lane r owns row r) works on one chunk at a
+// time, and the scans over the chunk results run level by level, one launch
+// per level, with the chunk results in global memory.  The problems are laid
+// out by decreasing NC_i, problem i's chunks at [c0_i, c0_i + NC_i), so every
+// c0_i is a multiple of NC_i: at tree level h the pairs of all problems with
+// NC_i >= 2h are the pairs (i, i + h), i a multiple of 2h, of one prefix of the
+// chunk array, and the level kernels need no per-problem lookup.  Per pass:
 //   k_cfold    chunk totals a_s (x) ... (x) a_{e-1} (eq. lqt_comb), folded one
 //              step at a time from the end in the low-rank form of fold_step,
 //   k_cup      up-sweep levels of the chunk totals (Alg. 1, left-anchored),
@@ -18,14 +23,28 @@
 //   k_croll    per chunk the rollout of x*_k and u*_k (eq. Control_LQT).
 // The chunk phases compute in R; the tree levels store and compute in RT
 // (RT = double with R = float is the mixed-precision form: FP32 chunk work,
-// FP64 tree levels and their (I + C J) solves).  k_cresid forms the shifted
-// problem of the refinement pass (lqt_refine.cuh).
+// FP64 tree levels and their (I + C J) solves).
+//
+// Refinement (one step of iterative refinement of the KKT system of the QP):
+// k_cresid evaluates, in FP64, the residuals of the optimality conditions at
+// the first pass's iterate (x^, u^, lambda^ with lambda^_k = S_k x^_k - v_k,
+// the gradient of the value function):
+//   e_k = F_k x^_k + c_k + L_k u^_k - x^_{k+1}                    (dynamics)
+//   g_k = H_k^T X_k (H_k x^_k - r_k) + F_k^T lambda^_{k+1} - lambda^_k (d/dx_k)
+//   h_k = U_k u^_k + L_k^T lambda^_{k+1}                             (d/du_k)
+//   g_T = H_T^T X_T (H_T x^_T - r_T) - lambda^_T
+// The correction (dx, du) minimises sum 1/2 dx^T H^T X H dx + g^T dx +
+// 1/2 du^T U du + h^T du subject to dx_{k+1} = F dx_k + L du_k + e_k, dx_0 = 0.
+// With du = w - U^{-1} h this is the LQT problem of Sec. II-B with linear
+// state terms eta_k = -g_k, eta_T = -g_T (no reference), offsets
+// c~_k = e_k - L U^{-1} h_k and control w; the second pass solves it with the
+// same kernels (its S and K equal the first pass's) and adds
+// x = x^ + dx, u = u^ + w - U^{-1} h.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include "lqt_lane_step.cuh"
-#include "lqt_refine.cuh"
 
 namespace lqt {
 namespace chain {
@@ -34,19 +53,72 @@ using namespace lanes;
 
 constexpr int kStatusSingular = 8;  // LQT_ESINGULAR
 
+template <typename R>
+struct Item {
+    DescT<R> D;
+    long long B;   // steps per chunk
+    long long c0;  // first chunk in the chunk arrays (a multiple of NC)
+    long long r0;  // first row of the residual kernel's index space (T + 1 rows each)
+    int NC;        // chunks (a power of two)
+    int pad_;
+    R* u_out;      // correction pass: the output u* (holds u^ until then)
+    const R* qh;   // correction pass: U^{-1} h_k (T x M)
+};
+
 template <typename R, typename RT>
 struct Args {
-    DescT<R> D;
-    long long B;  // steps per chunk
-    int NC;       // chunks (a power of two)
-    RT* E;        // NC chunk totals (LElem)
-    RT* V;        // NC value carries (LValue): the value at each chunk's end
-    RT* FE;       // NC chunk affine maps (LAffine)
-    RT* X;        // NC chunk start states
+    const Item<R>* items;  // count items, by decreasing NC (increasing c0)
+    int count;
+    long long C;     // total chunks
+    RT* E;           // C chunk totals (LElem)
+    RT* V;           // C value carries (LValue): the value at each chunk's end
+    RT* FE;          // C chunk affine maps (LAffine)
+    RT* X;           // C chunk start states
     int* status;
-    int out_mask;    // 1: write S, v, K (the refinement pass does not)
-    int refine_add;  // 1: x <- x + xi (refinement pass)
+    int out_mask;    // bit 1: write S and v; bit 2: write K
+    int refine_add;  // 1: correction pass: x <- x^ + dx, u_out <- u^ + w - qh
 };
+
+// The item whose chunks contain chunk c (items sorted by c0).
+template <typename R>
+__device__ __forceinline__ int find_chunk(const Item<R>* items, int count, long long c) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].c0 <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The item whose residual rows contain row q (items sorted by r0).
+template <typename R>
+__device__ __forceinline__ int find_row(const Item<R>* items, int count, long long q) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].r0 <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The constant matrices of the Newton correction problem: L = 0, U = I, H = I.
+template <typename R, int N, int M>
+__global__ void k_consts(R* L0, R* UI, R* HI) {
+    const int r = threadIdx.x;
+    for (int a = 0; a < M; ++a) L0[r * M + a] = R(0);
+    if (r < M)
+        for (int b = 0; b < M; ++b) UI[r * M + b] = r == b ? R(1) : R(0);
+    for (int j = 0; j < N; ++j) HI[r * N + j] = r == j ? R(1) : R(0);
+}
+
+// Items of a one-problem call, from kernel parameters.
+template <typename R>
+__global__ void k_set_items(Item<R>* d1, Item<R> a, Item<R>* d2, Item<R> b) {
+    *d1 = a;
+    if (d2) *d2 = b;
+}
 
 // ---- shared-memory sizes per group (elements of the kernel's arithmetic type)
 template <int N, int M>
@@ -125,18 +197,21 @@ __global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.NC) return;
+    if (c >= a.C) return;
+    const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
+    const DescT<R>& D = it.D;
     R* gs = sh + gi * S::SIZE;
     R* P = gs + S::P;
     R* sb = gs + S::SB;
     R* scr = gs + S::SCR_OFF;
-    const long long T = a.D.T;
-    const long long s0 = c * a.B < T ? c * a.B : T;
-    const long long e0 = s0 + a.B < T ? s0 + a.B : T;
+    const long long T = D.T;
+    const long long lc = c - it.c0;
+    const long long s0 = lc * it.B < T ? lc * it.B : T;
+    const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     bool ok = true;
     set_neutral<N, N>(P, g);
     for (long long k = e0 - 1; k >= s0; --k) {
-        load_step<R, N, M, false>(a.D, k, sb, scr, g, ok);
+        load_step<R, N, M, false>(D, k, sb, scr, g, ok);
         ok &= fold_step<R, N, M>(P, sb, scr, g);
     }
     RT* out = a.E + c * E::SIZE;
@@ -145,15 +220,16 @@ __global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
 }
 
 // ---- up-sweep level h: E[i] <- E[i] (x) E[i + h], i a multiple of 2h -------
+// (i < active: the chunks of the problems with NC >= 2h)
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cup(RT* E_, int NC, int h, int* status) {
+__global__ void __launch_bounds__(NG* N) k_cup(RT* E_, long long active, int h, int* status) {
     using E = LElem<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
-    if (i + h >= NC) return;
+    if (i >= active) return;
     RT* e1 = sh + gi * UpSmem<N>::SIZE;
     RT* e2 = e1 + E::SIZE;
     RT* scr = e2 + E::SIZE;
@@ -166,38 +242,59 @@ __global__ void __launch_bounds__(NG* N) k_cup(RT* E_, int NC, int h, int* statu
     flag(status, ok);
 }
 
-// ---- terminal value into V[0] (and S_T, v_T) -------------------------------
+// ---- terminal values (one CTA of N threads per problem): V[c0] <- the value
+// element (H_T^T X_T r_T, H_T^T X_T H_T), S_T, v_T, and X[c0 + NC - 1] <- x_0
 template <typename R, typename RT, int N>
 __global__ void __launch_bounds__(N) k_cterm(Args<R, RT> a) {
-    const DescT<R>& D = a.D;
+    __shared__ RT Y[2 * N * N + 2 * N];  // X_T H_T (pT x N) and X_T r_T, pT <= 2N
+    const Item<R>& it = a.items[blockIdx.x];
+    const DescT<R>& D = it.D;
     const int r = threadIdx.x;
+    const int pT = D.pT;
+    RT* xr = Y + 2 * N * N;
+    for (int i = r; i < pT; i += N) {
+        RT acc[N];
+        RT t0 = RT(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = RT(0);
+        for (int b = 0; b < pT; ++b) {
+            const RT xib = static_cast<RT>(D.XT[i * pT + b]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += xib * static_cast<RT>(D.HT[b * N + j]);
+            if (D.rT) t0 += xib * static_cast<RT>(D.rT[b]);
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) Y[i * N + j] = acc[j];
+        xr[i] = t0;
+    }
+    __syncthreads();
     RT acc[N];
     RT t = RT(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = RT(0);
-    for (int i = 0; i < D.pT; ++i) {
+    for (int i = 0; i < pT; ++i) {
         const RT hi = static_cast<RT>(D.HT[i * N + r]);
-        for (int b = 0; b < D.pT; ++b) {
-            const RT hx = hi * static_cast<RT>(D.XT[i * D.pT + b]);
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += hx * static_cast<RT>(D.HT[b * N + j]);
-            if (D.rT) t += hx * static_cast<RT>(D.rT[b]);
-        }
+        for (int j = 0; j < N; ++j) acc[j] += hi * Y[i * N + j];
+        t += hi * xr[i];
     }
-    RT* val = a.V;
+    if (D.etaT) t = static_cast<RT>(D.etaT[r]);
+    RT* val = a.V + it.c0 * LValue<N>::SIZE;
 #pragma unroll
     for (int j = 0; j < N; ++j) val[LValue<N>::OS + r * N + j] = acc[j];
     val[LValue<N>::OV + r] = t;
-    if (a.out_mask) {
+    a.X[(it.c0 + it.NC - 1) * N + r] = static_cast<RT>(D.x0[r]);
+    if (a.out_mask & 1) {
 #pragma unroll
         for (int j = 0; j < N; ++j) D.S[D.T * N * N + r * N + j] = static_cast<R>(acc[j]);
         D.v[D.T * N + r] = static_cast<R>(t);
     }
+    if (D.T == 0) D.x[r] = D.x0[r];
 }
 
 // ---- down-sweep level h: V[i + h] <- V[i]; V[i] <- E[i + h] (x) V[i] --------
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, int NC, int h,
+__global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, long long active, int h,
                                                  int* status) {
     using E = LElem<N>;
     using V = LValue<N>;
@@ -206,7 +303,7 @@ __global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, int NC, i
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
-    if (i + h >= NC) return;
+    if (i >= active) return;
     RT* e = sh + gi * DownSmem<N>::SIZE;
     RT* val = e + E::SIZE;
     RT* scr = val + V::SIZE;
@@ -230,8 +327,9 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.NC) return;
-    const DescT<R>& D = a.D;
+    if (c >= a.C) return;
+    const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
+    const DescT<R>& D = it.D;
     R* gs = sh + gi * S::SIZE;
     R* val = gs + S::VAL;
     R* Phi = gs + S::PHI;
@@ -241,8 +339,9 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     R* Ft = Kd + M * (N + 1);
     const int r = g.lr;
     const long long T = D.T;
-    const long long s0 = c * a.B < T ? c * a.B : T;
-    const long long e0 = s0 + a.B < T ? s0 + a.B : T;
+    const long long lc = c - it.c0;
+    const long long s0 = lc * it.B < T ? lc * it.B : T;
+    const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     copy_in(val, a.V + c * V::SIZE, V::SIZE, r, N);
 #pragma unroll
     for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = r == j ? R(1) : R(0);
@@ -252,13 +351,13 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     for (long long k = e0 - 1; k >= s0; --k) {
         load_step<R, N, M, false>(D, k, sb, scr, g, ok);
         ok &= riccati<R, N, M>(val, sb, Kd, Ft, scr, g);
-        if (a.out_mask) {
+        if (a.out_mask & 1) {
 #pragma unroll
             for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * N + j];
             D.v[k * N + r] = val[V::OV + r];
         }
         if (r < M) {
-            if (a.out_mask) {
+            if (a.out_mask & 2) {
 #pragma unroll
                 for (int j = 0; j < N; ++j) D.K[k * M * N + r * N + j] = Kd[r * (N + 1) + j];
             }
@@ -289,14 +388,14 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
 
 // ---- forward up-sweep level h: FE[j] <- FE[j] o FE[j - h], j = 2h q + 2h - 1
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, int NC, int h) {
+__global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, long long active, int h) {
     using A = LAffine<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
-    if (j >= NC) return;
+    if (j >= active) return;
     RT* f1 = sh + gi * FupSmem<N>::SIZE;
     RT* f2 = f1 + A::SIZE;
     copy_in(f1, FE + (j - h) * A::SIZE, A::SIZE, g.lr, N);
@@ -307,21 +406,21 @@ __global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, int NC, int h) {
 }
 
 // ---- forward down-sweep level h: X[j - h] <- X[j]; X[j] <- FE[j - h](X[j]) -
-template <typename R, typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, const R* x0, int NC, int h,
-                                                  int top) {
+// (each problem's top slot X[c0 + NC - 1] holds x_0 from k_cterm)
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, long long active, int h) {
     using A = LAffine<N>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
-    if (j >= NC) return;
+    if (j >= active) return;
     RT* f = sh + gi * FdownSmem<N>::SIZE;
     RT* x = f + A::SIZE;
     const int r = g.lr;
     copy_in(f, FE + (j - h) * A::SIZE, A::SIZE, r, N);
-    const RT xv = top ? static_cast<RT>(x0[r]) : X[j * N + r];
+    const RT xv = X[j * N + r];
     x[r] = xv;
     X[(j - h) * N + r] = xv;
     g.sync();
@@ -337,15 +436,17 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.NC) return;
-    const DescT<R>& D = a.D;
+    if (c >= a.C) return;
+    const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
+    const DescT<R>& D = it.D;
     R* xc = sh + gi * RollSmem<N, M>::SIZE;
     R* us = xc + N;
     const int r = g.lr;
     const long long T = D.T;
-    const long long s0 = c * a.B < T ? c * a.B : T;
-    const long long e0 = s0 + a.B < T ? s0 + a.B : T;
-    xc[r] = c == 0 ? D.x0[r] : static_cast<R>(a.X[c * N + r]);
+    const long long lc = c - it.c0;
+    const long long s0 = lc * it.B < T ? lc * it.B : T;
+    const long long e0 = s0 + it.B < T ? s0 + it.B : T;
+    xc[r] = lc == 0 ? D.x0[r] : static_cast<R>(a.X[c * N + r]);
     g.sync();
     for (long long k = s0; k < e0; ++k) {
         const R* F = D.F + k * D.sF;
@@ -358,7 +459,10 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
 #pragma unroll
             for (int j = 0; j < N; ++j) t -= D.K[k * M * N + r * N + j] * xc[j];
             us[r] = t;
-            D.u[k * M + r] = t;
+            if (a.refine_add)
+                it.u_out[k * M + r] = it.u_out[k * M + r] + (t - it.qh[k * M + r]);
+            else
+                D.u[k * M + r] = t;
         }
         g.sync();
         R t = D.c ? D.c[k * D.sc + r] : R(0);
@@ -371,42 +475,272 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
         g.sync();
         if (k == T - 1) D.x[T * N + r] = a.refine_add ? D.x[T * N + r] + t : t;
     }
-    if (T == 0 && c == 0) D.x[r] = D.x0[r];
 }
 
-// ---- shifted problem of the refinement pass ---------------------------------
-// Step k (one group per step, k = 0..T; k = T forms r'_T and x'_0):
-//   r'_k = r_k - H_k x^_k,  c'_k = F_k x^_k + c_k - x^_{k+1}
-// as compensated dot products (Dot2) of the first pass's trajectory x^.
-template <typename R, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cresid(DescT<R> D, R* rp, R* cp, R* rTp, R* x0p) {
+// ---- KKT residuals of the first pass's iterate (refinement) -----------------
+// One group per step k = 0..T (k = T: the terminal condition and x'_0 = 0),
+// all arithmetic in FP64 (products of FP32 inputs are exact in FP64).
+template <int N, int M>
+struct ResidSmem {
+    static constexpr int PMAX = 2 * N;
+    static constexpr int XK = 0, XK1 = N, UK = 2 * N, L0 = 2 * N + M, L1 = 3 * N + M,
+                         HX = 4 * N + M, Y = HX + PMAX, UM = Y + PMAX, RH = UM + M * M,
+                         SIZE = RH + M;
+};
+
+template <typename R, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const Item<R>* items2,
+                                                  int count, long long rows, int* status) {
+    using S = ResidSmem<N, M>;
+    using D64 = double;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    const long long T = D.T;
+    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    D64* xk = sh + S::XK;
+    D64* xk1 = sh + S::XK1;
+    D64* uk = sh + S::UK;
+    D64* lam0 = sh + S::L0;
+    D64* lam1 = sh + S::L1;
+    D64* hx = sh + S::HX;
+    D64* y = sh + S::Y;
+    D64* Um = sh + S::UM;
+    D64* rh = sh + S::RH;
     const long long stride = (long long)gridDim.x * NG;
-    for (long long k = (long long)blockIdx.x * NG + gi; k <= T; k += stride) {
-        const R* xk = D.x + k * N;
-        if (k == T) {
-            for (int i = r; i < D.pT; i += N) {
-                Dot2<R> d(D.rT ? D.rT[i] : R(0));
-                for (int j = 0; j < N; ++j) d.add_prod(-D.HT[i * N + j], xk[j]);
-                rTp[i] = d.value();
+    bool ok = true;
+    for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
+        const int ii = find_row(items1, count, q);
+        const DescT<R>& D = items1[ii].D;
+        const DescT<R>& D2 = items2[ii].D;
+        const long long k = q - items1[ii].r0;
+        const long long T = D.T;
+        const bool term = k == T;
+        const int p = term ? D.pT : D.p;
+        const R* H = term ? D.HT : D.H + k * D.sH;
+        const R* X = term ? D.XT : D.X + k * D.sX;
+        const R* rr = term ? D.rT : (D.r ? D.r + k * D.sr : nullptr);
+        xk[r] = static_cast<D64>(D.x[k * N + r]);
+        if (!term) {
+            xk1[r] = static_cast<D64>(D.x[(k + 1) * N + r]);
+            if (r < M) uk[r] = static_cast<D64>(D.u[k * M + r]);
+        }
+        g.sync();
+        // lambda^_k = S_k x^_k - v_k (and lambda^_{k+1}); H x^ - r
+        {
+            const R* Sk = D.S + k * N * N;
+            D64 t = -static_cast<D64>(D.v[k * N + r]);
+            for (int j = 0; j < N; ++j) t += static_cast<D64>(Sk[r * N + j]) * xk[j];
+            lam0[r] = t;
+            if (!term) {
+                const R* Sk1 = Sk + N * N;
+                D64 t1 = -static_cast<D64>(D.v[(k + 1) * N + r]);
+                for (int j = 0; j < N; ++j) t1 += static_cast<D64>(Sk1[r * N + j]) * xk1[j];
+                lam1[r] = t1;
             }
-            x0p[r] = R(0);
+            for (int i = r; i < p; i += N) {
+                D64 h = rr ? -static_cast<D64>(rr[i]) : 0.0;
+                for (int j = 0; j < N; ++j) h += static_cast<D64>(H[i * N + j]) * xk[j];
+                hx[i] = h;
+            }
+        }
+        g.sync();
+        for (int i = r; i < p; i += N) {
+            D64 t = 0.0;
+            for (int b = 0; b < p; ++b) t += static_cast<D64>(X[i * p + b]) * hx[b];
+            y[i] = t;
+        }
+        g.sync();
+        // g = H^T X (H x^ - r) - lambda^_k (+ F^T lambda^_{k+1})
+        D64 gr = -lam0[r];
+        for (int i = 0; i < p; ++i) gr += static_cast<D64>(H[i * N + r]) * y[i];
+        if (term) {
+            const_cast<R*>(D2.etaT)[r] = static_cast<R>(-gr);
+            const_cast<R*>(D2.x0)[r] = R(0);
+            g.sync();
             continue;
         }
-        const R* H = D.H + k * D.sH;
-        for (int i = r; i < D.p; i += N) {
-            Dot2<R> d(D.r ? D.r[k * D.sr + i] : R(0));
-            for (int j = 0; j < N; ++j) d.add_prod(-H[i * N + j], xk[j]);
-            rp[k * D.p + i] = d.value();
-        }
         const R* F = D.F + k * D.sF;
-        Dot2<R> d(D.c ? D.c[k * D.sc + r] : R(0));
-        for (int j = 0; j < N; ++j) d.add_prod(F[r * N + j], xk[j]);
-        d.add(-xk[N + r]);
-        cp[k * N + r] = d.value();
+        const R* L = D.L + k * D.sL;
+        const R* U = D.U + k * D.sU;
+        for (int j = 0; j < N; ++j) gr += static_cast<D64>(F[j * N + r]) * lam1[j];
+        // e = F x^ + c + L u^ - x^_{k+1}
+        D64 e = (D.c ? static_cast<D64>(D.c[k * D.sc + r]) : 0.0) - xk1[r];
+        for (int j = 0; j < N; ++j) e += static_cast<D64>(F[r * N + j]) * xk[j];
+        for (int b = 0; b < M; ++b) e += static_cast<D64>(L[r * M + b]) * uk[b];
+        // h = U u^ + L^T lambda^_{k+1}; U^{-1} h
+        if (r < M) {
+            D64 h = 0.0;
+            for (int b = 0; b < M; ++b) {
+                const D64 ub = static_cast<D64>(U[r * M + b]);
+                Um[r * M + b] = ub;
+                h += ub * uk[b];
+            }
+            for (int j = 0; j < N; ++j) h += static_cast<D64>(L[j * M + r]) * lam1[j];
+            rh[r] = h;
+        }
+        g.sync();
+        ok &= solve_gj<N, M, 1>(Um, M, rh, 1, g);
+        for (int b = 0; b < M; ++b) e -= static_cast<D64>(L[r * M + b]) * rh[b];
+        const_cast<R*>(D2.eta)[k * N + r] = static_cast<R>(-gr);
+        const_cast<R*>(D2.c)[k * N + r] = static_cast<R>(e);
+        if (r < M) const_cast<R*>(items2[ii].qh)[k * M + r] = static_cast<R>(rh[r]);
+        g.sync();
+    }
+    flag(status, ok);
+}
+
+// ---- Newton step of the Riccati recursion (refinement of S, v and K) -------
+// At the first pass's (S^, v^) the Riccati map of Sec. II-B has residuals
+//   R_k = Ric_k(S^_{k+1}) - S^_k,  rho_k = Vrec_k(S^_{k+1}, v^_{k+1}) - v^_k,
+//   R_T = H_T^T X_T H_T - S^_T,    rho_T = H_T^T X_T r_T - v^_T,
+// and its derivative at S^ is dS -> Phi_k^T dS Phi_k with the closed loop
+// Phi_k = F_k - L_k K_k (and dv -> Phi_k^T (dv - dS ct_k), ct_k = c_k + L_k d_k).
+// The Newton correction (dS, dv) therefore follows
+//   dS_k = Phi_k^T dS_{k+1} Phi_k + R_k,  dv_k = Phi_k^T (dv_{k+1} - dS_{k+1} ct_k) + rho_k,
+// which is the value recursion of the same operator for step elements with
+// A = Phi_k, b = ct_k, C = 0, J = R_k, eta = rho_k: the pipeline solves it as the
+// LQT problem F = Phi, c = ct, L = 0, U = I, H = I, X_k = R_k, eta_k = rho_k.
+// k_nresid forms that problem (FP64 arithmetic, stored in R); k_ngains
+// recomputes K_k in FP64 from S^_{k+1} + dS_{k+1}; k_nadd adds the corrections.
+template <int N, int M>
+struct NewtonSmem {  // double: val | step | riccati scratch | Kd | Ft
+    static constexpr int VAL = 0;
+    static constexpr int SB = LValue<N>::SIZE;
+    static constexpr int SCR = SB + StepLayout<N, M>::SIZE;
+    static constexpr int KD = SCR + riccati_scratch<N, M>();
+    static constexpr int FT = KD + M * (N + 1);
+    static constexpr int SIZE = FT + LAffine<N>::SIZE;
+};
+
+template <typename R, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_nresid(const Item<R>* items1, const Item<R>* items3,
+                                                  int count, long long rows, int* status) {
+    using S = NewtonSmem<N, M>;
+    using V = LValue<N>;
+    using A = LAffine<N>;
+    using D64 = double;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const int r = g.lr;
+    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    D64* val = sh + S::VAL;
+    D64* sb = sh + S::SB;
+    D64* scr = sh + S::SCR;
+    D64* Kd = sh + S::KD;
+    D64* Ft = sh + S::FT;
+    const long long stride = (long long)gridDim.x * NG;
+    bool ok = true;
+    for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
+        const int ii = find_row(items1, count, q);
+        const DescT<R>& D = items1[ii].D;
+        const DescT<R>& D3 = items3[ii].D;
+        const long long k = q - items1[ii].r0;
+        const long long T = D.T;
+        R* Rk = const_cast<R*>(D3.X) + k * N * N;
+        if (k == T) {
+            D64 acc[N];
+            D64 t = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = 0.0;
+            for (int i = 0; i < D.pT; ++i) {
+                const D64 hi = static_cast<D64>(D.HT[i * N + r]);
+                for (int b = 0; b < D.pT; ++b) {
+                    const D64 hx = hi * static_cast<D64>(D.XT[i * D.pT + b]);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) acc[j] += hx * static_cast<D64>(D.HT[b * N + j]);
+                    if (D.rT) t += hx * static_cast<D64>(D.rT[b]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+                Rk[r * N + j] = static_cast<R>(acc[j] - static_cast<D64>(D.S[T * N * N + r * N + j]));
+            const_cast<R*>(D3.etaT)[r] = static_cast<R>(t - static_cast<D64>(D.v[T * N + r]));
+            continue;
+        }
+        load_step<D64, N, M, false, R>(D, k, sb, scr, g, ok);
+        copy_in(val + V::OS, D.S + (k + 1) * N * N, N * N, r, N);
+        copy_in(val + V::OV, D.v + (k + 1) * N, N, r, N);
+        g.sync();
+        ok &= riccati<D64, N, M>(val, sb, Kd, Ft, scr, g);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            Rk[r * N + j] = static_cast<R>(val[V::OS + r * N + j] -
+                                           static_cast<D64>(D.S[k * N * N + r * N + j]));
+            const_cast<R*>(D3.F)[k * N * N + r * N + j] = static_cast<R>(Ft[A::OF + r * N + j]);
+        }
+        const_cast<R*>(D3.eta)[k * N + r] =
+            static_cast<R>(val[V::OV + r] - static_cast<D64>(D.v[k * N + r]));
+        const_cast<R*>(D3.c)[k * N + r] = static_cast<R>(Ft[A::OC + r]);
+        g.sync();
+    }
+    flag(status, ok);
+}
+
+// K_k from S_{k+1} = S^_{k+1} + dS_{k+1}, v_{k+1} = v^_{k+1} + dv_{k+1} (FP64).
+template <typename R, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const Item<R>* items3,
+                                                  int count, long long rows, int* status) {
+    using S = NewtonSmem<N, M>;
+    using V = LValue<N>;
+    using D64 = double;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const int r = g.lr;
+    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    D64* val = sh + S::VAL;
+    D64* sb = sh + S::SB;
+    D64* scr = sh + S::SCR;
+    D64* Kd = sh + S::KD;
+    const long long stride = (long long)gridDim.x * NG;
+    bool ok = true;
+    for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
+        const int ii = find_row(items1, count, q);
+        const DescT<R>& D = items1[ii].D;
+        const DescT<R>& D3 = items3[ii].D;
+        const long long k = q - items1[ii].r0;
+        if (k == D.T) continue;
+        load_step<D64, N, M, false, R, false>(D, k, sb, scr, g, ok);
+        const R* S1 = D.S + (k + 1) * N * N;
+        const R* dS1 = D3.S + (k + 1) * N * N;
+        for (int i = r; i < N * N; i += N)
+            val[V::OS + i] = static_cast<D64>(S1[i]) + static_cast<D64>(dS1[i]);
+        val[V::OV + r] = static_cast<D64>(D.v[(k + 1) * N + r]) +
+                         static_cast<D64>(D3.v[(k + 1) * N + r]);
+        g.sync();
+        ok &= gains<D64, N, M>(val, sb, Kd, scr, g);
+        if (r < M) {
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+                D.K[k * M * N + r * N + j] = static_cast<R>(Kd[r * (N + 1) + j]);
+        }
+        g.sync();
+    }
+    flag(status, ok);
+}
+
+// S_k <- S^_k + dS_k, v_k <- v^_k + dv_k for every problem (one thread per value).
+template <typename R, int N>
+__global__ void k_nadd(const Item<R>* items1, const Item<R>* items3, int count, long long rows) {
+    const long long per = (long long)N * N + N;
+    const long long total = rows * per;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long q = t / per;
+        const long long e = t - q * per;
+        const int ii = find_row(items1, count, q);
+        const DescT<R>& D = items1[ii].D;
+        const DescT<R>& D3 = items3[ii].D;
+        const long long k = q - items1[ii].r0;
+        if (e < (long long)N * N) {
+            const long long o = k * N * N + e;
+            D.S[o] = static_cast<R>(static_cast<double>(D.S[o]) + static_cast<double>(D3.S[o]));
+        } else {
+            const long long o = k * N + (e - (long long)N * N);
+            D.v[o] = static_cast<R>(static_cast<double>(D.v[o]) + static_cast<double>(D3.v[o]));
+        }
     }
 }
 

@@ -1,5 +1,5 @@
-// Internal interface between the C ABI (lqt_api.cu, lqt_chain.cu) and the
-// compiled variants of the chunked single-problem pipeline (lqt_chain.cuh).
+// Internal interface between the C ABI (lqt_api.cu, lqt_batch.cu, lqt_chain.cu)
+// and the compiled variants of the chunked pipeline (lqt_chain.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,23 +12,29 @@
 
 namespace lqt {
 
-// One solve as the launcher sees it: the problem, its outputs and the
-// workspace regions, all device pointers.
-struct ChainCall {
+// One problem of a chain call with its chunk geometry.
+struct ChainProblem {
     const lqt_problem* problem;
     const lqt_solution* solution;
     int NC;       // chunks (power of two)
     long long B;  // steps per chunk
-    bool refine, sequential;
-    int* status;
-    void *E, *V, *FE, *X;          // tree elements, carries, affine maps, start states (RT)
-    void *rp, *cp, *rTp, *x0p;     // shifted data of the refinement pass (R)
+};
+
+// A call: problems of one variant, by decreasing NC; the workspace starts
+// with the status word.
+struct ChainCall {
+    const ChainProblem* probs;
+    int count;
+    bool refine, newton, sequential;
+    void* ws;
+    size_t ws_bytes;
+    int* status;  // device status word (nullptr: the first word of ws)
 };
 
 struct ChainVariant {
     int dtype, n, m;
     int mixed;         // FP32 chunk work with FP64 tree levels
-    int rsize, rtsize; // bytes of R and RT
+    size_t (*workspace)(const ChainProblem* probs, int count, bool refine, bool newton);
     lqt_status (*run)(const ChainCall& call, cudaStream_t s, Prof* prof);
     const void* (*fold_kernel)();
     size_t (*fold_smem)();
@@ -71,14 +77,23 @@ DescT<R> make_desc(const lqt_problem* P, const lqt_solution* S) {
     d.K = static_cast<R*>(S->K);
     d.x = static_cast<R*>(S->x);
     d.u = static_cast<R*>(S->u);
+    d.eta = nullptr;
+    d.seta = 0;
+    d.etaT = nullptr;
     return d;
 }
 
 // Chain path entry points used by the C ABI (lqt_chain.cu).
 bool chain_supported(int dtype, int n, int m);
-lqt_status chain_workspace(const lqt_problem* P, bool refine, bool sequential, size_t* bytes,
-                           int* NC, long long* B, int* kernels);
-lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine,
+// Single problem: workspace bytes, chunk geometry and kernel launches.
+lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
+                           size_t* bytes, int* NC, long long* B, int* kernels);
+lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine, bool newton,
                        bool sequential, void* ws, size_t ws_bytes, cudaStream_t s, Prof* prof);
+// Batch of problems of one FP32 (n, m), no refinement: items[idx[0..count)].
+lqt_status chain_batch_workspace(const lqt_batch_item* items, const int* idx, int count,
+                                 size_t* bytes);
+lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int count, void* ws,
+                             size_t ws_bytes, int* status, cudaStream_t s);
 
 }  // namespace lqt

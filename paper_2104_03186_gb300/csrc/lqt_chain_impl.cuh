@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <string.h>
+
+#include <vector>
 
 #include "lqt_chain.cuh"
 #include "lqt_chain_api.h"
@@ -39,6 +42,9 @@ struct Launcher {
     static constexpr int NG_FUP = groups_for<N>(FUP_B);
     static constexpr int NG_FDOWN = groups_for<N>(FDOWN_B);
     static constexpr int NG_ROLL = groups_for<N>(ROLL_B);
+    static constexpr int RESID_B = ResidSmem<N, M>::SIZE * (int)sizeof(double);
+    static constexpr int NEWTON_B = NewtonSmem<N, M>::SIZE * (int)sizeof(double);
+    static constexpr int NG_NEWTON = groups_for<N>(NEWTON_B);
     static constexpr int NG_RESID = 256 / N;
 
     static cudaError_t prepare() {
@@ -55,88 +61,306 @@ struct Launcher {
                 cudaSuccess ||
             (e = chain_allow_smem(k_cfup<RT, N, NG_FUP>, d_fup, (size_t)NG_FUP * FUP_B)) !=
                 cudaSuccess ||
-            (e = chain_allow_smem(k_cfdown<R, RT, N, NG_FDOWN>, d_fdown,
+            (e = chain_allow_smem(k_cfdown<RT, N, NG_FDOWN>, d_fdown,
                                   (size_t)NG_FDOWN * FDOWN_B)) != cudaSuccess)
+            return e;
+        static bool d_nres[64], d_ngain[64];
+        if ((e = chain_allow_smem(k_nresid<R, N, M, NG_NEWTON>, d_nres,
+                                  (size_t)NG_NEWTON * NEWTON_B)) != cudaSuccess ||
+            (e = chain_allow_smem(k_ngains<R, N, M, NG_NEWTON>, d_ngain,
+                                  (size_t)NG_NEWTON * NEWTON_B)) != cudaSuccess)
             return e;
         return chain_allow_smem(k_croll<R, RT, N, M, NG_ROLL>, d_roll, (size_t)NG_ROLL * ROLL_B);
     }
 
     static int blocks(long long items, int ng) { return (int)((items + ng - 1) / ng); }
 
-    // One pass: backward scan, re-fold, forward scan, rollout.
-    static void pass(const Args<R, RT>& a, bool sequential, bool refine_pass, cudaStream_t s,
-                     Prof* prof) {
-        const int NC = a.NC;
+    // Workspace layout of a call (bytes from the start of the workspace).
+    struct Layout {
+        size_t items1, items2, items3, consts, E, V, FE, X, refine0, total;
+        long long C;
+    };
+
+    static size_t up(size_t x) { return (x + 255) / 256 * 256; }
+
+    static Layout layout(const ChainProblem* probs, int count, bool refine, bool newton) {
+        Layout L;
+        long long C = 0;
+        for (int i = 0; i < count; ++i) C += probs[i].NC;
+        L.C = C;
+        size_t off = 256;  // status word
+        L.items1 = off;
+        off += up((size_t)count * sizeof(Item<R>));
+        L.items2 = off;
+        if (refine) off += up((size_t)count * sizeof(Item<R>));
+        L.items3 = off;
+        if (newton) off += up((size_t)count * sizeof(Item<R>));
+        // the linear problem's constant matrices: L = 0 (N x M), U = I (M x M), H = I
+        L.consts = off;
+        if (newton) off += up((size_t)(N * M + M * M + N * N) * sizeof(R));
+        const size_t nc = (size_t)C;
+        L.E = off;
+        off += up(nc * LElem<N>::SIZE * sizeof(RT));
+        L.V = off;
+        off += up(nc * LValue<N>::SIZE * sizeof(RT));
+        L.FE = off;
+        off += up(nc * LAffine<N>::SIZE * sizeof(RT));
+        L.X = off;
+        off += up(nc * N * sizeof(RT));
+        L.refine0 = off;
+        if (refine)
+            for (int i = 0; i < count; ++i)
+                off += kkt_bytes(probs[i].problem->T) +
+                       (newton ? newton_bytes(probs[i].problem->T) : 0);
+        L.total = off;
+        return L;
+    }
+
+    // per problem, KKT correction: eta T x N, c~ T x N, U^{-1} h T x M,
+    // feedforward T x M, eta_T N, x'_0 N; Newton correction: Phi T x N x N,
+    // ct T x N, R (T + 1) x N x N, rho (T + 1) x N, dS (T + 1) x N x N, dv (T + 1) x N
+    static size_t kkt_bytes(long long T) {
+        const size_t t = (size_t)T;
+        return 2 * up(t * N * sizeof(R)) + 2 * up(t * M * sizeof(R)) + 2 * up(N * sizeof(R));
+    }
+    static size_t newton_bytes(long long T) {
+        const size_t t = (size_t)T;
+        return up(t * N * N * sizeof(R)) + up(t * N * sizeof(R)) +
+               2 * up((t + 1) * N * N * sizeof(R)) + 2 * up((t + 1) * N * sizeof(R));
+    }
+    // The correction problem of the KKT refinement: same matrices, linear state
+    // terms eta, offsets c~, no references, dx_0 = 0; its feedforward goes to
+    // dbuf and the rollout adds the correction into x and u.
+    static void set_correction(Item<R>& b, const Item<R>& a, R* eta, R* ctil, R* etaT, R* qh,
+                               R* dbuf, R* x0p) {
+        b = a;
+        b.D.r = nullptr;
+        b.D.rT = nullptr;
+        b.D.c = ctil;
+        b.D.sc = N;
+        b.D.eta = eta;
+        b.D.seta = N;
+        b.D.etaT = etaT;
+        b.D.x0 = x0p;
+        b.D.u = dbuf;
+        b.u_out = a.D.u;
+        b.qh = qh;
+    }
+
+    static size_t workspace(const ChainProblem* probs, int count, bool refine, bool newton) {
+        return layout(probs, count, refine, newton).total;
+    }
+
+    // Kernel names for the profile, by pass: the solve, the correction pass of
+    // the KKT refinement, the Newton correction of S and v.
+    static const char* pname(int kind, int phase) {
+        static const char* names[3][6] = {
+            {"chain_fold", "chain_up", "chain_down", "chain_refold", "chain_fwd", "chain_roll"},
+            {"chain_fold.refine", "chain_up.refine", "chain_down.refine", "chain_refold.refine",
+             "chain_fwd.refine", "chain_roll.refine"},
+            {"chain_fold.newton", "chain_up.newton", "chain_down.newton", "chain_refold.newton",
+             "chain_fwd.newton", "chain_roll.newton"}};
+        return names[kind][phase];
+    }
+
+    // One pass: backward scan, re-fold, then (unless backward_only) the forward
+    // scan and the rollout.
+    static void pass(const Args<R, RT>& a, const long long* active, int levels, bool sequential,
+                     int kind, bool backward_only, cudaStream_t s, Prof* prof) {
+        const long long C = a.C;
         if (!sequential) {
-            prof_mark(prof, s, refine_pass ? "chain_fold.refine" : "chain_fold");
+            prof_mark(prof, s, pname(kind, 0));
             k_cfold<R, RT, N, M, NG_FOLD>
-                <<<blocks(NC, NG_FOLD), NG_FOLD * N, (size_t)NG_FOLD * FOLD_B, s>>>(a);
-            if (NC > 1) prof_mark(prof, s, refine_pass ? "chain_up.refine" : "chain_up");
-            for (int h = 1; h < NC; h *= 2)
-                k_cup<RT, N, NG_UP><<<blocks(NC / (2 * h), NG_UP), NG_UP * N,
-                                      (size_t)NG_UP * UP_B, s>>>(a.E, NC, h, a.status);
+                <<<blocks(C, NG_FOLD), NG_FOLD * N, (size_t)NG_FOLD * FOLD_B, s>>>(a);
+            if (levels > 0) prof_mark(prof, s, pname(kind, 1));
+            for (int l = 0; l < levels; ++l) {
+                const int h = 1 << l;
+                k_cup<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
+                                      (size_t)NG_UP * UP_B, s>>>(a.E, active[l], h, a.status);
+            }
         }
-        prof_mark(prof, s, refine_pass ? "chain_down.refine" : "chain_down");
-        k_cterm<R, RT, N><<<1, N, 0, s>>>(a);
-        for (int h = NC / 2; h >= 1; h /= 2)
-            k_cdown<RT, N, NG_DOWN><<<blocks(NC / (2 * h), NG_DOWN), NG_DOWN * N,
-                                      (size_t)NG_DOWN * DOWN_B, s>>>(a.E, a.V, NC, h, a.status);
-        prof_mark(prof, s, refine_pass ? "chain_refold.refine" : "chain_refold");
+        prof_mark(prof, s, pname(kind, 2));
+        k_cterm<R, RT, N><<<a.count, N, 0, s>>>(a);
+        for (int l = levels - 1; l >= 0; --l) {
+            const int h = 1 << l;
+            k_cdown<RT, N, NG_DOWN><<<blocks(active[l] / (2 * h), NG_DOWN), NG_DOWN * N,
+                                      (size_t)NG_DOWN * DOWN_B, s>>>(a.E, a.V, active[l], h,
+                                                                     a.status);
+        }
+        prof_mark(prof, s, pname(kind, 3));
         k_crefold<R, RT, N, M, NG_REFOLD>
-            <<<blocks(NC, NG_REFOLD), NG_REFOLD * N, (size_t)NG_REFOLD * REFOLD_B, s>>>(a);
-        if (NC > 1) {
-            prof_mark(prof, s, refine_pass ? "chain_fwd.refine" : "chain_fwd");
-            for (int h = 1; h < NC; h *= 2)
-                k_cfup<RT, N, NG_FUP><<<blocks(NC / (2 * h), NG_FUP), NG_FUP * N,
-                                        (size_t)NG_FUP * FUP_B, s>>>(a.FE, NC, h);
-            for (int h = NC / 2; h >= 1; h /= 2)
-                k_cfdown<R, RT, N, NG_FDOWN><<<blocks(NC / (2 * h), NG_FDOWN), NG_FDOWN * N,
-                                               (size_t)NG_FDOWN * FDOWN_B, s>>>(
-                    a.FE, a.X, a.D.x0, NC, h, h == NC / 2 ? 1 : 0);
+            <<<blocks(C, NG_REFOLD), NG_REFOLD * N, (size_t)NG_REFOLD * REFOLD_B, s>>>(a);
+        if (backward_only) return;
+        if (levels > 0) {
+            prof_mark(prof, s, pname(kind, 4));
+            for (int l = 0; l < levels; ++l) {
+                const int h = 1 << l;
+                k_cfup<RT, N, NG_FUP><<<blocks(active[l] / (2 * h), NG_FUP), NG_FUP * N,
+                                        (size_t)NG_FUP * FUP_B, s>>>(a.FE, active[l], h);
+            }
+            for (int l = levels - 1; l >= 0; --l) {
+                const int h = 1 << l;
+                k_cfdown<RT, N, NG_FDOWN><<<blocks(active[l] / (2 * h), NG_FDOWN),
+                                            NG_FDOWN * N, (size_t)NG_FDOWN * FDOWN_B, s>>>(
+                    a.FE, a.X, active[l], h);
+            }
         }
-        prof_mark(prof, s, refine_pass ? "chain_roll.refine" : "chain_roll");
+        prof_mark(prof, s, pname(kind, 5));
         k_croll<R, RT, N, M, NG_ROLL>
-            <<<blocks(NC, NG_ROLL), NG_ROLL * N, (size_t)NG_ROLL * ROLL_B, s>>>(a);
+            <<<blocks(C, NG_ROLL), NG_ROLL * N, (size_t)NG_ROLL * ROLL_B, s>>>(a);
     }
 
     static lqt_status run(const ChainCall& call, cudaStream_t s, Prof* prof) {
         if (prepare() != cudaSuccess) return LQT_ECUDA;
-        const lqt_problem* P = call.problem;
-        const lqt_solution* sol = call.solution;
+        const int count = call.count;
+        if (count <= 0) return LQT_OK;
+        const bool refine = call.refine;
+        const bool newton = refine && call.newton;
+        const Layout L = layout(call.probs, count, refine, newton);
+        if (call.ws_bytes < L.total) return LQT_ENOMEM;
+        char* base = static_cast<char*>(call.ws);
+        // items of the first pass and of the correction pass
+        std::vector<Item<R>> it1((size_t)count), it2(refine ? (size_t)count : 0),
+            it3(newton ? (size_t)count : 0);
+        R* cL = reinterpret_cast<R*>(base + L.consts);
+        R* cU = cL + N * M;
+        R* cH = cU + M * M;
+        long long c0 = 0, r0 = 0;
+        size_t roff = L.refine0;
+        int maxNC = 1;
+        for (int i = 0; i < count; ++i) {
+            const ChainProblem& cp = call.probs[i];
+            Item<R>& a = it1[(size_t)i];
+            memset(&a, 0, sizeof(a));
+            a.D = make_desc<R>(cp.problem, cp.solution);
+            a.B = cp.B;
+            a.c0 = c0;
+            a.r0 = r0;
+            a.NC = cp.NC;
+            c0 += cp.NC;
+            r0 += cp.problem->T + 1;
+            if (cp.NC > maxNC) maxNC = cp.NC;
+            if (refine) {
+                const size_t t = (size_t)cp.problem->T;
+                R* eta = reinterpret_cast<R*>(base + roff);
+                R* ctil = reinterpret_cast<R*>(base + roff + up(t * N * sizeof(R)));
+                R* qh = reinterpret_cast<R*>(base + roff + 2 * up(t * N * sizeof(R)));
+                R* dbuf = reinterpret_cast<R*>(base + roff + 2 * up(t * N * sizeof(R)) +
+                                               up(t * M * sizeof(R)));
+                R* etaT = reinterpret_cast<R*>(base + roff + 2 * up(t * N * sizeof(R)) +
+                                               2 * up(t * M * sizeof(R)));
+                R* x0p = etaT + up(N * sizeof(R)) / sizeof(R);
+                char* nb = base + roff + kkt_bytes(cp.problem->T);
+                roff += kkt_bytes(cp.problem->T) + (newton ? newton_bytes(cp.problem->T) : 0);
+                set_correction(it2[(size_t)i], a, eta, ctil, etaT, qh, dbuf, x0p);
+                if (!newton) continue;
+                R* Phi = reinterpret_cast<R*>(nb);
+                R* ct = reinterpret_cast<R*>(nb + up(t * N * N * sizeof(R)));
+                R* Rk = reinterpret_cast<R*>(nb + up(t * N * N * sizeof(R)) +
+                                             up(t * N * sizeof(R)));
+                R* dS = Rk + up((t + 1) * N * N * sizeof(R)) / sizeof(R);
+                R* rho = dS + up((t + 1) * N * N * sizeof(R)) / sizeof(R);
+                R* dv = rho + up((t + 1) * N * sizeof(R)) / sizeof(R);
+                // the Newton correction of (S, v) as an LQT problem (k_nresid)
+                Item<R>& c3 = it3[(size_t)i];
+                c3 = a;
+                DescT<R>& D3 = c3.D;
+                D3.p = N;
+                D3.pT = N;
+                D3.F = Phi;
+                D3.sF = (long long)N * N;
+                D3.c = ct;
+                D3.sc = N;
+                D3.L = cL;
+                D3.sL = 0;
+                D3.U = cU;
+                D3.sU = 0;
+                D3.H = cH;
+                D3.sH = 0;
+                D3.X = Rk;
+                D3.sX = (long long)N * N;
+                D3.r = nullptr;
+                D3.sr = 0;
+                D3.HT = cH;
+                D3.XT = Rk + t * N * N;
+                D3.rT = nullptr;
+                D3.eta = rho;
+                D3.seta = N;
+                D3.etaT = rho + t * N;
+                D3.S = dS;
+                D3.v = dv;
+                D3.K = nullptr;
+                D3.x = nullptr;
+                D3.u = dbuf;
+            }
+        }
+        int levels = 0;
+        while ((1 << levels) < maxNC) ++levels;
+        std::vector<long long> active((size_t)levels + 1, 0);
+        for (int l = 0; l < levels; ++l)
+            for (int i = 0; i < count; ++i)
+                if (call.probs[i].NC >= (2 << l)) active[(size_t)l] += call.probs[i].NC;
+        Item<R>* d1 = reinterpret_cast<Item<R>*>(base + L.items1);
+        Item<R>* d2 = reinterpret_cast<Item<R>*>(base + L.items2);
+        Item<R>* d3 = reinterpret_cast<Item<R>*>(base + L.items3);
+        if (count == 1) {
+            // through kernel parameters (no pageable copy; capturable in a graph)
+            k_set_items<R><<<1, 1, 0, s>>>(d1, it1[0], refine ? d2 : nullptr,
+                                           refine ? it2[0] : it1[0]);
+            if (newton) k_set_items<R><<<1, 1, 0, s>>>(d3, it3[0], nullptr, it3[0]);
+        } else {
+            if (cudaMemcpyAsync(d1, it1.data(), it1.size() * sizeof(Item<R>),
+                                cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return LQT_ECUDA;
+            if (refine && cudaMemcpyAsync(d2, it2.data(), it2.size() * sizeof(Item<R>),
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return LQT_ECUDA;
+            if (newton && cudaMemcpyAsync(d3, it3.data(), it3.size() * sizeof(Item<R>),
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return LQT_ECUDA;
+        }
+        if (newton) k_consts<R, N, M><<<1, N, 0, s>>>(cL, cU, cH);
         Args<R, RT> a;
-        a.D = make_desc<R>(P, sol);
-        a.B = call.B;
-        a.NC = call.NC;
-        a.E = static_cast<RT*>(call.E);
-        a.V = static_cast<RT*>(call.V);
-        a.FE = static_cast<RT*>(call.FE);
-        a.X = static_cast<RT*>(call.X);
-        a.status = call.status;
-        a.out_mask = 1;
+        a.items = d1;
+        a.count = count;
+        a.C = L.C;
+        a.E = reinterpret_cast<RT*>(base + L.E);
+        a.V = reinterpret_cast<RT*>(base + L.V);
+        a.FE = reinterpret_cast<RT*>(base + L.FE);
+        a.X = reinterpret_cast<RT*>(base + L.X);
+        a.status = call.status ? call.status : reinterpret_cast<int*>(base);
+        a.out_mask = 3;
         a.refine_add = 0;
-        pass(a, call.sequential, false, s, prof);
-        if (call.refine && P->T > 0) {
-            R* rp = static_cast<R*>(call.rp);
-            R* cp = static_cast<R*>(call.cp);
-            R* rTp = static_cast<R*>(call.rTp);
-            R* x0p = static_cast<R*>(call.x0p);
+        pass(a, active.data(), levels, call.sequential, 0, false, s, prof);
+        if (newton) {
+            // Newton correction of S and v, then K from the corrected S and v
+            prof_mark(prof, s, "chain_newton_resid");
+            int gridn = blocks(r0, NG_NEWTON);
+            if (gridn > 4096) gridn = 4096;
+            k_nresid<R, N, M, NG_NEWTON><<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(
+                d1, d3, count, r0, a.status);
+            Args<R, RT> c = a;
+            c.items = d3;
+            c.out_mask = 1;
+            pass(c, active.data(), levels, call.sequential, 2, true, s, prof);
+            prof_mark(prof, s, "chain_newton_gains");
+            k_ngains<R, N, M, NG_NEWTON><<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(
+                d1, d3, count, r0, a.status);
+            prof_mark(prof, s, "chain_newton_add");
+            k_nadd<R, N><<<1024, 256, 0, s>>>(d1, d3, count, r0);
+        }
+        if (refine) {
+            // one step of iterative refinement of the KKT system for x* and u*
             prof_mark(prof, s, "chain_resid");
-            const long long items = P->T + 1;
-            int grid = blocks(items, NG_RESID);
+            int grid = blocks(r0, NG_RESID);
             if (grid > 4096) grid = 4096;
-            k_cresid<R, N, NG_RESID><<<grid, NG_RESID * N, 0, s>>>(a.D, rp, cp, rTp, x0p);
-            // the shifted problem: same matrices, r', c', r'_T, x'_0 = 0; S and K
-            // do not depend on r or c, so the pass does not write them again
+            k_cresid<R, N, M, NG_RESID><<<grid, NG_RESID * N, (size_t)NG_RESID * RESID_B, s>>>(
+                d1, d2, count, r0, a.status);
             Args<R, RT> b = a;
-            b.D.r = P->p > 0 ? rp : nullptr;
-            b.D.sr = P->p;
-            b.D.c = cp;
-            b.D.sc = N;
-            b.D.rT = P->pT > 0 ? rTp : nullptr;
-            b.D.x0 = x0p;
+            b.items = d2;
             b.out_mask = 0;
             b.refine_add = 1;
-            pass(b, call.sequential, true, s, prof);
+            pass(b, active.data(), levels, call.sequential, 1, false, s, prof);
         }
         prof_end(prof, s);
         return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
@@ -154,7 +378,7 @@ struct Launcher {
 #define LQT_CHAIN_VARIANT(R, RT, N, M)                                                         \
     ChainVariant {                                                                              \
         sizeof(R) == 8 ? LQT_F64 : LQT_F32, N, M, sizeof(RT) == 8 && sizeof(R) == 4,            \
-            (int)sizeof(R), (int)sizeof(RT), &chain::Launcher<R, RT, N, M>::run,                \
+            &chain::Launcher<R, RT, N, M>::workspace, &chain::Launcher<R, RT, N, M>::run,       \
             &chain::Launcher<R, RT, N, M>::fold_kernel, &chain::Launcher<R, RT, N, M>::fold_smem, \
             &chain::Launcher<R, RT, N, M>::fold_groups_per_cta                                  \
     }

@@ -28,6 +28,11 @@ struct DescT {
     long long sF, sc, sL, sU, sH, sr, sX;
     const R *HT, *rT, *XT, *x0;
     R *S, *v, *K, *x, *u;
+    // optional linear state terms replacing H^T X r (the correction problem of
+    // the refinement pass): eta_k = eta[k * seta .. + n), eta_T = etaT[0 .. n)
+    const R* eta;
+    long long seta;
+    const R* etaT;
 };
 using BatchDesc = DescT<float>;
 
@@ -51,10 +56,11 @@ constexpr int load_scratch() {
     return M * M + M * N;
 }
 
-// Step k of D into the step buffer sb.  WITH_C also forms C = L U^{-1} L^T
-// (the general combine needs it; fold_step and riccati do not).
-template <typename R, int N, int M, bool WITH_C>
-__device__ void load_step(const DescT<R>& D, long long k, R* sb, R* scr, const Group<N>& g,
+// Step k of D (inputs of type RI) into the step buffer sb (type R).  WITH_C
+// also forms C = L U^{-1} L^T (the general combine needs it; fold_step and
+// riccati do not); COST = false loads the dynamics only.
+template <typename R, int N, int M, bool WITH_C, typename RI = R, bool COST = true>
+__device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const Group<N>& g,
                           bool& ok) {
     using SL = StepLayout<N, M>;
     using E = LElem<N>;
@@ -65,21 +71,25 @@ __device__ void load_step(const DescT<R>& D, long long k, R* sb, R* scr, const G
     R* xr = Y + SL::PMAX * N;  // p: X r
     const int r = g.lr;
     const int p = D.p;
-    const R* F = D.F + k * D.sF;
-    const R* Lk = D.L + k * D.sL;
-    const R* Uk = D.U + k * D.sU;
-    const R* H = D.H + k * D.sH;
-    const R* X = D.X + k * D.sX;
-    const R* rk = D.r ? D.r + k * D.sr : nullptr;
+    const RI* F = D.F + k * D.sF;
+    const RI* Lk = D.L + k * D.sL;
+    const RI* Uk = D.U + k * D.sU;
+    const RI* H = D.H + k * D.sH;
+    const RI* X = D.X + k * D.sX;
+    const RI* rk = D.r ? D.r + k * D.sr : nullptr;
 #pragma unroll
-    for (int j = 0; j < N; ++j) e[E::OA + r * N + j] = __ldg(F + r * N + j);
+    for (int j = 0; j < N; ++j) e[E::OA + r * N + j] = R(__ldg(F + r * N + j));
 #pragma unroll
-    for (int a = 0; a < M; ++a) L[r * M + a] = __ldg(Lk + r * M + a);
+    for (int a = 0; a < M; ++a) L[r * M + a] = R(__ldg(Lk + r * M + a));
     if (r < M) {
 #pragma unroll
-        for (int b = 0; b < M; ++b) U[r * M + b] = __ldg(Uk + r * M + b);
+        for (int b = 0; b < M; ++b) U[r * M + b] = R(__ldg(Uk + r * M + b));
     }
-    e[E::OB + r] = D.c ? __ldg(D.c + k * D.sc + r) : R(0);
+    e[E::OB + r] = D.c ? R(__ldg(D.c + k * D.sc + r)) : R(0);
+    if (!COST) {  // dynamics only (F, c, L, U)
+        g.sync();
+        return;
+    }
     // Y = X H and X r, rows spread over the lanes
     for (int a = r; a < p; a += N) {
         R acc[N];
@@ -87,10 +97,10 @@ __device__ void load_step(const DescT<R>& D, long long k, R* sb, R* scr, const G
         for (int j = 0; j < N; ++j) acc[j] = R(0);
         R t = R(0);
         for (int b = 0; b < p; ++b) {
-            const R xab = __ldg(X + a * p + b);
+            const R xab = R(__ldg(X + a * p + b));
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += xab * __ldg(H + b * N + j);
-            if (rk) t += xab * __ldg(rk + b);
+            for (int j = 0; j < N; ++j) acc[j] += xab * R(__ldg(H + b * N + j));
+            if (rk) t += xab * R(__ldg(rk + b));
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) Y[a * N + j] = acc[j];
@@ -104,14 +114,14 @@ __device__ void load_step(const DescT<R>& D, long long k, R* sb, R* scr, const G
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = R(0);
         for (int a = 0; a < p; ++a) {
-            const R h = __ldg(H + a * N + r);
+            const R h = R(__ldg(H + a * N + r));
 #pragma unroll
             for (int j = 0; j < N; ++j) acc[j] += h * Y[a * N + j];
             t += h * xr[a];
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) e[E::OJ + r * N + j] = acc[j];
-        e[E::OE + r] = t;
+        e[E::OE + r] = D.eta ? R(D.eta[k * D.seta + r]) : t;
     }
     if (WITH_C) {
         // C = L U^{-1} L^T: solve U Z = L^T (M x M, N right-hand sides)
@@ -136,28 +146,26 @@ constexpr int riccati_scratch() {
     return N * M + N * N + M * M + N + N * N + N;
 }
 
-// One Riccati step on the value (S, v) in val (Sec. II-B): writes the gains
-// into Kd ([K | d], M x (N + 1), with u = d - K x) and the closed loop into Ft
-// (LAffine: F - L K, c + L d), and replaces val by (S_k, v_k).
+// The gains of one Riccati step (Sec. II-B, eq. Control_LQT) at the value
+// (S, v) in val: Kd = [K | d] (M x (N + 1), u = d - K x) from
+// G = U + L^T S L,  G [K | d] = [L^T S F | L^T (v - S c)].  Leaves SL = S L,
+// SF = S F and ev = v - S c in the scratch for the caller.
 template <typename R, int N, int M>
-__device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N>& g) {
+__device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& g) {
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     using V = LValue<N>;
     const R* e = sb + SLay::E;
     const R* F = e + E::OA;
     const R* c = e + E::OB;
-    const R* Q = e + E::OJ;
-    const R* q = e + E::OE;
     const R* L = sb + SLay::L;
     const R* U = sb + SLay::U;
     const R* S = val + V::OS;
     const R* v = val + V::OV;
     R* SL = scr;            // N x M
-    R* SF = SL + N * M;     // N x N  (later S Ft)
+    R* SF = SL + N * M;     // N x N
     R* G = SF + N * N;      // M x M
     R* ev = G + M * M;      // N
-    R* O = ev + N;          // N x N + N
     const int r = g.lr;
     row_mul<N, N, M>(SL, M, S, N, L, M, r);
     row_mul<N, N, N>(SF, N, S, N, F, N, r);
@@ -193,7 +201,30 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
         Kd[r * (N + 1) + N] = w;
     }
     g.sync();
-    const bool ok = solve_gj<N, M, N + 1>(G, M, Kd, N + 1, g);
+    return solve_gj<N, M, N + 1>(G, M, Kd, N + 1, g);
+}
+
+// One Riccati step on the value (S, v) in val (Sec. II-B): writes the gains
+// into Kd ([K | d], M x (N + 1), with u = d - K x) and the closed loop into Ft
+// (LAffine: F - L K, c + L d), and replaces val by (S_k, v_k).
+template <typename R, int N, int M>
+__device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N>& g) {
+    using SLay = StepLayout<N, M>;
+    using E = LElem<N>;
+    using V = LValue<N>;
+    const R* e = sb + SLay::E;
+    const R* F = e + E::OA;
+    const R* c = e + E::OB;
+    const R* Q = e + E::OJ;
+    const R* q = e + E::OE;
+    const R* L = sb + SLay::L;
+    R* SL = scr;            // N x M
+    R* SF = SL + N * M;     // N x N  (later S Ft)
+    R* G = SF + N * N;      // M x M
+    R* ev = G + M * M;      // N
+    R* O = ev + N;          // N x N + N
+    const int r = g.lr;
+    const bool ok = gains<R, N, M>(val, sb, Kd, scr, g);
     // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
     {
         R ft[N], sft[N];

@@ -23,7 +23,7 @@ struct Plan {
 
 // Kernel timing (lqt_profile_enable); owned by the C ABI.
 struct Prof {
-    static constexpr int MAXK = 16;
+    static constexpr int MAXK = 32;
     bool enabled = false;
     int device = -1;
     int count = 0;

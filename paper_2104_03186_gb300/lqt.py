@@ -44,7 +44,7 @@ class lqt_batch_item(ctypes.Structure):
     _fields_ = [("problem", lqt_problem), ("solution", lqt_solution)]
 
 
-LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO = 0, 1, 2
+LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO, LQT_REFINE_FULL = 0, 1, 2, 3
 
 
 class lqt_options(ctypes.Structure):
@@ -92,7 +92,7 @@ def _load() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
         "lqt_plan": (st, [P, O] + [ctypes.POINTER(ctypes.c_int32)] * 4),
         "lqt_solve_static": (st, [P, S, O, vp]),
-        "lqt_batch_workspace_bytes": (sz, [ctypes.c_int32]),
+        "lqt_batch_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
         "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
@@ -247,27 +247,39 @@ def lqt_solve_host(prob: Problem, out: Dict[str, object], device_buffer, stream=
     return int(st)
 
 
-def lqt_batch_workspace_bytes(count: int) -> int:
-    return int(_lib.lqt_batch_workspace_bytes(int(count)))
+def _items(problems, outputs):
+    count = len(problems)
+    arr = (lqt_batch_item * max(count, 1))()
+    for i, (P, out) in enumerate(zip(problems, outputs)):
+        arr[i].problem = P.struct
+        arr[i].solution = solution_struct(out)
+    return arr
+
+
+def lqt_batch_workspace_bytes(problems, outputs) -> int:
+    """Workspace bytes of lqt_solve_batched for these problems and outputs
+    (0: an item is invalid or unsupported)."""
+    return int(_lib.lqt_batch_workspace_bytes(_items(problems, outputs), len(problems)))
 
 
 def lqt_solve_batched(problems, outputs, workspace, stream=None) -> None:
     """Solve a ragged batch: problems[i] (Problem, device tensors) into
     outputs[i] (dict of device tensors).  Asynchronous; read the device status
     with lqt_workspace_status(workspace)."""
-    count = len(problems)
-    arr = (lqt_batch_item * max(count, 1))()
-    for i, (P, out) in enumerate(zip(problems, outputs)):
-        arr[i].problem = P.struct
-        arr[i].solution = solution_struct(out)
-    st = _lib.lqt_solve_batched(arr, count, _ptr(workspace), _nbytes(workspace),
-                                _stream_handle(stream))
+    st = _lib.lqt_solve_batched(_items(problems, outputs), len(problems), _ptr(workspace),
+                                _nbytes(workspace), _stream_handle(stream))
     if st != LQT_OK:
         raise LQTError(st, "lqt_solve_batched")
 
 
 # numpy mirror of lqt_batch_item, for building descriptor arrays column-wise
 BATCH_ITEM = np.dtype(lqt_batch_item)
+
+
+def lqt_batch_workspace_bytes_array(items: np.ndarray) -> int:
+    """lqt_batch_workspace_bytes over a C-contiguous numpy array of BATCH_ITEM."""
+    return int(_lib.lqt_batch_workspace_bytes(
+        items.ctypes.data_as(ctypes.POINTER(lqt_batch_item)), len(items)))
 
 
 def lqt_solve_batched_array(items: np.ndarray, workspace, stream=None) -> None:
@@ -285,7 +297,10 @@ def solve_batched(problems, stream=None, check: bool = True):
     import torch
 
     outs = [P.allocate_outputs() for P in problems]
-    ws = torch.empty(lqt_batch_workspace_bytes(len(problems)), dtype=torch.uint8, device="cuda")
+    nbytes = lqt_batch_workspace_bytes(problems, outs)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_batch_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     lqt_solve_batched(problems, outs, ws, stream)
     if check:
         st = lqt_workspace_status(ws, stream)

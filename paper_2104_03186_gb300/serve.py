@@ -9,8 +9,8 @@ predicted state x*_s.
 
 The loop admits arrived requests while their device memory fits the budget,
 groups whatever has been admitted into a batch as soon as a stream is free,
-and solves the batch with one lqt_solve_batched call (one persistent launch
-per state size present).  Batches on different streams run concurrently, so
+and solves the batch with one lqt_solve_batched call (per state size present,
+one persistent launch for n = 4 and one chunked pipeline for n >= 8).  Batches on different streams run concurrently, so
 requests that arrive while others are on the GPU start without waiting for
 them.  Per batch the references and initial states go up in one host-to-device
 copy and the optimal controls u* come back in one device-to-host copy.
@@ -147,8 +147,15 @@ class _Slot:
         if count > self.cap_items:
             self.cap_items = max(count, 2 * self.cap_items)
             self.items = np.zeros(self.cap_items, dtype=lqt.BATCH_ITEM)
-            self.ws = torch.empty(lqt.lqt_batch_workspace_bytes(self.cap_items),
-                                  dtype=torch.uint8, device="cuda")
+        if not hasattr(self, "ws"):
+            self.ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+
+    def ensure_ws(self, nbytes: int):
+        import torch
+
+        if nbytes > self.ws.numel():
+            self.ws = torch.empty(max(nbytes, 2 * self.ws.numel()), dtype=torch.uint8,
+                                  device="cuda")
 
 
 class Server:
@@ -323,6 +330,10 @@ class Server:
         S["x"] = S["K"] + np.uint64(4) * Tu * nm
         S["u"] = np.uint64(slot.d_u.data_ptr()) + u_off[:-1].astype(np.uint64) * np.uint64(4)
         st = slot.stream
+        nbytes = lqt.lqt_batch_workspace_bytes_array(it)
+        if nbytes == 0:
+            raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "batch workspace")
+        slot.ensure_ws(nbytes)
         with torch.cuda.stream(st):
             slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
             lqt.lqt_solve_batched_array(it, slot.ws, st)

@@ -72,9 +72,11 @@ def test_batch_rejects_unsupported_items():
 
     good = lqt.Problem.from_inputs(inputs.diag_tracking(4, T=10, seed=0).rounded_to(np.float32))
     bad = lqt.Problem.from_inputs(inputs.random_problem(5, 2, T=10, seed=0).rounded_to(np.float32))
-    ws = torch.empty(lqt.lqt_batch_workspace_bytes(2), dtype=torch.uint8, device="cuda")
+    outs = [good.allocate_outputs(), bad.allocate_outputs()]
+    assert lqt.lqt_batch_workspace_bytes([good, bad], outs) == 0
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     with pytest.raises(lqt.LQTError) as ei:
-        lqt.lqt_solve_batched([good, bad], [good.allocate_outputs(), bad.allocate_outputs()], ws)
+        lqt.lqt_solve_batched([good, bad], outs, ws)
     assert ei.value.status == lqt.LQT_EUNSUPPORTED
     small = torch.empty(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(lqt.LQTError) as ei:

@@ -41,18 +41,42 @@ def test_chain_sequential_matches_oracle(n, m):
     compare(gpu_solve(prob64, dtype=np.float64, sequential=True), oracle_solve(prob64), FP64_TOL)
 
 
-@pytest.mark.parametrize("n,m,kw", [
-    (8, 4, dict(p=4, pT=1)),                 # p < n, one terminal row
-    (8, 4, dict(p=16, pT=16)),               # p = 2n
-    (16, 8, dict(with_c=False, pT=0)),       # no offsets, no terminal cost
-    (16, 8, dict(time_varying=False)),       # step stride 0 for every matrix
-    (32, 16, dict(p=8, x_rank=3)),           # rank-deficient X_k
+@pytest.mark.parametrize("n,m,kw,refine", [
+    (8, 4, dict(p=4, pT=1), 1),                 # p < n, one terminal row
+    (8, 4, dict(p=16, pT=16), 1),               # p = 2n
+    (16, 8, dict(with_c=False, pT=0), 1),       # no offsets, no terminal cost
+    # step stride 0 for every matrix; F with spectral radius up to 1.05 held for
+    # all steps makes S ill-conditioned enough (FP32 solve: S 8e-6, v 1.8e-5)
+    # that S and v need the Newton step of the FULL refinement
+    (16, 8, dict(time_varying=False), 3),
+    (32, 16, dict(p=8, x_rank=3), 1),           # rank-deficient X_k
 ])
-def test_chain_shapes(n, m, kw):
+def test_chain_shapes(n, m, kw, refine):
     prob = _rand(n, m, 777, seed=11, **kw).rounded_to(np.float32)
-    compare(gpu_solve(prob), oracle_solve(prob), FP32_TOL)
+    compare(gpu_solve(prob, refine=refine), oracle_solve(prob), FP32_TOL)
     prob64 = _rand(n, m, 777, seed=12, **kw)
     compare(gpu_solve(prob64, dtype=np.float64), oracle_solve(prob64), FP64_TOL)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("sequential", [False, True])
+def test_chain_full_refinement(n, m, sequential):
+    """FULL refinement (FP64 tree levels, Newton step for S, v, K, KKT step
+    for x*, u*): every output at FP32 rounding level."""
+    prob = _rand(n, m, 500, seed=21 + n).rounded_to(np.float32)
+    errs = compare(gpu_solve(prob, refine=3, sequential=sequential), oracle_solve(prob), 1e-6)
+    assert max(errs.values()) < 1e-6
+
+
+def test_chain_kkt_refinement_fixes_trajectory():
+    """ON refinement: x* and u* reach FP32 rounding level even where the plain
+    FP32 solve misses 1e-5 (the precision-study workload)."""
+    prob = inputs.precision_study(T=2048, seed=3).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    plain = compare(gpu_solve(prob, refine=0), ref, 1.0)
+    refined = compare(gpu_solve(prob, refine=1), ref, FP32_TOL)
+    assert refined["x"] < 1e-6 and refined["u"] < 1e-6
+    assert refined["x"] < plain["x"] / 10
 
 
 @pytest.mark.parametrize("n,m", SIZES)
@@ -83,9 +107,12 @@ def test_chain_plan_spans_levels():
 @pytest.mark.parametrize("T", [4096])
 def test_precision_study_small(T):
     """The precision-study workload (n = 32, cond(X_k) = 1e6, U = 1e-3 I) at a
-    short horizon: FP64 within 1e-11 and the mixed form within 1e-5."""
+    short horizon: FP64 within 1e-11, the refined forms within 1e-5 (FULL
+    within 1e-6)."""
     prob = inputs.precision_study(T=T, seed=1)
     o64 = oracle_solve(prob)
     compare(gpu_solve(prob, dtype=np.float64), o64, FP64_TOL)
     p32 = prob.rounded_to(np.float32)
-    compare(gpu_solve(p32, refine=1), oracle_solve(p32), FP32_TOL)
+    o32 = oracle_solve(p32)
+    compare(gpu_solve(p32, refine=1), o32, FP32_TOL)
+    compare(gpu_solve(p32, refine=3), o32, 1e-6)
