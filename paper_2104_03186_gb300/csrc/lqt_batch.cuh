@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
             }
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                carry[V::OS + r * N + j] = acc[j];
+                carry[V::OS + r * V::LD + j] = acc[j];
                 D.S[T * N * N + r * N + j] = acc[j];
             }
             carry[V::OV + r] = t;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
                 float* ci = carry + i * V::SIZE;
                 float* ch = carry + (i + h) * V::SIZE;
 #pragma unroll
-                for (int j = 0; j < N; ++j) ch[V::OS + r * N + j] = ci[V::OS + r * N + j];
+                for (int j = 0; j < N; ++j) ch[V::OS + r * V::LD + j] = ci[V::OS + r * V::LD + j];
                 ch[V::OV + r] = ci[V::OV + r];
                 g.sync();
                 ok &= value_apply<N, N>(tree + (i + h) * E::SIZE, ci, scr, g);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
         float* val = carry + gi * V::SIZE;
         float* Phi = ftree + gi * A::SIZE;
 #pragma unroll
-        for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = r == j ? 1.f : 0.f;
+        for (int j = 0; j < N; ++j) Phi[A::OF + r * A::LD + j] = r == j ? 1.f : 0.f;
         Phi[A::OC + r] = 0.f;
         g.sync();
         float* Kd = scr + riccati_scratch<N, M>();
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
             load_step<float, N, M, false>(D, k, gs, scr, g, ok);
             ok &= riccati<float, N, M>(val, gs, Kd, Ft, scr, g);
 #pragma unroll
-            for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * N + j];
+            for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * V::LD + j];
             D.v[k * N + r] = val[V::OV + r];
             if (r < M) {
 #pragma unroll
@@ -167,14 +167,14 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
             for (int j = 0; j < N; ++j) pn[j] = 0.f;
 #pragma unroll
             for (int l = 0; l < N; ++l) {
-                const float pl = Phi[A::OF + r * N + l];
+                const float pl = Phi[A::OF + r * A::LD + l];
 #pragma unroll
-                for (int j = 0; j < N; ++j) pn[j] += pl * Ft[A::OF + l * N + j];
+                for (int j = 0; j < N; ++j) pn[j] += pl * Ft[A::OF + l * A::LD + j];
                 gm += pl * Ft[A::OC + l];
             }
             g.sync();
 #pragma unroll
-            for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = pn[j];
+            for (int j = 0; j < N; ++j) Phi[A::OF + r * A::LD + j] = pn[j];
             Phi[A::OC + r] = gm;
             g.sync();
         }

@@ -152,7 +152,7 @@ struct UpSmem {
 
 template <int N>
 struct DownSmem {
-    static constexpr int SIZE = LElem<N>::SIZE + LValue<N>::SIZE + 4 * N * N + 2 * N;
+    static constexpr int SIZE = LElem<N>::SIZE + LValue<N>::SIZE + value_scratch<N>();
 };
 
 template <int N>
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(N) k_cterm(Args<R, RT> a) {
     if (D.etaT) t = static_cast<RT>(D.etaT[r]);
     RT* val = a.V + it.c0 * LValue<N>::SIZE;
 #pragma unroll
-    for (int j = 0; j < N; ++j) val[LValue<N>::OS + r * N + j] = acc[j];
+    for (int j = 0; j < N; ++j) val[LValue<N>::OS + r * LValue<N>::LD + j] = acc[j];
     val[LValue<N>::OV + r] = t;
     a.X[(it.c0 + it.NC - 1) * N + r] = static_cast<RT>(D.x0[r]);
     if (a.out_mask & 1) {
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     copy_in(val, a.V + c * V::SIZE, V::SIZE, r, N);
 #pragma unroll
-    for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = r == j ? R(1) : R(0);
+    for (int j = 0; j < N; ++j) Phi[A::OF + r * A::LD + j] = r == j ? R(1) : R(0);
     Phi[A::OC + r] = R(0);
     g.sync();
     bool ok = true;
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
         ok &= riccati<R, N, M>(val, sb, Kd, Ft, scr, g);
         if (a.out_mask & 1) {
 #pragma unroll
-            for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * N + j];
+            for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * V::LD + j];
             D.v[k * N + r] = val[V::OV + r];
         }
         if (r < M) {
@@ -370,14 +370,14 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
         for (int j = 0; j < N; ++j) pn[j] = R(0);
 #pragma unroll 4
         for (int l = 0; l < N; ++l) {
-            const R pl = Phi[A::OF + r * N + l];
+            const R pl = Phi[A::OF + r * A::LD + l];
 #pragma unroll
-            for (int j = 0; j < N; ++j) pn[j] += pl * Ft[A::OF + l * N + j];
+            for (int j = 0; j < N; ++j) pn[j] += pl * Ft[A::OF + l * A::LD + j];
             gm += pl * Ft[A::OC + l];
         }
         g.sync();
 #pragma unroll
-        for (int j = 0; j < N; ++j) Phi[A::OF + r * N + j] = pn[j];
+        for (int j = 0; j < N; ++j) Phi[A::OF + r * A::LD + j] = pn[j];
         Phi[A::OC + r] = gm;
         g.sync();
     }
@@ -660,15 +660,16 @@ __global__ void __launch_bounds__(NG* N) k_nresid(const Item<R>* items1, const I
             continue;
         }
         load_step<D64, N, M, false, R>(D, k, sb, scr, g, ok);
-        copy_in(val + V::OS, D.S + (k + 1) * N * N, N * N, r, N);
+        for (int i = r; i < N * N; i += N)
+            val[V::OS + (i / N) * V::LD + i % N] = static_cast<D64>(D.S[(k + 1) * N * N + i]);
         copy_in(val + V::OV, D.v + (k + 1) * N, N, r, N);
         g.sync();
         ok &= riccati<D64, N, M>(val, sb, Kd, Ft, scr, g);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Rk[r * N + j] = static_cast<R>(val[V::OS + r * N + j] -
+            Rk[r * N + j] = static_cast<R>(val[V::OS + r * V::LD + j] -
                                            static_cast<D64>(D.S[k * N * N + r * N + j]));
-            const_cast<R*>(D3.F)[k * N * N + r * N + j] = static_cast<R>(Ft[A::OF + r * N + j]);
+            const_cast<R*>(D3.F)[k * N * N + r * N + j] = static_cast<R>(Ft[A::OF + r * A::LD + j]);
         }
         const_cast<R*>(D3.eta)[k * N + r] =
             static_cast<R>(val[V::OV + r] - static_cast<D64>(D.v[k * N + r]));
@@ -706,7 +707,7 @@ __global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const I
         const R* S1 = D.S + (k + 1) * N * N;
         const R* dS1 = D3.S + (k + 1) * N * N;
         for (int i = r; i < N * N; i += N)
-            val[V::OS + i] = static_cast<D64>(S1[i]) + static_cast<D64>(dS1[i]);
+            val[V::OS + (i / N) * V::LD + i % N] = static_cast<D64>(S1[i]) + static_cast<D64>(dS1[i]);
         val[V::OV + r] = static_cast<D64>(D.v[(k + 1) * N + r]) +
                          static_cast<D64>(D3.v[(k + 1) * N + r]);
         g.sync();

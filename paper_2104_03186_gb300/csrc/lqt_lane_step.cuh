@@ -39,21 +39,23 @@ using BatchDesc = DescT<float>;
 namespace lanes {
 
 // Group buffer of one step's model: an element-shaped block E (A = F_k,
-// b = c_k, C, eta, J), then L_k, U_k and the scratch Y = X H, X r.
+// b = c_k, C, eta, J), then L_k (N x M), U_k (M x M) and the scratch Y = X H
+// (p x N), X r.  Row strides are odd (lds).
 template <int N, int M>
 struct StepLayout {
     static constexpr int PMAX = 2 * N;  // largest p (rows of H) the lane path takes
+    static constexpr int LD = lds(N), LM = lds(M);
     static constexpr int E = 0;
     static constexpr int L = LElem<N>::SIZE;
-    static constexpr int U = L + N * M;
-    static constexpr int Y = U + M * M;
-    static constexpr int SIZE = Y + PMAX * N + PMAX;
+    static constexpr int U = L + N * LM;
+    static constexpr int Y = U + M * LM;
+    static constexpr int SIZE = Y + PMAX * LD + PMAX;
 };
 
 // Scratch of load_step with the C term (M x M copy of U and M x N right sides).
 template <int N, int M>
 constexpr int load_scratch() {
-    return M * M + M * N;
+    return M * lds(M) + M * lds(N);
 }
 
 // Step k of D (inputs of type RI) into the step buffer sb (type R).  WITH_C
@@ -64,11 +66,12 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
                           bool& ok) {
     using SL = StepLayout<N, M>;
     using E = LElem<N>;
+    constexpr int LD = SL::LD, LM = SL::LM;
     R* e = sb + SL::E;
     R* L = sb + SL::L;
     R* U = sb + SL::U;
-    R* Y = sb + SL::Y;        // p x N: X H
-    R* xr = Y + SL::PMAX * N;  // p: X r
+    R* Y = sb + SL::Y;          // p x N: X H
+    R* xr = Y + SL::PMAX * LD;  // p: X r
     const int r = g.lr;
     const int p = D.p;
     const RI* F = D.F + k * D.sF;
@@ -78,12 +81,12 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
     const RI* X = D.X + k * D.sX;
     const RI* rk = D.r ? D.r + k * D.sr : nullptr;
 #pragma unroll
-    for (int j = 0; j < N; ++j) e[E::OA + r * N + j] = R(__ldg(F + r * N + j));
+    for (int j = 0; j < N; ++j) e[E::OA + r * LD + j] = R(__ldg(F + r * N + j));
 #pragma unroll
-    for (int a = 0; a < M; ++a) L[r * M + a] = R(__ldg(Lk + r * M + a));
+    for (int a = 0; a < M; ++a) L[r * LM + a] = R(__ldg(Lk + r * M + a));
     if (r < M) {
 #pragma unroll
-        for (int b = 0; b < M; ++b) U[r * M + b] = R(__ldg(Uk + r * M + b));
+        for (int b = 0; b < M; ++b) U[r * LM + b] = R(__ldg(Uk + r * M + b));
     }
     e[E::OB + r] = D.c ? R(__ldg(D.c + k * D.sc + r)) : R(0);
     if (!COST) {  // dynamics only (F, c, L, U)
@@ -103,7 +106,7 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
             if (rk) t += xab * R(__ldg(rk + b));
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) Y[a * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) Y[a * LD + j] = acc[j];
         xr[a] = t;
     }
     g.sync();
@@ -116,45 +119,52 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         for (int a = 0; a < p; ++a) {
             const R h = R(__ldg(H + a * N + r));
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += h * Y[a * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += h * Y[a * LD + j];
             t += h * xr[a];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) e[E::OJ + r * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) e[E::OJ + r * LD + j] = acc[j];
         e[E::OE + r] = D.eta ? R(D.eta[k * D.seta + r]) : t;
     }
     if (WITH_C) {
         // C = L U^{-1} L^T: solve U Z = L^T (M x M, N right-hand sides)
         R* Um = scr;
-        R* Z = Um + M * M;
+        R* Z = Um + M * LM;
         if (r < M) {
 #pragma unroll
-            for (int b = 0; b < M; ++b) Um[r * M + b] = U[r * M + b];
+            for (int b = 0; b < M; ++b) Um[r * LM + b] = U[r * LM + b];
 #pragma unroll
-            for (int j = 0; j < N; ++j) Z[r * N + j] = L[j * M + r];
+            for (int j = 0; j < N; ++j) Z[r * LD + j] = L[j * LM + r];
         }
         g.sync();
-        ok &= solve_gj<N, M, N>(Um, M, Z, N, g);
-        row_mul<N, M, N>(e + E::OC, N, L, M, Z, N, r);
+        ok &= solve_gj<N, M, N>(Um, LM, Z, LD, g);
+        row_mul<N, M, N>(e + E::OC, LD, L, LM, Z, LD, r);
     }
     g.sync();
 }
 
-// Scratch of riccati (elements of R), excluding the caller's Kd and Ft.
+// Scratch of gains / riccati (elements of R), excluding the caller's Kd and Ft.
 template <int N, int M>
 constexpr int riccati_scratch() {
-    return N * M + N * N + M * M + N + N * N + N;
+    return N * lds(M) + N * lds(N) + M * lds(M) + N + N * lds(N) + N;
+}
+
+// Row stride of Kd = [K | d] (M x (N + 1)).
+template <int N>
+constexpr int kd_ld() {
+    return lds(N + 1);
 }
 
 // The gains of one Riccati step (Sec. II-B, eq. Control_LQT) at the value
-// (S, v) in val: Kd = [K | d] (M x (N + 1), u = d - K x) from
-// G = U + L^T S L,  G [K | d] = [L^T S F | L^T (v - S c)].  Leaves SL = S L,
-// SF = S F and ev = v - S c in the scratch for the caller.
+// (S, v) in val: Kd = [K | d] (M x (N + 1), row stride kd_ld, u = d - K x)
+// from G = U + L^T S L,  G [K | d] = [L^T S F | L^T (v - S c)].  Leaves
+// SL = S L, SF = S F and ev = v - S c in the scratch for the caller.
 template <typename R, int N, int M>
 __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& g) {
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     using V = LValue<N>;
+    constexpr int LD = SLay::LD, LM = SLay::LM, LK = kd_ld<N>();
     const R* e = sb + SLay::E;
     const R* F = e + E::OA;
     const R* c = e + E::OB;
@@ -162,17 +172,17 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
     const R* U = sb + SLay::U;
     const R* S = val + V::OS;
     const R* v = val + V::OV;
-    R* SL = scr;            // N x M
-    R* SF = SL + N * M;     // N x N
-    R* G = SF + N * N;      // M x M
-    R* ev = G + M * M;      // N
+    R* SL = scr;             // N x M
+    R* SF = SL + N * LM;     // N x N
+    R* G = SF + N * LD;      // M x M
+    R* ev = G + M * LM;      // N
     const int r = g.lr;
-    row_mul<N, N, M>(SL, M, S, N, L, M, r);
-    row_mul<N, N, N>(SF, N, S, N, F, N, r);
+    row_mul<N, N, M>(SL, LM, S, LD, L, LM, r);
+    row_mul<N, N, N>(SF, LD, S, LD, F, LD, r);
     {
         R t = v[r];
 #pragma unroll
-        for (int k = 0; k < N; ++k) t -= S[r * N + k] * c[k];
+        for (int k = 0; k < N; ++k) t -= S[r * LD + k] * c[k];
         ev[r] = t;
     }
     g.sync();
@@ -181,27 +191,27 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
         R gg[M], pp[N];
         R w = R(0);
 #pragma unroll
-        for (int b = 0; b < M; ++b) gg[b] = U[r * M + b];
+        for (int b = 0; b < M; ++b) gg[b] = U[r * LM + b];
 #pragma unroll
         for (int j = 0; j < N; ++j) pp[j] = R(0);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R lk = L[k * M + r];
-            const R sk = SL[k * M + r];
+            const R lk = L[k * LM + r];
+            const R sk = SL[k * LM + r];
 #pragma unroll
-            for (int b = 0; b < M; ++b) gg[b] += lk * SL[k * M + b];
+            for (int b = 0; b < M; ++b) gg[b] += lk * SL[k * LM + b];
 #pragma unroll
-            for (int j = 0; j < N; ++j) pp[j] += sk * F[k * N + j];
+            for (int j = 0; j < N; ++j) pp[j] += sk * F[k * LD + j];
             w += lk * ev[k];
         }
 #pragma unroll
-        for (int b = 0; b < M; ++b) G[r * M + b] = gg[b];
+        for (int b = 0; b < M; ++b) G[r * LM + b] = gg[b];
 #pragma unroll
-        for (int j = 0; j < N; ++j) Kd[r * (N + 1) + j] = pp[j];
-        Kd[r * (N + 1) + N] = w;
+        for (int j = 0; j < N; ++j) Kd[r * LK + j] = pp[j];
+        Kd[r * LK + N] = w;
     }
     g.sync();
-    return solve_gj<N, M, N + 1>(G, M, Kd, N + 1, g);
+    return solve_gj<N, M, N + 1>(G, LM, Kd, LK, g);
 }
 
 // One Riccati step on the value (S, v) in val (Sec. II-B): writes the gains
@@ -212,17 +222,19 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     using V = LValue<N>;
+    using A = LAffine<N>;
+    constexpr int LD = SLay::LD, LM = SLay::LM, LK = kd_ld<N>();
     const R* e = sb + SLay::E;
     const R* F = e + E::OA;
     const R* c = e + E::OB;
     const R* Q = e + E::OJ;
     const R* q = e + E::OE;
     const R* L = sb + SLay::L;
-    R* SL = scr;            // N x M
-    R* SF = SL + N * M;     // N x N  (later S Ft)
-    R* G = SF + N * N;      // M x M
-    R* ev = G + M * M;      // N
-    R* O = ev + N;          // N x N + N
+    R* SL = scr;             // N x M
+    R* SF = SL + N * LM;     // N x N  (later S Ft)
+    R* G = SF + N * LD;      // M x M
+    R* ev = G + M * LM;      // N
+    R* O = ev + N;           // N x N + N
     const int r = g.lr;
     const bool ok = gains<R, N, M>(val, sb, Kd, scr, g);
     // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
@@ -231,50 +243,50 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
         R ct = c[r];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            ft[j] = F[r * N + j];
-            sft[j] = SF[r * N + j];
+            ft[j] = F[r * LD + j];
+            sft[j] = SF[r * LD + j];
         }
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-            const R la = L[r * M + a];
-            const R sa = SL[r * M + a];
+            const R la = L[r * LM + a];
+            const R sa = SL[r * LM + a];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                ft[j] -= la * Kd[a * (N + 1) + j];
-                sft[j] -= sa * Kd[a * (N + 1) + j];
+                ft[j] -= la * Kd[a * LK + j];
+                sft[j] -= sa * Kd[a * LK + j];
             }
-            ct += la * Kd[a * (N + 1) + N];
+            ct += la * Kd[a * LK + N];
         }
         g.sync();
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Ft[LAffine<N>::OF + r * N + j] = ft[j];
-            SF[r * N + j] = sft[j];
+            Ft[A::OF + r * LD + j] = ft[j];
+            SF[r * LD + j] = sft[j];
         }
-        Ft[LAffine<N>::OC + r] = ct;
+        Ft[A::OC + r] = ct;
     }
     g.sync();
     // S <- F^T (S Ft) + Q ; v <- Ft^T (v - S c) + q
     {
         R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = Q[r * N + j];
+        for (int j = 0; j < N; ++j) acc[j] = Q[r * LD + j];
         R t = q[r];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R fk = F[k * N + r];
+            const R fk = F[k * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * N + j];
-            t += Ft[LAffine<N>::OF + k * N + r] * ev[k];
+            for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * LD + j];
+            t += Ft[A::OF + k * LD + r] * ev[k];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[r * N + j] = acc[j];
-        O[N * N + r] = t;
+        for (int j = 0; j < N; ++j) O[r * LD + j] = acc[j];
+        O[N * LD + r] = t;
     }
     g.sync();
 #pragma unroll
-    for (int j = 0; j < N; ++j) val[V::OS + r * N + j] = R(0.5) * (O[r * N + j] + O[j * N + r]);
-    val[V::OV + r] = O[N * N + r];
+    for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = R(0.5) * (O[r * LD + j] + O[j * LD + r]);
+    val[V::OV + r] = O[N * LD + r];
     g.sync();
     return ok;
 }
@@ -282,8 +294,9 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
 // Scratch of fold_step (elements of R).
 template <int N, int M>
 constexpr int fold_scratch() {
-    return 2 * N * N /*JF | A2F, later the staged C and J*/ + N * N /*F^T J2 F*/ +
-           3 * N * M /*P2, JL, Z*/ + 2 * N /*w, A2 c*/ + M * M /*G*/ + M * (2 * N + 1) /*rhs*/;
+    return 2 * N * lds(N) /*JF | A2F, later the staged C and J*/ + N * lds(N) /*F^T J2 F*/ +
+           2 * N * lds(M) /*P2, JL*/ + M * lds(N) /*Z*/ + 2 * N /*w, A2 c*/ + M * lds(M) /*G*/ +
+           M * lds(2 * N + 1) /*rhs*/;
 }
 
 // P <- a_k (x) P (eq. lqt_comb, a_k = (F, c, L U^{-1} L^T, H^T X r, H^T X H)
@@ -300,22 +313,23 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     constexpr int NR = 2 * N + 1;
+    constexpr int LD = SLay::LD, LM = SLay::LM, LR = lds(NR);
     const R* e1 = sb + SLay::E;
     const R* F = e1 + E::OA;
     const R* c = e1 + E::OB;
     const R* L = sb + SLay::L;
     const R* U = sb + SLay::U;
-    R* JF = scr;             // N x N
-    R* A2F = JF + N * N;     // N x N
-    R* FJF = A2F + N * N;    // N x N
-    R* P2 = FJF + N * N;     // N x M
-    R* JL = P2 + N * M;      // N x M
-    R* Z = JL + N * M;       // M x N
-    R* w = Z + M * N;        // N
-    R* A2c = w + N;          // N
-    R* G = A2c + N;          // M x M
-    R* rhs = G + M * M;      // M x NR
-    R* O = JF;               // staged C and J (2 N x N), after JF and A2F are consumed
+    R* JF = scr;              // N x N
+    R* A2F = JF + N * LD;     // N x N
+    R* FJF = A2F + N * LD;    // N x N
+    R* P2 = FJF + N * LD;     // N x M
+    R* JL = P2 + N * LM;      // N x M
+    R* Z = JL + N * LM;       // M x N
+    R* w = Z + M * LD;        // N
+    R* A2c = w + N;           // N
+    R* G = A2c + N;           // M x M
+    R* rhs = G + M * LM;      // M x NR
+    R* O = JF;                // staged C and J (2 N x N), after JF and A2F are consumed
     const int r = g.lr;
     // 1. JF = J2 F, JL = J2 L, w = eta2 - J2 c (row r of J2)
     {
@@ -327,17 +341,17 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         for (int a = 0; a < M; ++a) jl[a] = R(0);
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
-            const R jk = P[E::OJ + r * N + k];
+            const R jk = P[E::OJ + r * LD + k];
 #pragma unroll
-            for (int j = 0; j < N; ++j) jf[j] += jk * F[k * N + j];
+            for (int j = 0; j < N; ++j) jf[j] += jk * F[k * LD + j];
 #pragma unroll
-            for (int a = 0; a < M; ++a) jl[a] += jk * L[k * M + a];
+            for (int a = 0; a < M; ++a) jl[a] += jk * L[k * LM + a];
             t -= jk * c[k];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) JF[r * N + j] = jf[j];
+        for (int j = 0; j < N; ++j) JF[r * LD + j] = jf[j];
 #pragma unroll
-        for (int a = 0; a < M; ++a) JL[r * M + a] = jl[a];
+        for (int a = 0; a < M; ++a) JL[r * LM + a] = jl[a];
         w[r] = t;
     }
     //    A2F = A2 F, P2 = A2 L (also into the right sides, transposed), A2 c
@@ -350,19 +364,19 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         for (int a = 0; a < M; ++a) pl[a] = R(0);
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
-            const R ak = P[E::OA + r * N + k];
+            const R ak = P[E::OA + r * LD + k];
 #pragma unroll
-            for (int j = 0; j < N; ++j) af[j] += ak * F[k * N + j];
+            for (int j = 0; j < N; ++j) af[j] += ak * F[k * LD + j];
 #pragma unroll
-            for (int a = 0; a < M; ++a) pl[a] += ak * L[k * M + a];
+            for (int a = 0; a < M; ++a) pl[a] += ak * L[k * LM + a];
             t += ak * c[k];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) A2F[r * N + j] = af[j];
+        for (int j = 0; j < N; ++j) A2F[r * LD + j] = af[j];
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-            P2[r * M + a] = pl[a];
-            rhs[a * NR + N + 1 + r] = pl[a];
+            P2[r * LM + a] = pl[a];
+            rhs[a * LR + N + 1 + r] = pl[a];
         }
         A2c[r] = t;
     }
@@ -372,26 +386,26 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         R gg[M], zz[N];
         R t = R(0);
 #pragma unroll
-        for (int b = 0; b < M; ++b) gg[b] = U[r * M + b];
+        for (int b = 0; b < M; ++b) gg[b] = U[r * LM + b];
 #pragma unroll
         for (int j = 0; j < N; ++j) zz[j] = R(0);
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
-            const R lk = L[k * M + r];
+            const R lk = L[k * LM + r];
 #pragma unroll
-            for (int b = 0; b < M; ++b) gg[b] += lk * JL[k * M + b];
+            for (int b = 0; b < M; ++b) gg[b] += lk * JL[k * LM + b];
 #pragma unroll
-            for (int j = 0; j < N; ++j) zz[j] += lk * JF[k * N + j];
+            for (int j = 0; j < N; ++j) zz[j] += lk * JF[k * LD + j];
             t += lk * w[k];
         }
 #pragma unroll
-        for (int b = 0; b < M; ++b) G[r * M + b] = gg[b];
+        for (int b = 0; b < M; ++b) G[r * LM + b] = gg[b];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Z[r * N + j] = zz[j];
-            rhs[r * NR + j] = zz[j];
+            Z[r * LD + j] = zz[j];
+            rhs[r * LR + j] = zz[j];
         }
-        rhs[r * NR + N] = t;
+        rhs[r * LR + N] = t;
     }
     {
         R acc[N];
@@ -399,31 +413,31 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         for (int j = 0; j < N; ++j) acc[j] = R(0);
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
-            const R fk = F[k * N + r];
+            const R fk = F[k * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += fk * JF[k * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += fk * JF[k * LD + j];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) FJF[r * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) FJF[r * LD + j] = acc[j];
     }
     g.sync();
     // 3. [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]
-    const bool ok = solve_gj<N, M, NR>(G, M, rhs, NR, g);
+    const bool ok = solve_gj<N, M, NR>(G, LM, rhs, LR, g);
     // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (in place: A2 is not read again)
     {
         R aa[N];
         R t = A2c[r] + P[E::OB + r];
 #pragma unroll
-        for (int j = 0; j < N; ++j) aa[j] = A2F[r * N + j];
+        for (int j = 0; j < N; ++j) aa[j] = A2F[r * LD + j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
-            const R pa = P2[r * M + a];
+            const R pa = P2[r * LM + a];
 #pragma unroll
-            for (int j = 0; j < N; ++j) aa[j] -= pa * rhs[a * NR + j];
-            t += pa * rhs[a * NR + N];
+            for (int j = 0; j < N; ++j) aa[j] -= pa * rhs[a * LR + j];
+            t += pa * rhs[a * LR + N];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) P[E::OA + r * N + j] = aa[j];
+        for (int j = 0; j < N; ++j) P[E::OA + r * LD + j] = aa[j];
         P[E::OB + r] = t;
     }
     g.sync();
@@ -432,39 +446,39 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
     {
         R cc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) cc[j] = P[E::OC + r * N + j];
+        for (int j = 0; j < N; ++j) cc[j] = P[E::OC + r * LD + j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
-            const R pa = P2[r * M + a];
+            const R pa = P2[r * LM + a];
 #pragma unroll
-            for (int j = 0; j < N; ++j) cc[j] += pa * rhs[a * NR + N + 1 + j];
+            for (int j = 0; j < N; ++j) cc[j] += pa * rhs[a * LR + N + 1 + j];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[r * N + j] = cc[j];
+        for (int j = 0; j < N; ++j) O[r * LD + j] = cc[j];
     }
     {
         R jj[N];
         R t = e1[E::OE + r];
 #pragma unroll
-        for (int j = 0; j < N; ++j) jj[j] = e1[E::OJ + r * N + j] + FJF[r * N + j];
+        for (int j = 0; j < N; ++j) jj[j] = e1[E::OJ + r * LD + j] + FJF[r * LD + j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
-            const R za = Z[a * N + r];
+            const R za = Z[a * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) jj[j] -= za * rhs[a * NR + j];
-            t -= za * rhs[a * NR + N];
+            for (int j = 0; j < N; ++j) jj[j] -= za * rhs[a * LR + j];
+            t -= za * rhs[a * LR + N];
         }
 #pragma unroll 4
-        for (int k = 0; k < N; ++k) t += F[k * N + r] * w[k];
+        for (int k = 0; k < N; ++k) t += F[k * LD + r] * w[k];
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[N * N + r * N + j] = jj[j];
+        for (int j = 0; j < N; ++j) O[N * LD + r * LD + j] = jj[j];
         P[E::OE + r] = t;
     }
     g.sync();
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        P[E::OC + r * N + j] = R(0.5) * (O[r * N + j] + O[j * N + r]);
-        P[E::OJ + r * N + j] = R(0.5) * (O[N * N + r * N + j] + O[N * N + j * N + r]);
+        P[E::OC + r * LD + j] = R(0.5) * (O[r * LD + j] + O[j * LD + r]);
+        P[E::OJ + r * LD + j] = R(0.5) * (O[N * LD + r * LD + j] + O[N * LD + j * LD + r]);
     }
     g.sync();
     return ok;

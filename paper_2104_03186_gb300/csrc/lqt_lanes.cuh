@@ -3,7 +3,8 @@
 //
 // A group of LG = N lanes (N a power of two, N <= 32) owns one element; lane r
 // of the group owns row r of every N-row matrix, and the matrices live in
-// shared memory (row-major, leading dimension given).  Products are row
+// shared memory, row-major with an odd row stride (lds: the lanes reading one
+// column of their own rows then hit distinct banks).  Products are row
 // products: lane r reads its row of the left factor and the whole right
 // factor (broadcast reads).  Phases that read what other lanes wrote are
 // separated by a group sync.  The formulas are those of lqt_dense.cuh:
@@ -28,6 +29,9 @@ struct Group {
     }
     __device__ void sync() const { __syncwarp(mask); }
 };
+
+// Row stride of a shared-memory matrix with `cols` columns: the next odd number.
+constexpr int lds(int cols) { return cols | 1; }
 
 // IEEE round-to-nearest reciprocal in the arithmetic type
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
@@ -118,37 +122,49 @@ __device__ bool solve_gj(T* Mx, int ldm, T* Bx, int ldb, const Group<LG>& g) {
     return ok;
 }
 
-// Full element in shared memory: A[N][N], b[N], C[N][N], eta[N], J[N][N].
+// Full element in shared memory: A[N][N], b[N], C[N][N], eta[N], J[N][N]
+// (matrices with row stride LD).
 template <int N>
 struct LElem {
-    static constexpr int OA = 0, OB = N * N, OC = N * N + N, OE = 2 * N * N + N,
-                         OJ = 2 * N * N + 2 * N, SIZE = 3 * N * N + 2 * N;
+    static constexpr int LD = lds(N);
+    static constexpr int OA = 0, OB = N * LD, OC = OB + N, OE = OC + N * LD, OJ = OE + N,
+                         SIZE = OJ + N * LD;
 };
 
 template <int N>
 struct LValue {  // S[N][N], v[N]
-    static constexpr int OS = 0, OV = N * N, SIZE = N * N + N;
+    static constexpr int LD = lds(N);
+    static constexpr int OS = 0, OV = N * LD, SIZE = N * LD + N;
 };
 
 template <int N>
 struct LAffine {  // F[N][N], c[N]
-    static constexpr int OF = 0, OC = N * N, SIZE = N * N + N;
+    static constexpr int LD = lds(N);
+    static constexpr int OF = 0, OC = N * LD, SIZE = N * LD + N;
 };
 
 // Scratch a group needs for combine (elements of the arithmetic type).
 template <int N>
 constexpr int combine_scratch() {
-    return N * N /*Mx*/ + N * (2 * N + 1) /*Bx*/ + N /*w*/ + N * N /*JX or T3*/ + LElem<N>::SIZE;
+    return N * lds(N) /*Mx*/ + N * lds(2 * N + 1) /*Bx*/ + N /*w*/ + N * lds(N) /*JX or T3*/ +
+           LElem<N>::SIZE;
+}
+
+// Scratch of value_apply.
+template <int N>
+constexpr int value_scratch() {
+    return 4 * N * lds(N) + 2 * N;
 }
 
 template <int LG, int N, typename R>
 __device__ void set_neutral(R* e, const Group<LG>& g) {
+    constexpr int LD = LElem<N>::LD;
     const int r = g.lr;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        e[LElem<N>::OA + r * N + j] = r == j ? R(1) : R(0);
-        e[LElem<N>::OC + r * N + j] = R(0);
-        e[LElem<N>::OJ + r * N + j] = R(0);
+        e[LElem<N>::OA + r * LD + j] = r == j ? R(1) : R(0);
+        e[LElem<N>::OC + r * LD + j] = R(0);
+        e[LElem<N>::OJ + r * LD + j] = R(0);
     }
     e[LElem<N>::OB + r] = R(0);
     e[LElem<N>::OE + r] = R(0);
@@ -157,15 +173,16 @@ __device__ void set_neutral(R* e, const Group<LG>& g) {
 
 // out = e1 (x) e2 (eq. lqt_comb).  out may alias e1 or e2.
 template <int LG, int N, typename R>
-__device__ bool combine(const R* e1, const R* e2, R* out, R* scr,
-                        const Group<LG>& g) {
+__device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG>& g) {
     using E = LElem<N>;
+    constexpr int LD = E::LD;
     constexpr int NR = 2 * N + 1;
+    constexpr int LB = lds(NR);
     R* Mx = scr;
-    R* Bx = Mx + N * N;
-    R* w = Bx + N * NR;
+    R* Bx = Mx + N * LD;
+    R* w = Bx + N * LB;
     R* T = w + N;
-    R* O = T + N * N;  // result staged here, copied to out at the end
+    R* O = T + N * LD;  // result staged here, copied to out at the end
     const int r = g.lr;
     // Mx = I + C1 J2 ; Bx = [A1 | b1 + C1 eta2 | C1]
     {
@@ -175,48 +192,48 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr,
         R be = e1[E::OB + r];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R ck = e1[E::OC + r * N + k];
+            const R ck = e1[E::OC + r * LD + k];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += ck * e2[E::OJ + k * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += ck * e2[E::OJ + k * LD + j];
             be += ck * e2[E::OE + k];
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Mx[r * N + j] = acc[j];
-            Bx[r * NR + j] = e1[E::OA + r * N + j];
-            Bx[r * NR + N + 1 + j] = e1[E::OC + r * N + j];
+            Mx[r * LD + j] = acc[j];
+            Bx[r * LB + j] = e1[E::OA + r * LD + j];
+            Bx[r * LB + N + 1 + j] = e1[E::OC + r * LD + j];
         }
-        Bx[r * NR + N] = be;
+        Bx[r * LB + N] = be;
         // w = eta2 - J2 b1
         R t = e2[E::OE + r];
 #pragma unroll
-        for (int k = 0; k < N; ++k) t -= e2[E::OJ + r * N + k] * e1[E::OB + k];
+        for (int k = 0; k < N; ++k) t -= e2[E::OJ + r * LD + k] * e1[E::OB + k];
         w[r] = t;
     }
     g.sync();
-    const bool ok = solve_gj<LG, N, NR>(Mx, N, Bx, NR, g);
+    const bool ok = solve_gj<LG, N, NR>(Mx, LD, Bx, LB, g);
     // eta = X1^T w + eta1 ; JX = J2 X1 (into T)
     {
         R t = e1[E::OE + r];
 #pragma unroll
-        for (int k = 0; k < N; ++k) t += Bx[k * NR + r] * w[k];
+        for (int k = 0; k < N; ++k) t += Bx[k * LB + r] * w[k];
         O[E::OE + r] = t;
     }
-    row_mul<N, N, N>(T, N, e2 + E::OJ, N, Bx, NR, r);
+    row_mul<N, N, N>(T, LD, e2 + E::OJ, LD, Bx, LB, r);
     g.sync();
     // J = A1^T JX + J1
     {
         R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = e1[E::OJ + r * N + j];
+        for (int j = 0; j < N; ++j) acc[j] = e1[E::OJ + r * LD + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R a = e1[E::OA + k * N + r];
+            const R a = e1[E::OA + k * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += a * T[k * LD + j];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[E::OJ + r * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) O[E::OJ + r * LD + j] = acc[j];
     }
     g.sync();
     // A = A2 X1 ; b = A2 x2 + b2 ; T = A2 X3
@@ -227,18 +244,18 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr,
         for (int j = 0; j < N; ++j) aa[j] = tt[j] = R(0);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R a2 = e2[E::OA + r * N + k];
+            const R a2 = e2[E::OA + r * LD + k];
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                aa[j] += a2 * Bx[k * NR + j];
-                tt[j] += a2 * Bx[k * NR + N + 1 + j];
+                aa[j] += a2 * Bx[k * LB + j];
+                tt[j] += a2 * Bx[k * LB + N + 1 + j];
             }
-            bb += a2 * Bx[k * NR + N];
+            bb += a2 * Bx[k * LB + N];
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            O[E::OA + r * N + j] = aa[j];
-            T[r * N + j] = tt[j];
+            O[E::OA + r * LD + j] = aa[j];
+            T[r * LD + j] = tt[j];
         }
         O[E::OB + r] = bb;
     }
@@ -247,23 +264,23 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr,
     {
         R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = e2[E::OC + r * N + j];
+        for (int j = 0; j < N; ++j) acc[j] = e2[E::OC + r * LD + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R t = T[r * N + k];
+            const R t = T[r * LD + k];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += t * e2[E::OA + j * N + k];
+            for (int j = 0; j < N; ++j) acc[j] += t * e2[E::OA + j * LD + k];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[E::OC + r * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) O[E::OC + r * LD + j] = acc[j];
     }
     g.sync();
     // symmetrise C and J while copying out
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        out[E::OA + r * N + j] = O[E::OA + r * N + j];
-        out[E::OC + r * N + j] = R(0.5) * (O[E::OC + r * N + j] + O[E::OC + j * N + r]);
-        out[E::OJ + r * N + j] = R(0.5) * (O[E::OJ + r * N + j] + O[E::OJ + j * N + r]);
+        out[E::OA + r * LD + j] = O[E::OA + r * LD + j];
+        out[E::OC + r * LD + j] = R(0.5) * (O[E::OC + r * LD + j] + O[E::OC + j * LD + r]);
+        out[E::OJ + r * LD + j] = R(0.5) * (O[E::OJ + r * LD + j] + O[E::OJ + j * LD + r]);
     }
     out[E::OB + r] = O[E::OB + r];
     out[E::OE + r] = O[E::OE + r];
@@ -276,10 +293,11 @@ template <int LG, int N, typename R>
 __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
     using E = LElem<N>;
     using V = LValue<N>;
+    constexpr int LD = E::LD;
     R* Mx = scr;
-    R* X = Mx + N * N;
-    R* T = X + N * N;
-    R* e = T + N * N;
+    R* X = Mx + N * LD;
+    R* T = X + N * LD;
+    R* e = T + N * LD;
     R* O = e + N;
     const int r = g.lr;
     {
@@ -288,28 +306,28 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
         for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R ck = P[E::OC + r * N + k];
+            const R ck = P[E::OC + r * LD + k];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += ck * val[V::OS + k * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += ck * val[V::OS + k * LD + j];
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            Mx[r * N + j] = acc[j];
-            X[r * N + j] = P[E::OA + r * N + j];
+            Mx[r * LD + j] = acc[j];
+            X[r * LD + j] = P[E::OA + r * LD + j];
         }
         R t = val[V::OV + r];
 #pragma unroll
-        for (int k = 0; k < N; ++k) t -= val[V::OS + r * N + k] * P[E::OB + k];
+        for (int k = 0; k < N; ++k) t -= val[V::OS + r * LD + k] * P[E::OB + k];
         e[r] = t;
     }
     g.sync();
-    const bool ok = solve_gj<LG, N, N>(Mx, N, X, N, g);
+    const bool ok = solve_gj<LG, N, N>(Mx, LD, X, LD, g);
     // T = S X1 ; v' = X1^T e + eta
-    row_mul<N, N, N>(T, N, val + V::OS, N, X, N, r);
+    row_mul<N, N, N>(T, LD, val + V::OS, LD, X, LD, r);
     {
         R t = P[E::OE + r];
 #pragma unroll
-        for (int k = 0; k < N; ++k) t += X[k * N + r] * e[k];
+        for (int k = 0; k < N; ++k) t += X[k * LD + r] * e[k];
         O[V::OV + r] = t;
     }
     g.sync();
@@ -317,20 +335,20 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
     {
         R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = P[E::OJ + r * N + j];
+        for (int j = 0; j < N; ++j) acc[j] = P[E::OJ + r * LD + j];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-            const R a = P[E::OA + k * N + r];
+            const R a = P[E::OA + k * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += a * T[k * N + j];
+            for (int j = 0; j < N; ++j) acc[j] += a * T[k * LD + j];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[V::OS + r * N + j] = acc[j];
+        for (int j = 0; j < N; ++j) O[V::OS + r * LD + j] = acc[j];
     }
     g.sync();
 #pragma unroll
     for (int j = 0; j < N; ++j)
-        val[V::OS + r * N + j] = R(0.5) * (O[V::OS + r * N + j] + O[V::OS + j * N + r]);
+        val[V::OS + r * LD + j] = R(0.5) * (O[V::OS + r * LD + j] + O[V::OS + j * LD + r]);
     val[V::OV + r] = O[V::OV + r];
     g.sync();
     return ok;
@@ -338,9 +356,9 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
 
 // f2 after f1: (F2 F1, F2 c1 + c2) into out (may alias f1 or f2)
 template <int LG, int N, typename R>
-__device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr,
-                               const Group<LG>& g) {
+__device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr, const Group<LG>& g) {
     using A = LAffine<N>;
+    constexpr int LD = A::LD;
     const int r = g.lr;
     R acc[N];
     R c = f2[A::OC + r];
@@ -348,14 +366,14 @@ __device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr,
     for (int j = 0; j < N; ++j) acc[j] = R(0);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        const R a = f2[A::OF + r * N + k];
+        const R a = f2[A::OF + r * LD + k];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] += a * f1[A::OF + k * N + j];
+        for (int j = 0; j < N; ++j) acc[j] += a * f1[A::OF + k * LD + j];
         c += a * f1[A::OC + k];
     }
     g.sync();
 #pragma unroll
-    for (int j = 0; j < N; ++j) out[A::OF + r * N + j] = acc[j];
+    for (int j = 0; j < N; ++j) out[A::OF + r * LD + j] = acc[j];
     out[A::OC + r] = c;
     g.sync();
     (void)scr;
@@ -365,10 +383,11 @@ __device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr,
 template <int LG, int N, typename R>
 __device__ void affine_apply(const R* f, R* x, const Group<LG>& g) {
     using A = LAffine<N>;
+    constexpr int LD = A::LD;
     const int r = g.lr;
     R t = f[A::OC + r];
 #pragma unroll
-    for (int k = 0; k < N; ++k) t += f[A::OF + r * N + k] * x[k];
+    for (int k = 0; k < N; ++k) t += f[A::OF + r * LD + k] * x[k];
     g.sync();
     x[r] = t;
     g.sync();
