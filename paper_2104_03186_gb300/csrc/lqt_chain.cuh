@@ -45,6 +45,7 @@
 #include <cuda_runtime.h>
 
 #include "lqt_lane_step.cuh"
+#include "lqt_tma.cuh"
 
 namespace lqt {
 namespace chain {
@@ -166,8 +167,11 @@ struct FdownSmem {
 };
 
 template <int N, int M>
-struct RollSmem {
-    static constexpr int SIZE = N + M;
+struct RollSmem {  // x, u, then F_k (N x lds(N)), L_k (N x lds(M)), K_k (M x lds(N))
+    static constexpr int F = N + M;
+    static constexpr int L = F + N * lds(N);
+    static constexpr int K = L + N * lds(M);
+    static constexpr int SIZE = K + M * lds(N);
 };
 
 // Groups per CTA: at most 256 threads and about 100 KB of shared memory.
@@ -210,8 +214,10 @@ __global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
     const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     bool ok = true;
     set_neutral<N, N>(P, g);
+    // staging area for the step inputs: the scratch beyond the step's Y
+    constexpr int YS = StepLayout<N, M>::SIZE - StepLayout<N, M>::Y;
     for (long long k = e0 - 1; k >= s0; --k) {
-        load_step<R, N, M, false>(D, k, sb, scr, g, ok);
+        load_step<R, N, M, false>(D, k, sb, scr, g, ok, scr + YS, S::SCR - YS);
         ok &= fold_step<R, N, M>(P, sb, scr, g);
     }
     RT* out = a.E + c * E::SIZE;
@@ -348,21 +354,21 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     Phi[A::OC + r] = R(0);
     g.sync();
     bool ok = true;
+    constexpr int YS = StepLayout<N, M>::SIZE - StepLayout<N, M>::Y;
     for (long long k = e0 - 1; k >= s0; --k) {
-        load_step<R, N, M, false>(D, k, sb, scr, g, ok);
+        load_step<R, N, M, false>(D, k, sb, scr, g, ok, scr + YS, S::SCR - YS);
         ok &= riccati<R, N, M>(val, sb, Kd, Ft, scr, g);
+        // outputs by coalesced stores (lane r writes column r of each row)
         if (a.out_mask & 1) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) D.S[k * N * N + r * N + j] = val[V::OS + r * V::LD + j];
+#pragma unroll 8
+            for (int i = 0; i < N; ++i) D.S[k * N * N + i * N + r] = val[V::OS + i * V::LD + r];
             D.v[k * N + r] = val[V::OV + r];
         }
-        if (r < M) {
-            if (a.out_mask & 2) {
-#pragma unroll
-                for (int j = 0; j < N; ++j) D.K[k * M * N + r * N + j] = Kd[r * (N + 1) + j];
-            }
-            D.u[k * M + r] = Kd[r * (N + 1) + N];  // feedforward d_k, replaced in the rollout
+        if (a.out_mask & 2) {
+#pragma unroll 8
+            for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = Kd[i * (N + 1) + r];
         }
+        if (r < M) D.u[k * M + r] = Kd[r * (N + 1) + N];  // feedforward d_k, replaced in the rollout
         // chunk map after adding step k: Phi <- Phi Ft, gamma <- gamma + Phi ct
         R pn[N];
         R gm = Phi[A::OC + r];
@@ -448,16 +454,31 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     xc[r] = lc == 0 ? D.x0[r] : static_cast<R>(a.X[c * N + r]);
     g.sync();
+    constexpr int LD = lds(N), LM = lds(M);
+    R* Fs = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::F;
+    R* Ls = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::L;
+    R* Ks = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::K;
     for (long long k = s0; k < e0; ++k) {
+        // F_k and L_k into shared memory by coalesced asynchronous copies
         const R* F = D.F + k * D.sF;
         const R* Lk = D.L + k * D.sL;
+#pragma unroll 8
+        for (int t = r; t < N * N; t += N) cp_async<sizeof(R)>(Fs + (t / N) * LD + t % N, F + t);
+#pragma unroll 4
+        for (int t = r; t < N * M; t += N) cp_async<sizeof(R)>(Ls + (t / M) * LM + t % M, Lk + t);
+#pragma unroll 4
+        for (int t = r; t < M * N; t += N)
+            cp_async<sizeof(R)>(Ks + (t / N) * LD + t % N, D.K + k * M * N + t);
+        cp_async_commit();
         const R xr = xc[r];
         D.x[k * N + r] = a.refine_add ? D.x[k * N + r] + xr : xr;
+        cp_async_wait<0>();
+        g.sync();
         // u = d - K x (lanes a < M), published through shared memory
         if (r < M) {
             R t = D.u[k * M + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) t -= D.K[k * M * N + r * N + j] * xc[j];
+            for (int j = 0; j < N; ++j) t -= Ks[r * LD + j] * xc[j];
             us[r] = t;
             if (a.refine_add)
                 it.u_out[k * M + r] = it.u_out[k * M + r] + (t - it.qh[k * M + r]);
@@ -467,9 +488,9 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
         g.sync();
         R t = D.c ? D.c[k * D.sc + r] : R(0);
 #pragma unroll
-        for (int j = 0; j < N; ++j) t += __ldg(F + r * N + j) * xc[j];
+        for (int j = 0; j < N; ++j) t += Fs[r * LD + j] * xc[j];
 #pragma unroll
-        for (int b = 0; b < M; ++b) t += __ldg(Lk + r * M + b) * us[b];
+        for (int b = 0; b < M; ++b) t += Ls[r * LM + b] * us[b];
         g.sync();
         xc[r] = t;
         g.sync();
@@ -580,7 +601,7 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
             rh[r] = h;
         }
         g.sync();
-        ok &= solve_gj<N, M, 1>(Um, M, rh, 1, g);
+        ok &= solve_spd<N, M, 1>(Um, M, rh, 1, g);
         for (int b = 0; b < M; ++b) e -= static_cast<D64>(L[r * M + b]) * rh[b];
         const_cast<R*>(D2.eta)[k * N + r] = static_cast<R>(-gr);
         const_cast<R*>(D2.c)[k * N + r] = static_cast<R>(e);
@@ -665,11 +686,11 @@ __global__ void __launch_bounds__(NG* N) k_nresid(const Item<R>* items1, const I
         copy_in(val + V::OV, D.v + (k + 1) * N, N, r, N);
         g.sync();
         ok &= riccati<D64, N, M>(val, sb, Kd, Ft, scr, g);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            Rk[r * N + j] = static_cast<R>(val[V::OS + r * V::LD + j] -
-                                           static_cast<D64>(D.S[k * N * N + r * N + j]));
-            const_cast<R*>(D3.F)[k * N * N + r * N + j] = static_cast<R>(Ft[A::OF + r * A::LD + j]);
+#pragma unroll 8
+        for (int i = 0; i < N; ++i) {  // coalesced: lane r writes column r
+            Rk[i * N + r] = static_cast<R>(val[V::OS + i * V::LD + r] -
+                                           static_cast<D64>(D.S[k * N * N + i * N + r]));
+            const_cast<R*>(D3.F)[k * N * N + i * N + r] = static_cast<R>(Ft[A::OF + i * A::LD + r]);
         }
         const_cast<R*>(D3.eta)[k * N + r] =
             static_cast<R>(val[V::OV + r] - static_cast<D64>(D.v[k * N + r]));
@@ -712,11 +733,8 @@ __global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const I
                          static_cast<D64>(D3.v[(k + 1) * N + r]);
         g.sync();
         ok &= gains<D64, N, M>(val, sb, Kd, scr, g);
-        if (r < M) {
-#pragma unroll
-            for (int j = 0; j < N; ++j)
-                D.K[k * M * N + r * N + j] = static_cast<R>(Kd[r * (N + 1) + j]);
-        }
+#pragma unroll 8
+        for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = static_cast<R>(Kd[i * (N + 1) + r]);
         g.sync();
     }
     flag(status, ok);

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "lqt_lanes.cuh"
+#include "lqt_tma.cuh"
 
 namespace lqt {
 
@@ -60,10 +61,12 @@ constexpr int load_scratch() {
 
 // Step k of D (inputs of type RI) into the step buffer sb (type R).  WITH_C
 // also forms C = L U^{-1} L^T (the general combine needs it; fold_step and
-// riccati do not); COST = false loads the dynamics only.
+// riccati do not); COST = false loads the dynamics only.  With a staging area
+// (stage, stage_cap elements) large enough, X_k, H_k and r_k are first copied
+// to shared memory by coalesced loads.
 template <typename R, int N, int M, bool WITH_C, typename RI = R, bool COST = true>
 __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const Group<N>& g,
-                          bool& ok) {
+                          bool& ok, R* stage = nullptr, int stage_cap = 0) {
     using SL = StepLayout<N, M>;
     using E = LElem<N>;
     constexpr int LD = SL::LD, LM = SL::LM;
@@ -80,38 +83,94 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
     const RI* H = D.H + k * D.sH;
     const RI* X = D.X + k * D.sX;
     const RI* rk = D.r ? D.r + k * D.sr : nullptr;
-#pragma unroll
-    for (int j = 0; j < N; ++j) e[E::OA + r * LD + j] = R(__ldg(F + r * N + j));
-#pragma unroll
-    for (int a = 0; a < M; ++a) L[r * LM + a] = R(__ldg(Lk + r * M + a));
-    if (r < M) {
-#pragma unroll
-        for (int b = 0; b < M; ++b) U[r * LM + b] = R(__ldg(Uk + r * M + b));
-    }
+    // F, L, U by coalesced loads (consecutive lanes, consecutive elements)
+#pragma unroll 8
+    for (int t = r; t < N * N; t += N) e[E::OA + (t / N) * LD + t % N] = R(__ldg(F + t));
+#pragma unroll 4
+    for (int t = r; t < N * M; t += N) L[(t / M) * LM + t % M] = R(__ldg(Lk + t));
+#pragma unroll 4
+    for (int t = r; t < M * M; t += N) U[(t / M) * LM + t % M] = R(__ldg(Uk + t));
     e[E::OB + r] = D.c ? R(__ldg(D.c + k * D.sc + r)) : R(0);
     if (!COST) {  // dynamics only (F, c, L, U)
         g.sync();
         return;
     }
-    // Y = X H and X r, rows spread over the lanes
-    for (int a = r; a < p; a += N) {
+    const int lp = p | 1;
+    if (stage && p * lp + p * LD + p <= stage_cap) {
+        // X_k, H_k and r_k staged in shared memory by coalesced loads
+        R* Xs = stage;         // p x p, row stride lp
+        R* Hs = Xs + p * lp;   // p x N, row stride LD
+        R* rs = Hs + p * LD;   // p
+        if constexpr (sizeof(R) == sizeof(RI)) {
+            // asynchronous copies: every load of the lane is in flight at once
+            for (int a = 0; a < p; ++a)
+                for (int b = r; b < p; b += N) cp_async<sizeof(R)>(Xs + a * lp + b, X + a * p + b);
+            for (int b = 0; b < p; ++b) cp_async<sizeof(R)>(Hs + b * LD + r, H + b * N + r);
+            for (int b = r; b < p; b += N) {
+                if (rk) cp_async<sizeof(R)>(rs + b, rk + b);
+                else rs[b] = R(0);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+        } else {
+            for (int a = 0; a < p; ++a)
+                for (int b = r; b < p; b += N) Xs[a * lp + b] = R(__ldg(X + a * p + b));
+            for (int b = 0; b < p; ++b) Hs[b * LD + r] = R(__ldg(H + b * N + r));
+            for (int b = r; b < p; b += N) rs[b] = rk ? R(__ldg(rk + b)) : R(0);
+        }
+        g.sync();
+        // Y = X H and X r, rows spread over the lanes
+        for (int a = r; a < p; a += N) {
+            R acc[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = R(0);
+            R t = R(0);
+#pragma unroll 4
+            for (int b = 0; b < p; ++b) {
+                const R xab = Xs[a * lp + b];
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] += xab * Hs[b * LD + j];
+                t += xab * rs[b];
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) Y[a * LD + j] = acc[j];
+            xr[a] = t;
+        }
+        g.sync();
+        // J = H^T Y, eta = H^T (X r)
         R acc[N];
+        R t = R(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = R(0);
-        R t = R(0);
-        for (int b = 0; b < p; ++b) {
-            const R xab = R(__ldg(X + a * p + b));
+#pragma unroll 4
+        for (int a = 0; a < p; ++a) {
+            const R h = Hs[a * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += xab * R(__ldg(H + b * N + j));
-            if (rk) t += xab * R(__ldg(rk + b));
+            for (int j = 0; j < N; ++j) acc[j] += h * Y[a * LD + j];
+            t += h * xr[a];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) Y[a * LD + j] = acc[j];
-        xr[a] = t;
-    }
-    g.sync();
-    // J = H^T Y, eta = H^T (X r)
-    {
+        for (int j = 0; j < N; ++j) e[E::OJ + r * LD + j] = acc[j];
+        e[E::OE + r] = D.eta ? R(D.eta[k * D.seta + r]) : t;
+    } else {
+        // Y = X H and X r, rows spread over the lanes, operands from global memory
+        for (int a = r; a < p; a += N) {
+            R acc[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = R(0);
+            R t = R(0);
+            for (int b = 0; b < p; ++b) {
+                const R xab = R(__ldg(X + a * p + b));
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] += xab * R(__ldg(H + b * N + j));
+                if (rk) t += xab * R(__ldg(rk + b));
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) Y[a * LD + j] = acc[j];
+            xr[a] = t;
+        }
+        g.sync();
+        // J = H^T Y, eta = H^T (X r)
         R acc[N];
         R t = R(0);
 #pragma unroll
@@ -127,17 +186,14 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         e[E::OE + r] = D.eta ? R(D.eta[k * D.seta + r]) : t;
     }
     if (WITH_C) {
-        // C = L U^{-1} L^T: solve U Z = L^T (M x M, N right-hand sides)
-        R* Um = scr;
-        R* Z = Um + M * LM;
+        // C = L U^{-1} L^T: solve U Z = L^T (M x M SPD, N right-hand sides)
+        R* Z = scr + M * LM;
         if (r < M) {
-#pragma unroll
-            for (int b = 0; b < M; ++b) Um[r * LM + b] = U[r * LM + b];
 #pragma unroll
             for (int j = 0; j < N; ++j) Z[r * LD + j] = L[j * LM + r];
         }
         g.sync();
-        ok &= solve_gj<N, M, N>(Um, LM, Z, LD, g);
+        ok &= solve_spd<N, M, N>(U, LM, Z, LD, g);
         row_mul<N, M, N>(e + E::OC, LD, L, LM, Z, LD, r);
     }
     g.sync();
@@ -211,7 +267,7 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
         Kd[r * LK + N] = w;
     }
     g.sync();
-    return solve_gj<N, M, N + 1>(G, LM, Kd, LK, g);
+    return solve_spd<N, M, N + 1>(G, LM, Kd, LK, g);
 }
 
 // One Riccati step on the value (S, v) in val (Sec. II-B): writes the gains
@@ -422,7 +478,7 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
     }
     g.sync();
     // 3. [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]
-    const bool ok = solve_gj<N, M, NR>(G, LM, rhs, LR, g);
+    const bool ok = solve_spd<N, M, NR>(G, LM, rhs, LR, g);
     // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (in place: A2 is not read again)
     {
         R aa[N];

@@ -122,6 +122,55 @@ __device__ bool solve_gj(T* Mx, int ldm, T* Bx, int ldb, const Group<LG>& g) {
     return ok;
 }
 
+// Solves G Z = B for a symmetric positive definite G (R x R, row stride ldg)
+// and B (R x NR, row stride ldb) by Gauss-Jordan elimination without
+// pivoting (stable for SPD G).  The R + NR columns of [G | B] are spread over
+// the group's lanes (column j in lane j % LG, register slot j / LG) and stay
+// in registers; the factors of each pivot column are broadcast from its lane
+// by warp shuffles, so the elimination needs no group sync.  Z overwrites B.
+// Returns false for a non-positive or non-finite pivot.
+template <int LG, int R, int NR, typename T>
+__device__ bool solve_spd(const T* G, int ldg, T* B, int ldb, const Group<LG>& g) {
+    constexpr int COLS = R + NR;
+    constexpr int SL = (COLS + LG - 1) / LG;
+    const int lane = g.lr;
+    T col[SL][R];
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int j = s * LG + lane;
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            col[s][i] = j < R ? G[i * ldg + j] : (j < COLS ? B[i * ldb + (j - R)] : T(0));
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int ks = k / LG, kl = k % LG;
+        const T piv = __shfl_sync(g.mask, col[ks][k], kl, LG);
+        ok = ok && piv > T(0) && isfinite(piv);
+        const T inv = rcp(piv);
+        T f[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) f[i] = __shfl_sync(g.mask, col[ks][i], kl, LG) * inv;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const T pk = col[s][k];
+#pragma unroll
+            for (int i = 0; i < R; ++i) col[s][i] = i == k ? pk * inv : col[s][i] - f[i] * pk;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int j = s * LG + lane;
+        if (j >= R && j < COLS) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) B[i * ldb + (j - R)] = col[s][i];
+        }
+    }
+    g.sync();
+    return ok;
+}
+
 // Full element in shared memory: A[N][N], b[N], C[N][N], eta[N], J[N][N]
 // (matrices with row stride LD).
 template <int N>
