@@ -63,10 +63,12 @@ constexpr int load_scratch() {
 // also forms C = L U^{-1} L^T (the general combine needs it; fold_step and
 // riccati do not); COST = false loads the dynamics only.  With a staging area
 // (stage, stage_cap elements) large enough, X_k, H_k and r_k are first copied
-// to shared memory by coalesced loads.
+// to shared memory by coalesced loads; h_identity (H_k = I, p = N, checked by
+// the caller) then skips the products: J = X_k, eta = X_k r_k.
 template <typename R, int N, int M, bool WITH_C, typename RI = R, bool COST = true>
 __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const Group<N>& g,
-                          bool& ok, R* stage = nullptr, int stage_cap = 0) {
+                          bool& ok, R* stage = nullptr, int stage_cap = 0,
+                          bool h_identity = false) {
     using SL = StepLayout<N, M>;
     using E = LElem<N>;
     constexpr int LD = SL::LD, LM = SL::LM;
@@ -83,41 +85,75 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
     const RI* H = D.H + k * D.sH;
     const RI* X = D.X + k * D.sX;
     const RI* rk = D.r ? D.r + k * D.sr : nullptr;
-    // F, L, U by coalesced loads (consecutive lanes, consecutive elements)
-#pragma unroll 8
-    for (int t = r; t < N * N; t += N) e[E::OA + (t / N) * LD + t % N] = R(__ldg(F + t));
-#pragma unroll 4
-    for (int t = r; t < N * M; t += N) L[(t / M) * LM + t % M] = R(__ldg(Lk + t));
-#pragma unroll 4
-    for (int t = r; t < M * M; t += N) U[(t / M) * LM + t % M] = R(__ldg(Uk + t));
-    e[E::OB + r] = D.c ? R(__ldg(D.c + k * D.sc + r)) : R(0);
-    if (!COST) {  // dynamics only (F, c, L, U)
-        g.sync();
-        return;
-    }
     const int lp = p | 1;
-    if (stage && p * lp + p * LD + p <= stage_cap) {
-        // X_k, H_k and r_k staged in shared memory by coalesced loads
-        R* Xs = stage;         // p x p, row stride lp
-        R* Hs = Xs + p * lp;   // p x N, row stride LD
-        R* rs = Hs + p * LD;   // p
-        if constexpr (sizeof(R) == sizeof(RI)) {
-            // asynchronous copies: every load of the lane is in flight at once
+    const bool staged = COST && stage && p * lp + p * LD + p <= stage_cap;
+    if constexpr (sizeof(R) == sizeof(RI)) {
+        // every copy of the step in flight at once (cp.async, consecutive lanes
+        // on consecutive elements), one wait
+#pragma unroll 8
+        for (int t = r; t < N * N; t += N) cp_async<sizeof(R)>(e + E::OA + (t / N) * LD + t % N, F + t);
+#pragma unroll 4
+        for (int t = r; t < N * M; t += N) cp_async<sizeof(R)>(L + (t / M) * LM + t % M, Lk + t);
+#pragma unroll 4
+        for (int t = r; t < M * M; t += N) cp_async<sizeof(R)>(U + (t / M) * LM + t % M, Uk + t);
+        if (D.c) cp_async<sizeof(R)>(e + E::OB + r, D.c + k * D.sc + r);
+        else e[E::OB + r] = R(0);
+        if (staged) {
+            R* Xs = stage;
+            R* Hs = Xs + p * lp;
+            R* rs = Hs + p * LD;
             for (int a = 0; a < p; ++a)
                 for (int b = r; b < p; b += N) cp_async<sizeof(R)>(Xs + a * lp + b, X + a * p + b);
-            for (int b = 0; b < p; ++b) cp_async<sizeof(R)>(Hs + b * LD + r, H + b * N + r);
+            if (!h_identity)
+                for (int b = 0; b < p; ++b) cp_async<sizeof(R)>(Hs + b * LD + r, H + b * N + r);
             for (int b = r; b < p; b += N) {
                 if (rk) cp_async<sizeof(R)>(rs + b, rk + b);
                 else rs[b] = R(0);
             }
-            cp_async_commit();
-            cp_async_wait<0>();
-        } else {
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+    } else {
+#pragma unroll 8
+        for (int t = r; t < N * N; t += N) e[E::OA + (t / N) * LD + t % N] = R(__ldg(F + t));
+#pragma unroll 4
+        for (int t = r; t < N * M; t += N) L[(t / M) * LM + t % M] = R(__ldg(Lk + t));
+#pragma unroll 4
+        for (int t = r; t < M * M; t += N) U[(t / M) * LM + t % M] = R(__ldg(Uk + t));
+        e[E::OB + r] = D.c ? R(__ldg(D.c + k * D.sc + r)) : R(0);
+        if (staged) {
+            R* Xs = stage;
+            R* Hs = Xs + p * lp;
+            R* rs = Hs + p * LD;
             for (int a = 0; a < p; ++a)
                 for (int b = r; b < p; b += N) Xs[a * lp + b] = R(__ldg(X + a * p + b));
-            for (int b = 0; b < p; ++b) Hs[b * LD + r] = R(__ldg(H + b * N + r));
+            if (!h_identity)
+                for (int b = 0; b < p; ++b) Hs[b * LD + r] = R(__ldg(H + b * N + r));
             for (int b = r; b < p; b += N) rs[b] = rk ? R(__ldg(rk + b)) : R(0);
         }
+    }
+    if (!COST) {  // dynamics only (F, c, L, U)
+        g.sync();
+        return;
+    }
+    if (staged && h_identity) {
+        // H = I (p = N): J = X, eta = X r
+        g.sync();
+        const R* Xs = stage;
+        const R* rs = stage + p * lp + p * LD;
+        R t = R(0);
+#pragma unroll 8
+        for (int j = 0; j < N; ++j) {
+            const R xj = Xs[r * lp + j];
+            e[E::OJ + r * LD + j] = xj;
+            t += xj * rs[j];
+        }
+        e[E::OE + r] = D.eta ? R(D.eta[k * D.seta + r]) : t;
+    } else if (staged) {
+        // X_k, H_k and r_k staged in shared memory
+        R* Xs = stage;         // p x p, row stride lp
+        R* Hs = Xs + p * lp;   // p x N, row stride LD
+        R* rs = Hs + p * LD;   // p
         g.sync();
         // Y = X H and X r, rows spread over the lanes
         for (int a = r; a < p; a += N) {
@@ -250,7 +286,7 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
         for (int b = 0; b < M; ++b) gg[b] = U[r * LM + b];
 #pragma unroll
         for (int j = 0; j < N; ++j) pp[j] = R(0);
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R lk = L[k * LM + r];
             const R sk = SL[k * LM + r];
@@ -302,7 +338,7 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
             ft[j] = F[r * LD + j];
             sft[j] = SF[r * LD + j];
         }
-#pragma unroll
+#pragma unroll 4
         for (int a = 0; a < M; ++a) {
             const R la = L[r * LM + a];
             const R sa = SL[r * LM + a];
@@ -328,7 +364,7 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = Q[r * LD + j];
         R t = q[r];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R fk = F[k * LD + r];
 #pragma unroll
@@ -429,7 +465,7 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         }
 #pragma unroll
         for (int j = 0; j < N; ++j) A2F[r * LD + j] = af[j];
-#pragma unroll
+#pragma unroll 4
         for (int a = 0; a < M; ++a) {
             P2[r * LM + a] = pl[a];
             rhs[a * LR + N + 1 + r] = pl[a];

@@ -45,7 +45,7 @@ __device__ __forceinline__ void row_mul(R* out, int ldo, const R* X, int ldx, co
     R acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = R(0);
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
         const R xk = X[lr * ldx + k];
 #pragma unroll
@@ -63,7 +63,7 @@ __device__ __forceinline__ void row_mul_tn(R* out, int ldo, const R* X, int ldx,
     R acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = R(0);
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
         const R xk = X[k * ldx + lr];
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
         R be = e1[E::OB + r];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R ck = e1[E::OC + r * LD + k];
 #pragma unroll
@@ -275,7 +275,7 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG
         R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = e1[E::OJ + r * LD + j];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R a = e1[E::OA + k * LD + r];
 #pragma unroll
@@ -291,7 +291,7 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG
         R bb = e2[E::OB + r];
 #pragma unroll
         for (int j = 0; j < N; ++j) aa[j] = tt[j] = R(0);
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R a2 = e2[E::OA + r * LD + k];
 #pragma unroll
@@ -314,7 +314,7 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG
         R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = e2[E::OC + r * LD + j];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R t = T[r * LD + k];
 #pragma unroll
@@ -353,7 +353,7 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
         R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R ck = P[E::OC + r * LD + k];
 #pragma unroll
@@ -385,7 +385,7 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
         R acc[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = P[E::OJ + r * LD + j];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R a = P[E::OA + k * LD + r];
 #pragma unroll
@@ -413,7 +413,7 @@ __device__ void affine_compose(const R* f1, const R* f2, R* out, R* scr, const G
     R c = f2[A::OC + r];
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = R(0);
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < N; ++k) {
         const R a = f2[A::OF + r * LD + k];
 #pragma unroll

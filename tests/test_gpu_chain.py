@@ -116,3 +116,63 @@ def test_precision_study_small(T):
     o32 = oracle_solve(p32)
     compare(gpu_solve(p32, refine=1), o32, FP32_TOL)
     compare(gpu_solve(p32, refine=3), o32, 1e-6)
+
+
+def test_chain_fp64_refined_matches_oracle():
+    """FP64 with the KKT refinement (ON) and the FULL refinement."""
+    prob = _rand(16, 8, 600, seed=31)
+    ref = oracle_solve(prob)
+    compare(gpu_solve(prob, dtype=np.float64, refine=1), ref, FP64_TOL)
+    compare(gpu_solve(prob, dtype=np.float64, refine=3), ref, FP64_TOL)
+
+
+def test_chain_host_and_static_entry_points():
+    """The host-buffer solve and the no-workspace solve at a lane size."""
+    import torch
+
+    from paper_2104_03186_gb300 import lqt
+
+    prob = _rand(8, 4, 900, seed=41).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    Ph = lqt.Problem.from_inputs(prob, pin=True)
+    out_h = Ph.allocate_outputs(pin=True)
+    buf = torch.empty(lqt.lqt_host_solve_bytes(Ph, None), dtype=torch.uint8, device="cuda")
+    assert lqt.lqt_solve_host(Ph, out_h, buf, None, None) == lqt.LQT_OK
+    compare({k: v.double().numpy() for k, v in out_h.items()}, ref, FP32_TOL)
+    P = lqt.Problem.from_inputs(prob)
+    out = P.allocate_outputs()
+    lqt.lqt_solve_static(P, out, None, None)
+    torch.cuda.synchronize()
+    compare({k: v.double().cpu().numpy() for k, v in out.items()}, ref, FP32_TOL)
+
+
+def test_chain_no_stage_cost():
+    """p = 0: no stage tracking cost, only the terminal cost."""
+    prob = _rand(8, 4, 300, seed=51, p=0).rounded_to(np.float32)
+    compare(gpu_solve(prob), oracle_solve(prob), FP32_TOL)
+
+
+def test_batch_mixes_lane_sizes_and_edge_items():
+    """One batch with n = 4, 8, 16, 32 problems, p < n and p = 2n, a T = 0 item
+    and several chunk counts: every item against the oracle."""
+    from paper_2104_03186_gb300 import lqt
+
+    specs = [(4, 2, 7, {}), (8, 4, 1, {}), (8, 4, 3000, dict(p=16, pT=16)),
+             (16, 8, 513, dict(p=4, pT=2)), (32, 16, 2048, {}), (32, 16, 5, {}),
+             (16, 8, 0, {}), (8, 4, 64, dict(with_c=False))]
+    probs = []
+    for i, (n, m, T, kw) in enumerate(specs):
+        pr = _rand(n, m, max(T, 1), seed=60 + i, **kw).rounded_to(np.float32)
+        if T == 0:
+            pr.T = 0
+            for f in ("F", "c", "L", "U", "H", "r", "X"):
+                a = getattr(pr, f)
+                if a is not None and a.shape[0] > 1:
+                    setattr(pr, f, a[:0])
+        probs.append(pr)
+    Ps = [lqt.Problem.from_inputs(p) for p in probs]
+    outs = lqt.solve_batched(Ps)
+    for pr, out, (n, m, T, kw) in zip(probs, outs, specs):
+        g = {k: v.double().cpu().numpy() for k, v in out.items()}
+        names = ("S", "v", "x") if T == 0 else ("S", "v", "K", "x", "u")
+        compare(g, oracle_solve(pr), FP32_TOL, names=names)
