@@ -606,12 +606,15 @@ def run_precision(args, stream, flush, fp32_peak=None, fp64_peak=None):
              ("fp32_kkt_refined", np.float32, 1, False),
              ("fp32_fp64tree_newton_kkt_refined", np.float32, 3, False),
              ("fp64_scan", np.float64, 0, False),
+             ("fp32_kkt_refined_method2", np.float32, 1, False),
              ("fp32_sequential_riccati_kkt_refined", np.float32, 1, True)]
     flops = chain_flops_per_step(prob.n, prob.m, prob.p)
     out = {}
     for name, dt, refine, seq in forms:
         P = lqt.Problem.from_inputs(prob, dtype=dt)
         o = P.allocate_outputs()
+        if name.endswith("method2"):  # trajectory by Method 2 (forward element scan)
+            refine = lqt.options(refine, lqt.LQT_METHOD_2)
         ws = lqt.workspace_for(P, opts=refine)
         call = (lambda: lqt.lqt_riccati_sequential(P, o, ws, stream, refine)) if seq else \
             (lambda: lqt.lqt_solve(P, o, ws, stream, refine))

@@ -126,9 +126,19 @@ typedef struct {
  *   slow on this GPU, so FULL costs several times ON.
  *   LQT_REFINE_AUTO = LQT_REFINE_ON for FP32 solves, OFF for FP64 ones. */
 enum { LQT_REFINE_OFF = 0, LQT_REFINE_ON = 1, LQT_REFINE_AUTO = 2, LQT_REFINE_FULL = 3 };
+/* method: trajectory recovery (Sec. IV-C).  LQT_METHOD_DEFAULT (0) and
+ *   LQT_METHOD_1 take Method 1 (Lemma LQT_trajectory_combination: a forward
+ *   scan of the closed-loop affine maps from x_0).  LQT_METHOD_2 (n = 8, 16, 32
+ *   only; LQT_EUNSUPPORTED otherwise) takes Method 2 (Lemma
+ *   LQT_trajectory_method2): a forward scan of the same elements seeded with
+ *   (0, x_0, 0, 0, 0) (Remark LQT_init2) gives V_{S->k}, and
+ *   x*_k = (I + C_{S,k} S_k)^{-1} (b_{S,k} + C_{S,k} v_k) (eq. lqt_method_2);
+ *   u*_k follows from the control law. */
+enum { LQT_METHOD_DEFAULT = 0, LQT_METHOD_1 = 1, LQT_METHOD_2 = 2 };
 typedef struct {
     int32_t refine;
-    int32_t reserved[7]; /* must be 0 */
+    int32_t method;
+    int32_t reserved[6]; /* must be 0 */
 } lqt_options;
 
 /* Bytes of device workspace that lqt_solve needs for this problem and these

@@ -112,13 +112,18 @@ lqt_status validate(const lqt_problem* P, const lqt_solution* sol) {
 }
 
 lqt_status resolve_refine(const lqt_problem* P, const lqt_options* o, bool* refine,
-                          bool* newton = nullptr) {
+                          bool* newton = nullptr, bool* method2 = nullptr) {
     int mode = LQT_REFINE_AUTO;
     if (o) {
         for (int r : o->reserved)
             if (r != 0) return LQT_EINVAL;
+        if (o->method != LQT_METHOD_DEFAULT && o->method != LQT_METHOD_1 &&
+            o->method != LQT_METHOD_2)
+            return LQT_EINVAL;
         mode = o->refine;
     }
+    const bool m2 = o && o->method == LQT_METHOD_2;
+    if (method2) *method2 = m2;
     if (newton) *newton = mode == LQT_REFINE_FULL;
     if (mode == LQT_REFINE_AUTO)
         *refine = P->dtype == LQT_F32;
@@ -305,14 +310,16 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
                     int32_t* tile_threads_out, int32_t* tiles, int32_t* kernels) {
     lqt_status st = validate(prob, nullptr);
     if (st != LQT_OK) return st;
-    bool refine = false, newton = false;
-    if ((st = resolve_refine(prob, opts, &refine, &newton)) != LQT_OK) return st;
+    bool refine = false, newton = false, method2 = false;
+    if ((st = resolve_refine(prob, opts, &refine, &newton, &method2)) != LQT_OK) return st;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (var && method2) return LQT_EUNSUPPORTED;
     if (!var) {
         if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
         int NC = 0, nk = 0;
         long long B = 0;
-        if ((st = chain_workspace(prob, refine, newton, false, nullptr, &NC, &B, &nk)) != LQT_OK)
+        if ((st = chain_workspace(prob, refine, newton, false, method2, nullptr, &NC, &B, &nk)) !=
+            LQT_OK)
             return st;
         if (B > INT32_MAX) return LQT_EINVAL;
         if (chunk_steps) *chunk_steps = (int32_t)B;
@@ -333,14 +340,15 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
 
 size_t lqt_workspace_bytes(const lqt_problem* prob, const lqt_options* opts) {
     if (validate(prob, nullptr) != LQT_OK) return 0;
-    bool refine = false, newton = false;
-    if (resolve_refine(prob, opts, &refine, &newton) != LQT_OK) return 0;
+    bool refine = false, newton = false, method2 = false;
+    if (resolve_refine(prob, opts, &refine, &newton, &method2) != LQT_OK) return 0;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (var && method2) return 0;
     if (!var) {
         size_t bytes = 0;
         if (!chain_supported(prob->dtype, prob->n, prob->m) ||
-            chain_workspace(prob, refine, newton, false, &bytes, nullptr, nullptr, nullptr) !=
-                LQT_OK)
+            chain_workspace(prob, refine, newton, false, method2, &bytes, nullptr, nullptr,
+                            nullptr) != LQT_OK)
             return 0;
         return bytes;
     }
@@ -406,24 +414,25 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     lqt_status st = validate(prob, sol);
     if (st != LQT_OK) return st;
     if (!workspace || !aligned(workspace, kAlign)) return LQT_EINVAL;
-    bool refine = false, newton = false;
-    if ((st = resolve_refine(prob, opts, &refine, &newton)) != LQT_OK) return st;
+    bool refine = false, newton = false, method2 = false;
+    if ((st = resolve_refine(prob, opts, &refine, &newton, &method2)) != LQT_OK) return st;
     if (sequential && prob->p > 64) return LQT_EUNSUPPORTED;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
+    if (var && method2) return LQT_EUNSUPPORTED;
     if (!var) {
         // lane-group sizes: the chunked pipeline (one chunk when sequential)
         if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
         size_t need = 0;
-        if ((st = chain_workspace(prob, refine, newton, sequential, &need, nullptr, nullptr,
-                                  nullptr)) != LQT_OK)
+        if ((st = chain_workspace(prob, refine, newton, sequential, method2, &need, nullptr,
+                                  nullptr, nullptr)) != LQT_OK)
             return st;
         if (workspace_bytes < need) return LQT_ENOMEM;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         if (cudaMemsetAsync(workspace, 0, sizeof(int), s) != cudaSuccess) return LQT_ECUDA;
         Prof* prof = nullptr;
         if ((st = prof_begin(&prof)) != LQT_OK) return st;
-        return chain_solve(prob, sol, refine, newton, sequential, workspace, workspace_bytes, s,
-                           prof);
+        return chain_solve(prob, sol, refine, newton, sequential, method2, workspace,
+                           workspace_bytes, s, prof);
     }
     Plan plan;
     if ((st = make_plan(prob, *var, &plan)) != LQT_OK) return st;

@@ -117,7 +117,7 @@ lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, co
 bool chain_supported(int dtype, int n, int m) { return find_chain(dtype, n, m, false) != nullptr; }
 
 lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
-                           size_t* bytes, int* NC, long long* B, int* kernels) {
+                           bool method2, size_t* bytes, int* NC, long long* B, int* kernels) {
     if (P->p > 2 * P->n || P->pT > 2 * P->n) return LQT_EUNSUPPORTED;
     // FP64 tree levels with the FULL refinement (the Newton step); FP32 otherwise
     const bool mixed = refine && newton && P->dtype == LQT_F32;
@@ -129,12 +129,14 @@ lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool 
     if (st != LQT_OK) return st;
     ChainProblem cp{P, nullptr, nc, b};
     const bool rf = refine && P->T > 0;
-    if (bytes) *bytes = v->workspace(&cp, 1, rf, rf && newton);
+    if (bytes) *bytes = v->workspace(&cp, 1, rf, rf && newton, method2);
     if (NC) *NC = nc;
     if (B) *B = b;
     if (kernels) {
         const int l = levels(nc);
-        const int per_pass = sequential ? 3 : 4 + 4 * l;
+        // Method 2: the element copy, 2 l sweep levels, the seeds, the walk
+        const int fwd = method2 ? 2 * l + 2 : (sequential ? 0 : 2 * l);
+        const int per_pass = (sequential ? 2 : 3 + 2 * l) + fwd + (method2 ? 0 : 1);
         const int bwd = sequential ? 2 : 3 + 2 * l;
         int k = 1 + per_pass;  // the item upload, the solve
         if (rf) k += 1 + 1 + per_pass;  // item upload, KKT residuals, correction solve
@@ -145,7 +147,8 @@ lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool 
 }
 
 lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine, bool newton,
-                       bool sequential, void* ws, size_t ws_bytes, cudaStream_t s, Prof* prof) {
+                       bool sequential, bool method2, void* ws, size_t ws_bytes, cudaStream_t s,
+                       Prof* prof) {
     if (P->p > 2 * P->n || P->pT > 2 * P->n) return LQT_EUNSUPPORTED;
     const bool mixed = refine && newton && P->dtype == LQT_F32;
     const ChainVariant* v = find_chain(P->dtype, P->n, P->m, mixed);
@@ -156,7 +159,7 @@ lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refin
     if (st != LQT_OK) return st;
     ChainProblem cp{P, sol, NC, B};
     const bool rf = refine && P->T > 0;
-    ChainCall call{&cp, 1, rf, rf && newton, sequential, ws, ws_bytes, nullptr};
+    ChainCall call{&cp, 1, rf, rf && newton, sequential, method2, ws, ws_bytes, nullptr};
     return v->run(call, s, prof);
 }
 
@@ -170,7 +173,7 @@ lqt_status chain_batch_workspace(const lqt_batch_item* items, const int* idx, in
     std::vector<ChainProblem> probs;
     const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
     if (st != LQT_OK) return st;
-    *bytes = v->workspace(probs.data(), count, false, false);
+    *bytes = v->workspace(probs.data(), count, false, false, false);
     return LQT_OK;
 }
 
@@ -183,7 +186,7 @@ lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int co
     std::vector<ChainProblem> probs;
     const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
     if (st != LQT_OK) return st;
-    ChainCall call{probs.data(), count, false, false, false, ws, ws_bytes, status};
+    ChainCall call{probs.data(), count, false, false, false, false, ws, ws_bytes, status};
     return v->run(call, s, nullptr);
 }
 

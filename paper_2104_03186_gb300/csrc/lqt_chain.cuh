@@ -76,7 +76,7 @@ struct Args {
     RT* FE;          // C chunk affine maps (LAffine)
     RT* X;           // C chunk start states
     int* status;
-    int out_mask;    // bit 1: write S and v; bit 2: write K
+    int out_mask;    // bit 1: write S; bit 2: write K; bit 4: write v
     int refine_add;  // 1: correction pass: x <- x^ + dx, u_out <- u^ + w - qh
 };
 
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(N) k_cterm(Args<R, RT> a) {
     if (a.out_mask & 1) {
 #pragma unroll
         for (int j = 0; j < N; ++j) D.S[D.T * N * N + r * N + j] = static_cast<R>(acc[j]);
-        D.v[D.T * N + r] = static_cast<R>(t);
     }
+    if (a.out_mask & 4) D.v[D.T * N + r] = static_cast<R>(t);
     if (D.T == 0) D.x[r] = D.x0[r];
 }
 
@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
         if (a.out_mask & 1) {
 #pragma unroll 8
             for (int i = 0; i < N; ++i) D.S[k * N * N + i * N + r] = val[V::OS + i * V::LD + r];
-            D.v[k * N + r] = val[V::OV + r];
         }
+        if (a.out_mask & 4) D.v[k * N + r] = val[V::OV + r];
         if (a.out_mask & 2) {
 #pragma unroll 8
             for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = Kd[i * (N + 1) + r];
@@ -510,15 +510,180 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     }
 }
 
+// ---- Method 2 (Lemma LQT_trajectory_method2) --------------------------------
+// The forward conditional value functions V_{S->k} are the prefix products
+// e_0 (x) a_0 (x) ... (x) a_{k-1} of the same elements, seeded with the element
+// (0, x_0, 0, 0, 0) of Remark LQT_init2 (so A_{S,k} = 0).  The chunk totals E2
+// (a copy of the fold's output) are swept up right-anchored, the prefixes
+// swept down from the seed, and each chunk walks its steps:
+//   x*_k = (I + C_k S_k)^{-1} (b_k + C_k v_k)   (eq. lqt_method_2),
+//   u*_k = d_k - K_k x*_k, then P <- P (x) a_k.
+template <int N, int M>
+struct M2Smem {  // P | step | scratch (combine, and the state solve)
+    static constexpr int P = 0;
+    static constexpr int SB = LElem<N>::SIZE;
+    static constexpr int SCR_OFF = SB + StepLayout<N, M>::SIZE;
+    static constexpr int SCR = combine_scratch<N>() > load_scratch<N, M>() ? combine_scratch<N>()
+                                                                          : load_scratch<N, M>();
+    static constexpr int SIZE = SCR_OFF + SCR;
+};
+
+// up-sweep level h: E2[j] <- E2[j - h] (x) E2[j], j = 2h q + 2h - 1
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_m2up(RT* E2, long long active, int h, int* status) {
+    using E = LElem<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RT* sh = reinterpret_cast<RT*>(smem_raw);
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
+    if (j >= active) return;
+    RT* e1 = sh + gi * UpSmem<N>::SIZE;
+    RT* e2 = e1 + E::SIZE;
+    RT* scr = e2 + E::SIZE;
+    copy_in(e1, E2 + (j - h) * E::SIZE, E::SIZE, g.lr, N);
+    copy_in(e2, E2 + j * E::SIZE, E::SIZE, g.lr, N);
+    g.sync();
+    const bool ok = combine<N, N>(e1, e2, e2, scr, g);
+    for (int t = g.lr; t < E::SIZE; t += N) E2[j * E::SIZE + t] = e2[t];
+    flag(status, ok);
+}
+
+// the seed of each problem's prefix sweep: Pref[c0 + NC - 1] <- (0, x_0, 0, 0, 0)
+template <typename R, typename RT, int N>
+__global__ void __launch_bounds__(N) k_m2seed(const Item<R>* items, RT* Pref) {
+    using E = LElem<N>;
+    const Item<R>& it = items[blockIdx.x];
+    RT* e = Pref + (it.c0 + it.NC - 1) * E::SIZE;
+    const int r = threadIdx.x;
+    for (int t = r; t < E::SIZE; t += N) e[t] = RT(0);
+    __syncthreads();
+    e[E::OB + r] = static_cast<RT>(it.D.x0[r]);
+}
+
+// down-sweep level h: Pref[j - h] <- Pref[j]; Pref[j] <- Pref[j] (x) E2[j - h]
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_m2down(const RT* E2, RT* Pref, long long active, int h,
+                                                  int* status) {
+    using E = LElem<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RT* sh = reinterpret_cast<RT*>(smem_raw);
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
+    if (j >= active) return;
+    RT* e1 = sh + gi * UpSmem<N>::SIZE;
+    RT* e2 = e1 + E::SIZE;
+    RT* scr = e2 + E::SIZE;
+    copy_in(e1, Pref + j * E::SIZE, E::SIZE, g.lr, N);
+    copy_in(e2, E2 + (j - h) * E::SIZE, E::SIZE, g.lr, N);
+    for (int t = g.lr; t < E::SIZE; t += N) Pref[(j - h) * E::SIZE + t] = Pref[j * E::SIZE + t];
+    g.sync();
+    const bool ok = combine<N, N>(e1, e2, e1, scr, g);
+    for (int t = g.lr; t < E::SIZE; t += N) Pref[j * E::SIZE + t] = e1[t];
+    flag(status, ok);
+}
+
+// x = (I + C S)^{-1} (b + C v) for the prefix P and the value (S_k, v_k) of
+// step k (read from the outputs); writes x into xo (N values in shared memory)
+template <typename R, int N>
+__device__ bool m2_state(const R* P, const R* S, const R* v, R* xo, R* scr, const Group<N>& g) {
+    using E = LElem<N>;
+    constexpr int LD = E::LD;
+    R* Mx = scr;          // N x LD
+    R* w = Mx + N * LD;   // N (right side, stride 1)
+    const int r = g.lr;
+    {
+        R acc[N];
+        R t = P[E::OB + r];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = r == j ? R(1) : R(0);
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            const R ck = P[E::OC + r * LD + k];
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] += ck * S[k * N + j];
+            t += ck * v[k];
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) Mx[r * LD + j] = acc[j];
+        w[r] = t;
+    }
+    g.sync();
+    const bool ok = solve_gj<N, N, 1>(Mx, LD, w, 1, g);
+    xo[r] = w[r];
+    g.sync();
+    return ok;
+}
+
+template <typename R, typename RT, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_m2roll(Args<R, RT> a, const RT* Pref) {
+    using S = M2Smem<N, M>;
+    using E = LElem<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sh = reinterpret_cast<R*>(smem_raw);
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const long long c = (long long)blockIdx.x * NG + gi;
+    if (c >= a.C) return;
+    const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
+    const DescT<R>& D = it.D;
+    R* gs = sh + gi * S::SIZE;
+    R* P = gs + S::P;
+    R* sb = gs + S::SB;
+    R* scr = gs + S::SCR_OFF;
+    const int r = g.lr;
+    const long long T = D.T;
+    const long long lc = c - it.c0;
+    const long long s0 = lc * it.B < T ? lc * it.B : T;
+    const long long e0 = s0 + it.B < T ? s0 + it.B : T;
+    copy_in(P, Pref + c * E::SIZE, E::SIZE, r, N);
+    g.sync();
+    bool ok = true;
+    R* xs = scr + combine_scratch<N>() - N;  // the state (end of the scratch)
+    for (long long k = s0; k < e0; ++k) {
+        ok &= m2_state<R, N>(P, D.S + k * N * N, D.v + k * N, xs, scr, g);
+        const R xr = xs[r];
+        D.x[k * N + r] = a.refine_add ? D.x[k * N + r] + xr : xr;
+        if (r < M) {
+            R t = D.u[k * M + r];
+#pragma unroll 8
+            for (int j = 0; j < N; ++j) t -= D.K[k * M * N + r * N + j] * xs[j];
+            if (a.refine_add)
+                it.u_out[k * M + r] = it.u_out[k * M + r] + (t - it.qh[k * M + r]);
+            else
+                D.u[k * M + r] = t;
+        }
+        g.sync();
+        // P <- P (x) a_k
+        load_step<R, N, M, true>(D, k, sb, scr, g, ok);
+        ok &= combine<N, N>(P, sb + StepLayout<N, M>::E, P, scr, g);
+        if (k == T - 1) {
+            ok &= m2_state<R, N>(P, D.S + T * N * N, D.v + T * N, xs, scr, g);
+            D.x[T * N + r] = a.refine_add ? D.x[T * N + r] + xs[r] : xs[r];
+            g.sync();
+        }
+    }
+    flag(a.status, ok);
+}
+
 // ---- KKT residuals of the first pass's iterate (refinement) -----------------
 // One group per step k = 0..T (k = T: the terminal condition and x'_0 = 0),
 // all arithmetic in FP64 (products of FP32 inputs are exact in FP64).
 template <int N, int M>
-struct ResidSmem {
+struct ResidSmem {  // FP64 work vectors, then the step's matrices staged in R
     static constexpr int PMAX = 2 * N;
     static constexpr int XK = 0, XK1 = N, UK = 2 * N, L0 = 2 * N + M, L1 = 3 * N + M,
                          HX = 4 * N + M, Y = HX + PMAX, UM = Y + PMAX, RH = UM + M * M,
-                         SIZE = RH + M;
+                         D64SIZE = RH + M;
+    // staged (type R, odd row strides): S_k, S_{k+1}, F_k (N x lds(N)), L_k (N x lds(M)),
+    // U_k (M x lds(M))
+    static constexpr int SK = 0, SK1 = SK + N * lds(N), FK = SK1 + N * lds(N),
+                         LK = FK + N * lds(N), UKM = LK + N * lds(M), RSIZE = UKM + M * lds(M);
+    template <typename R>
+    static constexpr int bytes() {
+        return D64SIZE * (int)sizeof(double) + RSIZE * (int)sizeof(R);
+    }
 };
 
 template <typename R, int N, int M, int NG>
@@ -526,11 +691,14 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
                                                   int count, long long rows, int* status) {
     using S = ResidSmem<N, M>;
     using D64 = double;
+    constexpr int LD = lds(N), LM = lds(M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    unsigned char* base = smem_raw + (size_t)gi * S::template bytes<R>();
+    D64* sh = reinterpret_cast<D64*>(base);
+    R* st = reinterpret_cast<R*>(base + S::D64SIZE * sizeof(D64));
     D64* xk = sh + S::XK;
     D64* xk1 = sh + S::XK1;
     D64* uk = sh + S::UK;
@@ -540,6 +708,11 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
     D64* y = sh + S::Y;
     D64* Um = sh + S::UM;
     D64* rh = sh + S::RH;
+    R* Sk = st + S::SK;
+    R* Sk1 = st + S::SK1;
+    R* Fs = st + S::FK;
+    R* Ls = st + S::LK;
+    R* Us = st + S::UKM;
     const long long stride = (long long)gridDim.x * NG;
     bool ok = true;
     for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
@@ -553,24 +726,51 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
         const R* H = term ? D.HT : D.H + k * D.sH;
         const R* X = term ? D.XT : D.X + k * D.sX;
         const R* rr = term ? D.rT : (D.r ? D.r + k * D.sr : nullptr);
+        // the step's matrices by coalesced asynchronous copies
+#pragma unroll 8
+        for (int t = r; t < N * N; t += N) cp_async<sizeof(R)>(Sk + (t / N) * LD + t % N, D.S + k * N * N + t);
+        if (!term) {
+#pragma unroll 8
+            for (int t = r; t < N * N; t += N)
+                cp_async<sizeof(R)>(Sk1 + (t / N) * LD + t % N, D.S + (k + 1) * N * N + t);
+#pragma unroll 8
+            for (int t = r; t < N * N; t += N)
+                cp_async<sizeof(R)>(Fs + (t / N) * LD + t % N, D.F + k * D.sF + t);
+#pragma unroll 4
+            for (int t = r; t < N * M; t += N)
+                cp_async<sizeof(R)>(Ls + (t / M) * LM + t % M, D.L + k * D.sL + t);
+#pragma unroll 4
+            for (int t = r; t < M * M; t += N)
+                cp_async<sizeof(R)>(Us + (t / M) * LM + t % M, D.U + k * D.sU + t);
+        }
+        cp_async_commit();
         xk[r] = static_cast<D64>(D.x[k * N + r]);
         if (!term) {
             xk1[r] = static_cast<D64>(D.x[(k + 1) * N + r]);
             if (r < M) uk[r] = static_cast<D64>(D.u[k * M + r]);
         }
+        cp_async_wait<0>();
         g.sync();
-        // lambda^_k = S_k x^_k - v_k (and lambda^_{k+1}); H x^ - r
+        // the iterate's multipliers lambda^_k = S_k x^_k - v_k in the working
+        // precision R: the refinement needs exact residuals of some iterate,
+        // and these R values enter the FP64 products below exactly
         {
-            const R* Sk = D.S + k * N * N;
-            D64 t = -static_cast<D64>(D.v[k * N + r]);
-            for (int j = 0; j < N; ++j) t += static_cast<D64>(Sk[r * N + j]) * xk[j];
-            lam0[r] = t;
+            R t = -D.v[k * N + r];
+#pragma unroll 8
+            for (int j = 0; j < N; ++j) t += Sk[r * LD + j] * static_cast<R>(xk[j]);
+            lam0[r] = static_cast<D64>(t);
             if (!term) {
-                const R* Sk1 = Sk + N * N;
-                D64 t1 = -static_cast<D64>(D.v[(k + 1) * N + r]);
-                for (int j = 0; j < N; ++j) t1 += static_cast<D64>(Sk1[r * N + j]) * xk1[j];
-                lam1[r] = t1;
+                R t1 = -D.v[(k + 1) * N + r];
+#pragma unroll 8
+                for (int j = 0; j < N; ++j) t1 += Sk1[r * LD + j] * static_cast<R>(xk1[j]);
+                lam1[r] = static_cast<D64>(t1);
             }
+        }
+        // H x^ - r (H = I: x^ - r)
+        const bool hid = D.sH == 0 && p == N && !term && h_is_identity(D, g);
+        if (hid) {
+            hx[r] = xk[r] - (rr ? static_cast<D64>(rr[r]) : 0.0);
+        } else {
             for (int i = r; i < p; i += N) {
                 D64 h = rr ? -static_cast<D64>(rr[i]) : 0.0;
                 for (int j = 0; j < N; ++j) h += static_cast<D64>(H[i * N + j]) * xk[j];
@@ -586,35 +786,36 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
         g.sync();
         // g = H^T X (H x^ - r) - lambda^_k (+ F^T lambda^_{k+1})
         D64 gr = -lam0[r];
-        for (int i = 0; i < p; ++i) gr += static_cast<D64>(H[i * N + r]) * y[i];
+        if (hid) {
+            gr += y[r];
+        } else {
+            for (int i = 0; i < p; ++i) gr += static_cast<D64>(H[i * N + r]) * y[i];
+        }
         if (term) {
             const_cast<R*>(D2.etaT)[r] = static_cast<R>(-gr);
             const_cast<R*>(D2.x0)[r] = R(0);
             g.sync();
             continue;
         }
-        const R* F = D.F + k * D.sF;
-        const R* L = D.L + k * D.sL;
-        const R* U = D.U + k * D.sU;
-        for (int j = 0; j < N; ++j) gr += static_cast<D64>(F[j * N + r]) * lam1[j];
+        for (int j = 0; j < N; ++j) gr += static_cast<D64>(Fs[j * LD + r]) * lam1[j];
         // e = F x^ + c + L u^ - x^_{k+1}
         D64 e = (D.c ? static_cast<D64>(D.c[k * D.sc + r]) : 0.0) - xk1[r];
-        for (int j = 0; j < N; ++j) e += static_cast<D64>(F[r * N + j]) * xk[j];
-        for (int b = 0; b < M; ++b) e += static_cast<D64>(L[r * M + b]) * uk[b];
+        for (int j = 0; j < N; ++j) e += static_cast<D64>(Fs[r * LD + j]) * xk[j];
+        for (int b = 0; b < M; ++b) e += static_cast<D64>(Ls[r * LM + b]) * uk[b];
         // h = U u^ + L^T lambda^_{k+1}; U^{-1} h
         if (r < M) {
             D64 h = 0.0;
             for (int b = 0; b < M; ++b) {
-                const D64 ub = static_cast<D64>(U[r * M + b]);
+                const D64 ub = static_cast<D64>(Us[r * LM + b]);
                 Um[r * M + b] = ub;
                 h += ub * uk[b];
             }
-            for (int j = 0; j < N; ++j) h += static_cast<D64>(L[j * M + r]) * lam1[j];
+            for (int j = 0; j < N; ++j) h += static_cast<D64>(Ls[j * LM + r]) * lam1[j];
             rh[r] = h;
         }
         g.sync();
         ok &= solve_spd<N, M, 1>(Um, M, rh, 1, g);
-        for (int b = 0; b < M; ++b) e -= static_cast<D64>(L[r * M + b]) * rh[b];
+        for (int b = 0; b < M; ++b) e -= static_cast<D64>(Ls[r * LM + b]) * rh[b];
         const_cast<R*>(D2.eta)[k * N + r] = static_cast<R>(-gr);
         const_cast<R*>(D2.c)[k * N + r] = static_cast<R>(e);
         if (r < M) const_cast<R*>(items2[ii].qh)[k * M + r] = static_cast<R>(rh[r]);

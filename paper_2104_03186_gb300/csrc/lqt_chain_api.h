@@ -26,6 +26,7 @@ struct ChainCall {
     const ChainProblem* probs;
     int count;
     bool refine, newton, sequential;
+    bool method2;  // trajectory by Method 2 (Lemma LQT_trajectory_method2)
     void* ws;
     size_t ws_bytes;
     int* status;  // device status word (nullptr: the first word of ws)
@@ -34,7 +35,8 @@ struct ChainCall {
 struct ChainVariant {
     int dtype, n, m;
     int mixed;         // FP32 chunk work with FP64 tree levels
-    size_t (*workspace)(const ChainProblem* probs, int count, bool refine, bool newton);
+    size_t (*workspace)(const ChainProblem* probs, int count, bool refine, bool newton,
+                        bool method2);
     lqt_status (*run)(const ChainCall& call, cudaStream_t s, Prof* prof);
     const void* (*fold_kernel)();
     size_t (*fold_smem)();
@@ -87,9 +89,10 @@ DescT<R> make_desc(const lqt_problem* P, const lqt_solution* S) {
 bool chain_supported(int dtype, int n, int m);
 // Single problem: workspace bytes, chunk geometry and kernel launches.
 lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
-                           size_t* bytes, int* NC, long long* B, int* kernels);
+                           bool method2, size_t* bytes, int* NC, long long* B, int* kernels);
 lqt_status chain_solve(const lqt_problem* P, const lqt_solution* sol, bool refine, bool newton,
-                       bool sequential, void* ws, size_t ws_bytes, cudaStream_t s, Prof* prof);
+                       bool sequential, bool method2, void* ws, size_t ws_bytes, cudaStream_t s,
+                       Prof* prof);
 // Batch of problems of one FP32 (n, m), no refinement: items[idx[0..count)].
 lqt_status chain_batch_workspace(const lqt_batch_item* items, const int* idx, int count,
                                  size_t* bytes);

@@ -42,10 +42,12 @@ struct Launcher {
     static constexpr int NG_FUP = groups_for<N>(FUP_B);
     static constexpr int NG_FDOWN = groups_for<N>(FDOWN_B);
     static constexpr int NG_ROLL = groups_for<N>(ROLL_B);
-    static constexpr int RESID_B = ResidSmem<N, M>::SIZE * (int)sizeof(double);
+    static constexpr int RESID_B = ResidSmem<N, M>::template bytes<R>();
     static constexpr int NEWTON_B = NewtonSmem<N, M>::SIZE * (int)sizeof(double);
     static constexpr int NG_NEWTON = groups_for<N>(NEWTON_B);
-    static constexpr int NG_RESID = 256 / N;
+    static constexpr int NG_RESID = groups_for<N>(RESID_B);
+    static constexpr int M2_B = M2Smem<N, M>::SIZE * (int)sizeof(R);
+    static constexpr int NG_M2 = groups_for<N>(M2_B);
 
     static cudaError_t prepare() {
         static bool d_fold[64], d_refold[64], d_up[64], d_down[64], d_fup[64], d_fdown[64],
@@ -64,7 +66,17 @@ struct Launcher {
             (e = chain_allow_smem(k_cfdown<RT, N, NG_FDOWN>, d_fdown,
                                   (size_t)NG_FDOWN * FDOWN_B)) != cudaSuccess)
             return e;
-        static bool d_nres[64], d_ngain[64];
+        static bool d_nres[64], d_ngain[64], d_resid[64], d_m2up[64], d_m2down[64], d_m2roll[64];
+        if ((e = chain_allow_smem(k_m2up<RT, N, NG_UP>, d_m2up, (size_t)NG_UP * UP_B)) !=
+                cudaSuccess ||
+            (e = chain_allow_smem(k_m2down<RT, N, NG_UP>, d_m2down, (size_t)NG_UP * UP_B)) !=
+                cudaSuccess ||
+            (e = chain_allow_smem(k_m2roll<R, RT, N, M, NG_M2>, d_m2roll, (size_t)NG_M2 * M2_B)) !=
+                cudaSuccess)
+            return e;
+        if ((e = chain_allow_smem(k_cresid<R, N, M, NG_RESID>, d_resid,
+                                  (size_t)NG_RESID * RESID_B)) != cudaSuccess)
+            return e;
         if ((e = chain_allow_smem(k_nresid<R, N, M, NG_NEWTON>, d_nres,
                                   (size_t)NG_NEWTON * NEWTON_B)) != cudaSuccess ||
             (e = chain_allow_smem(k_ngains<R, N, M, NG_NEWTON>, d_ngain,
@@ -74,16 +86,18 @@ struct Launcher {
     }
 
     static int blocks(long long items, int ng) { return (int)((items + ng - 1) / ng); }
+    static char* base_of(const ChainCall& call) { return static_cast<char*>(call.ws); }
 
     // Workspace layout of a call (bytes from the start of the workspace).
     struct Layout {
-        size_t items1, items2, items3, consts, E, V, FE, X, refine0, total;
+        size_t items1, items2, items3, consts, E, V, FE, X, E2, Pref, refine0, total;
         long long C;
     };
 
     static size_t up(size_t x) { return (x + 255) / 256 * 256; }
 
-    static Layout layout(const ChainProblem* probs, int count, bool refine, bool newton) {
+    static Layout layout(const ChainProblem* probs, int count, bool refine, bool newton,
+                         bool method2 = false) {
         Layout L;
         long long C = 0;
         for (int i = 0; i < count; ++i) C += probs[i].NC;
@@ -107,6 +121,13 @@ struct Launcher {
         off += up(nc * LAffine<N>::SIZE * sizeof(RT));
         L.X = off;
         off += up(nc * N * sizeof(RT));
+        L.E2 = L.Pref = 0;
+        if (method2) {  // Method 2: a copy of the chunk totals and the prefixes
+            L.E2 = off;
+            off += up(nc * LElem<N>::SIZE * sizeof(RT));
+            L.Pref = off;
+            off += up(nc * LElem<N>::SIZE * sizeof(RT));
+        }
         L.refine0 = off;
         if (refine)
             for (int i = 0; i < count; ++i)
@@ -121,7 +142,8 @@ struct Launcher {
     // ct T x N, R (T + 1) x N x N, rho (T + 1) x N, dS (T + 1) x N x N, dv (T + 1) x N
     static size_t kkt_bytes(long long T) {
         const size_t t = (size_t)T;
-        return 2 * up(t * N * sizeof(R)) + 2 * up(t * M * sizeof(R)) + 2 * up(N * sizeof(R));
+        return 2 * up(t * N * sizeof(R)) + 2 * up(t * M * sizeof(R)) + 2 * up(N * sizeof(R)) +
+               up((t + 1) * N * sizeof(R)) /* v' of the correction pass (Method 2) */;
     }
     static size_t newton_bytes(long long T) {
         const size_t t = (size_t)T;
@@ -147,8 +169,9 @@ struct Launcher {
         b.qh = qh;
     }
 
-    static size_t workspace(const ChainProblem* probs, int count, bool refine, bool newton) {
-        return layout(probs, count, refine, newton).total;
+    static size_t workspace(const ChainProblem* probs, int count, bool refine, bool newton,
+                            bool method2) {
+        return layout(probs, count, refine, newton, method2).total;
     }
 
     // Kernel names for the profile, by pass: the solve, the correction pass of
@@ -166,12 +189,17 @@ struct Launcher {
     // One pass: backward scan, re-fold, then (unless backward_only) the forward
     // scan and the rollout.
     static void pass(const Args<R, RT>& a, const long long* active, int levels, bool sequential,
-                     int kind, bool backward_only, cudaStream_t s, Prof* prof) {
+                     int kind, bool backward_only, cudaStream_t s, Prof* prof, RT* E2 = nullptr,
+                     RT* Pref = nullptr) {
         const long long C = a.C;
+        const bool m2 = E2 != nullptr && !backward_only;
         if (!sequential) {
             prof_mark(prof, s, pname(kind, 0));
             k_cfold<R, RT, N, M, NG_FOLD>
                 <<<blocks(C, NG_FOLD), NG_FOLD * N, (size_t)NG_FOLD * FOLD_B, s>>>(a);
+            if (m2)  // the chunk totals, before the backward up-sweep overwrites them
+                cudaMemcpyAsync(E2, a.E, (size_t)C * LElem<N>::SIZE * sizeof(RT),
+                                cudaMemcpyDeviceToDevice, s);
             if (levels > 0) prof_mark(prof, s, pname(kind, 1));
             for (int l = 0; l < levels; ++l) {
                 const int h = 1 << l;
@@ -191,6 +219,26 @@ struct Launcher {
         k_crefold<R, RT, N, M, NG_REFOLD>
             <<<blocks(C, NG_REFOLD), NG_REFOLD * N, (size_t)NG_REFOLD * REFOLD_B, s>>>(a);
         if (backward_only) return;
+        if (m2) {
+            // Method 2: prefix scan of the elements from (0, x_0, 0, 0, 0)
+            prof_mark(prof, s, kind == 1 ? "chain_m2scan.refine" : "chain_m2scan");
+            for (int l = 0; l < levels; ++l) {
+                const int h = 1 << l;
+                k_m2up<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
+                                       (size_t)NG_UP * UP_B, s>>>(E2, active[l], h, a.status);
+            }
+            k_m2seed<R, RT, N><<<a.count, N, 0, s>>>(a.items, Pref);
+            for (int l = levels - 1; l >= 0; --l) {
+                const int h = 1 << l;
+                k_m2down<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
+                                         (size_t)NG_UP * UP_B, s>>>(E2, Pref, active[l], h,
+                                                                    a.status);
+            }
+            prof_mark(prof, s, kind == 1 ? "chain_m2roll.refine" : "chain_m2roll");
+            k_m2roll<R, RT, N, M, NG_M2>
+                <<<blocks(C, NG_M2), NG_M2 * N, (size_t)NG_M2 * M2_B, s>>>(a, Pref);
+            return;
+        }
         if (levels > 0) {
             prof_mark(prof, s, pname(kind, 4));
             for (int l = 0; l < levels; ++l) {
@@ -216,7 +264,10 @@ struct Launcher {
         if (count <= 0) return LQT_OK;
         const bool refine = call.refine;
         const bool newton = refine && call.newton;
-        const Layout L = layout(call.probs, count, refine, newton);
+        const bool method2 = call.method2;
+        const Layout L = layout(call.probs, count, refine, newton, method2);
+        RT* E2 = method2 ? reinterpret_cast<RT*>(base_of(call) + L.E2) : nullptr;
+        RT* Pref = method2 ? reinterpret_cast<RT*>(base_of(call) + L.Pref) : nullptr;
         if (call.ws_bytes < L.total) return LQT_ENOMEM;
         char* base = static_cast<char*>(call.ws);
         // items of the first pass and of the correction pass
@@ -250,9 +301,11 @@ struct Launcher {
                 R* etaT = reinterpret_cast<R*>(base + roff + 2 * up(t * N * sizeof(R)) +
                                                2 * up(t * M * sizeof(R)));
                 R* x0p = etaT + up(N * sizeof(R)) / sizeof(R);
+                R* vcorr = x0p + up(N * sizeof(R)) / sizeof(R);
                 char* nb = base + roff + kkt_bytes(cp.problem->T);
                 roff += kkt_bytes(cp.problem->T) + (newton ? newton_bytes(cp.problem->T) : 0);
                 set_correction(it2[(size_t)i], a, eta, ctil, etaT, qh, dbuf, x0p);
+                if (method2) it2[(size_t)i].D.v = vcorr;
                 if (!newton) continue;
                 R* Phi = reinterpret_cast<R*>(nb);
                 R* ct = reinterpret_cast<R*>(nb + up(t * N * N * sizeof(R)));
@@ -329,9 +382,9 @@ struct Launcher {
         a.FE = reinterpret_cast<RT*>(base + L.FE);
         a.X = reinterpret_cast<RT*>(base + L.X);
         a.status = call.status ? call.status : reinterpret_cast<int*>(base);
-        a.out_mask = 3;
+        a.out_mask = 7;
         a.refine_add = 0;
-        pass(a, active.data(), levels, call.sequential, 0, false, s, prof);
+        pass(a, active.data(), levels, call.sequential, 0, false, s, prof, E2, Pref);
         if (newton) {
             // Newton correction of S and v, then K from the corrected S and v
             prof_mark(prof, s, "chain_newton_resid");
@@ -341,7 +394,7 @@ struct Launcher {
                 d1, d3, count, r0, a.status);
             Args<R, RT> c = a;
             c.items = d3;
-            c.out_mask = 1;
+            c.out_mask = 5;
             pass(c, active.data(), levels, call.sequential, 2, true, s, prof);
             prof_mark(prof, s, "chain_newton_gains");
             k_ngains<R, N, M, NG_NEWTON><<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(
@@ -358,9 +411,11 @@ struct Launcher {
                 d1, d2, count, r0, a.status);
             Args<R, RT> b = a;
             b.items = d2;
-            b.out_mask = 0;
+            // the correction pass writes no S, v, K; with Method 2 its walk needs
+            // the pass's own v', kept in a workspace buffer
+            b.out_mask = method2 ? 4 : 0;
             b.refine_add = 1;
-            pass(b, active.data(), levels, call.sequential, 1, false, s, prof);
+            pass(b, active.data(), levels, call.sequential, 1, false, s, prof, E2, Pref);
         }
         prof_end(prof, s);
         return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;

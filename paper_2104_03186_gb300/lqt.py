@@ -47,13 +47,18 @@ class lqt_batch_item(ctypes.Structure):
 LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO, LQT_REFINE_FULL = 0, 1, 2, 3
 
 
+LQT_METHOD_DEFAULT, LQT_METHOD_1, LQT_METHOD_2 = 0, 1, 2
+
+
 class lqt_options(ctypes.Structure):
-    _fields_ = [("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("refine", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
-def options(refine: int = LQT_REFINE_AUTO) -> lqt_options:
+def options(refine: int = LQT_REFINE_AUTO, method: int = LQT_METHOD_DEFAULT) -> lqt_options:
     o = lqt_options()
     o.refine = refine
+    o.method = method
     return o
 
 

@@ -8,13 +8,17 @@ FP32_TOL = 1e-5   # relative Frobenius error per output, FP32 path vs FP64 oracl
 FP64_TOL = 1e-11  # same, FP64 path
 
 
-def gpu_solve(prob, dtype=np.float32, sequential=False, refine=None):
+def gpu_solve(prob, dtype=np.float32, sequential=False, refine=None, method=0):
     """CUDA path through the C ABI; refine=None takes the library default
-    (refinement for FP32, none for FP64)."""
+    (refinement for FP32, none for FP64); method 2 takes Method 2 for the
+    trajectory."""
     from paper_2104_03186_gb300 import lqt
 
     P = lqt.Problem.from_inputs(prob, dtype=dtype)
-    out = lqt.solve(P, sequential=sequential, opts=refine)
+    opts = refine
+    if method:
+        opts = lqt.options(lqt.LQT_REFINE_AUTO if refine is None else refine, method)
+    out = lqt.solve(P, sequential=sequential, opts=opts)
     return {k: v.double().cpu().numpy() for k, v in out.items()}
 
 

@@ -97,6 +97,14 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     opts = lib.options(lib.LQT_REFINE_ON)
     opts.reserved[3] = 1
     assert so.lqt_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(opts)) == 0
+    # an unknown trajectory method; Method 2 is not compiled for n <= 4
+    opts = lib.options(lib.LQT_REFINE_ON, method=7)
+    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
+                        1 << 30, None) == lib.LQT_EINVAL
+    opts = lib.options(lib.LQT_REFINE_ON, method=lib.LQT_METHOD_2)
+    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
+                        1 << 30, None) == lib.LQT_EUNSUPPORTED
+    assert so.lqt_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(opts)) == 0
     # unsupported size reports 0 workspace
     bad = lib.lqt_problem.from_buffer_copy(P.struct)
     bad.dtype = 7

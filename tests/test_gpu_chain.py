@@ -176,3 +176,26 @@ def test_batch_mixes_lane_sizes_and_edge_items():
         g = {k: v.double().cpu().numpy() for k, v in out.items()}
         names = ("S", "v", "x") if T == 0 else ("S", "v", "K", "x", "u")
         compare(g, oracle_solve(pr), FP32_TOL, names=names)
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("refine", [0, 1])
+def test_chain_method2_matches_oracle(n, m, refine):
+    """Trajectory by Method 2 (Lemma LQT_trajectory_method2: forward element scan
+    from (0, x_0, 0, 0, 0), x*_k = (I + C S_k)^{-1}(b + C v_k)) against the
+    oracle, FP32 (plain and refined) and FP64."""
+    prob = _rand(n, m, 700, seed=70 + n).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    compare(gpu_solve(prob, refine=refine, method=2), ref, FP32_TOL)
+    prob64 = _rand(n, m, 700, seed=71 + n)
+    compare(gpu_solve(prob64, dtype=np.float64, method=2), oracle_solve(prob64), FP64_TOL)
+
+
+def test_chain_method2_sequential_and_edge_cases():
+    """Method 2 with one chunk (the sequential path), T = 1, and the vehicle-style
+    diagonal tracking model."""
+    for T, seq in ((300, True), (1, False), (5, False)):
+        prob = _rand(8, 4, T, seed=80 + T).rounded_to(np.float32)
+        compare(gpu_solve(prob, refine=0, method=2, sequential=seq), oracle_solve(prob), FP32_TOL)
+    prob = inputs.diag_tracking(16, T=2000, seed=4).rounded_to(np.float32)
+    compare(gpu_solve(prob, method=2), oracle_solve(prob), FP32_TOL)
