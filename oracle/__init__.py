@@ -14,6 +14,10 @@ paper's formulas step by step:
 * ``affine_combine``  Lemma LQT_trajectory_combination.
 * ``method2_state``   Lemma LQT_trajectory_method2 / eq. lqt_method_2.
 
+``oracle.cross`` (numpy, float64) adds the generalised stage cost of
+Sec. IV-D (cross weight M_k, control offset s_k) by the paper's substitution
+around ``riccati``.
+
 Pins (tests that tie these to something other than themselves) live in
 ``tests/test_oracle_*.py``.  Every function here is pinned.
 

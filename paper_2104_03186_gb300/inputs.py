@@ -283,3 +283,51 @@ def precision_study(T: int = 65536, seed: int = 0, n: int = 32, m: int = 16,
     return LQTProblem(F=_c(F), c=None, L=_c(L), U=_c(1e-3 * np.eye(m))[None],
                       H=_c(np.eye(n))[None], r=_c(r), X=_c(X), HT=_c(np.eye(n)), rT=_c(rT),
                       XT=_c(XT), x0=_c(x0), T=T)
+
+
+# ---------------------------------------------------------------------------
+# Generalised stage cost (Sec. IV-D): cross weights M_k and control offsets s_k.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class CrossTerms:
+    M: Optional[np.ndarray]  # (1|T, p, m) or None (= 0)
+    s: Optional[np.ndarray]  # (1|T, m) or None (= 0)
+
+    def astype(self, dtype) -> "CrossTerms":
+        def cast(a):
+            return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+        return CrossTerms(M=cast(self.M), s=cast(self.s))
+
+    def rounded_to(self, dtype) -> "CrossTerms":
+        return self.astype(dtype).astype(np.float64)
+
+
+def _psd_sqrt(A):
+    """Symmetric square root of a stack of PSD matrices (eigenvalues clipped at 0)."""
+    lam, V = np.linalg.eigh(0.5 * (A + np.swapaxes(A, -1, -2)))
+    return (V * np.sqrt(np.maximum(lam, 0.0))[..., None, :]) @ np.swapaxes(V, -1, -2)
+
+
+def cross_terms(prob: LQTProblem, seed: int = 0, scale: float = 0.5,
+                time_varying: bool = True, with_s: bool = True) -> CrossTerms:
+    """Cross weights M_k = scale X_k^{1/2} G_k U_k^{1/2} with G_k a Gaussian
+    matrix divided by its spectral norm, so that the joint weight
+    [[X_k, M_k], [M_k^T, U_k]] >= (1 - scale) blockdiag(X_k, U_k) stays PSD
+    (and X_k - M_k U_k^{-1} M_k^T >= (1 - scale^2) X_k); control offsets
+    s_k ~ N(0, 1).  With time_varying=False and time-invariant X, U the
+    arrays have one row."""
+    rng = np.random.default_rng(seed)
+    T, m, p = prob.T, prob.m, prob.p
+    cnt = T if (time_varying or not prob.time_invariant("X")
+                or not prob.time_invariant("U")) else 1
+    cnt = max(cnt, 1)
+    G = rng.standard_normal((cnt, p, m))
+    norms = np.linalg.norm(G, ord=2, axis=(1, 2)) if p > 0 and m > 0 else np.ones(cnt)
+    G = G / np.maximum(norms, 1e-300)[:, None, None]
+    Xh = _psd_sqrt(np.broadcast_to(prob.X, (cnt, p, p)))
+    Uh = _psd_sqrt(np.broadcast_to(prob.U, (cnt, m, m)))
+    M = scale * Xh @ G @ Uh
+    s = rng.standard_normal((cnt, m)) if with_s else None
+    return CrossTerms(M=_c(M), s=None if s is None else _c(s))

@@ -7,6 +7,11 @@ Variables z = (u_k, ..., u_{T-1}, x_{k+1}, ..., x_T) with x_k fixed;
 cost  sum_{t=k}^{T-1} 1/2 (H_t x_t - r_t)^T X_t (H_t x_t - r_t) + 1/2 u_t^T U_t u_t
       + 1/2 (H_T x_T - r_T)^T X_T (H_T x_T - r_T);
 constraints x_{t+1} = F_t x_t + c_t + L_t u_t.
+
+With a cross weight M_t (p x m) and a control offset s_t (m) the stage cost is
+that of eq. generalised_cost (Sec. IV-D):
+1/2 e^T X e + e^T M (u - s) + 1/2 (u - s)^T U (u - s), e = H_t x_t - r_t,
+expanded term by term into the same quadratic program.
 """
 import numpy as np
 
@@ -17,8 +22,9 @@ def _step(a, t):
     return a[0] if a.shape[0] == 1 else a[t]
 
 
-def solve_from(prob, k, xk):
-    """Optimal (u_k..u_{T-1}, x_k..x_T, cost) of the tail problem started at x_k."""
+def solve_from(prob, k, xk, M=None, s=None):
+    """Optimal (u_k..u_{T-1}, x_k..x_T, cost) of the tail problem started at x_k
+    (with the generalised stage cost when M or s is given)."""
     n, m, T = prob.n, prob.m, prob.T
     N = T - k
     nu, nx = N * m, N * n
@@ -47,6 +53,24 @@ def solve_from(prob, k, xk):
             P[xidx(t), xidx(t)] += H.T @ X @ H
             q[xidx(t)] -= H.T @ X @ r
             const += 0.5 * r @ X @ r
+        Mt = _step(M, t)
+        st = _step(s, t)
+        st = np.zeros(m) if st is None else st
+        # 1/2 (u - s)^T U (u - s) beyond 1/2 u^T U u: -s^T U u + 1/2 s^T U s
+        q[uidx(t)] -= U @ st
+        const += 0.5 * st @ U @ st
+        if Mt is not None:
+            # (H x - r)^T M (u - s) = x^T H^T M u - x^T H^T M s - r^T M u + r^T M s
+            if t == k:
+                e = H @ xk - r
+                q[uidx(t)] += Mt.T @ e
+                const -= e @ Mt @ st
+            else:
+                P[xidx(t), uidx(t)] += H.T @ Mt
+                P[uidx(t), xidx(t)] += Mt.T @ H
+                q[xidx(t)] -= H.T @ Mt @ st
+                q[uidx(t)] -= Mt.T @ r
+                const += r @ Mt @ st
     rT = np.zeros(prob.pT) if prob.rT is None else prob.rT
     if N == 0:
         e = prob.HT @ xk - rT
@@ -81,23 +105,23 @@ def solve_from(prob, k, xk):
     return u, x, cost
 
 
-def value_function(prob, k):
+def value_function(prob, k, M=None, s=None):
     """(S_k, v_k, K_k, ff_k) of the tail problem at k, read off the brute-force
     solutions: V_k(x) = z + 1/2 x^T S_k x - v_k^T x is quadratic, so its Hessian
     and gradient come exactly from costs at 0, +-e_i and e_i + e_j; the first
     control u_k(x) = -K_k x + ff_k is affine in x."""
     n = prob.n
     I = np.eye(n)
-    V0 = solve_from(prob, k, np.zeros(n))
-    Vp = [solve_from(prob, k, I[i]) for i in range(n)]
-    Vm = [solve_from(prob, k, -I[i]) for i in range(n)]
+    V0 = solve_from(prob, k, np.zeros(n), M, s)
+    Vp = [solve_from(prob, k, I[i], M, s) for i in range(n)]
+    Vm = [solve_from(prob, k, -I[i], M, s) for i in range(n)]
     S = np.zeros((n, n))
     v = np.zeros(n)
     for i in range(n):
         S[i, i] = Vp[i][2] + Vm[i][2] - 2 * V0[2]
         v[i] = -(Vp[i][2] - Vm[i][2]) / 2
         for j in range(i + 1, n):
-            Vij = solve_from(prob, k, I[i] + I[j])[2]
+            Vij = solve_from(prob, k, I[i] + I[j], M, s)[2]
             S[i, j] = S[j, i] = Vij - Vp[i][2] - Vp[j][2] + V0[2]
     if k < prob.T:
         ff = V0[0][0]
@@ -107,8 +131,9 @@ def value_function(prob, k):
     return S, v, K, ff
 
 
-def total_cost(prob, u):
-    """Cost of eq. LQT_problem for a control sequence u (T, m) from x_0."""
+def total_cost(prob, u, M=None, s=None):
+    """Cost of eq. LQT_problem (eq. generalised_cost stages when M or s is
+    given) for a control sequence u (T, m) from x_0."""
     n, T = prob.n, prob.T
     x = prob.x0.copy()
     J = 0.0
@@ -117,7 +142,12 @@ def total_cost(prob, u):
         r = _step(prob.r, t)
         r = np.zeros(H.shape[0]) if r is None else r
         e = H @ x - r
-        J += 0.5 * e @ X @ e + 0.5 * u[t] @ U @ u[t]
+        st = _step(s, t)
+        du = u[t] - (0 if st is None else st)
+        J += 0.5 * e @ X @ e + 0.5 * du @ U @ du
+        Mt = _step(M, t)
+        if Mt is not None:
+            J += e @ Mt @ du
         c = _step(prob.c, t)
         x = _step(prob.F, t) @ x + (0 if c is None else c) + _step(prob.L, t) @ u[t]
     rT = np.zeros(prob.pT) if prob.rT is None else prob.rT
