@@ -411,6 +411,9 @@ def run_ours(args):
     precision = None if args.no_precision else run_precision(
         args, stream, flush, compute_peaks["fp32_tflops"], compute_peaks["fp64_tflops"])
 
+    # ---- generalised stage cost (cross weights, control offsets) -------------
+    cross = None if args.no_cross else run_cross(args, stream, flush)
+
     clk.__exit__(None, None, None)
     clocks = clk.result()
 
@@ -440,6 +443,7 @@ def run_ours(args):
         "batch": batch,
         "serving": serving,
         "precision_study": precision,
+        "cross": cross,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -651,6 +655,56 @@ def run_precision(args, stream, flush, fp32_peak=None, fp64_peak=None):
             "oracle_s": oracle_s}
 
 
+def run_cross(args, stream, flush):
+    """Generalised stage cost (Sec. IV-D) on the vehicle workload at T = 1e6:
+    cross weights M_k = 0.5 X^{1/2} G_k U^{1/2} and offsets s_k ~ N(0, 1)
+    (time-varying).  lqt_solve_cross (transform kernel, the refined solve of the
+    transformed problem, post kernel) against the same solve of the plain
+    problem, and its errors against the FP64 oracle."""
+    from oracle import cross as ocross
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    T = T_HEADLINE
+    prob = inputs.vehicle(T, seed=0)
+    ct = inputs.cross_terms(prob, seed=1, scale=0.5)
+    prob, ct = prob.rounded_to(np.float32), ct.rounded_to(np.float32)
+    opts = lqt.LQT_REFINE_ON
+    P = lqt.Problem.from_inputs(prob, dtype=np.float32)
+    C = lqt.Cross.from_inputs(ct, dtype=np.float32)
+    o = P.allocate_outputs()
+    ws = torch_empty_bytes(lqt.lqt_cross_workspace_bytes(P, C, opts))
+    call = lambda: lqt.lqt_solve_cross(P, C, o, ws, stream, opts)  # noqa: E731
+    for _ in range(3):
+        call()
+    st = lqt.lqt_workspace_status(ws, stream)
+    times = _time_solves(call, 10, flush, stream)
+    got = {k: v.double().cpu().numpy() for k, v in o.items()}
+    ws_plain = lqt.workspace_for(P, opts=opts)
+    plain = lambda: lqt.lqt_solve(P, o, ws_plain, stream, opts)  # noqa: E731
+    for _ in range(3):
+        plain()
+    tplain = _time_solves(plain, 10, flush, stream)
+    t0 = time.perf_counter()
+    ref = ocross.riccati_cross(prob, ct.M, ct.s)
+    oracle_s = time.perf_counter() - t0
+    errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+            for k in ("S", "v", "K", "x", "u")}
+    med, medp = float(np.median(times)), float(np.median(tplain))
+    return {"workload": "vehicle T=%d with time-varying cross weights M_k (2x2) and control "
+                        "offsets s_k; inputs rounded to FP32; refinement ON" % T,
+            "status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3),
+            "plain_solve_ms": medp, "transform_overhead_ms": med - medp,
+            "error_vs_fp64_oracle": errs, "oracle_s": oracle_s}
+
+
+def torch_empty_bytes(nbytes):
+    import torch
+
+    if nbytes == 0:
+        raise RuntimeError("workspace query returned 0")
+    return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
 # (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
 # None when the kernel has changed since the counters were taken.
@@ -670,6 +724,8 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-precision", action="store_true", help="skip the n = 32 precision study")
     ap.add_argument("--precision-T", type=int, default=65536)
+    ap.add_argument("--no-cross", action="store_true",
+                    help="skip the generalised-cost (cross weight) measurement")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling mode: run --warmup + this many solves of --T and exit "
                          "(no JSON line; for ncu captures)")

@@ -244,6 +244,43 @@ lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *w
 lqt_status lqt_solve_static(const lqt_problem *prob, const lqt_solution *sol,
                             const lqt_options *opts, void *stream);
 
+/* Generalised stage cost (Sec. IV-D, eq. generalised_cost): the stage cost of
+ * eq. LQT_problem becomes
+ *     1/2 e_k^T X_k e_k + e_k^T M_k (u_k - s_k) + 1/2 (u_k - s_k)^T U_k (u_k - s_k),
+ *     e_k = H_k x_k - r_k,
+ * with a cross weight M_k (p x m, row-major) and a control offset s_k (m);
+ * the joint weight [[X_k, M_k], [M_k^T, U_k]] must be positive semi-definite
+ * with U_k positive definite.  The terminal cost is unchanged.
+ *   M, s: per-step inputs as in lqt_problem (ptr NULL: zero; step stride 0:
+ *         time-invariant), device pointers, dtype of the problem.
+ * A NULL `cross` means M = 0, s = 0. */
+typedef struct {
+    lqt_in M;
+    lqt_in s;
+} lqt_cross;
+
+/* Bytes of device workspace lqt_solve_cross needs (0 on invalid arguments or
+ * an unsupported size): the workspace of lqt_solve for the problem plus the
+ * transformed per-step matrices. */
+size_t lqt_cross_workspace_bytes(const lqt_problem *prob, const lqt_cross *cross,
+                                 const lqt_options *opts);
+
+/* Solves the generalised-cost problem by the paper's reduction to
+ * eq. LQT_problem (Sec. IV-D): with W_k = U_k^{-1} M_k^T, a transform kernel
+ * writes F~_k = F_k - L_k W_k H_k, c~_k = c_k + L_k (W_k r_k + s_k) and
+ * X~_k = X_k - M_k W_k into the workspace (time-invariant where all their
+ * inputs are), lqt_solve solves the transformed problem (same options, so
+ * refinement and Method 2 apply to it), and a post kernel returns the outputs
+ * of the original problem: S_k, v_k and x*_k as solved, the gain of the
+ * original control law K_k = K~_k + W_k H_k, and
+ * u*_k = u~*_k - W_k (H_k x*_k - r_k) + s_k.  The transform runs in the
+ * problem's dtype.  Workspace rules, outputs and return values are those of
+ * lqt_solve; a U_k that is not positive definite is reported as LQT_ENOTSPD
+ * by lqt_workspace_status. */
+lqt_status lqt_solve_cross(const lqt_problem *prob, const lqt_cross *cross,
+                           const lqt_solution *sol, const lqt_options *opts, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
 /* Static string for a status code (never NULL). */
 const char *lqt_strerror(lqt_status status);
 

@@ -62,16 +62,12 @@ def transform(prob, M, s):
     Mk = np.zeros((T, p, m)) if M is None else _per_step(M, T)
     sk = np.zeros((T, m)) if s is None else _per_step(s, T)
 
-    W = np.empty((T, m, p))
-    Ft = np.empty((T, n, n))
-    ct = np.empty((T, n))
-    Xt = np.empty((T, p, p))
-    for k in range(T):
-        W[k] = np.linalg.solve(U[k], Mk[k].T)          # U^{-1} M^T
-        Ft[k] = F[k] - L[k] @ W[k] @ H[k]              # F~
-        ct[k] = c[k] + L[k] @ W[k] @ r[k] + L[k] @ sk[k]  # c~
-        Xt[k] = X[k] - Mk[k] @ W[k]                    # X~
-    WH = np.einsum("kij,kjl->kil", W, H) if T > 0 else np.zeros((0, m, n))
+    # per step k (batched over the time axis):
+    W = np.linalg.solve(U, np.swapaxes(Mk, 1, 2)) if T > 0 else np.zeros((0, m, p))  # U^{-1} M^T
+    WH = W @ H                                                      # U^{-1} M^T H
+    Ft = F - L @ WH                                                 # F~
+    ct = c + np.einsum("kij,kj->ki", L, np.einsum("kij,kj->ki", W, r) + sk)  # c~
+    Xt = X - Mk @ W                                                 # X~
     tp = dataclasses.replace(prob, F=Ft, c=ct, L=np.array(L), U=np.array(U), H=np.array(H),
                              r=np.array(r), X=Xt)
     return tp, W, WH
@@ -86,10 +82,7 @@ def riccati_cross(prob, M, s) -> dict:
     H = _per_step(prob.H, T)
     r = np.zeros((T, p)) if prob.r is None else _per_step(prob.r, T)
     sk = np.zeros((T, prob.m)) if s is None else _per_step(s, T)
-    u = np.empty_like(o["u"])
-    K = np.empty_like(o["K"])
-    for k in range(T):
-        e = H[k] @ o["x"][k] - r[k]                   # H x - r at the optimum
-        u[k] = o["u"][k] - W[k] @ e + sk[k]           # u = u~ - U^{-1} M^T (H x - r) + s
-        K[k] = o["K"][k] + WH[k]                      # K = K~ + U^{-1} M^T H
+    e = np.einsum("kij,kj->ki", H, o["x"][:T]) - r          # H x - r at the optimum
+    u = o["u"] - np.einsum("kij,kj->ki", W, e) + sk          # u = u~ - U^{-1} M^T (H x - r) + s
+    K = o["K"] + WH                                          # K = K~ + U^{-1} M^T H
     return {"S": o["S"], "v": o["v"], "K": K, "x": o["x"], "u": u}

@@ -72,6 +72,22 @@ const Variant* find_variant(int dtype, int n, int m) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// The chunked pipeline solves the lane-group sizes, and the n <= 4 problems
+// that ask for Method 2 or the FULL refinement where a small chain variant is
+// compiled.  False with *unsupported set: no kernel serves these options.
+bool use_chain(const lqt_problem* P, const Variant* var, bool newton, bool method2,
+               bool* unsupported) {
+    *unsupported = false;
+    if (!var) {
+        *unsupported = !chain_supported(P->dtype, P->n, P->m);
+        return !*unsupported;
+    }
+    const bool small_chain = chain_small_supported(P->dtype, P->n, P->m) &&
+                             P->p <= 2 * P->n && P->pT <= 2 * P->n;
+    if (method2 && !small_chain) *unsupported = true;
+    return (method2 || newton) && small_chain;
+}
+
 // Validates everything that does not depend on a compiled variant.
 lqt_status validate(const lqt_problem* P, const lqt_solution* sol) {
     if (!P) return LQT_EINVAL;
@@ -313,9 +329,10 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
     bool refine = false, newton = false, method2 = false;
     if ((st = resolve_refine(prob, opts, &refine, &newton, &method2)) != LQT_OK) return st;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (var && method2) return LQT_EUNSUPPORTED;
-    if (!var) {
-        if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
+    bool unsupported = false;
+    const bool chain = use_chain(prob, var, refine && newton, method2, &unsupported);
+    if (unsupported) return LQT_EUNSUPPORTED;
+    if (chain) {
         int NC = 0, nk = 0;
         long long B = 0;
         if ((st = chain_workspace(prob, refine, newton, false, method2, nullptr, &NC, &B, &nk)) !=
@@ -343,11 +360,12 @@ size_t lqt_workspace_bytes(const lqt_problem* prob, const lqt_options* opts) {
     bool refine = false, newton = false, method2 = false;
     if (resolve_refine(prob, opts, &refine, &newton, &method2) != LQT_OK) return 0;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (var && method2) return 0;
-    if (!var) {
+    bool unsupported = false;
+    const bool chain = use_chain(prob, var, refine && newton, method2, &unsupported);
+    if (unsupported) return 0;
+    if (chain) {
         size_t bytes = 0;
-        if (!chain_supported(prob->dtype, prob->n, prob->m) ||
-            chain_workspace(prob, refine, newton, false, method2, &bytes, nullptr, nullptr,
+        if (chain_workspace(prob, refine, newton, false, method2, &bytes, nullptr, nullptr,
                             nullptr) != LQT_OK)
             return 0;
         return bytes;
@@ -418,10 +436,11 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     if ((st = resolve_refine(prob, opts, &refine, &newton, &method2)) != LQT_OK) return st;
     if (sequential && prob->p > 64) return LQT_EUNSUPPORTED;
     const Variant* var = find_variant(prob->dtype, prob->n, prob->m);
-    if (var && method2) return LQT_EUNSUPPORTED;
-    if (!var) {
-        // lane-group sizes: the chunked pipeline (one chunk when sequential)
-        if (!chain_supported(prob->dtype, prob->n, prob->m)) return LQT_EUNSUPPORTED;
+    bool unsupported = false;
+    const bool chain = use_chain(prob, var, refine && newton, method2, &unsupported);
+    if (unsupported) return LQT_EUNSUPPORTED;
+    if (chain) {
+        // the chunked pipeline (one chunk when sequential)
         size_t need = 0;
         if ((st = chain_workspace(prob, refine, newton, sequential, method2, &need, nullptr,
                                   nullptr, nullptr)) != LQT_OK)

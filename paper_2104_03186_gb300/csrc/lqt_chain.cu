@@ -20,8 +20,8 @@ size_t up_c(size_t x) { return (x + kAlignC - 1) / kAlignC * kAlignC; }
 constexpr long long kMinChunk = 4;
 
 const ChainVariant* find_chain(int dtype, int n, int m, bool mixed) {
-    const ChainVariant* (*tables[])(int*) = {&chain_variants_n8, &chain_variants_n16,
-                                             &chain_variants_n32};
+    const ChainVariant* (*tables[])(int*) = {&chain_variants_n4, &chain_variants_n8,
+                                             &chain_variants_n16, &chain_variants_n32};
     for (auto t : tables) {
         int cnt = 0;
         const ChainVariant* v = t(&cnt);
@@ -114,7 +114,13 @@ lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, co
 
 }  // namespace
 
-bool chain_supported(int dtype, int n, int m) { return find_chain(dtype, n, m, false) != nullptr; }
+bool chain_supported(int dtype, int n, int m) {
+    return n >= 8 && find_chain(dtype, n, m, false) != nullptr;
+}
+
+bool chain_small_supported(int dtype, int n, int m) {
+    return n < 8 && find_chain(dtype, n, m, false) != nullptr;
+}
 
 lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
                            bool method2, size_t* bytes, int* NC, long long* B, int* kernels) {

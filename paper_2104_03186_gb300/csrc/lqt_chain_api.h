@@ -43,7 +43,9 @@ struct ChainVariant {
     int (*fold_groups)();
 };
 
-// Variants compiled in lqt_chain_n8.cu, lqt_chain_n16.cu and lqt_chain_n32.cu.
+// Variants compiled in lqt_chain_n4.cu, lqt_chain_n8.cu, lqt_chain_n16.cu and
+// lqt_chain_n32.cu.
+const ChainVariant* chain_variants_n4(int* count);
 const ChainVariant* chain_variants_n8(int* count);
 const ChainVariant* chain_variants_n16(int* count);
 const ChainVariant* chain_variants_n32(int* count);
@@ -86,7 +88,11 @@ DescT<R> make_desc(const lqt_problem* P, const lqt_solution* S) {
 }
 
 // Chain path entry points used by the C ABI (lqt_chain.cu).
+// Lane-group sizes (n >= 8): the chunked pipeline is the solver.
 bool chain_supported(int dtype, int n, int m);
+// n <= 4 sizes with a compiled chain variant: used for Method 2 and the FULL
+// refinement, which the thread-per-step kernels do not provide.
+bool chain_small_supported(int dtype, int n, int m);
 // Single problem: workspace bytes, chunk geometry and kernel launches.
 lqt_status chain_workspace(const lqt_problem* P, bool refine, bool newton, bool sequential,
                            bool method2, size_t* bytes, int* NC, long long* B, int* kernels);

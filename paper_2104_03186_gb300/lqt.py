@@ -44,6 +44,10 @@ class lqt_batch_item(ctypes.Structure):
     _fields_ = [("problem", lqt_problem), ("solution", lqt_solution)]
 
 
+class lqt_cross(ctypes.Structure):
+    _fields_ = [("M", lqt_in), ("s", lqt_in)]
+
+
 LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO, LQT_REFINE_FULL = 0, 1, 2, 3
 
 
@@ -99,6 +103,8 @@ def _load() -> ctypes.CDLL:
         "lqt_solve_static": (st, [P, S, O, vp]),
         "lqt_batch_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
         "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
+        "lqt_cross_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_cross), O]),
+        "lqt_solve_cross": (st, [P, ctypes.POINTER(lqt_cross), S, O, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +182,40 @@ class Problem:
         return {k: torch.empty(s, dtype=tdt, device=device) for k, s in shapes.items()}
 
 
+class Cross:
+    """Cross weights M_k (p x m) and control offsets s_k (m) of the generalised
+    stage cost (Sec. IV-D) as tensors, plus the lqt_cross struct that points
+    at them.  Either may be None (zero)."""
+
+    def __init__(self, M=None, s=None):
+        self.M, self.s = M, s
+        c = lqt_cross()
+        for f, a in (("M", M), ("s", s)):
+            if a is None:
+                setattr(c, f, lqt_in(None, 0))
+            else:
+                per_step = int(np.prod(a.shape[1:]))
+                setattr(c, f, lqt_in(_ptr(a), 0 if a.shape[0] == 1 else per_step))
+        self.struct = c
+
+    @classmethod
+    def from_inputs(cls, ct, dtype=np.float32, device="cuda"):
+        """Copy an inputs.CrossTerms (float64 numpy) to `dtype` tensors on `device`."""
+        import torch
+
+        tdt = torch.float32 if np.dtype(dtype) == np.float32 else torch.float64
+
+        def cv(a):
+            return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(
+                tdt).to(device)
+
+        return cls(cv(ct.M), cv(ct.s))
+
+
+def _cross(c):
+    return None if c is None else ctypes.byref(c.struct)
+
+
 def solution_struct(out: Dict[str, object]) -> lqt_solution:
     s = lqt_solution()
     for f in OUTPUT_FIELDS:
@@ -231,6 +271,22 @@ def lqt_riccati_sequential(prob: Problem, out: Dict[str, object], workspace, str
                                      _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
     if st != LQT_OK:
         raise LQTError(st, "lqt_riccati_sequential")
+
+
+def lqt_cross_workspace_bytes(prob: Problem, cross: Optional[Cross], opts=None) -> int:
+    return int(_lib.lqt_cross_workspace_bytes(ctypes.byref(prob.struct), _cross(cross),
+                                              _opts(opts)))
+
+
+def lqt_solve_cross(prob: Problem, cross: Optional[Cross], out: Dict[str, object], workspace,
+                    stream=None, opts=None) -> None:
+    """Generalised-cost solve (Sec. IV-D); asynchronous like lqt_solve."""
+    sol = solution_struct(out)
+    st = _lib.lqt_solve_cross(ctypes.byref(prob.struct), _cross(cross), ctypes.byref(sol),
+                              _opts(opts), _ptr(workspace), _nbytes(workspace),
+                              _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_cross")
 
 
 def lqt_workspace_status(workspace, stream=None) -> int:
@@ -368,6 +424,24 @@ def solve(prob: Problem, stream=None, check: bool = True, workspace=None, sequen
         lqt_riccati_sequential(prob, out, ws, stream, opts)
     else:
         lqt_solve(prob, out, ws, stream, opts)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return out
+
+
+def solve_cross(prob: Problem, cross: Optional[Cross], stream=None, check: bool = True,
+                opts=None):
+    """Allocate outputs and a workspace with torch and run lqt_solve_cross."""
+    import torch
+
+    out = prob.allocate_outputs()
+    nbytes = lqt_cross_workspace_bytes(prob, cross, opts)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_cross_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lqt_solve_cross(prob, cross, out, ws, stream, opts)
     if check:
         st = lqt_workspace_status(ws, stream)
         if st != LQT_OK:

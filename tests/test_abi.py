@@ -97,15 +97,44 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     opts = lib.options(lib.LQT_REFINE_ON)
     opts.reserved[3] = 1
     assert so.lqt_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(opts)) == 0
-    # an unknown trajectory method; Method 2 is not compiled for n <= 4
+    # an unknown trajectory method; Method 2 where no chain variant is compiled
     opts = lib.options(lib.LQT_REFINE_ON, method=7)
     assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
                         1 << 30, None) == lib.LQT_EINVAL
     opts = lib.options(lib.LQT_REFINE_ON, method=lib.LQT_METHOD_2)
-    assert so.lqt_solve(ctypes.byref(P.struct), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
+    small = lib.lqt_problem.from_buffer_copy(P.struct)
+    small.n, small.m = 2, 1  # no chain variant at (2, 1): Method 2 is not compiled there
+    assert so.lqt_solve(ctypes.byref(small), ctypes.byref(sol), ctypes.byref(opts), fake_ws,
                         1 << 30, None) == lib.LQT_EUNSUPPORTED
-    assert so.lqt_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(opts)) == 0
+    assert so.lqt_workspace_bytes(ctypes.byref(small), ctypes.byref(opts)) == 0
     # unsupported size reports 0 workspace
     bad = lib.lqt_problem.from_buffer_copy(P.struct)
     bad.dtype = 7
     assert so.lqt_workspace_bytes(ctypes.byref(bad), None) == 0
+
+
+def test_cross_arguments_rejected_before_any_device_work(lib):
+    """lqt_solve_cross: NULL or misaligned workspace, a cross weight stride
+    shorter than one step, a misaligned offset vector."""
+    so = lib.library()
+    P, arr = _host_problem(lib)
+    out = {k: np.zeros(s, np.float32) for k, s in
+           {"S": (17, 4, 4), "v": (17, 4), "K": (16, 2, 4), "x": (17, 4), "u": (16, 2)}.items()}
+    sol = lib.lqt_solution(*[o.ctypes.data for o in out.values()])
+    M = np.zeros((16, 2, 2), np.float32)
+    s = np.zeros((16, 3), np.float32)
+    fake_ws = ctypes.c_void_p(1 << 20)
+    good = lib.lqt_cross(lib.lqt_in(M.ctypes.data, 4), lib.lqt_in(s.ctypes.data, 3))
+    args = (ctypes.byref(P.struct), ctypes.byref(good), ctypes.byref(sol), None)
+    assert so.lqt_solve_cross(*args, None, 0, None) == lib.LQT_EINVAL
+    assert so.lqt_solve_cross(*args, ctypes.c_void_p((1 << 20) + 8), 1 << 30,
+                              None) == lib.LQT_EINVAL
+    short = lib.lqt_cross(lib.lqt_in(M.ctypes.data, 3), lib.lqt_in(None, 0))
+    assert so.lqt_solve_cross(ctypes.byref(P.struct), ctypes.byref(short), ctypes.byref(sol),
+                              None, fake_ws, 1 << 30, None) == lib.LQT_EINVAL
+    assert so.lqt_cross_workspace_bytes(ctypes.byref(P.struct), ctypes.byref(short), None) == 0
+    skew = lib.lqt_cross(lib.lqt_in(None, 0), lib.lqt_in(s.ctypes.data + 2, 3))
+    assert so.lqt_solve_cross(ctypes.byref(P.struct), ctypes.byref(skew), ctypes.byref(sol),
+                              None, fake_ws, 1 << 30, None) == lib.LQT_EINVAL
+    assert so.lqt_solve_cross(None, ctypes.byref(good), ctypes.byref(sol), None, fake_ws,
+                              1 << 30, None) == lib.LQT_EINVAL

@@ -58,7 +58,7 @@ def test_chain_shapes(n, m, kw, refine):
     compare(gpu_solve(prob64, dtype=np.float64), oracle_solve(prob64), FP64_TOL)
 
 
-@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("n,m", [(4, 2)] + SIZES)
 @pytest.mark.parametrize("sequential", [False, True])
 def test_chain_full_refinement(n, m, sequential):
     """FULL refinement (FP64 tree levels, Newton step for S, v, K, KKT step
@@ -178,7 +178,7 @@ def test_batch_mixes_lane_sizes_and_edge_items():
         compare(g, oracle_solve(pr), FP32_TOL, names=names)
 
 
-@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("n,m", [(4, 2)] + SIZES)
 @pytest.mark.parametrize("refine", [0, 1])
 def test_chain_method2_matches_oracle(n, m, refine):
     """Trajectory by Method 2 (Lemma LQT_trajectory_method2: forward element scan
@@ -199,3 +199,23 @@ def test_chain_method2_sequential_and_edge_cases():
         compare(gpu_solve(prob, refine=0, method=2, sequential=seq), oracle_solve(prob), FP32_TOL)
     prob = inputs.diag_tracking(16, T=2000, seed=4).rounded_to(np.float32)
     compare(gpu_solve(prob, method=2), oracle_solve(prob), FP32_TOL)
+
+
+def test_small_size_full_refinement_routes_to_chain():
+    """n = 4: FULL refinement and Method 2 run the chunked pipeline (n = 4 lane
+    groups), whose Newton step brings S, v, K of a time-invariant problem with
+    open-loop spectral radius up to 1.05 to FP32 level; the thread-per-step
+    kernels (ON) leave S near 1e-4 there."""
+    from paper_2104_03186_gb300 import lqt
+
+    prob = _rand(4, 2, 700, seed=504, time_varying=False).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    full = compare(gpu_solve(prob, refine=3), ref, FP32_TOL)
+    assert max(full.values()) < 2e-6
+    P = lqt.Problem.from_inputs(prob)
+    assert lqt.lqt_plan(P, 3)["tile_threads"] == 4      # lane group of n lanes
+    assert lqt.lqt_plan(P, 1)["tile_threads"] != 4      # thread-per-step tiles
+    compare(gpu_solve(prob, refine=3, method=2), ref, FP32_TOL)
+    prob64 = _rand(4, 2, 700, seed=505, time_varying=False)
+    compare(gpu_solve(prob64, dtype=np.float64, refine=3), oracle_solve(prob64), FP64_TOL)
+    compare(gpu_solve(prob64, dtype=np.float64, method=2), oracle_solve(prob64), FP64_TOL)

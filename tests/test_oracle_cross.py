@@ -133,16 +133,16 @@ def test_cross_zero_horizon(orc):
 
 
 CROSS_MUTATIONS = {
-    "W_uses_M_not_transposed": ("np.linalg.solve(U[k], Mk[k].T)", "np.linalg.solve(U[k], Mk[k])"),
-    "F_tilde_sign": ("Ft[k] = F[k] - L[k] @ W[k] @ H[k]", "Ft[k] = F[k] + L[k] @ W[k] @ H[k]"),
-    "c_tilde_drops_Ls": ("ct[k] = c[k] + L[k] @ W[k] @ r[k] + L[k] @ sk[k]",
-                         "ct[k] = c[k] + L[k] @ W[k] @ r[k]"),
-    "c_tilde_sign_of_r_term": ("ct[k] = c[k] + L[k] @ W[k] @ r[k] + L[k] @ sk[k]",
-                               "ct[k] = c[k] - L[k] @ W[k] @ r[k] + L[k] @ sk[k]"),
-    "X_tilde_sign": ("Xt[k] = X[k] - Mk[k] @ W[k]", "Xt[k] = X[k] + Mk[k] @ W[k]"),
-    "u_drops_offset": ("u[k] = o[\"u\"][k] - W[k] @ e + sk[k]", "u[k] = o[\"u\"][k] - W[k] @ e"),
-    "u_error_sign_of_r": ("e = H[k] @ o[\"x\"][k] - r[k]", "e = H[k] @ o[\"x\"][k] + r[k]"),
-    "K_without_WH": ("K[k] = o[\"K\"][k] + WH[k]", "K[k] = o[\"K\"][k]"),
+    "W_uses_M_not_transposed": ("np.linalg.solve(U, np.swapaxes(Mk, 1, 2))",
+                                "np.linalg.solve(U, Mk)"),
+    "F_tilde_sign": ("Ft = F - L @ WH", "Ft = F + L @ WH"),
+    "c_tilde_drops_Ls": ('np.einsum("kij,kj->ki", W, r) + sk)', 'np.einsum("kij,kj->ki", W, r))'),
+    "c_tilde_sign_of_r_term": ('np.einsum("kij,kj->ki", W, r) + sk)',
+                               '-np.einsum("kij,kj->ki", W, r) + sk)'),
+    "X_tilde_sign": ("Xt = X - Mk @ W", "Xt = X + Mk @ W"),
+    "u_drops_offset": ('np.einsum("kij,kj->ki", W, e) + sk', 'np.einsum("kij,kj->ki", W, e)'),
+    "u_error_sign_of_r": ('o["x"][:T]) - r', 'o["x"][:T]) + r'),
+    "K_without_WH": ('K = o["K"] + WH', 'K = o["K"]'),
 }
 
 
