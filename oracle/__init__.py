@@ -16,7 +16,8 @@ paper's formulas step by step:
 
 ``oracle.cross`` (numpy, float64) adds the generalised stage cost of
 Sec. IV-D (cross weight M_k, control offset s_k) by the paper's substitution
-around ``riccati``.
+around ``riccati``.  ``oracle.nonlinear`` runs the iterated linearise-and-solve
+passes of Sec. IV-D for the unicycle of Sec. VI-E around ``riccati``.
 
 Pins (tests that tie these to something other than themselves) live in
 ``tests/test_oracle_*.py``.  Every function here is pinned.

@@ -331,3 +331,64 @@ def cross_terms(prob: LQTProblem, seed: int = 0, scale: float = 0.5,
     M = scale * Xh @ G @ Uh
     s = rng.standard_normal((cnt, m)) if with_s else None
     return CrossTerms(M=_c(M), s=None if s is None else _c(s))
+
+
+# ---------------------------------------------------------------------------
+# Unicycle race-track tracking (Sec. VI-E, the nonlinear experiment).
+# ---------------------------------------------------------------------------
+
+def stadium_track(sigma, straight: float = 20.0, radius: float = 5.0):
+    """Position and unwrapped heading at arc length sigma along a stadium track
+    (two straights joined by two half circles, driven counter-clockwise from
+    (0, -radius) with heading 0); the heading grows by 2 pi per lap."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    per = 2 * straight + 2 * math.pi * radius
+    lap = np.floor(sigma / per)
+    t = sigma - lap * per
+    px = np.empty_like(t)
+    py = np.empty_like(t)
+    th = np.empty_like(t)
+    s1 = t < straight
+    s2 = (t >= straight) & (t < straight + math.pi * radius)
+    s3 = (t >= straight + math.pi * radius) & (t < 2 * straight + math.pi * radius)
+    s4 = t >= 2 * straight + math.pi * radius
+    px[s1], py[s1], th[s1] = t[s1], -radius, 0.0
+    a2 = (t[s2] - straight) / radius
+    px[s2], py[s2], th[s2] = straight + radius * np.sin(a2), -radius * np.cos(a2), a2
+    d3 = t[s3] - straight - math.pi * radius
+    px[s3], py[s3], th[s3] = straight - d3, radius, math.pi
+    a4 = (t[s4] - 2 * straight - math.pi * radius) / radius
+    px[s4], py[s4], th[s4] = -radius * np.sin(a4), radius * np.cos(a4), math.pi + a4
+    return px, py, th + 2 * math.pi * lap
+
+
+def unicycle_track(T: int, seed: int = 0, dt: float = 0.1, speed: float = 2.0,
+                   ref_every: int = 10, noise: float = 0.01) -> LQTProblem:
+    """Cost and initial state of the unicycle experiment (Sec. VI-E): state
+    (p_x, p_y, theta, s), control (a, omega); H_k = [I_3 0] (p = 3),
+    X_k = diag(100, 100, 1000) at steps with a reference point (every
+    `ref_every`-th step) and 1e-6 I otherwise, the same 1e-6 I at k = T;
+    U_k = diag(1, 100).  Reference points are positions and headings of a
+    stadium track (straights of 20, half circles of radius 5) driven at
+    `speed`, plus N(0, noise^2); r_k is held between reference points.
+    x_0 = start of the track + N(0, 0.1^2) in position, heading 0, at rest.
+    F, L, c are placeholders (identity, zero): the nonlinear solve
+    linearises the model itself."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(T + 1)
+    kref = (k // ref_every) * ref_every
+    px, py, th = stadium_track(speed * dt * kref)
+    r = np.stack([px, py, th], axis=1) + noise * rng.standard_normal((T + 1, 3))
+    r = r[(k // ref_every) * ref_every]          # held between reference points
+    is_ref = (k % ref_every) == 0
+    X = np.zeros((T + 1, 3, 3))
+    X[:, 0, 0] = np.where(is_ref, 100.0, 1e-6)
+    X[:, 1, 1] = X[:, 0, 0]
+    X[:, 2, 2] = np.where(is_ref, 1000.0, 1e-6)
+    X[T] = 1e-6 * np.eye(3)
+    H = np.hstack([np.eye(3), np.zeros((3, 1))])
+    x0 = np.array([0.0, -5.0, 0.0, 0.0])
+    x0[:2] += 0.1 * rng.standard_normal(2)
+    return LQTProblem(F=_c(np.eye(4))[None], c=None, L=_c(np.zeros((4, 2)))[None],
+                      U=_c(np.diag([1.0, 100.0]))[None], H=_c(H)[None], r=_c(r[:T]),
+                      X=_c(X[:T]), HT=_c(H), rT=_c(r[T]), XT=_c(X[T]), x0=_c(x0), T=T)
