@@ -414,6 +414,9 @@ def run_ours(args):
     # ---- generalised stage cost (cross weights, control offsets) -------------
     cross = None if args.no_cross else run_cross(args, stream, flush)
 
+    # ---- iterated nonlinear LQT (unicycle) ----------------------------------
+    nonlinear = None if args.no_nonlinear else run_nonlinear(args, stream, flush)
+
     clk.__exit__(None, None, None)
     clocks = clk.result()
 
@@ -444,6 +447,7 @@ def run_ours(args):
         "serving": serving,
         "precision_study": precision,
         "cross": cross,
+        "nonlinear": nonlinear,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -697,6 +701,47 @@ def run_cross(args, stream, flush):
             "error_vs_fp64_oracle": errs, "oracle_s": oracle_s}
 
 
+def run_nonlinear(args, stream, flush):
+    """Iterated nonlinear LQT (Sec. IV-D, Sec. VI-E): the unicycle on a stadium
+    track at T = 1e5 (about 280 laps), 10 linearise-and-solve passes, FP32
+    with refinement ON.  Parallel passes (Method 1, and Method 2) against the
+    sequential recursion on the GPU, and errors against the FP64 oracle."""
+    from oracle import nonlinear as onl
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    T, iters = 100_000, 10
+    prob = inputs.unicycle_track(T, seed=0).rounded_to(np.float32)
+    P = lqt.Problem.from_inputs(prob, dtype=np.float32)
+    o = P.allocate_outputs()
+    forms = {"method1": (lqt.LQT_REFINE_ON, False),
+             "method2": (lqt.options(lqt.LQT_REFINE_ON, lqt.LQT_METHOD_2), False),
+             "sequential": (lqt.LQT_REFINE_ON, True)}
+    t0 = time.perf_counter()
+    ref = onl.iterated_lqt(onl.Unicycle(0.1), prob, iters)
+    oracle_s = time.perf_counter() - t0
+    res = {}
+    for name, (opts, seq) in forms.items():
+        nl = lqt.nonlinear(iters, 0.1, seq)
+        ws = torch_empty_bytes(lqt.lqt_nonlinear_workspace_bytes(P, nl, opts))
+        call = lambda: lqt.lqt_solve_nonlinear(P, nl, o, ws, stream, opts)  # noqa: E731
+        call()
+        st = lqt.lqt_workspace_status(ws, stream)
+        times = _time_solves(call, 1 if seq else 5, flush, stream)
+        got = {k: v.double().cpu().numpy() for k, v in o.items()}
+        errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+                for k in ("S", "v", "K", "x", "u")}
+        med = float(np.median(times))
+        res[name] = {"status": int(st), "ms": med, "steps_per_s": iters * T / (med * 1e-3),
+                     "error_vs_fp64_oracle": errs}
+        del ws
+    for name in ("method1", "method2"):
+        res[name]["speedup_vs_sequential"] = res["sequential"]["ms"] / res[name]["ms"]
+    return {"workload": "unicycle (n=4, m=2, p=3) on a stadium track, T=%d, %d passes, "
+                        "reference points every 10th step; inputs rounded to FP32; "
+                        "refinement ON" % (T, iters),
+            "forms": res, "oracle_s": oracle_s}
+
+
 def torch_empty_bytes(nbytes):
     import torch
 
@@ -726,6 +771,8 @@ def main(argv=None):
     ap.add_argument("--precision-T", type=int, default=65536)
     ap.add_argument("--no-cross", action="store_true",
                     help="skip the generalised-cost (cross weight) measurement")
+    ap.add_argument("--no-nonlinear", action="store_true",
+                    help="skip the iterated nonlinear LQT (unicycle) measurement")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling mode: run --warmup + this many solves of --T and exit "
                          "(no JSON line; for ncu captures)")

@@ -281,6 +281,46 @@ lqt_status lqt_solve_cross(const lqt_problem *prob, const lqt_cross *cross,
                            const lqt_solution *sol, const lqt_options *opts, void *workspace,
                            size_t workspace_bytes, void *stream);
 
+/* Iterated nonlinear LQT (Sec. IV-D, "Extension to nonlinear control"):
+ * dynamics x_{k+1} = f(x_k, u_k) of a built-in model, the quadratic tracking
+ * cost of lqt_problem (H, r, X, U and the terminal terms; h(x) = H x,
+ * g(u) = u).  Each pass linearises f around the nominal trajectory by its
+ * first-order Taylor series (eq. nonlinear_linarisation), solves that LQT
+ * problem with lqt_solve (or the sequential recursion), and takes the optimal
+ * trajectory as the next nominal.  The first nominal is x_init (or x_0 at
+ * every step) and u_init (or 0).
+ *   LQT_MODEL_UNICYCLE (Sec. VI-E; n = 4, m = 2): state (p_x, p_y, theta, s),
+ *   control (a, omega), f = (p_x + s cos(theta) dt, p_y + s sin(theta) dt,
+ *   theta + omega dt, s + a dt). */
+enum { LQT_MODEL_UNICYCLE = 1 };
+typedef struct {
+    int32_t model;        /* LQT_MODEL_* */
+    int32_t iterations;   /* linearise-and-solve passes, at least 1 */
+    int32_t sequential;   /* 0: lqt_solve per pass; 1: lqt_riccati_sequential */
+    int32_t reserved;     /* must be 0 */
+    double dt;            /* time step of the model */
+    const void *x_init;   /* (T+1) x n device array of the problem's dtype, or NULL */
+    const void *u_init;   /* T x m device array, or NULL */
+} lqt_nonlinear;
+
+/* Bytes of device workspace lqt_solve_nonlinear needs (0 on invalid
+ * arguments or an unsupported size). */
+size_t lqt_nonlinear_workspace_bytes(const lqt_problem *prob, const lqt_nonlinear *nl,
+                                     const lqt_options *opts);
+
+/* Runs nl->iterations passes on `stream` (asynchronous).  prob supplies n, m,
+ * p, pT, T, dtype, the cost (H, r, X, U, HT, rT, XT) and x_0; its F, c and L
+ * are ignored.  Each pass solves the linearised problem in state deviations
+ * from the nominal (same minimiser, offsets that stay small) with `opts`;
+ * the nominal itself is kept in FP64 for either dtype.
+ * Outputs: S_k, K_k and v_k (absolute coordinates) of the last linearisation,
+ * and x*, u* of the last pass (the final nominal).  Workspace rules and return
+ * values are those of lqt_solve; the device status is read with
+ * lqt_workspace_status. */
+lqt_status lqt_solve_nonlinear(const lqt_problem *prob, const lqt_nonlinear *nl,
+                               const lqt_solution *sol, const lqt_options *opts, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
 /* Static string for a status code (never NULL). */
 const char *lqt_strerror(lqt_status status);
 

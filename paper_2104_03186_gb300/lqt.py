@@ -48,6 +48,15 @@ class lqt_cross(ctypes.Structure):
     _fields_ = [("M", lqt_in), ("s", lqt_in)]
 
 
+LQT_MODEL_UNICYCLE = 1
+
+
+class lqt_nonlinear(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("sequential", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("x_init", ctypes.c_void_p), ("u_init", ctypes.c_void_p)]
+
+
 LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO, LQT_REFINE_FULL = 0, 1, 2, 3
 
 
@@ -105,6 +114,8 @@ def _load() -> ctypes.CDLL:
         "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
         "lqt_cross_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_cross), O]),
         "lqt_solve_cross": (st, [P, ctypes.POINTER(lqt_cross), S, O, vp, sz, vp]),
+        "lqt_nonlinear_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_nonlinear), O]),
+        "lqt_solve_nonlinear": (st, [P, ctypes.POINTER(lqt_nonlinear), S, O, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -289,6 +300,34 @@ def lqt_solve_cross(prob: Problem, cross: Optional[Cross], out: Dict[str, object
         raise LQTError(st, "lqt_solve_cross")
 
 
+def nonlinear(iterations: int = 10, dt: float = 0.1, sequential: bool = False,
+              model: int = LQT_MODEL_UNICYCLE, x_init=None, u_init=None) -> lqt_nonlinear:
+    """An lqt_nonlinear struct; x_init / u_init are device tensors (kept alive
+    by the caller) or None."""
+    nl = lqt_nonlinear()
+    nl.model, nl.iterations, nl.sequential, nl.reserved = model, iterations, int(sequential), 0
+    nl.dt = dt
+    nl.x_init = _ptr(x_init)
+    nl.u_init = _ptr(u_init)
+    return nl
+
+
+def lqt_nonlinear_workspace_bytes(prob: Problem, nl: lqt_nonlinear, opts=None) -> int:
+    return int(_lib.lqt_nonlinear_workspace_bytes(ctypes.byref(prob.struct), ctypes.byref(nl),
+                                                  _opts(opts)))
+
+
+def lqt_solve_nonlinear(prob: Problem, nl: lqt_nonlinear, out: Dict[str, object], workspace,
+                        stream=None, opts=None) -> None:
+    """Iterated nonlinear LQT (Sec. IV-D); asynchronous like lqt_solve."""
+    sol = solution_struct(out)
+    st = _lib.lqt_solve_nonlinear(ctypes.byref(prob.struct), ctypes.byref(nl), ctypes.byref(sol),
+                                  _opts(opts), _ptr(workspace), _nbytes(workspace),
+                                  _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_nonlinear")
+
+
 def lqt_workspace_status(workspace, stream=None) -> int:
     return int(_lib.lqt_workspace_status(_ptr(workspace), _stream_handle(stream)))
 
@@ -442,6 +481,26 @@ def solve_cross(prob: Problem, cross: Optional[Cross], stream=None, check: bool 
         raise LQTError(LQT_EUNSUPPORTED, "lqt_cross_workspace_bytes")
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     lqt_solve_cross(prob, cross, out, ws, stream, opts)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return out
+
+
+def solve_nonlinear(prob: Problem, iterations: int = 10, dt: float = 0.1, sequential=False,
+                    stream=None, check: bool = True, opts=None, x_init=None, u_init=None):
+    """Allocate outputs and a workspace with torch and run lqt_solve_nonlinear
+    (the unicycle model)."""
+    import torch
+
+    nl = nonlinear(iterations, dt, sequential, LQT_MODEL_UNICYCLE, x_init, u_init)
+    out = prob.allocate_outputs()
+    nbytes = lqt_nonlinear_workspace_bytes(prob, nl, opts)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_nonlinear_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lqt_solve_nonlinear(prob, nl, out, ws, stream, opts)
     if check:
         st = lqt_workspace_status(ws, stream)
         if st != LQT_OK:

@@ -138,3 +138,36 @@ def test_cross_arguments_rejected_before_any_device_work(lib):
                               None, fake_ws, 1 << 30, None) == lib.LQT_EINVAL
     assert so.lqt_solve_cross(None, ctypes.byref(good), ctypes.byref(sol), None, fake_ws,
                               1 << 30, None) == lib.LQT_EINVAL
+
+
+def test_nonlinear_arguments_rejected_before_any_device_work(lib):
+    """lqt_solve_nonlinear: unknown model, zero passes, a size other than the
+    unicycle's, reserved field set, misaligned first nominal."""
+    so = lib.library()
+    P, arr = _host_problem(lib)
+    out = {k: np.zeros(s, np.float32) for k, s in
+           {"S": (17, 4, 4), "v": (17, 4), "K": (16, 2, 4), "x": (17, 4), "u": (16, 2)}.items()}
+    sol = lib.lqt_solution(*[o.ctypes.data for o in out.values()])
+    fake_ws = ctypes.c_void_p(1 << 20)
+
+    def call(nl, prob=P.struct):
+        return so.lqt_solve_nonlinear(ctypes.byref(prob), ctypes.byref(nl), ctypes.byref(sol),
+                                      None, fake_ws, 1 << 30, None)
+
+    nl = lib.nonlinear(10, 0.1)
+    assert so.lqt_solve_nonlinear(ctypes.byref(P.struct), ctypes.byref(nl), ctypes.byref(sol),
+                                  None, None, 0, None) == lib.LQT_EINVAL
+    bad = lib.nonlinear(10, 0.1, model=7)
+    assert call(bad) == lib.LQT_EINVAL
+    assert call(lib.nonlinear(0, 0.1)) == lib.LQT_EINVAL
+    bad = lib.nonlinear(10, 0.1)
+    bad.reserved = 1
+    assert call(bad) == lib.LQT_EINVAL
+    assert call(lib.nonlinear(10, float("nan"))) == lib.LQT_EINVAL
+    bad = lib.nonlinear(10, 0.1)
+    bad.x_init = (1 << 20) + 2
+    assert call(bad) == lib.LQT_EINVAL
+    small = lib.lqt_problem.from_buffer_copy(P.struct)
+    small.n, small.m = 2, 1
+    assert call(nl, small) == lib.LQT_EINVAL
+    assert so.lqt_nonlinear_workspace_bytes(ctypes.byref(small), ctypes.byref(nl), None) == 0
