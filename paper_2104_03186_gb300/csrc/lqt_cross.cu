@@ -20,8 +20,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lqt.h"
 #include "lqt_lanes.cuh"
+#include "lqt_variants.h"
 
 namespace lqt {
 namespace {
@@ -161,6 +164,225 @@ __global__ void __launch_bounds__(kPreThreads) k_cross_pre(CrossPre<R> a) {
     }
 }
 
+// One thread per step for the compiled small sizes (n = NX, m = MX, p <= PX):
+// the same arithmetic as k_cross_pre with every matrix in registers (the p
+// loops run to the compile-time bound with run-time guards, so indexing stays
+// static).
+// Time-varying outputs leave through a shared-memory stage so that each block
+// writes one contiguous run per array (a thread's own rows are 16 to 256
+// bytes apart from its neighbours').
+constexpr int kSmallThreads = 64;
+
+// Copies the rows the block's threads left in the stage to out[k0 * E ...]
+// (one contiguous run), or, for a time-invariant output, step 0's row alone.
+template <typename R>
+__device__ __forceinline__ void stage_flush(const R* stage, int lds, int E, R* out,
+                                            long long stride, long long k0, int nvalid,
+                                            bool first) {
+    __syncthreads();
+    if (stride) {
+        const int count = nvalid * E;
+        R* dst = out + k0 * E;
+        for (int i = threadIdx.x; i < count; i += kSmallThreads)
+            dst[i] = stage[(i / E) * lds + i % E];
+    } else if (first) {
+        for (int e = 0; e < E; ++e) out[e] = stage[threadIdx.x * lds + e];
+    }
+    __syncthreads();
+}
+
+template <typename R, int NX, int MX, int PX>
+__global__ void __launch_bounds__(kSmallThreads) k_cross_pre_small(CrossPre<R> a) {
+    constexpr int LDS = (NX * NX > PX * PX ? NX * NX : PX * PX) | 1;
+    __shared__ R stage[kSmallThreads * LDS];
+    const long long k0 = (long long)blockIdx.x * kSmallThreads;
+    const long long k = k0 + threadIdx.x;
+    const bool valid = k < a.rows;
+    const int nvalid = (int)(a.rows - k0 < kSmallThreads ? a.rows - k0 : kSmallThreads);
+    const long long kk = valid ? k : k0;  // in-range index for the loads of idle threads
+    constexpr int n = NX, m = MX;
+    const int p = a.p;
+    const R* U = a.U + a.sU * kk;
+    const R* M = a.M ? a.M + a.sM * kk : nullptr;
+    const R* H = a.H ? a.H + a.sH * kk : nullptr;
+    const R* r = a.r ? a.r + a.sr * kk : nullptr;
+    const R* s = a.s ? a.s + a.ss * kk : nullptr;
+    const R* L = a.L + a.sL * kk;
+    const bool first = k == 0;
+    R W[MX][PX];  // U^{-1} M^T
+#pragma unroll
+    for (int i = 0; i < MX; ++i)
+#pragma unroll
+        for (int j = 0; j < PX; ++j) W[i][j] = (M && i < m && j < p) ? M[j * m + i] : R(0);
+    if (M) {
+        // Cholesky U = R R^T in registers
+        R C[MX][MX];
+#pragma unroll
+        for (int i = 0; i < MX; ++i)
+#pragma unroll
+            for (int j = 0; j < MX; ++j) C[i][j] = (i < m && j < m) ? U[i * m + j] : R(1);
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < MX; ++j) {
+            if (j < m) {
+                R d = C[j][j];
+#pragma unroll
+                for (int l = 0; l < MX; ++l)
+                    if (l < j) d -= C[j][l] * C[j][l];
+                ok = ok && d > R(0) && isfinite(d);
+                const R ljj = sqrt(d);
+                const R inv = R(1) / ljj;
+                C[j][j] = inv;  // the factor's diagonal is kept as its reciprocal
+#pragma unroll
+                for (int i = 0; i < MX; ++i)
+                    if (i > j && i < m) {
+                        R acc = C[i][j];
+#pragma unroll
+                        for (int l = 0; l < MX; ++l)
+                            if (l < j) acc -= C[i][l] * C[j][l];
+                        C[i][j] = acc * inv;
+                    }
+            }
+        }
+        if (!ok && valid) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
+        // R y = M^T, then R^T w = y, for the p columns
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if (j < p) {
+#pragma unroll
+                for (int i = 0; i < MX; ++i)
+                    if (i < m) {
+                        R acc = W[i][j];
+#pragma unroll
+                        for (int l = 0; l < MX; ++l)
+                            if (l < i) acc -= C[i][l] * W[l][j];
+                        W[i][j] = acc * C[i][i];
+                    }
+#pragma unroll
+                for (int i = MX - 1; i >= 0; --i)
+                    if (i < m) {
+                        R acc = W[i][j];
+#pragma unroll
+                        for (int l = 0; l < MX; ++l)
+                            if (l > i && l < m) acc -= C[l][i] * W[l][j];
+                        W[i][j] = acc * C[i][i];
+                    }
+            }
+    }
+    R WH[MX * NX], g[MX];
+#pragma unroll
+    for (int i = 0; i < MX; ++i) {
+        R acc = (s && i < m) ? s[i] : R(0);
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if (M && r && i < m && j < p) acc += W[i][j] * r[j];
+        g[i] = acc;
+#pragma unroll
+        for (int l = 0; l < NX; ++l) {
+            R h = R(0);
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if (M && i < m && j < p && l < n) h += W[i][j] * H[j * n + l];
+            WH[i * NX + l] = h;
+        }
+    }
+    // outputs, each packed to its run-time size in this thread's stage row
+    R* row = stage + threadIdx.x * LDS;
+    if (a.WH) {
+#pragma unroll
+        for (int i = 0; i < MX; ++i)
+#pragma unroll
+            for (int l = 0; l < NX; ++l)
+                if (i < m && l < n) row[i * n + l] = WH[i * NX + l];
+        stage_flush(stage, LDS, m * n, a.WH, a.oW, k0, nvalid, first);
+    }
+    if (a.g) {
+#pragma unroll
+        for (int i = 0; i < MX; ++i)
+            if (i < m) row[i] = g[i];
+        stage_flush(stage, LDS, m, a.g, a.og, k0, nvalid, first);
+    }
+    if (a.Ft) {
+        const R* F = a.F + a.sF * kk;
+#pragma unroll
+        for (int i = 0; i < NX; ++i)
+#pragma unroll
+            for (int l = 0; l < NX; ++l)
+                if (i < n && l < n) {
+                    R acc = F[i * n + l];
+#pragma unroll
+                    for (int q = 0; q < MX; ++q)
+                        if (q < m) acc -= L[i * m + q] * WH[q * NX + l];
+                    row[i * n + l] = acc;
+                }
+        stage_flush(stage, LDS, n * n, a.Ft, a.oF, k0, nvalid, first);
+    }
+    if (a.ct) {
+        const R* c = a.c ? a.c + a.sc * kk : nullptr;
+#pragma unroll
+        for (int i = 0; i < NX; ++i)
+            if (i < n) {
+                R acc = c ? c[i] : R(0);
+#pragma unroll
+                for (int q = 0; q < MX; ++q)
+                    if (q < m) acc += L[i * m + q] * g[q];
+                row[i] = acc;
+            }
+        stage_flush(stage, LDS, n, a.ct, a.oc, k0, nvalid, first);
+    }
+    if (a.M && a.Xt) {
+        const R* X = a.X + a.sX * kk;
+        // upper triangle computed once, mirrored: X~ exactly symmetric
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if (i <= j && j < p) {
+                    R acc = X[i * p + j];
+#pragma unroll
+                    for (int q = 0; q < MX; ++q)
+                        if (q < m) acc -= M[i * m + q] * W[q][j];
+                    row[i * p + j] = acc;
+                    row[j * p + i] = acc;
+                }
+        stage_flush(stage, LDS, p * p, a.Xt, a.oX, k0, nvalid, first);
+    }
+}
+
+// Small sizes: a block per 256 steps.  K += W H as one contiguous run of the
+// block's steps (coalesced), then one thread per step for u, whose W H rows
+// the first phase has just brought into L1.
+constexpr int kPostThreads = 256;
+
+template <typename R, int NX, int MX>
+__global__ void __launch_bounds__(kPostThreads)
+    k_cross_post_small(long long T, R* K, R* u, const R* x, const R* WH, long long oW, const R* g,
+                       long long og, const int* pre_status, int* status) {
+    constexpr int n = NX, m = MX, MN = MX * NX;
+    const long long k0 = (long long)blockIdx.x * kPostThreads;
+    const int nb = (int)(T - k0 < kPostThreads ? T - k0 : kPostThreads);
+    for (int i = threadIdx.x; i < nb * MN; i += kPostThreads) {
+        const long long k = k0 + i / MN;
+        K[k0 * MN + i] += WH[oW * k + i % MN];
+    }
+    if ((int)threadIdx.x < nb) {
+        const long long k = k0 + threadIdx.x;
+        const R* wh = WH + oW * k;
+        R xk[NX];
+#pragma unroll
+        for (int l = 0; l < n; ++l) xk[l] = x[k * n + l];
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+            R acc = u[k * m + i] + g[og * k + i];
+#pragma unroll
+            for (int l = 0; l < n; ++l) acc -= wh[i * n + l] * xk[l];
+            u[k * m + i] = acc;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *pre_status != 0)
+        *status = *pre_status;  // the root cause wins
+}
+
 // K_k += (W H)_k, u_k += g_k - (W H)_k x*_k; then the transform status is
 // written into the solve's status word (a failed transform is the root cause).
 template <typename R>
@@ -286,6 +508,45 @@ lqt_status plan_cross(const lqt_problem* P, const lqt_cross* X, const lqt_option
     return LQT_OK;
 }
 
+// The compiled small (n, m) variants get the register kernels: p <= 2 and
+// p <= 8 instantiations.  False: no small kernel for this size.
+template <typename R>
+bool launch_pre_small(const CrossPre<R>& a, unsigned blocks, cudaStream_t s) {
+    bool done = false;
+#define LQT_CROSS_PRE_SMALL(RR, N, M)                                                         \
+    if constexpr (std::is_same<R, RR>::value) {                                              \
+        if (!done && a.n == N && a.m == M) {                                                 \
+            if (a.p <= 2)                                                                    \
+                k_cross_pre_small<R, N, M, 2><<<blocks, kSmallThreads, 0, s>>>(a);           \
+            else                                                                             \
+                k_cross_pre_small<R, N, M, 8><<<blocks, kSmallThreads, 0, s>>>(a);           \
+            done = true;                                                                     \
+        }                                                                                    \
+    }
+    LQT_VARIANTS(LQT_CROSS_PRE_SMALL)
+#undef LQT_CROSS_PRE_SMALL
+    return done;
+}
+
+template <typename R>
+bool launch_post_small(long long T, int n, int m, R* K, R* u, const R* x, const R* WH,
+                       long long oW, const R* g, long long og, const int* pre_status,
+                       int* status, unsigned blocks, cudaStream_t s) {
+    bool done = false;
+#define LQT_CROSS_POST_SMALL(RR, N, M)                                                        \
+    if constexpr (std::is_same<R, RR>::value) {                                              \
+        if (!done && n == N && m == M) {                                                     \
+            k_cross_post_small<R, N, M><<<(unsigned)((T + kPostThreads - 1) / kPostThreads), \
+                                          kPostThreads, 0, s>>>(T, K, u, x, WH, oW, g, og,   \
+                                                                pre_status, status);         \
+            done = true;                                                                     \
+        }                                                                                    \
+    }
+    LQT_VARIANTS(LQT_CROSS_POST_SMALL)
+#undef LQT_CROSS_POST_SMALL
+    return done;
+}
+
 template <typename R, int G>
 lqt_status launch_pre(const lqt_problem* P, const lqt_cross* X, const CrossPlan& cp, char* base,
                       cudaStream_t s) {
@@ -320,6 +581,12 @@ lqt_status launch_pre(const lqt_problem* P, const lqt_cross* X, const CrossPlan&
     a.oW = cp.oW;
     a.og = cp.og;
     a.status = reinterpret_cast<int*>(base + cp.pre_status);
+    if (a.p <= 8) {
+        const long long blocks = (cp.rows + kSmallThreads - 1) / kSmallThreads;
+        if (blocks > INT32_MAX) return LQT_EINVAL;
+        if (launch_pre_small(a, (unsigned)blocks, s))
+            return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    }
     constexpr int groups = kPreThreads / G;
     const size_t smem = (size_t)groups * a.group_elems * sizeof(R);
     if (smem > 227 * 1024) return LQT_EUNSUPPORTED;
@@ -340,10 +607,19 @@ lqt_status launch_post(const lqt_problem* P, const lqt_solution* sol, const Cros
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return LQT_ECUDA;
+    const bool small = P->n <= 4 && P->m <= 4;
     const long long work = P->T * (long long)P->m * P->n;
     long long blocks = (work + 255) / 256;
-    if (blocks > 8LL * sms) blocks = 8LL * sms;
+    if (blocks > 16LL * sms) blocks = 16LL * sms;
     if (blocks < 1) blocks = 1;
+    if (small &&
+        launch_post_small<R>(P->T, P->n, P->m, static_cast<R*>(sol->K), static_cast<R*>(sol->u),
+                             static_cast<const R*>(sol->x),
+                             reinterpret_cast<const R*>(base + cp.WH), cp.oW,
+                             reinterpret_cast<const R*>(base + cp.g), cp.og,
+                             reinterpret_cast<const int*>(base + cp.pre_status),
+                             reinterpret_cast<int*>(base), (unsigned)blocks, s))
+        return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
     k_cross_post<R><<<(unsigned)blocks, 256, 0, s>>>(
         P->T, P->n, P->m, static_cast<R*>(sol->K), static_cast<R*>(sol->u),
         static_cast<const R*>(sol->x), reinterpret_cast<const R*>(base + cp.WH), cp.oW,
