@@ -859,10 +859,10 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
         fwd_group(s, e, g, lo, cnt);
         const int lrel = (int)(lo - tbase);
         R* in = rows + (g & 1) * SM::FIN;
-        WarpRows<R, M * N, kStageG>::load_async(P.K, tbase, in + SM::FIK, SM::FROW, lrel, cnt);
+        WarpRows<R, M * N, kStageG>::load_async_stream(P.K, tbase, in + SM::FIK, SM::FROW, lrel, cnt);
         WarpRows<R, M, kStageG>::load_async(P.u, tbase, in + SM::FID, SM::FROW, lrel, cnt);
         if (P.refine_add)
-            WarpRows<R, N, kStageG>::load_async(P.x, tbase, in + SM::FIX, SM::FROW, lrel, cnt);
+            WarpRows<R, N, kStageG>::load_async_stream(P.x, tbase, in + SM::FIX, SM::FROW, lrel, cnt);
         cp_async_commit();
     };
     prefetch(0);

@@ -124,6 +124,15 @@ __device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
                  : "memory");
 }
 
+// 16-byte asynchronous copy that bypasses L1 (cached in L2 only): for
+// streaming records that no thread reads twice, so that they do not evict the
+// lines of other loads.
+__device__ __forceinline__ void cp_async_cg16(void* dst_smem, const void* src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)),
+                 "l"(src_gmem)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -194,6 +203,28 @@ struct WarpRows {
             if (v * VEC < cnt_r * WX)
                 cp_async<VEC * (int)sizeof(R)>(rows + r * rowstride + v * VEC,
                                                g + (long long)lo_r * WX + v * VEC);
+        }
+    }
+
+    // global -> shared rows, asynchronously and bypassing L1 where the vectors
+    // are 16 bytes (streaming records)
+    __device__ static void load_async_stream(const R* gX, long long base, R* rows, int rowstride,
+                                             int lo, int cnt) {
+        const int lane = threadIdx.x & 31;
+        const R* g = gX + base * WX;
+#pragma unroll
+        for (int it = 0; it < NV; ++it) {
+            const int f = it * 32 + lane;
+            const int r = f / NV, v = f % NV;
+            const int lo_r = __shfl_sync(0xffffffffu, lo, r);
+            const int cnt_r = __shfl_sync(0xffffffffu, cnt, r);
+            if (v * VEC < cnt_r * WX) {
+                if constexpr (VEC * sizeof(R) == 16)
+                    cp_async_cg16(rows + r * rowstride + v * VEC, g + (long long)lo_r * WX + v * VEC);
+                else
+                    cp_async<VEC * (int)sizeof(R)>(rows + r * rowstride + v * VEC,
+                                                   g + (long long)lo_r * WX + v * VEC);
+            }
         }
     }
 
