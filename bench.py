@@ -778,9 +778,11 @@ def main(argv=None):
                          "(no JSON line; for ncu captures)")
     ap.add_argument("--T", type=int, default=T_HEADLINE, help="horizon of --profile-solves")
     ap.add_argument("--refine", type=int, default=1, help="refinement in --profile-solves")
-    ap.add_argument("--profile-workload", choices=("vehicle", "precision"), default="vehicle",
-                    help="workload of --profile-solves: the vehicle (n = 4) or the n = 32 "
-                         "precision study")
+    ap.add_argument("--profile-workload",
+                    choices=("vehicle", "precision", "cross", "nonlinear"), default="vehicle",
+                    help="workload of --profile-solves: the vehicle (n = 4), the n = 32 "
+                         "precision study, the vehicle with cross weights and offsets "
+                         "(lqt_solve_cross), or the unicycle (lqt_solve_nonlinear, 10 passes)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -800,17 +802,29 @@ def run_profile_solves(args):
 
     if args.profile_workload == "precision":
         pr = inputs.precision_study(T=args.T, seed=0)
+    elif args.profile_workload == "nonlinear":
+        pr = inputs.unicycle_track(args.T, seed=0)
     else:
         pr = inputs.vehicle(args.T, seed=0)
     P = lqt.Problem.from_inputs(pr.rounded_to(np.float32))
     out = P.allocate_outputs()
-    ws = lqt.workspace_for(P, opts=args.refine)
+    if args.profile_workload == "cross":
+        C = lqt.Cross.from_inputs(inputs.cross_terms(pr, seed=1, scale=0.5).rounded_to(np.float32))
+        ws = torch_empty_bytes(lqt.lqt_cross_workspace_bytes(P, C, args.refine))
+        call = lambda: lqt.lqt_solve_cross(P, C, out, ws, None, args.refine)  # noqa: E731
+    elif args.profile_workload == "nonlinear":
+        nl = lqt.nonlinear(10, 0.1)
+        ws = torch_empty_bytes(lqt.lqt_nonlinear_workspace_bytes(P, nl, args.refine))
+        call = lambda: lqt.lqt_solve_nonlinear(P, nl, out, ws, None, args.refine)  # noqa: E731
+    else:
+        ws = lqt.workspace_for(P, opts=args.refine)
+        call = lambda: lqt.lqt_solve(P, out, ws, None, args.refine)  # noqa: E731
     for _ in range(args.warmup + args.profile_solves):
-        lqt.lqt_solve(P, out, ws, None, args.refine)
+        call()
     torch.cuda.synchronize()
     st = lqt.lqt_workspace_status(ws)
-    print("profile solves done: T=%d refine=%d status=%d plan=%s" % (
-        args.T, args.refine, st, lqt.lqt_plan(P, args.refine)))
+    print("profile solves done: %s T=%d refine=%d status=%d" % (
+        args.profile_workload, args.T, args.refine, st))
     return 0 if st == lqt.LQT_OK else 1
 
 
