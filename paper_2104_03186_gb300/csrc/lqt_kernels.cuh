@@ -384,6 +384,8 @@ constexpr int tile_threads() {
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
     using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][W]
@@ -457,6 +459,8 @@ __device__ __forceinline__ void terminal_value(const Params<R>& P, Value<R, N>& 
 // ===========================================================================
 template <typename R, int N, int TP>
 __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* tree = reinterpret_cast<R*>(smem_raw);            // [ELEM][TP]
     R* carry = tree + (size_t)Dims<N>::ELEM * TP;        // [VALUE][TP]
@@ -540,6 +544,8 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
     using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -708,6 +714,8 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
 // ===========================================================================
 template <typename R, int N, int TP>
 __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* tree = reinterpret_cast<R*>(smem_raw);      // [AFFINE][TP]
     R* xs = tree + (size_t)Dims<N>::AFFINE * TP;   // [N][TP]
@@ -781,6 +789,8 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
 // ===========================================================================
 template <typename R, int N, int M, int W>
 __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
     using SM = Smem<R, N, M, W>;
     using ML = ModelLayout<N, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -23,6 +23,30 @@ static cudaError_t allow_smem(Kernel k, bool* done, size_t bytes) {
     return err;
 }
 
+// Launch with programmatic stream serialization when `pdl`: the kernel may be
+// scheduled while its predecessor in the stream finishes (it waits in
+// griddep_wait()).  Measured on one GB300 (vehicle, refined, A/B in one
+// session): T = 100 0.101 -> 0.092 ms, T = 1e3 0.138 -> 0.128 ms, T = 1e5
+// 0.176 -> 0.174 ms, but T = 1e6 0.365 -> 0.380 ms; so it is used for short
+// chunks only (the plan's B <= kPdlMaxChunk).
+constexpr int kPdlMaxChunk = 4;
+
+template <typename R>
+static cudaError_t launch_pdl(void (*kernel)(const Params<R>), unsigned grid, unsigned block,
+                              size_t smem, cudaStream_t stream, const Params<R>& P, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, P);
+}
+
 template <typename R, int N, int M>
 lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t stream, Prof* prof) {
     constexpr int W = tile_threads<R, N, M>();
@@ -42,21 +66,27 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
         (err = allow_smem(k_fwd_down<R, N, M, W>, done_fdown, smem_fdown)) != cudaSuccess)
         return LQT_ECUDA;
     const int tiles = plan.tiles;
+    const bool pdl = plan.B <= kPdlMaxChunk;
     if (tiles > 0) {
         prof_mark(prof, stream, P.refine_add ? "bwd_up.refine" : "bwd_up");
-        k_bwd_up<R, N, M, W><<<tiles, W, smem_up, stream>>>(P);
+        err = launch_pdl<R>(k_bwd_up<R, N, M, W>, tiles, W, smem_up, stream, P, pdl);
+        if (err != cudaSuccess) return LQT_ECUDA;
     }
     prof_mark(prof, stream, P.refine_add ? "bwd_top.refine" : "bwd_top");
-    k_bwd_top<R, N, TP><<<1, TP, smem_top, stream>>>(P);
+    err = launch_pdl<R>(k_bwd_top<R, N, TP>, 1, TP, smem_top, stream, P, pdl);
+    if (err != cudaSuccess) return LQT_ECUDA;
     if (tiles > 0) {
         prof_mark(prof, stream, P.refine_add ? "bwd_down.refine" : "bwd_down");
-        k_bwd_down<R, N, M, W><<<tiles, W, smem_down, stream>>>(P);
+        err = launch_pdl<R>(k_bwd_down<R, N, M, W>, tiles, W, smem_down, stream, P, pdl);
+        if (err != cudaSuccess) return LQT_ECUDA;
     }
     prof_mark(prof, stream, P.refine_add ? "fwd_top.refine" : "fwd_top");
-    k_fwd_top<R, N, TP><<<1, TP, smem_ftop, stream>>>(P);
+    err = launch_pdl<R>(k_fwd_top<R, N, TP>, 1, TP, smem_ftop, stream, P, pdl);
+    if (err != cudaSuccess) return LQT_ECUDA;
     if (tiles > 0) {
         prof_mark(prof, stream, P.refine_add ? "fwd_down.refine" : "fwd_down");
-        k_fwd_down<R, N, M, W><<<tiles, W, smem_fdown, stream>>>(P);
+        err = launch_pdl<R>(k_fwd_down<R, N, M, W>, tiles, W, smem_fdown, stream, P, pdl);
+        if (err != cudaSuccess) return LQT_ECUDA;
     }
     return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
 }

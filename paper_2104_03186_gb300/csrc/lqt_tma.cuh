@@ -124,6 +124,19 @@ __device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
                  : "memory");
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may be scheduled while its predecessor in
+// the stream still runs; griddep_wait() returns once the predecessor grid has
+// completed and its memory operations are visible (at once when there is no
+// such predecessor).  griddep_launch_dependents() lets the next kernel be
+// scheduled; the kernels call it on entry and wait before any global access.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // 16-byte asynchronous copy that bypasses L1 (cached in L2 only): for
 // streaming records that no thread reads twice, so that they do not evict the
 // lines of other loads.
