@@ -43,13 +43,15 @@ struct Variant {
     int dtype, n, m;
     int W, TP;
     int elem, value, affine;  // components of an element, a value, an affine map
-    lqt_status (*solve)(const void* params, const Plan& plan, cudaStream_t s, Prof* prof);
+    lqt_status (*solve)(const void* params, const Plan& plan, cudaStream_t s, Prof* prof,
+                        cudaEvent_t bwd_done);
     lqt_status (*seq)(const void* params, cudaStream_t s);
 };
 
 template <typename R, int N, int M>
-lqt_status solve_thunk(const void* params, const Plan& plan, cudaStream_t s, Prof* prof) {
-    return launch_solve<R, N, M>(*static_cast<const Params<R>*>(params), plan, s, prof);
+lqt_status solve_thunk(const void* params, const Plan& plan, cudaStream_t s, Prof* prof,
+                       cudaEvent_t bwd_done) {
+    return launch_solve<R, N, M>(*static_cast<const Params<R>*>(params), plan, s, prof, bwd_done);
 }
 
 template <typename R, int N, int M>
@@ -384,7 +386,8 @@ namespace {
 template <typename R>
 lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
                     void* ws, const Layout& L, const Plan& plan, int out_mask, int refine_emit,
-                    int refine_add, bool sequential, cudaStream_t s, Prof* prof) {
+                    int refine_add, bool sequential, cudaStream_t s, Prof* prof,
+                    cudaEvent_t bwd_done = nullptr) {
     Params<R> K;
     fill_params(K, P, sol, ws, &L, &plan);
     K.out_mask = out_mask;
@@ -394,17 +397,17 @@ lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution
         if (prof) prof_mark(prof, s, refine_add ? "riccati_seq.refine" : "riccati_seq");
         return var.seq(&K, s);
     }
-    return var.solve(&K, plan, s, prof);
+    return var.solve(&K, plan, s, prof, bwd_done);
 }
 
 template <typename R>
 lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
                      void* ws, const Layout& L, const Plan& plan, bool refine, bool sequential,
-                     cudaStream_t s, Prof* prof) {
+                     cudaStream_t s, Prof* prof, cudaEvent_t bwd_done) {
     refine = refine && P->T > 0;
     // pass 1: the problem; when refining it also writes the shifted data
     lqt_status st = run_pass<R>(var, P, sol, ws, L, plan, OUT_ALL, refine ? 1 : 0, 0, sequential,
-                                s, prof);
+                                s, prof, sequential ? nullptr : bwd_done);
     if (st != LQT_OK || !refine) {
         if (prof) prof_end(prof, s);
         return st;
@@ -427,8 +430,12 @@ lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solutio
     return st;
 }
 
+// bwd_done (may be null): recorded on the stream once S, v and K are final,
+// where the path can tell (the thread-per-chunk kernels); *recorded says so.
 lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const lqt_options* opts,
-                        void* workspace, size_t workspace_bytes, void* stream, bool sequential) {
+                        void* workspace, size_t workspace_bytes, void* stream, bool sequential,
+                        cudaEvent_t bwd_done = nullptr, bool* recorded = nullptr) {
+    if (recorded) *recorded = false;
     lqt_status st = validate(prob, sol);
     if (st != LQT_OK) return st;
     if (!workspace || !aligned(workspace, kAlign)) return LQT_EINVAL;
@@ -461,9 +468,12 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     if (cudaMemsetAsync(workspace, 0, sizeof(int), s) != cudaSuccess) return LQT_ECUDA;
     Prof* prof = nullptr;
     if ((st = prof_begin(&prof)) != LQT_OK) return st;
+    if (recorded) *recorded = bwd_done != nullptr && !sequential;
     if (prob->dtype == LQT_F64)
-        return run_solve<double>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof);
-    return run_solve<float>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof);
+        return run_solve<double>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof,
+                                 bwd_done);
+    return run_solve<float>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof,
+                            bwd_done);
 }
 
 }  // namespace
@@ -511,6 +521,45 @@ int lqt_profile_read(float* ms, const char** names, int max_entries) {
     }
     return g_prof.count;
 }
+
+}  // extern "C"
+
+namespace lqt {
+namespace {
+
+// Per host thread and device: a non-blocking stream and two events with which
+// lqt_solve_host copies S, v and K back while the rest of the solve runs.
+struct HostAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t bwd = nullptr, done = nullptr;
+};
+
+HostAux* host_aux() {
+    thread_local HostAux aux[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    HostAux& a = aux[dev];
+    if (!a.s) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
+            if (e1) cudaEventDestroy(e1);
+            cudaStreamDestroy(s);
+            return nullptr;
+        }
+        a.s = s;
+        a.bwd = e1;
+        a.done = e2;
+    }
+    return &a;
+}
+
+}  // namespace
+}  // namespace lqt
+
+extern "C" {
 
 size_t lqt_host_solve_bytes(const lqt_problem* prob, const lqt_options* opts) {
     if (validate(prob, nullptr) != LQT_OK) return 0;
@@ -583,9 +632,29 @@ lqt_status lqt_solve_host(const lqt_problem* hp, const lqt_solution* hs, const l
         *douts[i] = base + off;
         off += align_up(sizes[i] * es);
     }
-    st = lqt_solve(&dp, &ds, opts, ws, ws_bytes, stream);
+    // S, v, K are final once the first pass's backward kernels end: where the
+    // path records that point, they go back on the auxiliary stream while the
+    // forward scan and the refinement pass run (the host link, not the copy
+    // engines, is the limit, so one stream carries them)
+    HostAux* aux = host_aux();
+    bool recorded = false;
+    st = solve_common(&dp, &ds, opts, ws, ws_bytes, stream, false, aux ? aux->bwd : nullptr,
+                      &recorded);
     if (st != LQT_OK) return st;
-    for (int i = 0; i < 5; ++i)
+    int first = 0;
+    if (aux && recorded) {
+        if (cudaStreamWaitEvent(aux->s, aux->bwd, 0) != cudaSuccess) return LQT_ECUDA;
+        for (int i = 0; i < 3; ++i)
+            if (sizes[i] && houts[i] &&
+                cudaMemcpyAsync(houts[i], *douts[i], sizes[i] * es, cudaMemcpyDeviceToHost,
+                                aux->s) != cudaSuccess)
+                return LQT_ECUDA;
+        if (cudaEventRecord(aux->done, aux->s) != cudaSuccess ||
+            cudaStreamWaitEvent(s, aux->done, 0) != cudaSuccess)
+            return LQT_ECUDA;
+        first = 3;
+    }
+    for (int i = first; i < 5; ++i)
         if (sizes[i] && houts[i] &&
             cudaMemcpyAsync(houts[i], *douts[i], sizes[i] * es, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)

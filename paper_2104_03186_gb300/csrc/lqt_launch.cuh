@@ -45,7 +45,10 @@ inline void prof_end(Prof* prof, cudaStream_t stream) {
 }
 
 template <typename R, int N, int M>
-lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t stream, Prof* prof);
+// bwd_done (may be null) is recorded on the stream once the first pass has
+// written S, v and K.
+lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t stream, Prof* prof,
+                        cudaEvent_t bwd_done = nullptr);
 
 template <typename R, int N, int M>
 lqt_status launch_seq(const Params<R>& P, cudaStream_t stream);

@@ -48,7 +48,8 @@ static cudaError_t launch_pdl(void (*kernel)(const Params<R>), unsigned grid, un
 }
 
 template <typename R, int N, int M>
-lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t stream, Prof* prof) {
+lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t stream, Prof* prof,
+                        cudaEvent_t bwd_done) {
     constexpr int W = tile_threads<R, N, M>();
     constexpr int TP = top_threads();
     using SM = Smem<R, N, M, W>;
@@ -80,6 +81,8 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
         err = launch_pdl<R>(k_bwd_down<R, N, M, W>, tiles, W, smem_down, stream, P, pdl);
         if (err != cudaSuccess) return LQT_ECUDA;
     }
+    // S, v and K are final here (a second refinement pass does not write them)
+    if (bwd_done && cudaEventRecord(bwd_done, stream) != cudaSuccess) return LQT_ECUDA;
     prof_mark(prof, stream, P.refine_add ? "fwd_top.refine" : "fwd_top");
     err = launch_pdl<R>(k_fwd_top<R, N, TP>, 1, TP, smem_ftop, stream, P, pdl);
     if (err != cudaSuccess) return LQT_ECUDA;
@@ -102,7 +105,7 @@ lqt_status launch_seq(const Params<R>& P, cudaStream_t stream) {
 
 #define LQT_INSTANTIATE(R, N, M)                                                             \
     template lqt_status launch_solve<R, N, M>(const Params<R>&, const Plan&, cudaStream_t, \
-                                              Prof*);                                      \
+                                              Prof*, cudaEvent_t);                         \
     template lqt_status launch_seq<R, N, M>(const Params<R>&, cudaStream_t);
 
 }  // namespace lqt
