@@ -283,7 +283,7 @@ def run_ours(args):
         got = {k: v.double().cpu().numpy() for k, v in out.items()}
         errors = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
                   for k in ("S", "v", "K", "x", "u")}
-        del ref, got
+        del got
 
     # ---- timed region: K solves, one event pair per solve ---------------------
     kern = {}
@@ -419,6 +419,12 @@ def run_ours(args):
     # ---- generalised stage cost (cross weights, control offsets) -------------
     cross = None if args.no_cross else run_cross(args, stream, flush)
 
+    # ---- partial condensing of the headline workload ----------------------
+    condensed = None
+    if not args.no_condensed:
+        condensed = run_condensed(args, stream, flush, prob, ref, float(np.median(times)))
+    del ref
+
     # ---- iterated nonlinear LQT (unicycle) ----------------------------------
     nonlinear = None if args.no_nonlinear else run_nonlinear(args, stream, flush)
 
@@ -453,6 +459,7 @@ def run_ours(args):
         "precision_study": precision,
         "cross": cross,
         "nonlinear": nonlinear,
+        "condensed": condensed,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -747,6 +754,33 @@ def run_nonlinear(args, stream, flush):
             "forms": res, "oracle_s": oracle_s}
 
 
+def run_condensed(args, stream, flush, prob, ref, plain_ms):
+    """Partial condensing (Sec. V-C) of the vehicle workload: blocks of B = 2
+    steps (n = 4, stacked m = 4, p = 4, generalised stage cost), solved by
+    lqt_solve_condensed; the same FP32 inputs and refinement as the headline,
+    errors against the same FP64 oracle."""
+    from paper_2104_03186_gb300 import lqt
+
+    B = 2
+    opts = lqt.LQT_REFINE_ON
+    P = lqt.Problem.from_inputs(prob, dtype=np.float32)
+    o = P.allocate_outputs()
+    ws = torch_empty_bytes(lqt.lqt_condensed_workspace_bytes(P, B, opts))
+    call = lambda: lqt.lqt_solve_condensed(P, B, o, ws, stream, opts)  # noqa: E731
+    for _ in range(3):
+        call()
+    st = lqt.lqt_workspace_status(ws, stream)
+    times = _time_solves(call, 10, flush, stream)
+    got = {k: v.double().cpu().numpy() for k, v in o.items()}
+    errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
+            for k in ("S", "v", "K", "x", "u")}
+    med = float(np.median(times))
+    return {"workload": "vehicle T=%d condensed in blocks of B=%d (n=4, m=4, p=4, "
+                        "T/B steps); FP32, refinement ON" % (prob.T, B),
+            "status": int(st), "ms": med, "steps_per_s": prob.T / (med * 1e-3),
+            "plain_solve_ms": plain_ms, "error_vs_fp64_oracle": errs}
+
+
 def torch_empty_bytes(nbytes):
     import torch
 
@@ -776,6 +810,8 @@ def main(argv=None):
     ap.add_argument("--precision-T", type=int, default=65536)
     ap.add_argument("--no-cross", action="store_true",
                     help="skip the generalised-cost (cross weight) measurement")
+    ap.add_argument("--no-condensed", action="store_true",
+                    help="skip the partial-condensing measurement")
     ap.add_argument("--no-nonlinear", action="store_true",
                     help="skip the iterated nonlinear LQT (unicycle) measurement")
     ap.add_argument("--profile-solves", type=int, default=0,

@@ -323,6 +323,24 @@ lqt_status lqt_solve_nonlinear(const lqt_problem *prob, const lqt_nonlinear *nl,
                                const lqt_solution *sol, const lqt_options *opts, void *workspace,
                                size_t workspace_bytes, void *stream);
 
+/* Partial condensing (Sec. V-C, "Block processing"): the problem is rewritten
+ * in blocks of B steps whose state is the block's first state and whose
+ * control is the stack of the block's B controls.  Eliminating the states
+ * inside each block gives an LQT problem of ceil(T / B) steps with n states,
+ * B m controls and the generalised stage cost of Sec. IV-D (the block's
+ * intermediate tracking costs couple its first state and its controls), which
+ * lqt_solve_cross solves.  An expansion kernel then re-runs each block's B
+ * Riccati steps and its rollout, so `sol` receives S, v, K, x*, u* at every
+ * step, as from lqt_solve (a shorter last block is padded with steps that
+ * change nothing).  Available where the condensed size (n, B m) is compiled:
+ * FP32 (n, m, B) in {(2,1,2), (3,1,2), (4,1,2), (4,1,4), (4,2,2)}, FP64
+ * (4,1,2), with p <= 8; B = 1 is lqt_solve itself.  Workspace and return
+ * values as for lqt_solve (LQT_EUNSUPPORTED for other sizes and for T = 0). */
+size_t lqt_condensed_workspace_bytes(const lqt_problem *prob, int32_t B, const lqt_options *opts);
+lqt_status lqt_solve_condensed(const lqt_problem *prob, int32_t B, const lqt_solution *sol,
+                               const lqt_options *opts, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
 /* Static string for a status code (never NULL). */
 const char *lqt_strerror(lqt_status status);
 

@@ -115,6 +115,8 @@ def _load() -> ctypes.CDLL:
         "lqt_cross_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_cross), O]),
         "lqt_solve_cross": (st, [P, ctypes.POINTER(lqt_cross), S, O, vp, sz, vp]),
         "lqt_nonlinear_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_nonlinear), O]),
+        "lqt_condensed_workspace_bytes": (sz, [P, ctypes.c_int32, O]),
+        "lqt_solve_condensed": (st, [P, ctypes.c_int32, S, O, vp, sz, vp]),
         "lqt_solve_nonlinear": (st, [P, ctypes.POINTER(lqt_nonlinear), S, O, vp, sz, vp]),
     }
     for name, (res, args) in sig.items():
@@ -328,6 +330,21 @@ def lqt_solve_nonlinear(prob: Problem, nl: lqt_nonlinear, out: Dict[str, object]
         raise LQTError(st, "lqt_solve_nonlinear")
 
 
+def lqt_condensed_workspace_bytes(prob: Problem, B: int, opts=None) -> int:
+    return int(_lib.lqt_condensed_workspace_bytes(ctypes.byref(prob.struct), int(B), _opts(opts)))
+
+
+def lqt_solve_condensed(prob: Problem, B: int, out: Dict[str, object], workspace, stream=None,
+                        opts=None) -> None:
+    """Partial condensing in blocks of B steps (Sec. V-C); asynchronous like lqt_solve."""
+    sol = solution_struct(out)
+    st = _lib.lqt_solve_condensed(ctypes.byref(prob.struct), int(B), ctypes.byref(sol),
+                                  _opts(opts), _ptr(workspace), _nbytes(workspace),
+                                  _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_condensed")
+
+
 def lqt_workspace_status(workspace, stream=None) -> int:
     return int(_lib.lqt_workspace_status(_ptr(workspace), _stream_handle(stream)))
 
@@ -501,6 +518,23 @@ def solve_nonlinear(prob: Problem, iterations: int = 10, dt: float = 0.1, sequen
         raise LQTError(LQT_EUNSUPPORTED, "lqt_nonlinear_workspace_bytes")
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     lqt_solve_nonlinear(prob, nl, out, ws, stream, opts)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return out
+
+
+def solve_condensed(prob: Problem, B: int, stream=None, check: bool = True, opts=None):
+    """Allocate outputs and a workspace with torch and run lqt_solve_condensed."""
+    import torch
+
+    out = prob.allocate_outputs()
+    nbytes = lqt_condensed_workspace_bytes(prob, B, opts)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_condensed_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lqt_solve_condensed(prob, B, out, ws, stream, opts)
     if check:
         st = lqt_workspace_status(ws, stream)
         if st != LQT_OK:

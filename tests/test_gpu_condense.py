@@ -1,0 +1,57 @@
+"""Partial condensing (Sec. V-C) through lqt_solve_condensed: the condensed
+problem (blocks of B steps, stacked controls, generalised stage cost) solved by
+lqt_solve_cross and expanded back to every step.  Condensing is exact, so the
+oracle is the plain FP64 solution of the original problem."""
+import numpy as np
+import pytest
+
+from gpu_util import FP32_TOL, FP64_TOL, compare, oracle_solve
+from paper_2104_03186_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(prob, B, dtype=np.float32, refine=None):
+    from paper_2104_03186_gb300 import lqt
+
+    P = lqt.Problem.from_inputs(prob, dtype=dtype)
+    out = lqt.solve_condensed(P, B, opts=refine)
+    return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("n,m,B", [(2, 1, 2), (3, 1, 2), (4, 1, 2), (4, 1, 4), (4, 2, 2)])
+@pytest.mark.parametrize("T", [1, 7, 1000])
+def test_condensed_fp32_matches_plain_oracle(n, m, B, T):
+    """T = 7 leaves a shorter last block (padded)."""
+    prob = inputs.random_problem(n, m, T=T, seed=10 * n + m + T).rounded_to(np.float32)
+    compare(_solve(prob, B), oracle_solve(prob), FP32_TOL)
+
+
+def test_condensed_fp64_matches_plain_oracle():
+    for T in (5, 800):
+        prob = inputs.random_problem(4, 1, T=T, seed=T)
+        compare(_solve(prob, 2, dtype=np.float64), oracle_solve(prob), FP64_TOL)
+
+
+def test_condensed_vehicle_and_time_invariant():
+    """The vehicle workload (n = 4, m = 2, p = 2; condensed to m = 4, p = 4) and
+    a time-invariant random problem with offsets."""
+    prob = inputs.vehicle(4001, seed=3).rounded_to(np.float32)
+    compare(_solve(prob, 2), oracle_solve(prob), FP32_TOL)
+    prob = inputs.random_problem(4, 1, 3, T=999, seed=5, time_varying=False).rounded_to(np.float32)
+    compare(_solve(prob, 4), oracle_solve(prob), FP32_TOL)
+
+
+def test_condensed_vehicle_long_horizon():
+    """The vehicle benchmark's horizon, T = 1e6, every output."""
+    prob = inputs.vehicle(1_000_000, seed=0).rounded_to(np.float32)
+    compare(_solve(prob, 2), oracle_solve(prob), FP32_TOL)
+
+
+def test_condensed_unsupported_and_passthrough():
+    from paper_2104_03186_gb300 import lqt
+
+    P = lqt.Problem.from_inputs(inputs.random_problem(8, 4, T=50, seed=1).rounded_to(np.float32))
+    assert lqt.lqt_condensed_workspace_bytes(P, 2) == 0
+    prob = inputs.random_problem(4, 2, T=300, seed=2).rounded_to(np.float32)
+    compare(_solve(prob, 1), oracle_solve(prob), FP32_TOL)
