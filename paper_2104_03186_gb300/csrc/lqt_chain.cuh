@@ -26,7 +26,9 @@
 // FP64 tree levels and their (I + C J) solves).
 //
 // Refinement (one step of iterative refinement of the KKT system of the QP):
-// k_cresid evaluates, in FP64, the residuals of the optimality conditions at
+// k_cresid evaluates, in twice the working precision (FP64 arithmetic, or
+// compensated FP32 dot products for FP32 problems), the residuals of the
+// optimality conditions at
 // the first pass's iterate (x^, u^, lambda^ with lambda^_k = S_k x^_k - v_k,
 // the gradient of the value function):
 //   e_k = F_k x^_k + c_k + L_k u^_k - x^_{k+1}                    (dynamics)
@@ -45,6 +47,7 @@
 #include <cuda_runtime.h>
 
 #include "lqt_lane_step.cuh"
+#include "lqt_refine.cuh"
 #include "lqt_tma.cuh"
 
 namespace lqt {
@@ -668,21 +671,61 @@ __global__ void __launch_bounds__(NG* N) k_m2roll(Args<R, RT> a, const RT* Pref)
 }
 
 // ---- KKT residuals of the first pass's iterate (refinement) -----------------
-// One group per step k = 0..T (k = T: the terminal condition and x'_0 = 0),
-// all arithmetic in FP64 (products of FP32 inputs are exact in FP64).
+// One group per step k = 0..T (k = T: the terminal condition and x'_0 = 0).
+// The residuals are small differences of large terms, so every sum runs in
+// twice the working precision: FP64 arithmetic for FP64 problems, and for FP32
+// problems the compensated dot product of lqt_refine.cuh on the FP32 pipe
+// (GB300's FP64 rate is 1/64 of FP32).  Products of FP32 inputs are exact in
+// either form; the intermediate vectors H x^ - r and X (H x^ - r) are carried
+// as (hi, lo) pairs.
+template <typename R>
+struct XAcc;
+
+template <>
+struct XAcc<double> {
+    double s;
+    __device__ explicit XAcc(double a) : s(a) {}
+    __device__ void add(double a) { s += a; }
+    __device__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ void add_prod2(double a, double bh, double bl) { s = fma(a, bh + bl, s); }
+    __device__ void split(double& h, double& l) const {
+        h = s;
+        l = 0.0;
+    }
+    __device__ double value() const { return s; }
+};
+
+template <>
+struct XAcc<float> {
+    Dot2<float> d;
+    __device__ explicit XAcc(float a) : d(a) {}
+    __device__ void add(float a) { d.add(a); }
+    __device__ void add_prod(float a, float b) { d.add_prod(a, b); }
+    // a (bh + bl) with bl below the rounding of bh: the small product joins
+    // the compensation term
+    __device__ void add_prod2(float a, float bh, float bl) {
+        d.add_prod(a, bh);
+        d.c = fma_rn(a, bl, d.c);
+    }
+    __device__ void split(float& h, float& l) const {  // h + l = s + c, |l| <= ulp(h) / 2
+        h = add_rn(d.s, d.c);
+        l = sub_rn(d.c, sub_rn(h, d.s));
+    }
+    __device__ float value() const { return d.value(); }
+};
+
 template <int N, int M>
-struct ResidSmem {  // FP64 work vectors, then the step's matrices staged in R
+struct ResidSmem {  // work vectors and the step's matrices (odd row strides), type R
     static constexpr int PMAX = 2 * N;
     static constexpr int XK = 0, XK1 = N, UK = 2 * N, L0 = 2 * N + M, L1 = 3 * N + M,
-                         HX = 4 * N + M, Y = HX + PMAX, UM = Y + PMAX, RH = UM + M * M,
-                         D64SIZE = RH + M;
-    // staged (type R, odd row strides): S_k, S_{k+1}, F_k (N x lds(N)), L_k (N x lds(M)),
-    // U_k (M x lds(M))
-    static constexpr int SK = 0, SK1 = SK + N * lds(N), FK = SK1 + N * lds(N),
-                         LK = FK + N * lds(N), UKM = LK + N * lds(M), RSIZE = UKM + M * lds(M);
+                         HXH = 4 * N + M, HXL = HXH + PMAX, YH = HXL + PMAX, YL = YH + PMAX,
+                         UM = YL + PMAX, RH = UM + M * lds(M), VEC = RH + M;
+    // S_k, S_{k+1}, F_k (N x lds(N)), L_k (N x lds(M)), U_k (M x lds(M))
+    static constexpr int SK = VEC, SK1 = SK + N * lds(N), FK = SK1 + N * lds(N),
+                         LK = FK + N * lds(N), UKM = LK + N * lds(M), SIZE = UKM + M * lds(M);
     template <typename R>
     static constexpr int bytes() {
-        return D64SIZE * (int)sizeof(double) + RSIZE * (int)sizeof(R);
+        return (SIZE * (int)sizeof(R) + 15) / 16 * 16;
     }
 };
 
@@ -690,29 +733,29 @@ template <typename R, int N, int M, int NG>
 __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const Item<R>* items2,
                                                   int count, long long rows, int* status) {
     using S = ResidSmem<N, M>;
-    using D64 = double;
+    using X = XAcc<R>;
     constexpr int LD = lds(N), LM = lds(M);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    unsigned char* base = smem_raw + (size_t)gi * S::template bytes<R>();
-    D64* sh = reinterpret_cast<D64*>(base);
-    R* st = reinterpret_cast<R*>(base + S::D64SIZE * sizeof(D64));
-    D64* xk = sh + S::XK;
-    D64* xk1 = sh + S::XK1;
-    D64* uk = sh + S::UK;
-    D64* lam0 = sh + S::L0;
-    D64* lam1 = sh + S::L1;
-    D64* hx = sh + S::HX;
-    D64* y = sh + S::Y;
-    D64* Um = sh + S::UM;
-    D64* rh = sh + S::RH;
-    R* Sk = st + S::SK;
-    R* Sk1 = st + S::SK1;
-    R* Fs = st + S::FK;
-    R* Ls = st + S::LK;
-    R* Us = st + S::UKM;
+    R* sh = reinterpret_cast<R*>(smem_raw + (size_t)gi * S::template bytes<R>());
+    R* xk = sh + S::XK;
+    R* xk1 = sh + S::XK1;
+    R* uk = sh + S::UK;
+    R* lam0 = sh + S::L0;
+    R* lam1 = sh + S::L1;
+    R* hxh = sh + S::HXH;
+    R* hxl = sh + S::HXL;
+    R* yh = sh + S::YH;
+    R* yl = sh + S::YL;
+    R* Um = sh + S::UM;
+    R* rh = sh + S::RH;
+    R* Sk = sh + S::SK;
+    R* Sk1 = sh + S::SK1;
+    R* Fs = sh + S::FK;
+    R* Ls = sh + S::LK;
+    R* Us = sh + S::UKM;
     const long long stride = (long long)gridDim.x * NG;
     bool ok = true;
     for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
@@ -724,7 +767,7 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
         const bool term = k == T;
         const int p = term ? D.pT : D.p;
         const R* H = term ? D.HT : D.H + k * D.sH;
-        const R* X = term ? D.XT : D.X + k * D.sX;
+        const R* Xm = term ? D.XT : D.X + k * D.sX;
         const R* rr = term ? D.rT : (D.r ? D.r + k * D.sr : nullptr);
         // the step's matrices by coalesced asynchronous copies
 #pragma unroll 8
@@ -744,81 +787,87 @@ __global__ void __launch_bounds__(NG* N) k_cresid(const Item<R>* items1, const I
                 cp_async<sizeof(R)>(Us + (t / M) * LM + t % M, D.U + k * D.sU + t);
         }
         cp_async_commit();
-        xk[r] = static_cast<D64>(D.x[k * N + r]);
+        xk[r] = D.x[k * N + r];
         if (!term) {
-            xk1[r] = static_cast<D64>(D.x[(k + 1) * N + r]);
-            if (r < M) uk[r] = static_cast<D64>(D.u[k * M + r]);
+            xk1[r] = D.x[(k + 1) * N + r];
+            if (r < M) uk[r] = D.u[k * M + r];
         }
         cp_async_wait<0>();
         g.sync();
         // the iterate's multipliers lambda^_k = S_k x^_k - v_k in the working
         // precision R: the refinement needs exact residuals of some iterate,
-        // and these R values enter the FP64 products below exactly
+        // and these R values enter the products below exactly
         {
             R t = -D.v[k * N + r];
 #pragma unroll 8
-            for (int j = 0; j < N; ++j) t += Sk[r * LD + j] * static_cast<R>(xk[j]);
-            lam0[r] = static_cast<D64>(t);
+            for (int j = 0; j < N; ++j) t += Sk[r * LD + j] * xk[j];
+            lam0[r] = t;
             if (!term) {
                 R t1 = -D.v[(k + 1) * N + r];
 #pragma unroll 8
-                for (int j = 0; j < N; ++j) t1 += Sk1[r * LD + j] * static_cast<R>(xk1[j]);
-                lam1[r] = static_cast<D64>(t1);
+                for (int j = 0; j < N; ++j) t1 += Sk1[r * LD + j] * xk1[j];
+                lam1[r] = t1;
             }
         }
-        // H x^ - r (H = I: x^ - r)
+        // H x^ - r (H = I: x^ - r), as (hi, lo)
         const bool hid = D.sH == 0 && p == N && !term && h_is_identity(D, g);
         if (hid) {
-            hx[r] = xk[r] - (rr ? static_cast<D64>(rr[r]) : 0.0);
+            X h(xk[r]);
+            if (rr) h.add(-rr[r]);
+            h.split(hxh[r], hxl[r]);
         } else {
             for (int i = r; i < p; i += N) {
-                D64 h = rr ? -static_cast<D64>(rr[i]) : 0.0;
-                for (int j = 0; j < N; ++j) h += static_cast<D64>(H[i * N + j]) * xk[j];
-                hx[i] = h;
+                X h(rr ? -rr[i] : R(0));
+                for (int j = 0; j < N; ++j) h.add_prod(H[i * N + j], xk[j]);
+                h.split(hxh[i], hxl[i]);
             }
         }
         g.sync();
+        // y = X (H x^ - r), as (hi, lo)
         for (int i = r; i < p; i += N) {
-            D64 t = 0.0;
-            for (int b = 0; b < p; ++b) t += static_cast<D64>(X[i * p + b]) * hx[b];
-            y[i] = t;
+            X t(R(0));
+            for (int b = 0; b < p; ++b) t.add_prod2(Xm[i * p + b], hxh[b], hxl[b]);
+            t.split(yh[i], yl[i]);
         }
         g.sync();
         // g = H^T X (H x^ - r) - lambda^_k (+ F^T lambda^_{k+1})
-        D64 gr = -lam0[r];
+        X gr(-lam0[r]);
         if (hid) {
-            gr += y[r];
+            gr.add(yh[r]);
+            gr.add(yl[r]);
         } else {
-            for (int i = 0; i < p; ++i) gr += static_cast<D64>(H[i * N + r]) * y[i];
+            for (int i = 0; i < p; ++i) gr.add_prod2(H[i * N + r], yh[i], yl[i]);
         }
         if (term) {
-            const_cast<R*>(D2.etaT)[r] = static_cast<R>(-gr);
+            const_cast<R*>(D2.etaT)[r] = -gr.value();
             const_cast<R*>(D2.x0)[r] = R(0);
             g.sync();
             continue;
         }
-        for (int j = 0; j < N; ++j) gr += static_cast<D64>(Fs[j * LD + r]) * lam1[j];
+        for (int j = 0; j < N; ++j) gr.add_prod(Fs[j * LD + r], lam1[j]);
         // e = F x^ + c + L u^ - x^_{k+1}
-        D64 e = (D.c ? static_cast<D64>(D.c[k * D.sc + r]) : 0.0) - xk1[r];
-        for (int j = 0; j < N; ++j) e += static_cast<D64>(Fs[r * LD + j]) * xk[j];
-        for (int b = 0; b < M; ++b) e += static_cast<D64>(Ls[r * LM + b]) * uk[b];
-        // h = U u^ + L^T lambda^_{k+1}; U^{-1} h
+        X e(D.c ? D.c[k * D.sc + r] : R(0));
+        e.add(-xk1[r]);
+        for (int j = 0; j < N; ++j) e.add_prod(Fs[r * LD + j], xk[j]);
+        for (int b = 0; b < M; ++b) e.add_prod(Ls[r * LM + b], uk[b]);
+        // h = U u^ + L^T lambda^_{k+1}; U^{-1} h in the working precision (h is
+        // the residual itself, so its rounding is relative to h)
         if (r < M) {
-            D64 h = 0.0;
+            X h(R(0));
             for (int b = 0; b < M; ++b) {
-                const D64 ub = static_cast<D64>(Us[r * LM + b]);
-                Um[r * M + b] = ub;
-                h += ub * uk[b];
+                const R ub = Us[r * LM + b];
+                Um[r * LM + b] = ub;
+                h.add_prod(ub, uk[b]);
             }
-            for (int j = 0; j < N; ++j) h += static_cast<D64>(Ls[j * LM + r]) * lam1[j];
-            rh[r] = h;
+            for (int j = 0; j < N; ++j) h.add_prod(Ls[j * LM + r], lam1[j]);
+            rh[r] = h.value();
         }
         g.sync();
-        ok &= solve_spd<N, M, 1>(Um, M, rh, 1, g);
-        for (int b = 0; b < M; ++b) e -= static_cast<D64>(Ls[r * LM + b]) * rh[b];
-        const_cast<R*>(D2.eta)[k * N + r] = static_cast<R>(-gr);
-        const_cast<R*>(D2.c)[k * N + r] = static_cast<R>(e);
-        if (r < M) const_cast<R*>(items2[ii].qh)[k * M + r] = static_cast<R>(rh[r]);
+        ok &= solve_spd<N, M, 1>(Um, LM, rh, 1, g);
+        for (int b = 0; b < M; ++b) e.add_prod(-Ls[r * LM + b], rh[b]);
+        const_cast<R*>(D2.eta)[k * N + r] = -gr.value();
+        const_cast<R*>(D2.c)[k * N + r] = e.value();
+        if (r < M) const_cast<R*>(items2[ii].qh)[k * M + r] = rh[r];
         g.sync();
     }
     flag(status, ok);
