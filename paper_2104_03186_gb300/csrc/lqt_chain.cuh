@@ -684,6 +684,7 @@ struct XAcc;
 template <>
 struct XAcc<double> {
     double s;
+    __device__ XAcc() : s(0.0) {}
     __device__ explicit XAcc(double a) : s(a) {}
     __device__ void add(double a) { s += a; }
     __device__ void add_prod(double a, double b) { s = fma(a, b, s); }
@@ -698,6 +699,7 @@ struct XAcc<double> {
 template <>
 struct XAcc<float> {
     Dot2<float> d;
+    __device__ XAcc() : d(0.0f) {}
     __device__ explicit XAcc(float a) : d(a) {}
     __device__ void add(float a) { d.add(a); }
     __device__ void add_prod(float a, float b) { d.add_prod(a, b); }
@@ -997,6 +999,359 @@ __global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const I
         ok &= gains<D64, N, M>(val, sb, Kd, scr, g);
 #pragma unroll 8
         for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = static_cast<R>(Kd[i * (N + 1) + r]);
+        g.sync();
+    }
+    flag(status, ok);
+}
+
+// ---- the Newton step in compensated FP32 (FP32 problems) -------------------
+// The same residuals and gains as k_nresid / k_ngains, with every sum in twice
+// the working precision on the FP32 pipe (XAcc<float>).  The residual of the
+// Riccati map is evaluated in its symmetric form around the first pass's FP32
+// gain K~ (which the pass wrote into the K output):
+//   (F - L K~)^T S (F - L K~) + K~^T U K~ + Q
+//     = F^T S F - K~^T W - W^T K~ + K~^T G K~ + Q = Ric(S) + (K~ - K)^T G (K~ - K),
+//   W = L^T S F, G = L^T S L + U, K = G^{-1} W,
+// so the error of K~ enters only to second order; likewise for the vector
+// recursion with e = v - S c, w = L^T e, d~ = G^{-1} w (FP32):
+//   F^T e - K~^T w - W^T d~ + K~^T G d~ + q = Vrec(S, v) + (K~ - K)^T G (d - d~).
+// The gains at S^ + dS take one step of iterative refinement of G K = W from
+// K~, with the residual W - G K~ in twice the working precision.
+// Row a of L^T Y (+ Z row a), Y = (Yh, Yl) N x C in shared memory (stride ldy):
+// out[c] = sum_j L[j][a] Y[j][c], CH independent compensated accumulators at a
+// time (each sum is a serial chain, so several run side by side).
+template <int N, int M, int CH>
+__device__ __forceinline__ void lt_times_x(const float* L, int a, const float* Yh,
+                                           const float* Yl, int ldy, int C, float* outh,
+                                           float* outl, const float* init = nullptr) {
+    using X = XAcc<float>;
+    for (int c0 = 0; c0 < C; c0 += CH) {
+        X t[CH];
+#pragma unroll
+        for (int cc = 0; cc < CH; ++cc)
+            if (init) t[cc].add(init[c0 + cc]);
+        for (int j = 0; j < N; ++j) {
+            const float l = L[j * M + a];
+#pragma unroll
+            for (int cc = 0; cc < CH; ++cc) t[cc].add_prod2(l, Yh[j * ldy + c0 + cc], Yl[j * ldy + c0 + cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < CH; ++cc) t[cc].split(outh[c0 + cc], outl[c0 + cc]);
+    }
+}
+
+template <int N, int M>
+struct NewtonCSmem {  // float: (hi, lo) intermediates, odd row strides
+    static constexpr int LD = lds(N), LM = lds(M), PMAX = 2 * N;
+    static constexpr int SFH = 0, SFL = SFH + N * LD, SLH = SFL + N * LD, SLL = SLH + N * LM,
+                         WH = SLL + N * LM, WL = WH + M * LD, GH = WL + M * LD, GL = GH + M * LM,
+                         GKH = GL + M * LM, GKL = GKH + M * LD, XHH = GKL + M * LD,
+                         XHL = XHH + PMAX * LD, RR = XHL + PMAX * LD, EH = RR + N * LD,
+                         EL = EH + N, WVH = EL + N, WVL = WVH + M, DD = WVL + M, GDH = DD + M,
+                         GDL = GDH + M, XRH = GDL + M, XRL = XRH + PMAX, SIZE = XRL + PMAX;
+};
+
+template <int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_nresid_c(const Item<float>* items1,
+                                                    const Item<float>* items3, int count,
+                                                    long long rows, int* status) {
+    using S = NewtonCSmem<N, M>;
+    using X = XAcc<float>;
+    constexpr int LD = S::LD, LM = S::LM, NCH = N < 8 ? N : 8, MCH = M < 8 ? M : 8;
+    static_assert(N % NCH == 0 && M % MCH == 0, "column chunks");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const int r = g.lr;
+    float* sh = reinterpret_cast<float*>(smem_raw) + gi * S::SIZE;
+    float *SFh = sh + S::SFH, *SFl = sh + S::SFL, *SLh = sh + S::SLH, *SLl = sh + S::SLL;
+    float *Wh = sh + S::WH, *Wl = sh + S::WL, *Gh = sh + S::GH, *Gl = sh + S::GL;
+    float *GKh = sh + S::GKH, *GKl = sh + S::GKL, *XHh = sh + S::XHH, *XHl = sh + S::XHL;
+    float *RR = sh + S::RR, *eh = sh + S::EH, *el = sh + S::EL, *wvh = sh + S::WVH;
+    float *wvl = sh + S::WVL, *dd = sh + S::DD, *gdh = sh + S::GDH, *gdl = sh + S::GDL;
+    float *xrh = sh + S::XRH, *xrl = sh + S::XRL;
+    const long long stride = (long long)gridDim.x * NG;
+    bool ok = true;
+    for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
+        const int ii = find_row(items1, count, q);
+        const DescT<float>& D = items1[ii].D;
+        const DescT<float>& D3 = items3[ii].D;
+        const long long k = q - items1[ii].r0;
+        const long long T = D.T;
+        float* Rk = const_cast<float*>(D3.X) + k * N * N;
+        if (k == T) {
+            // R_T = H_T^T X_T H_T - S^_T, rho_T = H_T^T X_T r_T - v^_T
+            const int pT = D.pT;
+            for (int i = r; i < pT; i += N) {
+                for (int c = 0; c < N; ++c) {
+                    X t(0.0f);
+                    for (int b = 0; b < pT; ++b) t.add_prod(D.XT[i * pT + b], D.HT[b * N + c]);
+                    t.split(XHh[i * LD + c], XHl[i * LD + c]);
+                }
+                X t(0.0f);
+                if (D.rT)
+                    for (int b = 0; b < pT; ++b) t.add_prod(D.XT[i * pT + b], D.rT[b]);
+                t.split(xrh[i], xrl[i]);
+            }
+            g.sync();
+            for (int c = 0; c < N; ++c) {
+                X t(-D.S[T * N * N + r * N + c]);
+                for (int i = 0; i < pT; ++i) t.add_prod2(D.HT[i * N + r], XHh[i * LD + c], XHl[i * LD + c]);
+                RR[r * LD + c] = t.value();
+            }
+            X rho(-D.v[T * N + r]);
+            for (int i = 0; i < pT; ++i) rho.add_prod2(D.HT[i * N + r], xrh[i], xrl[i]);
+            g.sync();
+#pragma unroll 8
+            for (int i = 0; i < N; ++i) Rk[i * N + r] = 0.5f * (RR[i * LD + r] + RR[r * LD + i]);
+            const_cast<float*>(D3.etaT)[r] = rho.value();
+            g.sync();
+            continue;
+        }
+        const float* F = D.F + k * D.sF;
+        const float* L = D.L + k * D.sL;
+        const float* U = D.U + k * D.sU;
+        const float* c = D.c ? D.c + k * D.sc : nullptr;
+        const float* S1 = D.S + (k + 1) * N * N;
+        const float* Sk = D.S + k * N * N;
+        const float* Kt = D.K + k * M * N;
+        const int p = D.p;
+        const float* H = D.H ? D.H + k * D.sH : nullptr;
+        const float* Xm = D.X ? D.X + k * D.sX : nullptr;
+        const float* rr = D.r ? D.r + k * D.sr : nullptr;
+        const bool hid = D.sH == 0 && p == N && h_is_identity(D, g);
+        // S F and S L (row r), e = v - S c, and X H, X r
+        for (int c0 = 0; c0 < N; c0 += NCH) {
+            X t[NCH];
+            for (int j = 0; j < N; ++j) {
+                const float sj = S1[r * N + j];
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) t[cc].add_prod(sj, F[j * N + c0 + cc]);
+            }
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) t[cc].split(SFh[r * LD + c0 + cc], SFl[r * LD + c0 + cc]);
+        }
+        for (int a0 = 0; a0 < M; a0 += MCH) {
+            X t[MCH];
+            for (int j = 0; j < N; ++j) {
+                const float sj = S1[r * N + j];
+#pragma unroll
+                for (int aa = 0; aa < MCH; ++aa) t[aa].add_prod(sj, L[j * M + a0 + aa]);
+            }
+#pragma unroll
+            for (int aa = 0; aa < MCH; ++aa) t[aa].split(SLh[r * LM + a0 + aa], SLl[r * LM + a0 + aa]);
+        }
+        {
+            X e(D.v[(k + 1) * N + r]);
+            if (c)
+                for (int j = 0; j < N; ++j) e.add_prod(-S1[r * N + j], c[j]);
+            e.split(eh[r], el[r]);
+        }
+        if (hid) {
+            X t(0.0f);
+            if (rr)
+                for (int b = 0; b < N; ++b) t.add_prod(Xm[r * N + b], rr[b]);
+            t.split(xrh[r], xrl[r]);
+        } else {
+            for (int i = r; i < p; i += N) {
+                for (int cl = 0; cl < N; ++cl) {
+                    X t(0.0f);
+                    for (int b = 0; b < p; ++b) t.add_prod(Xm[i * p + b], H[b * N + cl]);
+                    t.split(XHh[i * LD + cl], XHl[i * LD + cl]);
+                }
+                X t(0.0f);
+                if (rr)
+                    for (int b = 0; b < p; ++b) t.add_prod(Xm[i * p + b], rr[b]);
+                t.split(xrh[i], xrl[i]);
+            }
+        }
+        g.sync();
+        // W = L^T S F, G = L^T S L + U, w = L^T e (rows a = r < M)
+        if (r < M) {
+            lt_times_x<N, M, NCH>(L, r, SFh, SFl, LD, N, Wh + r * LD, Wl + r * LD);
+            lt_times_x<N, M, MCH>(L, r, SLh, SLl, LM, M, Gh + r * LM, Gl + r * LM, U + r * M);
+            X w(0.0f);
+            for (int j = 0; j < N; ++j) w.add_prod2(L[j * M + r], eh[j], el[j]);
+            w.split(wvh[r], wvl[r]);
+            dd[r] = wvh[r] + wvl[r];
+        }
+        g.sync();
+        // d~ = G^{-1} w in FP32; G K~ (rows a = r < M)
+        ok &= solve_spd<N, M, 1>(Gh, LM, dd, 1, g);
+        if (r < M)
+            for (int c0 = 0; c0 < N; c0 += NCH) {
+                X t[NCH];
+                for (int b = 0; b < M; ++b) {
+                    const float gh = Gh[r * LM + b], gl = Gl[r * LM + b];
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc) t[cc].add_prod2(Kt[b * N + c0 + cc], gh, gl);
+                }
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) t[cc].split(GKh[r * LD + c0 + cc], GKl[r * LD + c0 + cc]);
+            }
+        if (r < M) {
+            X t(0.0f);
+            for (int b = 0; b < M; ++b) t.add_prod2(dd[b], Gh[r * LM + b], Gl[r * LM + b]);
+            t.split(gdh[r], gdl[r]);
+        }
+        g.sync();
+        // row r of R_k = F^T S F - K~^T W - W^T K~ + K~^T G K~ + Q - S^_k
+        for (int c0 = 0; c0 < N; c0 += NCH) {
+            X t[NCH];
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) {
+                t[cc].add(-Sk[r * N + c0 + cc]);
+                if (hid) t[cc].add(Xm[r * N + c0 + cc]);
+            }
+            for (int j = 0; j < N; ++j) {
+                const float f = F[j * N + r];
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc)
+                    t[cc].add_prod2(f, SFh[j * LD + c0 + cc], SFl[j * LD + c0 + cc]);
+            }
+            for (int a = 0; a < M; ++a) {
+                const float kr = Kt[a * N + r];
+                const float wrh = Wh[a * LD + r], wrl = Wl[a * LD + r];
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) {
+                    t[cc].add_prod2(-kr, Wh[a * LD + c0 + cc], Wl[a * LD + c0 + cc]);
+                    t[cc].add_prod2(-Kt[a * N + c0 + cc], wrh, wrl);
+                    t[cc].add_prod2(kr, GKh[a * LD + c0 + cc], GKl[a * LD + c0 + cc]);
+                }
+            }
+            if (!hid)
+                for (int i = 0; i < p; ++i) {
+                    const float h = H[i * N + r];
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc)
+                        t[cc].add_prod2(h, XHh[i * LD + c0 + cc], XHl[i * LD + c0 + cc]);
+                }
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) RR[r * LD + c0 + cc] = t[cc].value();
+        }
+        // rho_k = F^T e - K~^T w - W^T d~ + K~^T G d~ + q - v^_k
+        X rho(-D.v[k * N + r]);
+        if (hid) {
+            rho.add(xrh[r]);
+            rho.add(xrl[r]);
+        } else {
+            for (int i = 0; i < p; ++i) rho.add_prod2(H[i * N + r], xrh[i], xrl[i]);
+        }
+        for (int j = 0; j < N; ++j) rho.add_prod2(F[j * N + r], eh[j], el[j]);
+        for (int a = 0; a < M; ++a) {
+            const float kr = Kt[a * N + r];
+            rho.add_prod2(-kr, wvh[a], wvl[a]);
+            rho.add_prod2(-dd[a], Wh[a * LD + r], Wl[a * LD + r]);
+            rho.add_prod2(kr, gdh[a], gdl[a]);
+        }
+        g.sync();
+        // symmetrised R_k, the closed loop Phi_k = F - L K~ and ct_k = c + L d~
+        // (FP32: they enter the correction's dynamics, whose relative error is
+        // then of the order of K~'s)
+#pragma unroll 4
+        for (int i = 0; i < N; ++i) {
+            Rk[i * N + r] = 0.5f * (RR[i * LD + r] + RR[r * LD + i]);
+            float f = F[i * N + r];
+            for (int a = 0; a < M; ++a) f -= L[i * M + a] * Kt[a * N + r];
+            const_cast<float*>(D3.F)[k * N * N + i * N + r] = f;
+        }
+        const_cast<float*>(D3.eta)[k * N + r] = rho.value();
+        {
+            float t = c ? c[r] : 0.0f;
+            for (int a = 0; a < M; ++a) t += L[r * M + a] * dd[a];
+            const_cast<float*>(D3.c)[k * N + r] = t;
+        }
+        g.sync();
+    }
+    flag(status, ok);
+}
+
+// K_k at S^_{k+1} + dS_{k+1}: one step of iterative refinement of G K = W from
+// the first pass's K~, with S held as the (hi, lo) pair (S^, dS).
+template <int N, int M>
+struct NewtonGSmem {  // float: S F, S L, W, G as (hi, lo), and the residual Z
+    static constexpr int LD = lds(N), LM = lds(M);
+    static constexpr int SFH = 0, SFL = SFH + N * LD, SLH = SFL + N * LD, SLL = SLH + N * LM,
+                         WH = SLL + N * LM, WL = WH + M * LD, GH = WL + M * LD, GL = GH + M * LM,
+                         Z = GL + M * LM, SIZE = Z + M * LD;
+};
+
+template <int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_ngains_c(const Item<float>* items1,
+                                                    const Item<float>* items3, int count,
+                                                    long long rows, int* status) {
+    using S = NewtonGSmem<N, M>;
+    using X = XAcc<float>;
+    constexpr int LD = S::LD, LM = S::LM, NCH = N < 8 ? N : 8, MCH = M < 8 ? M : 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Group<N> g;
+    const int gi = threadIdx.x / N;
+    const int r = g.lr;
+    float* sh = reinterpret_cast<float*>(smem_raw) + gi * S::SIZE;
+    float *SFh = sh + S::SFH, *SFl = sh + S::SFL, *SLh = sh + S::SLH, *SLl = sh + S::SLL;
+    float *Wh = sh + S::WH, *Wl = sh + S::WL, *Gh = sh + S::GH, *Gl = sh + S::GL;
+    float* Z = sh + S::Z;  // M x LD
+    const long long stride = (long long)gridDim.x * NG;
+    bool ok = true;
+    for (long long q = (long long)blockIdx.x * NG + gi; q < rows; q += stride) {
+        const int ii = find_row(items1, count, q);
+        const DescT<float>& D = items1[ii].D;
+        const DescT<float>& D3 = items3[ii].D;
+        const long long k = q - items1[ii].r0;
+        if (k == D.T) continue;
+        const float* F = D.F + k * D.sF;
+        const float* L = D.L + k * D.sL;
+        const float* U = D.U + k * D.sU;
+        const float* Sh = D.S + (k + 1) * N * N;
+        const float* Sl = D3.S + (k + 1) * N * N;
+        float* Kt = D.K + k * M * N;
+        for (int c0 = 0; c0 < N; c0 += NCH) {
+            X t[NCH];
+            for (int j = 0; j < N; ++j) {
+                const float sh_ = Sh[r * N + j], sl_ = Sl[r * N + j];
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) t[cc].add_prod2(F[j * N + c0 + cc], sh_, sl_);
+            }
+#pragma unroll
+            for (int cc = 0; cc < NCH; ++cc) t[cc].split(SFh[r * LD + c0 + cc], SFl[r * LD + c0 + cc]);
+        }
+        for (int a0 = 0; a0 < M; a0 += MCH) {
+            X t[MCH];
+            for (int j = 0; j < N; ++j) {
+                const float sh_ = Sh[r * N + j], sl_ = Sl[r * N + j];
+#pragma unroll
+                for (int aa = 0; aa < MCH; ++aa) t[aa].add_prod2(L[j * M + a0 + aa], sh_, sl_);
+            }
+#pragma unroll
+            for (int aa = 0; aa < MCH; ++aa) t[aa].split(SLh[r * LM + a0 + aa], SLl[r * LM + a0 + aa]);
+        }
+        g.sync();
+        if (r < M) {
+            lt_times_x<N, M, NCH>(L, r, SFh, SFl, LD, N, Wh + r * LD, Wl + r * LD);
+            lt_times_x<N, M, MCH>(L, r, SLh, SLl, LM, M, Gh + r * LM, Gl + r * LM, U + r * M);
+        }
+        g.sync();
+        // Z = W - G K~ (rows a = r < M)
+        if (r < M)
+            for (int c0 = 0; c0 < N; c0 += NCH) {
+                X t[NCH];
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) {
+                    t[cc].add(Wh[r * LD + c0 + cc]);
+                    t[cc].add(Wl[r * LD + c0 + cc]);
+                }
+                for (int b = 0; b < M; ++b) {
+                    const float gh = Gh[r * LM + b], gl = Gl[r * LM + b];
+#pragma unroll
+                    for (int cc = 0; cc < NCH; ++cc) t[cc].add_prod2(-Kt[b * N + c0 + cc], gh, gl);
+                }
+#pragma unroll
+                for (int cc = 0; cc < NCH; ++cc) Z[r * LD + c0 + cc] = t[cc].value();
+            }
+        g.sync();
+        ok &= solve_spd<N, M, N>(Gh, LM, Z, LD, g);
+#pragma unroll 4
+        for (int a = 0; a < M; ++a) Kt[a * N + r] += Z[a * LD + r];
         g.sync();
     }
     flag(status, ok);

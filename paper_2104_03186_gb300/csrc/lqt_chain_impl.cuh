@@ -45,6 +45,12 @@ struct Launcher {
     static constexpr int RESID_B = ResidSmem<N, M>::template bytes<R>();
     static constexpr int NEWTON_B = NewtonSmem<N, M>::SIZE * (int)sizeof(double);
     static constexpr int NG_NEWTON = groups_for<N>(NEWTON_B);
+    // FP32 problems: the compensated-FP32 Newton kernels
+    static constexpr int NEWTON_C_B = NewtonCSmem<N, M>::SIZE * (int)sizeof(float);
+    static constexpr int NG_NEWTON_C = groups_for<N>(NEWTON_C_B);
+    static constexpr int NEWTON_G_B = NewtonGSmem<N, M>::SIZE * (int)sizeof(float);
+    static constexpr int NG_NEWTON_G = groups_for<N>(NEWTON_G_B);
+    static constexpr bool kCompNewton = sizeof(R) == 4;
     static constexpr int NG_RESID = groups_for<N>(RESID_B);
     static constexpr int M2_B = M2Smem<N, M>::SIZE * (int)sizeof(R);
     static constexpr int NG_M2 = groups_for<N>(M2_B);
@@ -77,6 +83,14 @@ struct Launcher {
         if ((e = chain_allow_smem(k_cresid<R, N, M, NG_RESID>, d_resid,
                                   (size_t)NG_RESID * RESID_B)) != cudaSuccess)
             return e;
+        if constexpr (kCompNewton) {
+            static bool d_nres_c[64], d_ngain_c[64];
+            if ((e = chain_allow_smem(k_nresid_c<N, M, NG_NEWTON_C>, d_nres_c,
+                                      (size_t)NG_NEWTON_C * NEWTON_C_B)) != cudaSuccess ||
+                (e = chain_allow_smem(k_ngains_c<N, M, NG_NEWTON_G>, d_ngain_c,
+                                      (size_t)NG_NEWTON_G * NEWTON_G_B)) != cudaSuccess)
+                return e;
+        }
         if ((e = chain_allow_smem(k_nresid<R, N, M, NG_NEWTON>, d_nres,
                                   (size_t)NG_NEWTON * NEWTON_B)) != cudaSuccess ||
             (e = chain_allow_smem(k_ngains<R, N, M, NG_NEWTON>, d_ngain,
@@ -388,17 +402,32 @@ struct Launcher {
         if (newton) {
             // Newton correction of S and v, then K from the corrected S and v
             prof_mark(prof, s, "chain_newton_resid");
-            int gridn = blocks(r0, NG_NEWTON);
+            int gridn = blocks(r0, kCompNewton ? NG_NEWTON_C : NG_NEWTON);
             if (gridn > 4096) gridn = 4096;
-            k_nresid<R, N, M, NG_NEWTON><<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(
-                d1, d3, count, r0, a.status);
+            if constexpr (kCompNewton)
+                k_nresid_c<N, M, NG_NEWTON_C>
+                    <<<gridn, NG_NEWTON_C * N, (size_t)NG_NEWTON_C * NEWTON_C_B, s>>>(
+                        d1, d3, count, r0, a.status);
+            else
+                k_nresid<R, N, M, NG_NEWTON>
+                    <<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(d1, d3, count, r0,
+                                                                                a.status);
             Args<R, RT> c = a;
             c.items = d3;
             c.out_mask = 5;
             pass(c, active.data(), levels, call.sequential, 2, true, s, prof);
             prof_mark(prof, s, "chain_newton_gains");
-            k_ngains<R, N, M, NG_NEWTON><<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(
-                d1, d3, count, r0, a.status);
+            if constexpr (kCompNewton) {
+                int gridg = blocks(r0, NG_NEWTON_G);
+                if (gridg > 4096) gridg = 4096;
+                k_ngains_c<N, M, NG_NEWTON_G>
+                    <<<gridg, NG_NEWTON_G * N, (size_t)NG_NEWTON_G * NEWTON_G_B, s>>>(
+                        d1, d3, count, r0, a.status);
+            }
+            else
+                k_ngains<R, N, M, NG_NEWTON>
+                    <<<gridn, NG_NEWTON * N, (size_t)NG_NEWTON * NEWTON_B, s>>>(d1, d3, count, r0,
+                                                                                a.status);
             prof_mark(prof, s, "chain_newton_add");
             k_nadd<R, N><<<1024, 256, 0, s>>>(d1, d3, count, r0);
         }
