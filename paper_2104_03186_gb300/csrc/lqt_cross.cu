@@ -660,6 +660,8 @@ lqt_status lqt_solve_cross(const lqt_problem* prob, const lqt_cross* cross,
     if (workspace_bytes < cp.total) return LQT_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prob->T == 0) return lqt_solve(prob, sol, opts, workspace, cp.solver, stream);
+    // one post-transform block per kPostThreads steps
+    if ((prob->T + kPostThreads - 1) / kPostThreads > INT32_MAX) return LQT_EINVAL;
     // argument check of the transformed solve before anything is launched:
     // lqt_solve validates everything, then reports LQT_ENOMEM for a zero-byte
     // workspace without launching

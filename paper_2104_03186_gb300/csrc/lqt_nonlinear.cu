@@ -217,6 +217,7 @@ lqt_status run_nl(const lqt_problem* P, const lqt_nonlinear* nl, const lqt_solut
     const long long T = P->T;
     const R dt = static_cast<R>(nl->dt);
     const long long rows = T + 1;
+    if ((rows + 127) / 128 > INT32_MAX) return LQT_EINVAL;
     const unsigned grid_init = (unsigned)((rows * 4 + 255) / 256 < 4096 ? (rows * 4 + 255) / 256 : 4096);
     k_nl_init<R><<<grid_init, 256, 0, s>>>(T, static_cast<const R*>(nl->x_init),
                                             static_cast<const R*>(nl->u_init),
