@@ -820,10 +820,12 @@ def main(argv=None):
     ap.add_argument("--T", type=int, default=T_HEADLINE, help="horizon of --profile-solves")
     ap.add_argument("--refine", type=int, default=1, help="refinement in --profile-solves")
     ap.add_argument("--profile-workload",
-                    choices=("vehicle", "precision", "cross", "nonlinear"), default="vehicle",
+                    choices=("vehicle", "precision", "cross", "nonlinear", "batch"),
+                    default="vehicle",
                     help="workload of --profile-solves: the vehicle (n = 4), the n = 32 "
                          "precision study, the vehicle with cross weights and offsets "
-                         "(lqt_solve_cross), or the unicycle (lqt_solve_nonlinear, 10 passes)")
+                         "(lqt_solve_cross), the unicycle (lqt_solve_nonlinear, 10 passes), or "
+                         "the ragged batch (lqt_solve_batched, --batch-count problems)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -841,6 +843,16 @@ def run_profile_solves(args):
 
     from paper_2104_03186_gb300 import inputs, lqt
 
+    if args.profile_workload == "batch":
+        Ps = [lqt.Problem.from_inputs(p, dtype=np.float32) for p in gen_batch(args.batch_count, 7)]
+        outs = [P.allocate_outputs() for P in Ps]
+        ws = torch_empty_bytes(lqt.lqt_batch_workspace_bytes(Ps, outs))
+        for _ in range(args.warmup + args.profile_solves):
+            lqt.lqt_solve_batched(Ps, outs, ws)
+        torch.cuda.synchronize()
+        st = lqt.lqt_workspace_status(ws)
+        print("profile solves done: batch of %d status=%d" % (len(Ps), st))
+        return 0 if st == lqt.LQT_OK else 1
     if args.profile_workload == "precision":
         pr = inputs.precision_study(T=args.T, seed=0)
     elif args.profile_workload == "nonlinear":
