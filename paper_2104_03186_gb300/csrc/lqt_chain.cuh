@@ -179,9 +179,11 @@ struct RollSmem {  // x, u, then F_k (N x lds(N)), L_k (N x lds(M)), K_k (M x ld
 
 // Groups per CTA: at most 256 threads and about 100 KB of shared memory.
 template <int N>
+// Groups per CTA: at most 256 threads, and at most 112 KB of shared memory so
+// that two CTAs share an SM (228 KB, 1 KB of it reserved per CTA).
 constexpr int groups_for(int bytes_per_group) {
     int g = 256 / N;
-    while (g > 1 && g * bytes_per_group > 100 * 1024) --g;
+    while (g > 1 && g * bytes_per_group > 112 * 1024) --g;
     return g;
 }
 
