@@ -40,7 +40,7 @@ struct Layout {
                                                            LAffine<N>::SIZE
                                    ? combine_scratch<N>()
                                    : riccati_scratch<N, M>() + M * (N + 1) + LAffine<N>::SIZE;
-    static constexpr int G_SIZE = G_SCR + SCR;
+    static constexpr int G_SIZE = gstride<N>(G_SCR + SCR);
     // CTA: tree of chunk totals, value carries, affine maps, chunk start states
     static constexpr int TREE = 0;
     static constexpr int CARRY = TREE + NG * LElem<N>::SIZE;

@@ -177,10 +177,9 @@ struct RollSmem {  // x, u, then F_k (N x lds(N)), L_k (N x lds(M)), K_k (M x ld
     static constexpr int SIZE = K + M * lds(N);
 };
 
-// Groups per CTA: at most 256 threads and about 100 KB of shared memory.
-template <int N>
 // Groups per CTA: at most 256 threads, and at most 112 KB of shared memory so
 // that two CTAs share an SM (228 KB, 1 KB of it reserved per CTA).
+template <int N>
 constexpr int groups_for(int bytes_per_group) {
     int g = 256 / N;
     while (g > 1 && g * bytes_per_group > 112 * 1024) --g;
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
     if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
-    R* gs = sh + gi * S::SIZE;
+    R* gs = sh + gi * gstride<N>(S::SIZE);
     R* P = gs + S::P;
     R* sb = gs + S::SB;
     R* scr = gs + S::SCR_OFF;
@@ -252,7 +251,7 @@ __global__ void __launch_bounds__(NG* N) k_cup(RT* E_, long long active, int h, 
     const int gi = threadIdx.x / N;
     const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
     if (i >= active) return;
-    RT* e1 = sh + gi * UpSmem<N>::SIZE;
+    RT* e1 = sh + gi * gstride<N>(UpSmem<N>::SIZE);
     RT* e2 = e1 + E::SIZE;
     RT* scr = e2 + E::SIZE;
     copy_in(e1, E_ + i * E::SIZE, E::SIZE, g.lr, N);
@@ -326,7 +325,7 @@ __global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, long long
     const int gi = threadIdx.x / N;
     const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
     if (i >= active) return;
-    RT* e = sh + gi * DownSmem<N>::SIZE;
+    RT* e = sh + gi * gstride<N>(DownSmem<N>::SIZE);
     RT* val = e + E::SIZE;
     RT* scr = val + V::SIZE;
     copy_in(e, E_ + (i + h) * E::SIZE, E::SIZE, g.lr, N);
@@ -352,7 +351,7 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
-    R* gs = sh + gi * S::SIZE;
+    R* gs = sh + gi * gstride<N>(S::SIZE);
     R* val = gs + S::VAL;
     R* Phi = gs + S::PHI;
     R* sb = gs + S::SB;
@@ -419,7 +418,7 @@ __global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, long long active, int h)
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
     if (j >= active) return;
-    RT* f1 = sh + gi * FupSmem<N>::SIZE;
+    RT* f1 = sh + gi * gstride<N>(FupSmem<N>::SIZE);
     RT* f2 = f1 + A::SIZE;
     copy_in(f1, FE + (j - h) * A::SIZE, A::SIZE, g.lr, N);
     copy_in(f2, FE + j * A::SIZE, A::SIZE, g.lr, N);
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, long long
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
     if (j >= active) return;
-    RT* f = sh + gi * FdownSmem<N>::SIZE;
+    RT* f = sh + gi * gstride<N>(FdownSmem<N>::SIZE);
     RT* x = f + A::SIZE;
     const int r = g.lr;
     copy_in(f, FE + (j - h) * A::SIZE, A::SIZE, r, N);
@@ -462,7 +461,7 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
-    R* xc = sh + gi * RollSmem<N, M>::SIZE;
+    R* xc = sh + gi * gstride<N>(RollSmem<N, M>::SIZE);
     R* us = xc + N;
     const int r = g.lr;
     const long long T = D.T;
@@ -472,9 +471,9 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     xc[r] = lc == 0 ? D.x0[r] : static_cast<R>(a.X[c * N + r]);
     g.sync();
     constexpr int LD = lds(N), LM = lds(M);
-    R* Fs = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::F;
-    R* Ls = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::L;
-    R* Ks = sh + gi * RollSmem<N, M>::SIZE + RollSmem<N, M>::K;
+    R* Fs = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::F;
+    R* Ls = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::L;
+    R* Ks = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::K;
     for (long long k = s0; k < e0; ++k) {
         // F_k and L_k into shared memory by coalesced asynchronous copies
         const R* F = D.F + k * D.sF;
@@ -543,7 +542,7 @@ __global__ void __launch_bounds__(NG* N) k_m2up(RT* E2, long long active, int h,
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
     if (j >= active) return;
-    RT* e1 = sh + gi * UpSmem<N>::SIZE;
+    RT* e1 = sh + gi * gstride<N>(UpSmem<N>::SIZE);
     RT* e2 = e1 + E::SIZE;
     RT* scr = e2 + E::SIZE;
     copy_in(e1, E2 + (j - h) * E::SIZE, E::SIZE, g.lr, N);
@@ -577,7 +576,7 @@ __global__ void __launch_bounds__(NG* N) k_m2down(const RT* E2, RT* Pref, long l
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
     if (j >= active) return;
-    RT* e1 = sh + gi * UpSmem<N>::SIZE;
+    RT* e1 = sh + gi * gstride<N>(UpSmem<N>::SIZE);
     RT* e2 = e1 + E::SIZE;
     RT* scr = e2 + E::SIZE;
     copy_in(e1, Pref + j * E::SIZE, E::SIZE, g.lr, N);
@@ -633,7 +632,7 @@ __global__ void __launch_bounds__(NG* N) k_m2roll(Args<R, RT> a, const RT* Pref)
     if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
-    R* gs = sh + gi * S::SIZE;
+    R* gs = sh + gi * gstride<N>(S::SIZE);
     R* P = gs + S::P;
     R* sb = gs + S::SB;
     R* scr = gs + S::SCR_OFF;
@@ -729,7 +728,7 @@ struct ResidSmem {  // work vectors and the step's matrices (odd row strides), t
                          LK = FK + N * lds(N), UKM = LK + N * lds(M), SIZE = UKM + M * lds(M);
     template <typename R>
     static constexpr int bytes() {
-        return (SIZE * (int)sizeof(R) + 15) / 16 * 16;
+        return gstride<N>(SIZE) * (int)sizeof(R);
     }
 };
 
@@ -911,7 +910,7 @@ __global__ void __launch_bounds__(NG* N) k_nresid(const Item<R>* items1, const I
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * gstride<N>(S::SIZE);
     D64* val = sh + S::VAL;
     D64* sb = sh + S::SB;
     D64* scr = sh + S::SCR;
@@ -977,7 +976,7 @@ __global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const I
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * S::SIZE;
+    D64* sh = reinterpret_cast<D64*>(smem_raw) + gi * gstride<N>(S::SIZE);
     D64* val = sh + S::VAL;
     D64* sb = sh + S::SB;
     D64* scr = sh + S::SCR;
@@ -1065,7 +1064,7 @@ __global__ void __launch_bounds__(NG* N) k_nresid_c(const Item<float>* items1,
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    float* sh = reinterpret_cast<float*>(smem_raw) + gi * S::SIZE;
+    float* sh = reinterpret_cast<float*>(smem_raw) + gi * gstride<N>(S::SIZE);
     float *SFh = sh + S::SFH, *SFl = sh + S::SFL, *SLh = sh + S::SLH, *SLl = sh + S::SLL;
     float *Wh = sh + S::WH, *Wl = sh + S::WL, *Gh = sh + S::GH, *Gl = sh + S::GL;
     float *GKh = sh + S::GKH, *GKl = sh + S::GKL, *XHh = sh + S::XHH, *XHl = sh + S::XHL;
@@ -1289,7 +1288,7 @@ __global__ void __launch_bounds__(NG* N) k_ngains_c(const Item<float>* items1,
     const Group<N> g;
     const int gi = threadIdx.x / N;
     const int r = g.lr;
-    float* sh = reinterpret_cast<float*>(smem_raw) + gi * S::SIZE;
+    float* sh = reinterpret_cast<float*>(smem_raw) + gi * gstride<N>(S::SIZE);
     float *SFh = sh + S::SFH, *SFl = sh + S::SFL, *SLh = sh + S::SLH, *SLl = sh + S::SLL;
     float *Wh = sh + S::WH, *Wl = sh + S::WL, *Gh = sh + S::GH, *Gl = sh + S::GL;
     float* Z = sh + S::Z;  // M x LD

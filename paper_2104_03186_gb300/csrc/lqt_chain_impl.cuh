@@ -28,13 +28,13 @@ static cudaError_t chain_allow_smem(Kernel k, bool* done, size_t bytes) {
 
 template <typename R, typename RT, int N, int M>
 struct Launcher {
-    static constexpr int FOLD_B = FoldSmem<N, M>::SIZE * (int)sizeof(R);
-    static constexpr int REFOLD_B = RefoldSmem<N, M>::SIZE * (int)sizeof(R);
-    static constexpr int UP_B = UpSmem<N>::SIZE * (int)sizeof(RT);
-    static constexpr int DOWN_B = DownSmem<N>::SIZE * (int)sizeof(RT);
-    static constexpr int FUP_B = FupSmem<N>::SIZE * (int)sizeof(RT);
-    static constexpr int FDOWN_B = FdownSmem<N>::SIZE * (int)sizeof(RT);
-    static constexpr int ROLL_B = RollSmem<N, M>::SIZE * (int)sizeof(R);
+    static constexpr int FOLD_B = gstride<N>(FoldSmem<N, M>::SIZE) * (int)sizeof(R);
+    static constexpr int REFOLD_B = gstride<N>(RefoldSmem<N, M>::SIZE) * (int)sizeof(R);
+    static constexpr int UP_B = gstride<N>(UpSmem<N>::SIZE) * (int)sizeof(RT);
+    static constexpr int DOWN_B = gstride<N>(DownSmem<N>::SIZE) * (int)sizeof(RT);
+    static constexpr int FUP_B = gstride<N>(FupSmem<N>::SIZE) * (int)sizeof(RT);
+    static constexpr int FDOWN_B = gstride<N>(FdownSmem<N>::SIZE) * (int)sizeof(RT);
+    static constexpr int ROLL_B = gstride<N>(RollSmem<N, M>::SIZE) * (int)sizeof(R);
     static constexpr int NG_FOLD = groups_for<N>(FOLD_B);
     static constexpr int NG_REFOLD = groups_for<N>(REFOLD_B);
     static constexpr int NG_UP = groups_for<N>(UP_B);
@@ -43,16 +43,16 @@ struct Launcher {
     static constexpr int NG_FDOWN = groups_for<N>(FDOWN_B);
     static constexpr int NG_ROLL = groups_for<N>(ROLL_B);
     static constexpr int RESID_B = ResidSmem<N, M>::template bytes<R>();
-    static constexpr int NEWTON_B = NewtonSmem<N, M>::SIZE * (int)sizeof(double);
+    static constexpr int NEWTON_B = gstride<N>(NewtonSmem<N, M>::SIZE) * (int)sizeof(double);
     static constexpr int NG_NEWTON = groups_for<N>(NEWTON_B);
     // FP32 problems: the compensated-FP32 Newton kernels
-    static constexpr int NEWTON_C_B = NewtonCSmem<N, M>::SIZE * (int)sizeof(float);
+    static constexpr int NEWTON_C_B = gstride<N>(NewtonCSmem<N, M>::SIZE) * (int)sizeof(float);
     static constexpr int NG_NEWTON_C = groups_for<N>(NEWTON_C_B);
-    static constexpr int NEWTON_G_B = NewtonGSmem<N, M>::SIZE * (int)sizeof(float);
+    static constexpr int NEWTON_G_B = gstride<N>(NewtonGSmem<N, M>::SIZE) * (int)sizeof(float);
     static constexpr int NG_NEWTON_G = groups_for<N>(NEWTON_G_B);
     static constexpr bool kCompNewton = sizeof(R) == 4;
     static constexpr int NG_RESID = groups_for<N>(RESID_B);
-    static constexpr int M2_B = M2Smem<N, M>::SIZE * (int)sizeof(R);
+    static constexpr int M2_B = gstride<N>(M2Smem<N, M>::SIZE) * (int)sizeof(R);
     static constexpr int NG_M2 = groups_for<N>(M2_B);
 
     static cudaError_t prepare() {

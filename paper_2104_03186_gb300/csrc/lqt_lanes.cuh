@@ -33,6 +33,18 @@ struct Group {
 // Row stride of a shared-memory matrix with `cols` columns: the next odd number.
 constexpr int lds(int cols) { return cols | 1; }
 
+// Distance, in elements, between the shared-memory blocks of neighbouring
+// groups: the block rounded up to 32 elements, plus N when several groups share
+// a warp.  The 32 / N groups of a warp then start N banks apart; with the odd
+// row strides of lds() the column sweeps of all lanes of the warp fall in
+// distinct banks (FP32; for FP64 within each half-warp wavefront), where an
+// unpadded block of a multiple of 32 elements put every group's lane r on one
+// bank.
+template <int N>
+constexpr int gstride(int size) {
+    return (size + 31) / 32 * 32 + (N < 32 ? N : 0);
+}
+
 // IEEE round-to-nearest reciprocal in the arithmetic type
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
