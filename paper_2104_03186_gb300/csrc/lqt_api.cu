@@ -186,13 +186,13 @@ Layout layout(const Variant& var, const Plan& plan, size_t es, const lqt_problem
     size_t off = kStatusBytes;
     const size_t t = (size_t)plan.tiles;
     L.tree = off;
-    off += align_up(t * var.elem * plan.W * es);
+    off += align_up(t * var.elem * tstride(plan.W, (int)es) * es);
     L.tile_agg = off;
     off += align_up(t * var.elem * es);
     L.tile_carry = off;
     off += align_up(t * var.value * es);
     L.ftree = off;
-    off += align_up(t * var.affine * plan.W * es);
+    off += align_up(t * var.affine * tstride(plan.W, (int)es) * es);
     L.ftile_agg = off;
     off += align_up(t * var.affine * es);
     L.ftile_x = off;

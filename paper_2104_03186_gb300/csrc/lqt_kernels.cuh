@@ -332,6 +332,18 @@ __device__ __forceinline__ void r_prefetch(const Params<R>& P, R* buf, long long
 // area.
 constexpr int kSmemHead = 16;
 
+// The in-tile and top-level trees are stored field-major: field f of tree slot
+// i sits at f * tstride(W, sizeof(R)) + tslot<R>(i).  One spare slot after
+// every 32 slots (16 for FP64) puts the slots that one tree level touches
+// (i = 2h t and 2h t + h, or 2h t + 2h - 1 and 2h t + h - 1) in distinct banks;
+// unpadded, threads of a level 2h slots apart shared banks up to 16-fold.
+__host__ __device__ constexpr int tree_shift(int es) { return es == 8 ? 4 : 5; }
+__host__ __device__ constexpr int tstride(int w, int es) { return w + (w >> tree_shift(es)); }
+template <typename R>
+__device__ __forceinline__ int tslot(int i) {
+    return i + (i >> tree_shift((int)sizeof(R)));
+}
+
 template <typename R, int N, int M, int W>
 struct Smem {
     static constexpr int NW = W / 32;
@@ -346,11 +358,12 @@ struct Smem {
     static constexpr int FX = 2 * FIN, FU = FX + round4(kStageG * N),
                          FC = FU + round4(kStageG * M), FR = FC + round4(kStageG * N),
                          FROW = FR + kStageG * 4;
-    static constexpr int UP_BIG = Dims<N>::ELEM * W;
-    static constexpr int DOWN_BIG_A = (Dims<N>::ELEM + Dims<N>::VALUE) * W;
+    static constexpr int WS = tstride(W, (int)sizeof(R));  // tree slots per field
+    static constexpr int UP_BIG = Dims<N>::ELEM * WS;
+    static constexpr int DOWN_BIG_A = (Dims<N>::ELEM + Dims<N>::VALUE) * WS;
     static constexpr int DOWN_BIG_B = NW * 32 * DROW;
     static constexpr int DOWN_BIG = DOWN_BIG_A > DOWN_BIG_B ? DOWN_BIG_A : DOWN_BIG_B;
-    static constexpr int FDOWN_BIG_A = (Dims<N>::AFFINE + N) * W;
+    static constexpr int FDOWN_BIG_A = (Dims<N>::AFFINE + N) * WS;
     static constexpr int FDOWN_BIG_B = NW * 32 * FROW;
     static constexpr int FDOWN_BIG = FDOWN_BIG_A > FDOWN_BIG_B ? FDOWN_BIG_A : FDOWN_BIG_B;
     static constexpr int RBUF = W * kRBuf;
@@ -388,8 +401,9 @@ __global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
     griddep_wait();
     using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][W]
+    R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][WS]
     R* sm = tree + SM::UP_BIG + SM::RBUF;
+    constexpr int WS = SM::WS;
     model_prologue<R, N, M>(P, sm);
 
     const int tid = threadIdx.x;
@@ -405,20 +419,21 @@ __global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
         load_step<R, N, M>(P, k, sm, nullptr, st);
         ok &= fold_step<R, N, M>(st, P.has_c != 0, acc);
     }
-    store_elem(acc, ElemView<R, N>{tree + tid, W});
+    store_elem(acc, ElemView<R, N>{tree + tslot<R>(tid), WS});
     __syncthreads();
     bool ok2 = true;
 #pragma unroll 1
     for (int h = 1; h < Weff; h <<= 1) {
         const int i = tid * 2 * h;
         if (i < Weff)
-            ok2 &= combine_view<R, N>(ElemView<R, N>{tree + i, W}, ElemView<R, N>{tree + i + h, W},
-                                      ElemView<R, N>{tree + i, W});
+            ok2 &= combine_view<R, N>(ElemView<R, N>{tree + tslot<R>(i), WS},
+                                      ElemView<R, N>{tree + tslot<R>(i + h), WS},
+                                      ElemView<R, N>{tree + tslot<R>(i), WS});
         __syncthreads();
     }
-    if (tid < Dims<N>::ELEM) P.tile_agg[(size_t)blockIdx.x * Dims<N>::ELEM + tid] = tree[tid * W];
-    cta_bulk_store(P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W, tree,
-                   (uint32_t)(Dims<N>::ELEM * W * sizeof(R)));
+    if (tid < Dims<N>::ELEM) P.tile_agg[(size_t)blockIdx.x * Dims<N>::ELEM + tid] = tree[tid * WS];
+    cta_bulk_store(P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS, tree,
+                   (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)));
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!ok2) set_status(P.status, ST_SINGULAR);
 }
@@ -462,8 +477,9 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     griddep_launch_dependents();
     griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw);            // [ELEM][TP]
-    R* carry = tree + (size_t)Dims<N>::ELEM * TP;        // [VALUE][TP]
+    constexpr int TS = tstride(TP, (int)sizeof(R));      // tree slots per field
+    R* tree = reinterpret_cast<R*>(smem_raw);            // [ELEM][TS]
+    R* carry = tree + (size_t)Dims<N>::ELEM * TS;        // [VALUE][TS]
     const int tid = threadIdx.x;
     const int tiles = P.tiles;
     const int g = tiles > 0 ? (tiles + TP - 1) / TP : 1;
@@ -474,10 +490,10 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
 
     // thread partial: tile totals t0..t1-1 folded right to left (neutral if empty)
     {
-        ElemView<R, N> mine{tree + tid, TP};
+        ElemView<R, N> mine{tree + tslot<R>(tid), TS};
         if (t1 > t0) {
             const R* src = P.tile_agg + (size_t)(t1 - 1) * Dims<N>::ELEM;
-            for (int k = 0; k < Dims<N>::ELEM; ++k) mine.p[k * TP] = src[k];
+            for (int k = 0; k < Dims<N>::ELEM; ++k) mine.p[k * TS] = src[k];
             for (int t = t1 - 2; t >= t0; --t)
                 ok &= combine_view<R, N>(
                     ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1}, mine,
@@ -493,14 +509,15 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     for (int h = 1; h < Teff; h <<= 1) {
         const int i = tid * 2 * h;
         if (i < Teff)
-            ok &= combine_view<R, N>(ElemView<R, N>{tree + i, TP}, ElemView<R, N>{tree + i + h, TP},
-                                     ElemView<R, N>{tree + i, TP});
+            ok &= combine_view<R, N>(ElemView<R, N>{tree + tslot<R>(i), TS},
+                                     ElemView<R, N>{tree + tslot<R>(i + h), TS},
+                                     ElemView<R, N>{tree + tslot<R>(i), TS});
         __syncthreads();
     }
     if (tid == 0) {
         Value<R, N> z;
         terminal_value<R, N>(P, z);
-        store_value(z, ValueView<R, N>{carry, TP});
+        store_value(z, ValueView<R, N>{carry, TS});
         R* ST = P.S + (size_t)P.T * N * N;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -517,17 +534,17 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
         const int i = tid * 2 * h;
         if (i < Teff) {
             Value<R, N> c;
-            load_value(c, ValueView<R, N>{carry + i, TP});
-            store_value(c, ValueView<R, N>{carry + i + h, TP});
-            ok &= value_apply<R, N>(ElemView<R, N>{tree + i + h, TP}, c);
-            store_value(c, ValueView<R, N>{carry + i, TP});
+            load_value(c, ValueView<R, N>{carry + tslot<R>(i), TS});
+            store_value(c, ValueView<R, N>{carry + tslot<R>(i + h), TS});
+            ok &= value_apply<R, N>(ElemView<R, N>{tree + tslot<R>(i + h), TS}, c);
+            store_value(c, ValueView<R, N>{carry + tslot<R>(i), TS});
         }
         __syncthreads();
     }
     // per-tile carries for this thread's tiles
     if (t1 > t0) {
         Value<R, N> c;
-        load_value(c, ValueView<R, N>{carry + tid, TP});
+        load_value(c, ValueView<R, N>{carry + tslot<R>(tid), TS});
         for (int t = t1 - 1; t >= t0; --t) {
             store_value(c, ValueView<R, N>{P.tile_carry + (size_t)t * Dims<N>::VALUE, 1});
             if (t > t0)
@@ -550,8 +567,9 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
-    R* tree = big;                                       // [ELEM][W]
-    R* carry = big + (size_t)Dims<N>::ELEM * W;          // [VALUE][W]
+    constexpr int WS = SM::WS;
+    R* tree = big;                                       // [ELEM][WS]
+    R* carry = big + (size_t)Dims<N>::ELEM * WS;         // [VALUE][WS]
     R* rbuf = big + SM::DOWN_BIG + threadIdx.x * kRBuf;
     R* sm = big + SM::DOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
@@ -568,11 +586,11 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
 
     uint32_t phase = 0;
-    const bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * W,
-                                       (uint32_t)(Dims<N>::ELEM * W * sizeof(R)), bar, phase);
+    const bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS,
+                                       (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)), bar, phase);
     const int Weff = next_pow2(geo.live(W));
     if (tid < Dims<N>::VALUE)
-        carry[tid * W] = P.tile_carry[(size_t)blockIdx.x * Dims<N>::VALUE + tid];
+        carry[tid * WS] = P.tile_carry[(size_t)blockIdx.x * Dims<N>::VALUE + tid];
     __syncthreads();
     bool ok_sing = true;
 #pragma unroll 1
@@ -580,15 +598,15 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
         const int i = tid * 2 * h;
         if (i < Weff) {
             Value<R, N> c;
-            load_value(c, ValueView<R, N>{carry + i, W});
-            store_value(c, ValueView<R, N>{carry + i + h, W});
-            ok_sing &= value_apply<R, N>(ElemView<R, N>{tree + i + h, W}, c);
-            store_value(c, ValueView<R, N>{carry + i, W});
+            load_value(c, ValueView<R, N>{carry + tslot<R>(i), WS});
+            store_value(c, ValueView<R, N>{carry + tslot<R>(i + h), WS});
+            ok_sing &= value_apply<R, N>(ElemView<R, N>{tree + tslot<R>(i + h), WS}, c);
+            store_value(c, ValueView<R, N>{carry + tslot<R>(i), WS});
         }
         __syncthreads();
     }
     Value<R, N> val;
-    load_value(val, ValueView<R, N>{carry + tid, W});
+    load_value(val, ValueView<R, N>{carry + tslot<R>(tid), WS});
     __syncthreads();  // the big area becomes the warp staging rows
 
     const int lane = tid & 31, warp = tid >> 5;
@@ -679,9 +697,9 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     __syncthreads();  // the big area becomes the forward tree
     // forward up-sweep (right-anchored): after level d, slot j = i + 2^{d+1} - 1
     // holds the composite of chunks [i, i + 2^{d+1}); slot i + 2^d - 1 keeps [i, i + 2^d)
-    R* ftree = big;  // [AFFINE][W]
+    R* ftree = big;  // [AFFINE][WS]
     {
-        AffineView<R, N> mine{ftree + tid, W};
+        AffineView<R, N> mine{ftree + tslot<R>(tid), WS};
 #pragma unroll
         for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -694,14 +712,16 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     for (int h = 1; h < Weff; h <<= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
         if (j < Weff)
-            affine_compose_view<R, N>(AffineView<R, N>{ftree + j - h, W}, AffineView<R, N>{ftree + j, W},
-                                      AffineView<R, N>{ftree + j, W});
+            affine_compose_view<R, N>(AffineView<R, N>{ftree + tslot<R>(j - h), WS},
+                                      AffineView<R, N>{ftree + tslot<R>(j), WS},
+                                      AffineView<R, N>{ftree + tslot<R>(j), WS});
         __syncthreads();
     }
     if (tid < Dims<N>::AFFINE)
-        P.ftile_agg[(size_t)blockIdx.x * Dims<N>::AFFINE + tid] = ftree[tid * W + Weff - 1];
-    cta_bulk_store(P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W, ftree,
-                   (uint32_t)(Dims<N>::AFFINE * W * sizeof(R)));
+        P.ftile_agg[(size_t)blockIdx.x * Dims<N>::AFFINE + tid] =
+            ftree[tid * WS + tslot<R>(Weff - 1)];
+    cta_bulk_store(P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * WS, ftree,
+                   (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)));
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!finite) set_status(P.status, ST_NONFINITE);
     if (!ok_sing) set_status(P.status, ST_SINGULAR);
@@ -717,8 +737,9 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
     griddep_launch_dependents();
     griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw);      // [AFFINE][TP]
-    R* xs = tree + (size_t)Dims<N>::AFFINE * TP;   // [N][TP]
+    constexpr int TS = tstride(TP, (int)sizeof(R));  // tree slots per field
+    R* tree = reinterpret_cast<R*>(smem_raw);      // [AFFINE][TS]
+    R* xs = tree + (size_t)Dims<N>::AFFINE * TS;   // [N][TS]
     const int tid = threadIdx.x;
     const int tiles = P.tiles;
     const int g = tiles > 0 ? (tiles + TP - 1) / TP : 1;
@@ -726,7 +747,7 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
     const int Teff = next_pow2(used);
     const int t0 = min(tid * g, tiles), t1 = min(t0 + g, tiles);
     {
-        AffineView<R, N> mine{tree + tid, TP};
+        AffineView<R, N> mine{tree + tslot<R>(tid), TS};
 #pragma unroll
         for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -742,15 +763,16 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
     for (int h = 1; h < Teff; h <<= 1) {
         const int j = tid * 2 * h + 2 * h - 1;
         if (j < Teff)
-            affine_compose_view<R, N>(AffineView<R, N>{tree + j - h, TP}, AffineView<R, N>{tree + j, TP},
-                                      AffineView<R, N>{tree + j, TP});
+            affine_compose_view<R, N>(AffineView<R, N>{tree + tslot<R>(j - h), TS},
+                                      AffineView<R, N>{tree + tslot<R>(j), TS},
+                                      AffineView<R, N>{tree + tslot<R>(j), TS});
         __syncthreads();
     }
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const R x0 = P.x0[i];
-            xs[i * TP + Teff - 1] = x0;
+            xs[i * TS + tslot<R>(Teff - 1)] = x0;
             if (!P.refine_add) P.x[i] = x0;  // second pass: x*_0 = x^_0 + 0 stays
         }
     }
@@ -761,19 +783,19 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
         if (j < Teff) {
             R xv[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) xv[i] = xs[i * TP + j];
+            for (int i = 0; i < N; ++i) xv[i] = xs[i * TS + tslot<R>(j)];
 #pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * TP + j - h] = xv[i];
-            affine_apply_view<R, N>(AffineView<R, N>{tree + j - h, TP}, xv);
+            for (int i = 0; i < N; ++i) xs[i * TS + tslot<R>(j - h)] = xv[i];
+            affine_apply_view<R, N>(AffineView<R, N>{tree + tslot<R>(j - h), TS}, xv);
 #pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * TP + j] = xv[i];
+            for (int i = 0; i < N; ++i) xs[i * TS + tslot<R>(j)] = xv[i];
         }
         __syncthreads();
     }
     if (t1 > t0) {
         R xv[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) xv[i] = xs[i * TP + tid];
+        for (int i = 0; i < N; ++i) xv[i] = xs[i * TS + tslot<R>(tid)];
         for (int t = t0; t < t1; ++t) {
 #pragma unroll
             for (int i = 0; i < N; ++i) P.ftile_x[(size_t)t * N + i] = xv[i];
@@ -796,19 +818,20 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
-    R* ftree = big;                                      // [AFFINE][W]
-    R* xs = big + (size_t)Dims<N>::AFFINE * W;           // [N][W]
+    constexpr int WS = SM::WS;
+    R* ftree = big;                                      // [AFFINE][WS]
+    R* xs = big + (size_t)Dims<N>::AFFINE * WS;          // [N][WS]
     R* sm = big + SM::FDOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
     if (tid == 0) mbar_init(bar, 1);
     model_prologue<R, N, M>(P, sm);
 
     uint32_t phase = 0;
-    const bool ok_load = cta_bulk_load(ftree, P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * W,
-                                       (uint32_t)(Dims<N>::AFFINE * W * sizeof(R)), bar, phase);
+    const bool ok_load = cta_bulk_load(ftree, P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * WS,
+                                       (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)), bar, phase);
     const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
     const int Weff = next_pow2(geo.live(W));
-    if (tid < N) xs[tid * W + Weff - 1] = P.ftile_x[(size_t)blockIdx.x * N + tid];
+    if (tid < N) xs[tid * WS + tslot<R>(Weff - 1)] = P.ftile_x[(size_t)blockIdx.x * N + tid];
     __syncthreads();
 #pragma unroll 1
     for (int h = Weff / 2; h >= 1; h >>= 1) {
@@ -816,12 +839,12 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
         if (j < Weff) {
             R xv[N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) xv[i] = xs[i * W + j];
+            for (int i = 0; i < N; ++i) xv[i] = xs[i * WS + tslot<R>(j)];
 #pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * W + j - h] = xv[i];
-            affine_apply_view<R, N>(AffineView<R, N>{ftree + j - h, W}, xv);
+            for (int i = 0; i < N; ++i) xs[i * WS + tslot<R>(j - h)] = xv[i];
+            affine_apply_view<R, N>(AffineView<R, N>{ftree + tslot<R>(j - h), WS}, xv);
 #pragma unroll
-            for (int i = 0; i < N; ++i) xs[i * W + j] = xv[i];
+            for (int i = 0; i < N; ++i) xs[i * WS + tslot<R>(j)] = xv[i];
         }
         __syncthreads();
     }
@@ -832,8 +855,8 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
     R x[N], xnext[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        x[i] = xs[i * W + tid];
-        xnext[i] = tid + 1 < W ? xs[i * W + tid + 1] : R(0);
+        x[i] = xs[i * WS + tslot<R>(tid)];
+        xnext[i] = tid + 1 < W ? xs[i * WS + tslot<R>(tid + 1)] : R(0);
     }
     if (tid == W - 1 && blockIdx.x + 1 < (unsigned)P.tiles) {
 #pragma unroll

@@ -55,9 +55,10 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
     using SM = Smem<R, N, M, W>;
     static bool done_up[64], done_top[64], done_down[64], done_ftop[64], done_fdown[64];
     const size_t smem_up = SM::bytes(SM::UP_BIG, P.p);
-    const size_t smem_top = (size_t)(Dims<N>::ELEM + Dims<N>::VALUE) * TP * sizeof(R);
+    constexpr int TS = tstride(TP, (int)sizeof(R));
+    const size_t smem_top = (size_t)(Dims<N>::ELEM + Dims<N>::VALUE) * TS * sizeof(R);
     const size_t smem_down = SM::bytes(SM::DOWN_BIG, P.p);
-    const size_t smem_ftop = (size_t)(Dims<N>::AFFINE + N) * TP * sizeof(R);
+    const size_t smem_ftop = (size_t)(Dims<N>::AFFINE + N) * TS * sizeof(R);
     const size_t smem_fdown = SM::bytes(SM::FDOWN_BIG, P.p);
     cudaError_t err;
     if ((err = allow_smem(k_bwd_up<R, N, M, W>, done_up, smem_up)) != cudaSuccess ||
