@@ -136,7 +136,8 @@ __device__ __forceinline__ void model_prologue(const Params<R>& P, R* sm) {
 // from the shared model area where the input is time-invariant.
 template <typename R, int N, int M>
 __device__ __forceinline__ void load_step(const Params<R>& P, long long k, const R* sm,
-                                          const R* r_staged, Step<R, N, M>& st) {
+                                          const R* r_staged, Step<R, N, M>& st,
+                                          int r_stride = 1) {
     using ML = ModelLayout<N, M>;
     if (P.dyn_invariant) {
 #pragma unroll
@@ -184,7 +185,7 @@ __device__ __forceinline__ void load_step(const Params<R>& P, long long k, const
         for (int i = 0; i < N; ++i) st.q[i] = R(0);
         if (r) {
             for (int a = 0; a < p; ++a) {
-                const R ra = r_staged ? r_staged[a] : __ldg(r + a);
+                const R ra = r_staged ? r_staged[a * r_stride] : __ldg(r + a);
 #pragma unroll
                 for (int i = 0; i < N; ++i) st.q[i] += sHX[a * N + i] * ra;
             }
@@ -307,23 +308,29 @@ __device__ __forceinline__ void fwd_group(long long s, long long e, int g, long 
 }
 
 // Per-thread prefetch of the references r_k of one staged group ahead
-// (p <= kRStage; two buffers of kStageG steps each).
+// (p <= kRStage; two buffers of kStageG steps each).  The buffers of a CTA are
+// slot-major: value q of thread t at q * W + t, so that the lanes of a warp
+// write and read consecutive words (a thread-major buffer of 16 values put
+// every lane of a warp on the same two banks).
 constexpr int kRStage = 4;
-constexpr int kRBuf = 2 * kStageG * kRStage;  // floats per thread
+constexpr int kRBuf = 2 * kStageG * kRStage;  // values per thread
 
 template <typename R>
 __device__ __forceinline__ bool r_stageable(const Params<R>& P) {
     return P.r != nullptr && P.p <= kRStage;
 }
 
-// Issue the copies of r for steps [lo, lo + cnt) into buf (slot jj at jj * kRStage)
-// and commit them as one group (an empty group when nothing is staged).
+// Issue the copies of r for steps [lo, lo + cnt) into buf (value a of slot jj
+// at (jj * kRStage + a) * stride) and commit them as one group (an empty group
+// when nothing is staged).
 template <typename R>
-__device__ __forceinline__ void r_prefetch(const Params<R>& P, R* buf, long long lo, int cnt) {
+__device__ __forceinline__ void r_prefetch(const Params<R>& P, R* buf, long long lo, int cnt,
+                                           int stride) {
     if (r_stageable(P))
         for (int jj = 0; jj < cnt; ++jj)
             for (int a = 0; a < P.p; ++a)
-                cp_async<sizeof(R)>(buf + jj * kRStage + a, P.r + (lo + jj) * P.sr + a);
+                cp_async<sizeof(R)>(buf + (jj * kRStage + a) * stride,
+                                    P.r + (lo + jj) * P.sr + a);
     cp_async_commit();
 }
 
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     constexpr int WS = SM::WS;
     R* tree = big;                                       // [ELEM][WS]
     R* carry = big + (size_t)Dims<N>::ELEM * WS;         // [VALUE][WS]
-    R* rbuf = big + SM::DOWN_BIG + threadIdx.x * kRBuf;
+    R* rbuf = big + SM::DOWN_BIG + threadIdx.x;  // slot-major, stride W
     R* sm = big + SM::DOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
     if (tid == 0) mbar_init(bar, 1);
@@ -581,7 +588,7 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
         long long lo;
         int cnt;
         bwd_group(s, e, 0, lo, cnt);
-        r_prefetch(P, rbuf, lo, cnt);
+        r_prefetch(P, rbuf, lo, cnt, W);
     }
     model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
 
@@ -628,7 +635,7 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
             long long lo1;
             int cnt1;
             bwd_group(s, e, g + 1, lo1, cnt1);
-            r_prefetch(P, rbuf + ((g + 1) & 1) * kStageG * kRStage, lo1, cnt1);
+            r_prefetch(P, rbuf + ((g + 1) & 1) * kStageG * kRStage * W, lo1, cnt1, W);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -636,11 +643,11 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
         long long lo;
         int cnt;
         bwd_group(s, e, g, lo, cnt);
-        const R* rg = rbuf + (g & 1) * kStageG * kRStage;
+        const R* rg = rbuf + (g & 1) * kStageG * kRStage * W;
         for (int jj = cnt - 1; jj >= 0; --jj) {
             const long long k = lo + jj;
             Step<R, N, M> st;
-            load_step<R, N, M>(P, k, sm, staged ? rg + jj * kRStage : nullptr, st);
+            load_step<R, N, M>(P, k, sm, staged ? rg + jj * kRStage * W : nullptr, st, W);
             R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
             ok &= riccati_step<R, N, M>(st, P.has_c != 0, val.S, val.v, K, d, Ft, ct, Rc, Rinv);
             // records of step k into this lane's staging row
