@@ -175,10 +175,20 @@ int refine_r_stride(int p) { return p <= kRStage ? kRStage : p; }
 
 struct Layout {
     size_t tree, tile_agg, tile_carry, ftree, ftile_agg, ftile_x;
+    // refinement: maps recorded by the first pass's top-level scan (0: none)
+    size_t top_fac;
     // refinement: shifted references and offsets, zero initial state
     size_t rp, rTp, cp, x0p;
     size_t total;
 };
+
+// The second pass of a refined solve replays the first pass's top-level
+// backward scan from recorded maps when every top-scan thread holds one tile
+// and the staged maps fit the CTA's shared memory.
+bool top_replay(const Variant& var, const Plan& plan, size_t es) {
+    return plan.tiles > 0 && plan.tiles <= var.TP &&
+           top_smem_bytes(var.elem, var.value, var.n, var.TP, (int)es, true) <= kTopSmemMax;
+}
 
 Layout layout(const Variant& var, const Plan& plan, size_t es, const lqt_problem* P,
               bool refine) {
@@ -198,6 +208,11 @@ Layout layout(const Variant& var, const Plan& plan, size_t es, const lqt_problem
     L.ftile_x = off;
     off += align_up(t * var.n * es);
     L.rp = L.rTp = L.cp = L.x0p = 0;
+    L.top_fac = 0;
+    if (refine && top_replay(var, plan, es)) {
+        L.top_fac = off;
+        off += align_up((size_t)top_fac_elems(var.n, var.TP) * es);
+    }
     if (refine) {
         const size_t T = (size_t)P->T, n = (size_t)P->n;
         L.rp = off;
@@ -254,6 +269,7 @@ void fill_params(Params<R>& K, const lqt_problem* P, const lqt_solution* sol, vo
         K.ftree = reinterpret_cast<R*>(base + L->ftree);
         K.ftile_agg = reinterpret_cast<R*>(base + L->ftile_agg);
         K.ftile_x = reinterpret_cast<R*>(base + L->ftile_x);
+        if (L->top_fac) K.top_fac = reinterpret_cast<R*>(base + L->top_fac);
         if (L->rp | L->rTp | L->cp | L->x0p) {
             K.rp = reinterpret_cast<R*>(base + L->rp);
             K.rTp = reinterpret_cast<R*>(base + L->rTp);
@@ -393,6 +409,9 @@ lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution
     K.out_mask = out_mask;
     K.refine_emit = refine_emit;
     K.refine_add = refine_add;
+    // the first pass of a refined solve records the top scan's maps, the
+    // second (same matrices) replays them
+    K.top_mode = K.top_fac ? (refine_add ? 2 : (refine_emit ? 1 : 0)) : 0;
     if (sequential) {
         if (prof) prof_mark(prof, s, refine_add ? "riccati_seq.refine" : "riccati_seq");
         return var.seq(&K, s);

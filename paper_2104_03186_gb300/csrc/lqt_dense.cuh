@@ -428,11 +428,20 @@ __device__ __forceinline__ bool solve_pivoted(R (&Mx)[N][N], R (&B)[N][NR]) {
 //   eta = X1^T (eta2 - J2 b1) + eta1,  J = A1^T J2 X1 + J1
 // using (I + J2 C1)^{-1} = M^{-T} and M^{-T} J2 = J2 M^{-1} (C, J symmetric).
 // `out` may alias e1 (in-place up-sweep); it must not alias e2.
+//
+// The vector parts are linear in the operands' vectors,
+//   b = b2 + G1 b1 + G2 eta2,   eta = eta1 + H1 eta2 + H2 b1,
+// with G1 = A2 M^{-1}, G2 = A2 M^{-1} C1, H1 = X1^T, H2 = -(J2 X1)^T.  With REC
+// the elimination also carries I (for M^{-1}) and the four maps are written
+// to fac (4 N^2 values, row-major G1 | G2 | H1 | H2), so that a problem with
+// the same matrices and other vectors can be combined by combine_replay.
+// Entry e of the maps is stored at fac[e * fs].
 // ---------------------------------------------------------------------------
-template <typename R, int N>
+template <typename R, int N, bool REC = false>
 __device__ __forceinline__ bool combine_view(ElemView<R, N> e1, ElemView<R, N> e2,
-                                             ElemView<R, N> out) {
-    constexpr int NR = 2 * N + 1;
+                                             ElemView<R, N> out, R* fac = nullptr, int fs = 1) {
+    constexpr int NI = 2 * N + 1;  // first column of I when recording
+    constexpr int NR = NI + (REC ? N : 0);
     R Mx[N][N];
     R B[N][NR];
 #pragma unroll
@@ -445,6 +454,7 @@ __device__ __forceinline__ bool combine_view(ElemView<R, N> e1, ElemView<R, N> e
             Mx[i][j] = t;
             B[i][j] = e1.A(i, j);
             B[i][N + 1 + j] = e1.C(i, j);
+            if constexpr (REC) B[i][NI + j] = (i == j) ? R(1) : R(0);
         }
         R t = e1.b(i);
 #pragma unroll
@@ -520,6 +530,21 @@ __device__ __forceinline__ bool combine_view(ElemView<R, N> e1, ElemView<R, N> e
             for (int k = 0; k < N; ++k) t += T3[i][k] * e2.A(j, k);
             Cn[sym<N>(i, j)] = t;
         }
+    if constexpr (REC) {
+        // T3 = A2 M^{-1} C1 is G2; e2 is not aliased by out
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                R g = R(0);
+#pragma unroll
+                for (int k = 0; k < N; ++k) g += e2.A(i, k) * B[k][NI + j];
+                fac[(i * N + j) * fs] = g;
+                fac[(N * N + i * N + j) * fs] = T3[i][j];
+                fac[(2 * N * N + i * N + j) * fs] = B[j][i];
+                fac[(3 * N * N + i * N + j) * fs] = -JX[j][i];
+            }
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
 #pragma unroll
@@ -535,14 +560,45 @@ __device__ __forceinline__ bool combine_view(ElemView<R, N> e1, ElemView<R, N> e
     return ok;
 }
 
+// The vector parts of e1 (x) e2 from the maps combine_view<REC> recorded for
+// operands with the same matrices: out.b, out.eta (out may alias e1).
+template <typename R, int N>
+__device__ __forceinline__ void combine_replay(const R* fac, int fs, ElemView<R, N> e1,
+                                               ElemView<R, N> e2, ElemView<R, N> out) {
+    R b1[N], h1[N], b2[N], h2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        b1[i] = e1.b(i);
+        h1[i] = e1.eta(i);
+        b2[i] = e2.b(i);
+        h2[i] = e2.eta(i);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        R b = b2[i], h = h1[i];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            b += fac[(i * N + k) * fs] * b1[k] + fac[(N * N + i * N + k) * fs] * h2[k];
+            h += fac[(2 * N * N + i * N + k) * fs] * h2[k] +
+                 fac[(3 * N * N + i * N + k) * fs] * b1[k];
+        }
+        out.b(i) = b;
+        out.eta(i) = h;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Value carry through an element: (S, v) <- value part of P (x) (0, 0, 0, v, S)
 // (eq. lqt_comb with A2 = b2 = C2 = 0, as in the proof of Lemma LQT_assoc):
 //   X1 = (I + C_P S)^{-1} A_P
 //   S <- A_P^T S X1 + J_P,   v <- X1^T (v - S b_P) + eta_P
+// With REC the maps of the vector part, v <- eta_P + V1 v + V2 b_P with
+// V1 = X1^T and V2 = -(S X1)^T, are written to fac (2 N^2 values, V1 | V2)
+// for value_replay (entry e at fac[e * fs]).
 // ---------------------------------------------------------------------------
-template <typename R, int N>
-__device__ __forceinline__ bool value_apply(ElemView<R, N> P, Value<R, N>& val) {
+template <typename R, int N, bool REC = false>
+__device__ __forceinline__ bool value_apply(ElemView<R, N> P, Value<R, N>& val,
+                                            R* fac = nullptr, int fs = 1) {
     R Mx[N][N];
     R X[N][N];
 #pragma unroll
@@ -581,6 +637,15 @@ __device__ __forceinline__ bool value_apply(ElemView<R, N> P, Value<R, N>& val) 
         for (int k = 0; k < N; ++k) t += X[k][i] * e[k];
         val.v[i] = t;
     }
+    if constexpr (REC) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                fac[(i * N + j) * fs] = X[j][i];
+                fac[(N * N + i * N + j) * fs] = -SX[j][i];
+            }
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -591,6 +656,24 @@ __device__ __forceinline__ bool value_apply(ElemView<R, N> P, Value<R, N>& val) 
             val.S[sym<N>(i, j)] = t;
         }
     return ok;
+}
+
+// The vector part of value_apply from the maps value_apply<REC> recorded
+// for an element and a value with the same matrices: v <- eta_P + V1 v + V2 b_P.
+template <typename R, int N>
+__device__ __forceinline__ void value_replay(const R* fac, int fs, ElemView<R, N> P,
+                                             R (&v)[N]) {
+    R vn[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        R t = P.eta(i);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            t += fac[(i * N + k) * fs] * v[k] + fac[(N * N + i * N + k) * fs] * P.b(k);
+        vn[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = vn[i];
 }
 
 template <typename R, int N>

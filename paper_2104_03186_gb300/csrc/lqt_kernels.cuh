@@ -75,6 +75,11 @@ struct Params {
     int out_mask;        // OUT_S | OUT_V | OUT_K: which of S, v, K this pass writes
     int refine_emit;     // first pass of a refined solve: write r', c', r'_T, x'_0
     int refine_add;      // second pass: x <- x + xi instead of x <- xi
+    // top-level backward scan: 0 full operators; 1 full operators that also
+    // record the maps of their vector parts in top_fac; 2 the vector parts
+    // alone from top_fac (a pass whose matrices equal the recording pass's)
+    int top_mode;
+    R* top_fac;
 };
 
 __device__ __forceinline__ void set_status(int* status, int code) {
@@ -351,6 +356,32 @@ __device__ __forceinline__ int tslot(int i) {
     return i + (i >> tree_shift((int)sizeof(R)));
 }
 
+// Factor store of the top-level backward scan (k_bwd_top, modes 1 and 2):
+// the 4 N^2 map entries of each of the up-sweep's combines (combine_view<REC>),
+// then the 2 N^2 of each of the down-sweep's value applies (value_apply<REC>).
+// Entry-major: entry e of node u at e * tp + u (fewer than tp nodes per
+// sweep), so that the threads of a level, which handle consecutive nodes,
+// touch consecutive words.
+__host__ __device__ constexpr int top_fac_up(int n) { return 4 * n * n; }
+__host__ __device__ constexpr int top_fac_dn(int n) { return 2 * n * n; }
+__host__ __device__ constexpr long long top_fac_elems(int n, int tp) {
+    return (long long)tp * (top_fac_up(n) + top_fac_dn(n));
+}
+// Dynamic shared memory of k_bwd_top: the tree and the carries, plus the
+// staged factor store when it replays.
+// Staging area of the tile totals (one per thread at most), whole 16-byte units.
+__host__ __device__ constexpr long long top_stage_elems(int elem, int tp, int es) {
+    return ((long long)tp * elem * es + 15) / 16 * 16 / es;
+}
+__host__ __device__ constexpr long long top_smem_bytes(int elem, int value, int n, int tp,
+                                                       int es, bool replay) {
+    return ((long long)(elem + value) * tstride(tp, es) + (replay ? top_fac_elems(n, tp) : 0) +
+            top_stage_elems(elem, tp, es)) *
+               es +
+           16;  // the mbarrier of the bulk copies
+}
+constexpr long long kTopSmemMax = 227 * 1024;
+
 template <typename R, int N, int M, int W>
 struct Smem {
     static constexpr int NW = W / 32;
@@ -479,49 +510,70 @@ __device__ __forceinline__ void terminal_value(const Params<R>& P, Value<R, N>& 
 // (g = ceil(tiles / TP)), the CTA sweeps the partial totals, and the value
 // carries flow back from the terminal value (S_T, v_T) of Lemma LQT_assoc.
 // ===========================================================================
-template <typename R, int N, int TP>
+// MODE (the pass's Params::top_mode) selects the kernel: 0 full operators,
+// 1 full operators recording their maps, 2 replay.  One kernel per mode keeps
+// each one's code small: the single warp that works at the upper levels
+// otherwise stalls on instruction fetch.  Modes 1 and 2 need one tile per
+// thread (tiles <= TP), which the host checks.
+template <typename R, int N, int TP, int MODE>
 __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     griddep_launch_dependents();
     griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TS = tstride(TP, (int)sizeof(R));      // tree slots per field
+    constexpr int FU = top_fac_up(N), FD = top_fac_dn(N);
     R* tree = reinterpret_cast<R*>(smem_raw);            // [ELEM][TS]
     R* carry = tree + (size_t)Dims<N>::ELEM * TS;        // [VALUE][TS]
+    R* sfac = carry + (size_t)Dims<N>::VALUE * TS;       // mode 2: staged factor store
     const int tid = threadIdx.x;
     const int tiles = P.tiles;
     const int g = tiles > 0 ? (tiles + TP - 1) / TP : 1;
     const int used = tiles > 0 ? (tiles + g - 1) / g : 1;
     const int Teff = next_pow2(used);
     const int t0 = min(tid * g, tiles), t1 = min(t0 + g, tiles);
+    constexpr int mode = MODE;
+    if (mode != 0 && g != 1) {  // the factor store covers one tile per thread
+        if (tid == 0) set_status(P.status, ST_SINGULAR);
+        return;
+    }
     bool ok = true;
 
+    // Shared memory after the carries: [mode 2: the recorded maps of both
+    // sweeps] | the tile totals as stored ([tiles][ELEM], one tile per thread)
+    // | the mbarrier of the bulk copies that bring both in.
+    constexpr int E = Dims<N>::ELEM;
+    constexpr long long kFacElems = mode == 2 ? top_fac_elems(N, TP) : 0;
+    constexpr uint32_t kFacBytes = (uint32_t)(kFacElems * sizeof(R));
+    static_assert(kFacBytes % 16 == 0, "bulk copy of 16-byte multiples");
+    R* stg = sfac + kFacElems;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(stg + top_stage_elems(E, TP, (int)sizeof(R)));
+    const bool bulk = g == 1 && tiles > 0;  // tile totals by bulk copy
+    const bool stage = mode == 2 && Teff > 1;
+    // the copy may round up past the last tile into the buffer's alignment padding
+    const uint32_t agg_bytes = (uint32_t)(((size_t)tiles * E * sizeof(R) + 15) / 16 * 16);
+    if ((bulk || stage) && tid == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (stage ? kFacBytes : 0u) + (bulk ? agg_bytes : 0u));
+        if (stage) bulk_g2s(sfac, P.top_fac, kFacBytes, bar);
+        if (bulk) bulk_g2s(stg, P.tile_agg, agg_bytes, bar);
+    }
     // thread partial: tile totals t0..t1-1 folded right to left (neutral if empty)
-    {
-        ElemView<R, N> mine{tree + tslot<R>(tid), TS};
-        if (t1 > t0) {
-            const R* src = P.tile_agg + (size_t)(t1 - 1) * Dims<N>::ELEM;
-            for (int k = 0; k < Dims<N>::ELEM; ++k) mine.p[k * TS] = src[k];
-            for (int t = t1 - 2; t >= t0; --t)
-                ok &= combine_view<R, N>(
-                    ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1}, mine,
-                    mine);
-        } else {
-            Elem<R, N> e;
-            set_neutral(e);
-            store_elem(e, mine);
-        }
+    ElemView<R, N> mine{tree + tslot<R>(tid), TS};
+    if (mode == 0 && !bulk && t1 > t0) {  // several tiles per thread (mode 0 only)
+        const R* src = P.tile_agg + (size_t)(t1 - 1) * E;
+        for (int k = 0; k < E; ++k) mine.p[k * TS] = src[k];
+        for (int t = t1 - 2; t >= t0; --t)
+            ok &= combine_view<R, N>(
+                ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * E, 1}, mine, mine);
     }
-    __syncthreads();
-#pragma unroll 1
-    for (int h = 1; h < Teff; h <<= 1) {
-        const int i = tid * 2 * h;
-        if (i < Teff)
-            ok &= combine_view<R, N>(ElemView<R, N>{tree + tslot<R>(i), TS},
-                                     ElemView<R, N>{tree + tslot<R>(i + h), TS},
-                                     ElemView<R, N>{tree + tslot<R>(i), TS});
-        __syncthreads();
+    if (t1 <= t0) {
+        Elem<R, N> e;
+        set_neutral(e);
+        store_elem(e, mine);
     }
-    if (tid == 0) {
+    // The terminal value (S_T, v_T) seeds the down-sweep.  The last thread
+    // never combines in the up-sweep (Teff <= TP), so it forms it meanwhile.
+    if (tid == TP - 1) {
         Value<R, N> z;
         terminal_value<R, N>(P, z);
         store_value(z, ValueView<R, N>{carry, TS});
@@ -535,28 +587,98 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
             if (P.out_mask & OUT_V) P.v[(size_t)P.T * N + i] = z.v[i];
         }
     }
+    __syncthreads();  // the mbarrier is initialised before anyone waits on it
+    if (bulk || stage) {
+        const bool ok_load = mbar_wait(bar, 0);
+        if (!ok_load) {
+            mbar_wait(bar, 0);  // one more bounded wait for the copies in flight
+            if (tid == 0) set_status(P.status, ST_TIMEOUT);
+        }
+    }
+    if (bulk && t1 > t0) {
+        // this thread's tile total into its tree slot (mode 2: the vectors alone)
+        const R* row = stg + (size_t)tid * E;
+        if (mode == 2) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                mine.b(k) = row[Dims<N>::OB + k];
+                mine.eta(k) = row[Dims<N>::OE + k];
+            }
+        } else {
+#pragma unroll 4
+            for (int k = 0; k < E; ++k) mine.p[k * TS] = row[k];
+        }
+    }
     __syncthreads();
+    // up-sweep; the combines of level h are numbered after those of the lower
+    // levels (Teff / 2h of them), thread order within a level
+    int node = 0;
+#pragma unroll 1
+    for (int h = 1; h < Teff; h <<= 1) {
+        const int i = tid * 2 * h;
+        if (i < Teff) {
+            const ElemView<R, N> e1{tree + tslot<R>(i), TS}, e2{tree + tslot<R>(i + h), TS};
+            if (mode == 2)
+                combine_replay<R, N>(sfac + node + tid, TP, e1, e2, e1);
+            else if (mode == 1)
+                ok &= combine_view<R, N, true>(e1, e2, e1, P.top_fac + node + tid, TP);
+            else
+                ok &= combine_view<R, N>(e1, e2, e1);
+        }
+        node += Teff / (2 * h);
+        __syncthreads();
+    }
+    // down-sweep, applies numbered the same way from the top level
+    R* gdn = P.top_fac + (long long)TP * FU;
+    const R* sdn = sfac + (long long)TP * FU;
+    node = 0;
 #pragma unroll 1
     for (int h = Teff / 2; h >= 1; h >>= 1) {
         const int i = tid * 2 * h;
         if (i < Teff) {
-            Value<R, N> c;
-            load_value(c, ValueView<R, N>{carry + tslot<R>(i), TS});
-            store_value(c, ValueView<R, N>{carry + tslot<R>(i + h), TS});
-            ok &= value_apply<R, N>(ElemView<R, N>{tree + tslot<R>(i + h), TS}, c);
-            store_value(c, ValueView<R, N>{carry + tslot<R>(i), TS});
+            const ValueView<R, N> ci{carry + tslot<R>(i), TS}, ch{carry + tslot<R>(i + h), TS};
+            const ElemView<R, N> el{tree + tslot<R>(i + h), TS};
+            if (mode == 2) {
+                // the values' S equal the recording pass's: only v moves
+                R v[N];
+#pragma unroll
+                for (int k = 0; k < N; ++k) v[k] = ci.v(k);
+#pragma unroll
+                for (int k = 0; k < N; ++k) ch.v(k) = v[k];
+                value_replay<R, N>(sdn + node + tid, TP, el, v);
+#pragma unroll
+                for (int k = 0; k < N; ++k) ci.v(k) = v[k];
+            } else {
+                Value<R, N> c;
+                load_value(c, ci);
+                store_value(c, ch);
+                if (mode == 1)
+                    ok &= value_apply<R, N, true>(el, c, gdn + node + tid, TP);
+                else
+                    ok &= value_apply<R, N>(el, c);
+                store_value(c, ci);
+            }
         }
+        node += Teff / (2 * h);
         __syncthreads();
     }
     // per-tile carries for this thread's tiles
     if (t1 > t0) {
-        Value<R, N> c;
-        load_value(c, ValueView<R, N>{carry + tslot<R>(tid), TS});
-        for (int t = t1 - 1; t >= t0; --t) {
-            store_value(c, ValueView<R, N>{P.tile_carry + (size_t)t * Dims<N>::VALUE, 1});
-            if (t > t0)
-                ok &= value_apply<R, N>(
-                    ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1}, c);
+        if (mode == 2) {
+            // S of the carries stays as the recording pass wrote it
+            R* dst = P.tile_carry + (size_t)t0 * Dims<N>::VALUE + Dims<N>::SYM;
+#pragma unroll
+            for (int k = 0; k < N; ++k) dst[k] = carry[(Dims<N>::SYM + k) * TS + tslot<R>(tid)];
+        } else {
+            Value<R, N> c;
+            load_value(c, ValueView<R, N>{carry + tslot<R>(tid), TS});
+            for (int t = t1 - 1; t >= t0; --t) {
+                store_value(c, ValueView<R, N>{P.tile_carry + (size_t)t * Dims<N>::VALUE, 1});
+                if (t > t0)
+                    ok &= value_apply<R, N>(
+                        ElemView<R, N>{const_cast<R*>(P.tile_agg) + (size_t)t * Dims<N>::ELEM, 1},
+                        c);
+            }
         }
     }
     if (!ok) set_status(P.status, ST_SINGULAR);

@@ -53,16 +53,24 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
     constexpr int W = tile_threads<R, N, M>();
     constexpr int TP = top_threads();
     using SM = Smem<R, N, M, W>;
-    static bool done_up[64], done_top[64], done_down[64], done_ftop[64], done_fdown[64];
+    static bool done_up[64], done_top[64], done_top1[64], done_top2[64], done_down[64],
+        done_ftop[64], done_fdown[64];
     const size_t smem_up = SM::bytes(SM::UP_BIG, P.p);
-    constexpr int TS = tstride(TP, (int)sizeof(R));
-    const size_t smem_top = (size_t)(Dims<N>::ELEM + Dims<N>::VALUE) * TS * sizeof(R);
+    constexpr long long kTopReplay =
+        top_smem_bytes(Dims<N>::ELEM, Dims<N>::VALUE, N, TP, (int)sizeof(R), true);
+    const size_t smem_top_full = (size_t)top_smem_bytes(Dims<N>::ELEM, Dims<N>::VALUE, N, TP,
+                                                        (int)sizeof(R), false);
+    const size_t smem_top_max = kTopReplay <= kTopSmemMax ? (size_t)kTopReplay : smem_top_full;
+    const size_t smem_top = P.top_mode == 2 ? (size_t)kTopReplay : smem_top_full;
+    if (smem_top > smem_top_max) return LQT_EINVAL;
     const size_t smem_down = SM::bytes(SM::DOWN_BIG, P.p);
-    const size_t smem_ftop = (size_t)(Dims<N>::AFFINE + N) * TS * sizeof(R);
+    const size_t smem_ftop = (size_t)(Dims<N>::AFFINE + N) * tstride(TP, (int)sizeof(R)) * sizeof(R);
     const size_t smem_fdown = SM::bytes(SM::FDOWN_BIG, P.p);
     cudaError_t err;
     if ((err = allow_smem(k_bwd_up<R, N, M, W>, done_up, smem_up)) != cudaSuccess ||
-        (err = allow_smem(k_bwd_top<R, N, TP>, done_top, smem_top)) != cudaSuccess ||
+        (err = allow_smem(k_bwd_top<R, N, TP, 0>, done_top, smem_top_full)) != cudaSuccess ||
+        (err = allow_smem(k_bwd_top<R, N, TP, 1>, done_top1, smem_top_full)) != cudaSuccess ||
+        (err = allow_smem(k_bwd_top<R, N, TP, 2>, done_top2, smem_top_max)) != cudaSuccess ||
         (err = allow_smem(k_bwd_down<R, N, M, W>, done_down, smem_down)) != cudaSuccess ||
         (err = allow_smem(k_fwd_top<R, N, TP>, done_ftop, smem_ftop)) != cudaSuccess ||
         (err = allow_smem(k_fwd_down<R, N, M, W>, done_fdown, smem_fdown)) != cudaSuccess)
@@ -75,7 +83,10 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
         if (err != cudaSuccess) return LQT_ECUDA;
     }
     prof_mark(prof, stream, P.refine_add ? "bwd_top.refine" : "bwd_top");
-    err = launch_pdl<R>(k_bwd_top<R, N, TP>, 1, TP, smem_top, stream, P, pdl);
+    err = launch_pdl<R>(P.top_mode == 2   ? k_bwd_top<R, N, TP, 2>
+                        : P.top_mode == 1 ? k_bwd_top<R, N, TP, 1>
+                                          : k_bwd_top<R, N, TP, 0>,
+                        1, TP, smem_top, stream, P, pdl);
     if (err != cudaSuccess) return LQT_ECUDA;
     if (tiles > 0) {
         prof_mark(prof, stream, P.refine_add ? "bwd_down.refine" : "bwd_down");
