@@ -240,6 +240,24 @@ def test_refined_fp64_on_request():
     compare(gpu_solve(prob, dtype=np.float64, refine=1), oracle_solve(prob), FP64_TOL)
 
 
+@pytest.mark.parametrize("dt_nm", [("f32", 1, 1), ("f32", 2, 1), ("f32", 3, 2), ("f32", 4, 4),
+                                   ("f64", 1, 1), ("f64", 2, 2)],
+                         ids=lambda v: "%s_n%d_m%d" % v)
+@pytest.mark.parametrize("T", [700, 150001])
+def test_refined_second_pass_replays_top_scan(dt_nm, T):
+    """The refinement pass runs its top-level backward scan from the maps the
+    first pass recorded (FP32 at every n <= 4, FP64 at n <= 2, where they fit
+    the CTA's shared memory): a few tiles (one or two levels) and about 150
+    tiles (eight levels), time-varying random data."""
+    dt, n, m = dt_nm
+    prob = inputs.random_problem(n, m, min(n, 2), T=T, seed=300 + n + m)
+    if dt == "f32":
+        prob = _f32(prob)
+        compare(gpu_solve(prob, refine=1), oracle_solve(prob), FP32_TOL)
+    else:
+        compare(gpu_solve(prob, dtype=np.float64, refine=1), oracle_solve(prob), FP64_TOL)
+
+
 def test_sequential_baseline_refined_matches_parallel():
     prob = _f32(inputs.vehicle(20000, seed=6))
     o = oracle_solve(prob)
