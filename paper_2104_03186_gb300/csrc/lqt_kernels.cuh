@@ -532,7 +532,9 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     const int Teff = next_pow2(used);
     const int t0 = min(tid * g, tiles), t1 = min(t0 + g, tiles);
     constexpr int mode = MODE;
-    if (mode != 0 && g != 1) {  // the factor store covers one tile per thread
+    if (mode != 0 && g != 1) {
+        // the factor store covers one tile per thread; the host rejects other
+        // plans before launching, so this only guards against a bad caller
         if (tid == 0) set_status(P.status, ST_SINGULAR);
         return;
     }

@@ -62,7 +62,9 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
                                                         (int)sizeof(R), false);
     const size_t smem_top_max = kTopReplay <= kTopSmemMax ? (size_t)kTopReplay : smem_top_full;
     const size_t smem_top = P.top_mode == 2 ? (size_t)kTopReplay : smem_top_full;
-    if (smem_top > smem_top_max) return LQT_EINVAL;
+    // recording and replay need one tile per top-scan thread (layout() only
+    // reserves the factor store then); k_bwd_top re-checks
+    if (smem_top > smem_top_max || (P.top_mode != 0 && plan.tiles > TP)) return LQT_EINVAL;
     const size_t smem_down = SM::bytes(SM::DOWN_BIG, P.p);
     const size_t smem_ftop = (size_t)(Dims<N>::AFFINE + N) * tstride(TP, (int)sizeof(R)) * sizeof(R);
     const size_t smem_fdown = SM::bytes(SM::FDOWN_BIG, P.p);
