@@ -2,6 +2,8 @@
 // planning, workspace layout, dispatch to the compiled (dtype, n, m) variants,
 // kernel timing and the host-buffer solve.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 #include <string.h>
 
@@ -24,16 +26,17 @@ constexpr size_t kStatusBytes = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int sm_count_current() {
-    static int cache[64];
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (cache[dev] == 0) {
+    if (cache[dev].load(std::memory_order_relaxed) == 0) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;
-        cache[dev] = sms;
+        cache[dev].store(sms, std::memory_order_relaxed);
+        return sms;
     }
-    return cache[dev];
+    return cache[dev].load(std::memory_order_relaxed);
 }
 
 size_t elem_bytes(int dtype) { return dtype == LQT_F64 ? 8 : 4; }

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 
 #include "lqt_batch.cuh"
@@ -13,7 +15,7 @@ template <int N, int M, int NG>
 void launch_batch(const BatchDesc* d, int count, int* ticket, int* status, cudaStream_t s,
                   cudaError_t* err) {
     using Lay = batch::Layout<N, M, NG>;
-    static bool attr[64];
+    static std::atomic<bool> attr[64];
     int dev = 0;
     if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return;
     const size_t smem = Lay::bytes();

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <string.h>
 
 #include <vector>
@@ -15,7 +17,7 @@ namespace lqt {
 namespace chain {
 
 template <typename Kernel>
-static cudaError_t chain_allow_smem(Kernel k, bool* done, size_t bytes) {
+static cudaError_t chain_allow_smem(Kernel k, std::atomic<bool>* done, size_t bytes) {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
@@ -56,7 +58,7 @@ struct Launcher {
     static constexpr int NG_M2 = groups_for<N>(M2_B);
 
     static cudaError_t prepare() {
-        static bool d_fold[64], d_refold[64], d_up[64], d_down[64], d_fup[64], d_fdown[64],
+        static std::atomic<bool> d_fold[64], d_refold[64], d_up[64], d_down[64], d_fup[64], d_fdown[64],
             d_roll[64];
         cudaError_t e;
         if ((e = chain_allow_smem(k_cfold<R, RT, N, M, NG_FOLD>, d_fold,
@@ -72,7 +74,7 @@ struct Launcher {
             (e = chain_allow_smem(k_cfdown<RT, N, NG_FDOWN>, d_fdown,
                                   (size_t)NG_FDOWN * FDOWN_B)) != cudaSuccess)
             return e;
-        static bool d_nres[64], d_ngain[64], d_resid[64], d_m2up[64], d_m2down[64], d_m2roll[64];
+        static std::atomic<bool> d_nres[64], d_ngain[64], d_resid[64], d_m2up[64], d_m2down[64], d_m2roll[64];
         if ((e = chain_allow_smem(k_m2up<RT, N, NG_UP>, d_m2up, (size_t)NG_UP * UP_B)) !=
                 cudaSuccess ||
             (e = chain_allow_smem(k_m2down<RT, N, NG_UP>, d_m2down, (size_t)NG_UP * UP_B)) !=
@@ -84,7 +86,7 @@ struct Launcher {
                                   (size_t)NG_RESID * RESID_B)) != cudaSuccess)
             return e;
         if constexpr (kCompNewton) {
-            static bool d_nres_c[64], d_ngain_c[64];
+            static std::atomic<bool> d_nres_c[64], d_ngain_c[64];
             if ((e = chain_allow_smem(k_nresid_c<N, M, NG_NEWTON_C>, d_nres_c,
                                       (size_t)NG_NEWTON_C * NEWTON_C_B)) != cudaSuccess ||
                 (e = chain_allow_smem(k_ngains_c<N, M, NG_NEWTON_G>, d_ngain_c,

@@ -2,6 +2,8 @@
 // translation units only).
 #pragma once
 
+#include <atomic>
+
 #include "lqt_kernels.cuh"
 #include "lqt_launch.cuh"
 
@@ -9,17 +11,17 @@ namespace lqt {
 
 // Raise the dynamic shared-memory cap of a kernel once per device.
 template <typename Kernel>
-static cudaError_t allow_smem(Kernel k, bool* done, size_t bytes) {
+static cudaError_t allow_smem(Kernel k, std::atomic<bool>* done, size_t bytes) {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (done[dev] || bytes <= 48 * 1024) return cudaSuccess;
+    if (done[dev].load(std::memory_order_relaxed) || bytes <= 48 * 1024) return cudaSuccess;
     int optin = 0;
     err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (err == cudaSuccess) done[dev] = true;
+    if (err == cudaSuccess) done[dev].store(true, std::memory_order_relaxed);
     return err;
 }
 
@@ -53,7 +55,7 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
     constexpr int W = tile_threads<R, N, M>();
     constexpr int TP = top_threads();
     using SM = Smem<R, N, M, W>;
-    static bool done_up[64], done_top[64], done_top1[64], done_top2[64], done_down[64],
+    static std::atomic<bool> done_up[64], done_top[64], done_top1[64], done_top2[64], done_down[64],
         done_ftop[64], done_fdown[64];
     const size_t smem_up = SM::bytes(SM::UP_BIG, P.p);
     constexpr long long kTopReplay =
@@ -110,7 +112,7 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
 
 template <typename R, int N, int M>
 lqt_status launch_seq(const Params<R>& P, cudaStream_t stream) {
-    static bool done[64];
+    static std::atomic<bool> done[64];
     const size_t smem = (size_t)ModelLayout<N, M>::size(P.p) * sizeof(R);
     if (allow_smem(k_riccati_seq<R, N, M>, done, smem) != cudaSuccess) return LQT_ECUDA;
     k_riccati_seq<R, N, M><<<1, 32, smem, stream>>>(P);

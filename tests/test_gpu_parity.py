@@ -120,6 +120,47 @@ def test_host_buffer_solve():
     compare({k: v.double().numpy() for k, v in out.items()}, oracle_solve(prob), FP32_TOL)
 
 
+def test_host_buffer_solves_from_two_threads():
+    """Two host threads call lqt_solve_host at once, each on its own stream
+    with its own buffers and problem (the end-to-end benchmark does this), a
+    few times each: every result matches its oracle."""
+    import threading
+
+    import torch
+
+    from paper_2104_03186_gb300 import lqt
+
+    probs = [_f32(inputs.vehicle(60_000 + 977 * i, seed=40 + i)) for i in range(2)]
+    refs = [oracle_solve(p) for p in probs]
+    dev = torch.cuda.current_device()
+    ctx = []
+    for prob in probs:
+        P = lqt.Problem.from_inputs(prob, pin=True)
+        out = P.allocate_outputs(pin=True)
+        buf = torch.empty(lqt.lqt_host_solve_bytes(P), dtype=torch.uint8, device="cuda")
+        ctx.append((P, out, buf, torch.cuda.Stream()))
+    results, errors = [None, None], []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(dev)
+            P, out, buf, s = ctx[i]
+            for _ in range(4):
+                assert lqt.lqt_solve_host(P, out, buf, s) == lqt.LQT_OK
+            results[i] = {k: v.double().numpy() for k, v in out.items()}
+        except BaseException as e:
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for res, ref in zip(results, refs):
+        compare(res, ref, FP32_TOL)
+
+
 def test_not_spd_control_cost_is_reported():
     from paper_2104_03186_gb300 import lqt
 
