@@ -390,8 +390,13 @@ def run_ours(args):
             raise lqt.LQTError(stt, "host solve")
     e2e_single_s = max_over_ranks(float(np.median(e2e_times)), world)
     del dev_buf, out_h, Ph
-    e2e_wall = max_over_ranks(e2e_concurrent(prob, opts, e2e_steps), world)
-    e2e_s = e2e_wall / (E2E_THREADS * e2e_steps)  # per solve, amortised
+    e2e_threads, e2e_note = E2E_THREADS, None
+    try:
+        e2e_wall = e2e_concurrent(prob, opts, e2e_steps)
+    except Exception as e:  # keep the line: fall back to the single-thread figure
+        e2e_threads, e2e_note = 1, "concurrent measurement failed: %r" % (e,)
+        e2e_wall = e2e_single_s * e2e_steps
+    e2e_s = max_over_ranks(e2e_wall, world) / (e2e_threads * e2e_steps)  # per solve
 
     if rank != 0:
         if world > 1:
@@ -510,11 +515,12 @@ def run_ours(args):
         "e2e": {"value": world * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms": 1e3 * e2e_s,
                 "entry_point": "lqt_solve_host (pinned host buffers, copies inside)",
-                "host_threads": E2E_THREADS,
-                "timing": "%d host threads, each with its own stream, device buffer and pinned "
-                          "buffers, %d solves each; every solve copies its inputs in and all "
-                          "outputs back; value = all solves' steps / wall time" %
-                          (E2E_THREADS, e2e_steps),
+                "host_threads": e2e_threads,
+                "timing": e2e_note or (
+                    "%d host threads, each with its own stream, device buffer and pinned "
+                    "buffers, %d solves each; every solve copies its inputs in and all "
+                    "outputs back; value = all solves' steps / wall time" %
+                    (e2e_threads, e2e_steps)),
                 "single_thread_ms": 1e3 * e2e_single_s,
                 "single_thread_value": world * T / e2e_single_s},
         "clocks": clocks,

@@ -120,6 +120,7 @@ def test_host_buffer_solve():
     compare({k: v.double().numpy() for k, v in out.items()}, oracle_solve(prob), FP32_TOL)
 
 
+@pytest.mark.timeout(300)
 def test_host_buffer_solves_from_two_threads():
     """Two host threads call lqt_solve_host at once, each on its own stream
     with its own buffers and problem (the end-to-end benchmark does this), a
@@ -282,7 +283,7 @@ def test_refined_fp64_on_request():
 
 
 @pytest.mark.parametrize("dt_nm", [("f32", 1, 1), ("f32", 2, 1), ("f32", 3, 2), ("f32", 4, 4),
-                                   ("f64", 1, 1), ("f64", 2, 2)],
+                                   ("f64", 1, 1), ("f64", 2, 1)],
                          ids=lambda v: "%s_n%d_m%d" % v)
 @pytest.mark.parametrize("T", [700, 150001])
 def test_refined_second_pass_replays_top_scan(dt_nm, T):
