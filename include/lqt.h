@@ -178,7 +178,10 @@ lqt_status lqt_workspace_status(const void *workspace, void *stream);
  * back; the call synchronises `stream` and returns the device status of the
  * solve.  At the thread-per-chunk sizes (n <= 4) S, v and K are copied back on
  * an internal stream (one per host thread and device) as soon as the first
- * pass's backward scan has written them, while the rest of the solve runs.  Returns LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED or LQT_ECUDA on
+ * pass's backward scan has written them, while the rest of the solve runs.
+ * Several host threads may call it at once, each with its own stream, device
+ * buffer and host buffers; one caller's copies then overlap another's
+ * kernels.  Returns LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED or LQT_ECUDA on
  * failure. */
 size_t lqt_host_solve_bytes(const lqt_problem *host_prob, const lqt_options *opts);
 lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host_sol,

@@ -507,8 +507,9 @@ __device__ __forceinline__ void terminal_value(const Params<R>& P, Value<R, N>& 
 
 // ===========================================================================
 // bwd_top: one CTA of TP threads.  Thread t folds tiles [t g, (t+1) g)
-// (g = ceil(tiles / TP)), the CTA sweeps the partial totals, and the value
-// carries flow back from the terminal value (S_T, v_T) of Lemma LQT_assoc.
+// (g = ceil(tiles / TP); with g = 1 the tile totals come in by bulk copy), the
+// CTA sweeps the partial totals, and the value carries flow back from the
+// terminal value (S_T, v_T) of Lemma LQT_assoc.
 // ===========================================================================
 // MODE (the pass's Params::top_mode) selects the kernel: 0 full operators,
 // 1 full operators recording their maps, 2 replay.  One kernel per mode keeps
