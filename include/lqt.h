@@ -177,8 +177,10 @@ lqt_status lqt_workspace_status(const void *workspace, void *stream);
  * opts) bytes, 256-byte aligned), lqt_solve runs there, and the outputs are copied
  * back; the call synchronises `stream` and returns the device status of the
  * solve.  At the thread-per-chunk sizes (n <= 4) S, v and K are copied back on
- * an internal stream (one per host thread and device) as soon as the first
- * pass's backward scan has written them, while the rest of the solve runs.
+ * an internal stream as soon as the first pass's backward scan has written
+ * them, while the rest of the solve runs.  That stream and two events are
+ * created on a host thread's first call for a device and are kept until the
+ * process exits (they are not released when the thread ends).
  * Several host threads may call it at once, each with its own stream, device
  * buffer and host buffers; one caller's copies then overlap another's
  * kernels.  Returns LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED or LQT_ECUDA on

@@ -551,6 +551,10 @@ namespace {
 
 // Per host thread and device: a non-blocking stream and two events with which
 // lqt_solve_host copies S, v and K back while the rest of the solve runs.
+// Per host thread and device: the stream that copies S, v, K back early and
+// its two events.  Created on first use and deliberately never destroyed: a
+// thread_local destructor can run after the CUDA runtime has shut down at
+// process exit.
 struct HostAux {
     cudaStream_t s = nullptr;
     cudaEvent_t bwd = nullptr, done = nullptr;
