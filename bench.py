@@ -138,6 +138,16 @@ def e2e_concurrent(prob, opts, steps: int) -> float:
     return max(ends) - t0
 
 
+def secondary(name: str, fn):
+    """Run one secondary measurement (no collectives inside).  An exception is
+    reported in its place, so that the headline line is still printed."""
+    try:
+        return fn()
+    except Exception as e:
+        sys.stderr.write("bench: %s failed: %r\n" % (name, e))
+        return {"error": "%s failed: %r" % (name, e)}
+
+
 def throughput(total_units: float, seconds: float) -> float:
     return total_units / seconds if seconds > 0 else float("nan")
 
@@ -453,7 +463,8 @@ def run_ours(args):
 
     # ---- T sweep: parallel vs sequential Riccati on this GPU ---------------
     sweep = []
-    if not args.no_sweep:
+
+    def run_sweep():
         for Ts in SWEEP_T:
             ps = inputs.vehicle(Ts, seed=0).rounded_to(np.float32)
             Pq = lqt.Problem.from_inputs(ps, dtype=np.float32)
@@ -473,27 +484,34 @@ def run_ours(args):
                           "speedup": float(np.median(ts) / np.median(tp))})
             del o2, w2, Pq
 
+    if not args.no_sweep:
+        err = secondary("sweep", run_sweep)
+        if err is not None:
+            sweep.append(err)
+
     # ---- ragged batch: 4096 problems, one persistent launch per (n, m) ----
-    batch = None if args.no_batch else run_batch(args, stream, flush)
+    batch = None if args.no_batch else secondary("batch", lambda: run_batch(args, stream, flush))
 
     # ---- serving: Poisson request streams through the continuous batcher ----
-    serving = None if args.no_serve else run_serving(args)
+    serving = None if args.no_serve else secondary("serving", lambda: run_serving(args))
 
     # ---- precision study (n = 32) -------------------------------------------
-    precision = None if args.no_precision else run_precision(
-        args, stream, flush, compute_peaks["fp32_tflops"], compute_peaks["fp64_tflops"])
+    precision = None if args.no_precision else secondary("precision study", lambda: run_precision(
+        args, stream, flush, compute_peaks["fp32_tflops"], compute_peaks["fp64_tflops"]))
 
     # ---- generalised stage cost (cross weights, control offsets) -------------
-    cross = None if args.no_cross else run_cross(args, stream, flush)
+    cross = None if args.no_cross else secondary("cross", lambda: run_cross(args, stream, flush))
 
     # ---- partial condensing of the headline workload ----------------------
     condensed = None
     if not args.no_condensed:
-        condensed = run_condensed(args, stream, flush, prob, ref, float(np.median(times)))
+        condensed = secondary("condensed", lambda: run_condensed(
+            args, stream, flush, prob, ref, float(np.median(times))))
     del ref
 
     # ---- iterated nonlinear LQT (unicycle) ----------------------------------
-    nonlinear = None if args.no_nonlinear else run_nonlinear(args, stream, flush)
+    nonlinear = None if args.no_nonlinear else secondary(
+        "nonlinear", lambda: run_nonlinear(args, stream, flush))
 
     clk.__exit__(None, None, None)
     clocks = clk.result()
