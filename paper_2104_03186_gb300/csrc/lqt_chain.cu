@@ -12,10 +12,6 @@
 namespace lqt {
 namespace {
 
-constexpr size_t kAlignC = 256;
-constexpr size_t kStatusC = 256;
-size_t up_c(size_t x) { return (x + kAlignC - 1) / kAlignC * kAlignC; }
-
 // smallest chunk the planner makes, in steps
 constexpr long long kMinChunk = 4;
 
