@@ -1,5 +1,6 @@
-"""Host-side logic of bench.py on CPU: clock parsing, throughput arithmetic and
-the max-over-ranks reduction with two gloo ranks."""
+"""Host-side logic of bench.py on CPU: clock parsing, throughput arithmetic,
+the max-over-ranks reduction with two gloo ranks, the reporting of a failed
+secondary measurement, and the reference arm under torchrun with two ranks."""
 import os
 import socket
 import sys
@@ -64,3 +65,35 @@ def test_max_over_ranks_two_gloo_ranks():
         assert p.exitcode == 0
     assert res == {0: 1.5, 1: 1.5}
     assert bench.max_over_ranks(2.5, 1) == 2.5
+
+
+def test_secondary_reports_a_failure_in_its_place():
+    assert bench.secondary("ok", lambda: {"value": 1}) == {"value": 1}
+
+    def boom():
+        raise RuntimeError("device status 8")
+
+    got = bench.secondary("batch", boom)
+    assert set(got) == {"error"} and "batch failed" in got["error"] and "status 8" in got["error"]
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """`bench.py --impl reference` launched as the scaling run launches it: rank
+    0 alone times the oracle and prints one JSON line; rank 1 exits 0 without
+    work (no GPU needed)."""
+    import json
+    import subprocess
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    res = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, res.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
