@@ -352,7 +352,7 @@ constexpr int kSmemHead = 16;
 __host__ __device__ constexpr int tree_shift(int es) { return es == 8 ? 4 : 5; }
 __host__ __device__ constexpr int tstride(int w, int es) { return w + (w >> tree_shift(es)); }
 template <typename R>
-__device__ __forceinline__ int tslot(int i) {
+__host__ __device__ __forceinline__ constexpr int tslot(int i) {
     return i + (i >> tree_shift((int)sizeof(R)));
 }
 

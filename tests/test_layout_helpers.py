@@ -1,0 +1,27 @@
+"""Host-side checks of the shared-memory layout helpers of the CUDA scan
+kernels (padded tree slots, lane-group block spacing, the replayed top scan's
+shared memory), compiled with nvcc from tests/host/layout_check.cu against the
+library's own headers and run on the CPU."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2104_03186_gb300", "csrc")
+
+
+def test_layout_helpers(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "layout_check")
+    cmd = [nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "host", "layout_check.cu"), "-o", exe]
+    res = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-3000:]
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, run.stdout[-3000:]
+    assert "layout checks ok" in run.stdout
