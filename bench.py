@@ -21,6 +21,7 @@ import os
 import platform
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -28,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+from paper_2104_03186_gb300 import accuracy  # noqa: E402  (numpy only: error measures)
 
 METRIC = "LQT steps/s: parallel scan vs sequential Riccati, 1 GB300, ≤1e-5 err; p99 ms"
 UNIT = "time-steps/s"
@@ -190,11 +193,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        fd, self.path = tempfile.mkstemp(prefix="lqt_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv",
@@ -216,7 +219,9 @@ class ClockSampler:
         if self.proc is None or not os.path.exists(self.path):
             return None
         with open(self.path) as f:
-            return parse_clocks(f.read())
+            text = f.read()
+        os.unlink(self.path)
+        return parse_clocks(text)
 
 
 # --------------------------------------------------------------------------
@@ -350,8 +355,7 @@ def run_ours(args):
         ref = oracle.riccati(prob, keep_kv_kc=False)
         oracle_s = time.perf_counter() - t0
         got = {k: v.double().cpu().numpy() for k, v in out.items()}
-        errors = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-                  for k in ("S", "v", "K", "x", "u")}
+        errors = accuracy.errors(got, ref)
         del got
 
     # ---- timed region: K solves, one event pair per solve ---------------------
@@ -615,10 +619,10 @@ def run_batch(args, stream, flush):
             pr = probs[int(i)].astype(np.float64)
             ref = oracle.riccati(pr, keep_kv_kc=False)
             got = {k: v.double().cpu().numpy() for k, v in outs[int(i)].items()}
-            e = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-                 for k in ("S", "v", "K", "x", "u")}
-            for k, v in e.items():
-                errs[k] = max(errs.get(k, 0.0), v)
+            for k, v in accuracy.errors(got, ref).items():
+                w = errs.setdefault(k, {"fro": 0.0, "step_max": 0.0})
+                w["fro"] = max(w["fro"], v["fro"])
+                w["step_max"] = max(w["step_max"], v["step_max"])
     by_n = {int(n): int(sum(p.T for p in probs if p.n == n)) for n in (4, 8, 16)}
     return {"workload": "%d problems, n in {4,8,16} uniform, m=n/2, T uniform in [64,4096], "
                         "time-varying F_k (I+0.05N(0,1), spectral radius <= 1.05), L_k~N(0,1/n), "
@@ -742,8 +746,7 @@ def run_precision(args, stream, flush, fp32_peak=None, fp64_peak=None):
             kms[name_k] = kms.get(name_k, 0.0) + ms_k
         lqt.lqt_profile_enable(0)
         got = {k: v.double().cpu().numpy() for k, v in o.items()}
-        errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-                for k in ("S", "v", "K", "x", "u")}
+        errs = accuracy.errors(got, ref)
         med = float(np.median(times))
         e = {"status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3),
              "error_vs_fp64_oracle": errs, "plan": lqt.lqt_plan(P, refine) if not seq else None,
@@ -796,8 +799,7 @@ def run_cross(args, stream, flush):
     t0 = time.perf_counter()
     ref = ocross.riccati_cross(prob, ct.M, ct.s)
     oracle_s = time.perf_counter() - t0
-    errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-            for k in ("S", "v", "K", "x", "u")}
+    errs = accuracy.errors(got, ref)
     med, medp = float(np.median(times)), float(np.median(tplain))
     return {"workload": "vehicle T=%d with time-varying cross weights M_k (2x2) and control "
                         "offsets s_k; inputs rounded to FP32; refinement ON" % T,
@@ -833,8 +835,7 @@ def run_nonlinear(args, stream, flush):
         st = lqt.lqt_workspace_status(ws, stream)
         times = _time_solves(call, 1 if seq else 5, flush, stream)
         got = {k: v.double().cpu().numpy() for k, v in o.items()}
-        errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-                for k in ("S", "v", "K", "x", "u")}
+        errs = accuracy.errors(got, ref)
         med = float(np.median(times))
         res[name] = {"status": int(st), "ms": med, "steps_per_s": iters * T / (med * 1e-3),
                      "error_vs_fp64_oracle": errs}
@@ -865,8 +866,7 @@ def run_condensed(args, stream, flush, prob, ref, plain_ms):
     st = lqt.lqt_workspace_status(ws, stream)
     times = _time_solves(call, 10, flush, stream)
     got = {k: v.double().cpu().numpy() for k, v in o.items()}
-    errs = {k: float(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]))
-            for k in ("S", "v", "K", "x", "u")}
+    errs = accuracy.errors(got, ref)
     med = float(np.median(times))
     return {"workload": "vehicle T=%d condensed in blocks of B=%d (n=4, m=4, p=4, "
                         "T/B steps); FP32, refinement ON" % (prob.T, B),

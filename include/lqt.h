@@ -135,10 +135,21 @@ enum { LQT_REFINE_OFF = 0, LQT_REFINE_ON = 1, LQT_REFINE_AUTO = 2, LQT_REFINE_FU
  *   x*_k = (I + C_{S,k} S_k)^{-1} (b_{S,k} + C_{S,k} v_k) (eq. lqt_method_2);
  *   u*_k follows from the control law. */
 enum { LQT_METHOD_DEFAULT = 0, LQT_METHOD_1 = 1, LQT_METHOD_2 = 2 };
+/* wait_probe_polls: diagnostic of the bounded device waits (n <= 4 sizes
+ *   only; LQT_EUNSUPPORTED elsewhere).  0 (the default) does nothing.  When
+ *   positive, the backward down-sweep kernel of each pass also waits on a
+ *   barrier that nothing completes, giving up after this many polls: exactly
+ *   what a bulk copy that never lands would cause.  The wait runs out, the
+ *   kernel records LQT_ETIMEOUT in the status word and carries on, so the
+ *   solve still writes its outputs and lqt_workspace_status() returns
+ *   LQT_ETIMEOUT.  No copy is attached to that barrier, so nothing is left in
+ *   flight.  The real bulk copies always wait with the library's own limit
+ *   (2^24 polls).  Used by the tests of the timeout path. */
 typedef struct {
     int32_t refine;
     int32_t method;
-    int32_t reserved[6]; /* must be 0 */
+    int32_t wait_probe_polls;
+    int32_t reserved[5]; /* must be 0 */
 } lqt_options;
 
 /* Bytes of device workspace that lqt_solve needs for this problem and these
@@ -167,8 +178,10 @@ lqt_status lqt_riccati_sequential(const lqt_problem *prob, const lqt_solution *s
                                   size_t workspace_bytes, void *stream);
 
 /* Synchronises `stream` and returns the device status word of the last solve
- * that used `workspace`: LQT_OK, LQT_ENOTSPD, LQT_ENONFINITE or LQT_ESINGULAR
- * (LQT_ECUDA if the read itself failed). */
+ * that used `workspace`: LQT_OK, LQT_ENOTSPD, LQT_ENONFINITE, LQT_ESINGULAR or
+ * LQT_ETIMEOUT (a bounded device wait ran out; the outputs are then not to be
+ * trusted), or LQT_ECUDA if the read itself failed.  The next solve on the
+ * workspace clears the word first. */
 lqt_status lqt_workspace_status(const void *workspace, void *stream);
 
 /* Host-buffer solve: every pointer in `host_prob` and `host_sol` is a HOST
@@ -239,14 +252,19 @@ lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *w
  *     with refinement; without refinement the need stays near 20 MB for any T
  *     (the launch plan keeps about one tile per SM).
  *   - The first call on a device looks up the array's device address for that
- *     device (the device must be current).  Make that first call before any
- *     stream capture.  A failed look-up returns LQT_ECUDA.
+ *     device (the device must be current) and keeps it for later calls.  Make
+ *     that first call before any stream capture.  A failed look-up returns
+ *     LQT_ECUDA.  The kept address belongs to the device's current context:
+ *     after cudaDeviceReset the library's module is loaded again and the array
+ *     may move, so do not call this entry point after a device reset.
  *   - All calls share the one array, and it keeps the last call's contents.
  *     Calls whose work overlaps on the GPU (different streams, or several host
  *     threads) race on it and give wrong results: serialise them.
- *   - The call waits for `stream` to finish the solve and returns the device
- *     status of that solve (LQT_OK, LQT_ENOTSPD, LQT_ENONFINITE or
- *     LQT_ESINGULAR), or the argument and launch errors of lqt_solve. */
+ *   - The call waits for `stream` to finish the solve (a stream
+ *     synchronisation, so the call itself cannot be recorded into a CUDA
+ *     graph) and returns the device status of that solve (LQT_OK,
+ *     LQT_ENOTSPD, LQT_ENONFINITE or LQT_ESINGULAR), or the argument and
+ *     launch errors of lqt_solve. */
 #define LQT_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 lqt_status lqt_solve_static(const lqt_problem *prob, const lqt_solution *sol,
                             const lqt_options *opts, void *stream);

@@ -138,6 +138,7 @@ lqt_status resolve_refine(const lqt_problem* P, const lqt_options* o, bool* refi
     if (o) {
         for (int r : o->reserved)
             if (r != 0) return LQT_EINVAL;
+        if (o->wait_probe_polls < 0) return LQT_EINVAL;
         if (o->method != LQT_METHOD_DEFAULT && o->method != LQT_METHOD_1 &&
             o->method != LQT_METHOD_2)
             return LQT_EINVAL;
@@ -291,6 +292,8 @@ void fill_params(Params<R>& K, const lqt_problem* P, const lqt_solution* sol, vo
         P->F.step_stride == 0 && P->L.step_stride == 0 && P->U.step_stride == 0 ? 1 : 0;
     K.c_invariant = (P->c.ptr == nullptr || P->c.step_stride == 0) ? 1 : 0;
     K.out_mask = OUT_ALL;
+    K.wait_limit = kWaitLimit;
+    K.wait_probe = 0;
 }
 
 std::mutex g_prof_mu;
@@ -405,10 +408,11 @@ namespace {
 template <typename R>
 lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
                     void* ws, const Layout& L, const Plan& plan, int out_mask, int refine_emit,
-                    int refine_add, bool sequential, cudaStream_t s, Prof* prof,
+                    int refine_add, bool sequential, int wait_probe, cudaStream_t s, Prof* prof,
                     cudaEvent_t bwd_done = nullptr) {
     Params<R> K;
     fill_params(K, P, sol, ws, &L, &plan);
+    K.wait_probe = wait_probe;
     K.out_mask = out_mask;
     K.refine_emit = refine_emit;
     K.refine_add = refine_add;
@@ -425,11 +429,11 @@ lqt_status run_pass(const Variant& var, const lqt_problem* P, const lqt_solution
 template <typename R>
 lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solution* sol,
                      void* ws, const Layout& L, const Plan& plan, bool refine, bool sequential,
-                     cudaStream_t s, Prof* prof, cudaEvent_t bwd_done) {
+                     int wait_probe, cudaStream_t s, Prof* prof, cudaEvent_t bwd_done) {
     refine = refine && P->T > 0;
     // pass 1: the problem; when refining it also writes the shifted data
     lqt_status st = run_pass<R>(var, P, sol, ws, L, plan, OUT_ALL, refine ? 1 : 0, 0, sequential,
-                                s, prof, sequential ? nullptr : bwd_done);
+                                wait_probe, s, prof, sequential ? nullptr : bwd_done);
     if (st != LQT_OK || !refine) {
         if (prof) prof_end(prof, s);
         return st;
@@ -447,7 +451,7 @@ lqt_status run_solve(const Variant& var, const lqt_problem* P, const lqt_solutio
     P2.c.step_stride = P->n;
     P2.rT = P->pT > 0 ? base + L.rTp : nullptr;
     P2.x0 = base + L.x0p;
-    st = run_pass<R>(var, &P2, sol, ws, L, plan, 0, 0, 1, sequential, s, prof);
+    st = run_pass<R>(var, &P2, sol, ws, L, plan, 0, 0, 1, sequential, wait_probe, s, prof);
     if (prof) prof_end(prof, s);
     return st;
 }
@@ -468,6 +472,9 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     bool unsupported = false;
     const bool chain = use_chain(prob, var, refine && newton, method2, &unsupported);
     if (unsupported) return LQT_EUNSUPPORTED;
+    // the diagnostic wait lives in the thread-per-chunk scan kernels
+    const int wait_probe = opts ? opts->wait_probe_polls : 0;
+    if (wait_probe > 0 && (chain || sequential)) return LQT_EUNSUPPORTED;
     if (chain) {
         // the chunked pipeline (one chunk when sequential)
         size_t need = 0;
@@ -492,10 +499,10 @@ lqt_status solve_common(const lqt_problem* prob, const lqt_solution* sol, const 
     if ((st = prof_begin(&prof)) != LQT_OK) return st;
     if (recorded) *recorded = bwd_done != nullptr && !sequential;
     if (prob->dtype == LQT_F64)
-        return run_solve<double>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof,
-                                 bwd_done);
-    return run_solve<float>(*var, prob, sol, workspace, L, plan, refine, sequential, s, prof,
-                            bwd_done);
+        return run_solve<double>(*var, prob, sol, workspace, L, plan, refine, sequential,
+                                 wait_probe, s, prof, bwd_done);
+    return run_solve<float>(*var, prob, sol, workspace, L, plan, refine, sequential, wait_probe, s,
+                            prof, bwd_done);
 }
 
 }  // namespace

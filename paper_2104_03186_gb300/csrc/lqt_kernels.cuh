@@ -80,6 +80,9 @@ struct Params {
     // alone from top_fac (a pass whose matrices equal the recording pass's)
     int top_mode;
     R* top_fac;
+    long long wait_limit;  // polls of each bounded mbarrier wait
+    int wait_probe;        // > 0: k_bwd_down also waits this many polls on a barrier
+                           // nothing completes (diagnostic of the timeout path)
 };
 
 __device__ __forceinline__ void set_status(int* status, int code) {
@@ -592,9 +595,9 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
     }
     __syncthreads();  // the mbarrier is initialised before anyone waits on it
     if (bulk || stage) {
-        const bool ok_load = mbar_wait(bar, 0);
+        const bool ok_load = mbar_wait(bar, 0, P.wait_limit);
         if (!ok_load) {
-            mbar_wait(bar, 0);  // one more bounded wait for the copies in flight
+            mbar_wait(bar, 0, P.wait_limit);  // one more bounded wait for the copies in flight
             if (tid == 0) set_status(P.status, ST_TIMEOUT);
         }
     }
@@ -698,6 +701,7 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     using SM = Smem<R, N, M, W>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* probe_bar = bar + 1;  // second word of the head: the diagnostic wait
     R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
     constexpr int WS = SM::WS;
     R* tree = big;                                       // [ELEM][WS]
@@ -705,7 +709,10 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     R* rbuf = big + SM::DOWN_BIG + threadIdx.x;  // slot-major, stride W
     R* sm = big + SM::DOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
-    if (tid == 0) mbar_init(bar, 1);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        if (P.wait_probe > 0) mbar_init(probe_bar, 1);
+    }
     long long s, e;
     const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
     geo.chunk(tid, s, e);
@@ -718,8 +725,13 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
     model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
 
     uint32_t phase = 0;
-    const bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS,
-                                       (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)), bar, phase);
+    bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS,
+                                 (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)), bar, phase,
+                                 P.wait_limit);
+    // Diagnostic: a wait on a barrier that no copy and no thread completes runs
+    // out after P.wait_probe polls, as a lost bulk copy would; the kernel then
+    // flags the timeout and carries on like after any other timed-out wait.
+    if (P.wait_probe > 0 && !mbar_wait(probe_bar, 0, P.wait_probe)) ok_load = false;
     const int Weff = next_pow2(geo.live(W));
     if (tid < Dims<N>::VALUE)
         carry[tid * WS] = P.tile_carry[(size_t)blockIdx.x * Dims<N>::VALUE + tid];
@@ -960,7 +972,8 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
 
     uint32_t phase = 0;
     const bool ok_load = cta_bulk_load(ftree, P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * WS,
-                                       (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)), bar, phase);
+                                       (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)), bar, phase,
+                                       P.wait_limit);
     const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
     const int Weff = next_pow2(geo.live(W));
     if (tid < N) xs[tid * WS + tslot<R>(Weff - 1)] = P.ftile_x[(size_t)blockIdx.x * N + tid];

@@ -19,7 +19,9 @@ void* g_addr[kMaxDevices];  // device address of g_static_scratch, per device
 
 // Host code cannot use g_static_scratch as a pointer (on the host the name is
 // only a stand-in for the symbol): ask the runtime for its address on the
-// current device, once per device.
+// current device, once per device.  The kept address is that of the device's
+// current context; a device reset reloads the module, after which it may be
+// stale (the header tells callers not to use this entry point after one).
 lqt_status scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LQT_ECUDA;

@@ -42,9 +42,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < kWaitLimit; ++i)
+// Bounded wait of at most `limit` polls; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitLimit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -90,13 +91,14 @@ __device__ __forceinline__ void fence_proxy_async() {
 // wait timeout.  `bar` must be initialised with count 1; `phase` is its
 // current parity and is flipped.
 __device__ __forceinline__ bool cta_bulk_load(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar, uint32_t& phase) {
+                                              uint64_t* bar, uint32_t& phase,
+                                              long long limit = kWaitLimit) {
     if (threadIdx.x == 0) {
         mbar_expect_tx(bar, bytes);
         bulk_g2s(dst, src, bytes, bar);
     }
-    bool ok = mbar_wait(bar, phase);
-    if (!ok) mbar_wait(bar, phase);  // give the copy in flight one more bounded wait
+    bool ok = mbar_wait(bar, phase, limit);
+    if (!ok) mbar_wait(bar, phase, limit);  // give the copy in flight one more bounded wait
     phase ^= 1u;
     return ok;
 }

@@ -65,13 +65,17 @@ LQT_METHOD_DEFAULT, LQT_METHOD_1, LQT_METHOD_2 = 0, 1, 2
 
 class lqt_options(ctypes.Structure):
     _fields_ = [("refine", ctypes.c_int32), ("method", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("wait_probe_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
-def options(refine: int = LQT_REFINE_AUTO, method: int = LQT_METHOD_DEFAULT) -> lqt_options:
+def options(refine: int = LQT_REFINE_AUTO, method: int = LQT_METHOD_DEFAULT,
+            wait_probe_polls: int = 0) -> lqt_options:
+    """lqt_options; wait_probe_polls > 0 runs the diagnostic wait that runs out
+    (n <= 4 sizes, see include/lqt.h)."""
     o = lqt_options()
     o.refine = refine
     o.method = method
+    o.wait_probe_polls = wait_probe_polls
     return o
 
 

@@ -44,6 +44,7 @@ class Request:
     done: float = math.nan
     u: Optional[np.ndarray] = None
     out: Optional[Dict[str, object]] = None
+    result: Optional[Dict[str, np.ndarray]] = None  # S, v, K, x, u (keep_results only)
     refs: int = 0           # warm requests still pointing at this one's outputs
 
 
@@ -81,6 +82,18 @@ class ModelPool:
         P.n, P.m, P.p, P.pT, P.T, P.dtype, P.arrays, P.struct = n, m, p, pr.pT, T, \
             lqt.LQT_F32, {}, s
         return P
+
+
+def unpack_outputs(buf: np.ndarray, n: int, m: int, T: int) -> Dict[str, np.ndarray]:
+    """Split a request's packed output buffer (S, v, K, x, as written by the
+    solve) into arrays with the time step on the first axis."""
+    sizes = ((T + 1) * n * n, (T + 1) * n, T * m * n, (T + 1) * n)
+    shapes = ((T + 1, n, n), (T + 1, n), (T, m, n), (T + 1, n))
+    out, a = {}, 0
+    for name, size, shape in zip(("S", "v", "K", "x"), sizes, shapes):
+        out[name] = buf[a: a + size].reshape(shape)
+        a += size
+    return out
 
 
 def out_bytes(n: int, m: int, T: int) -> int:
@@ -160,8 +173,11 @@ class _Slot:
 
 class Server:
     def __init__(self, pool: ModelPool, memory_budget: int = 4 << 30, streams: int = 4,
-                 max_batch: int = 1024):
+                 max_batch: int = 1024, keep_results: bool = False):
         self.pool = pool
+        # keep_results: copy every request's S, v, K, x* and u* to the host as it
+        # completes (Request.result), before its device outputs are released
+        self.keep_results = keep_results
         self.budget = memory_budget
         self.slots = [_Slot() for _ in range(streams)]
         self.max_batch = max_batch
@@ -239,6 +255,10 @@ class Server:
                     mt = q.T * self.pool.models[q.n][0].m
                     q.u = hu[off: off + mt].reshape(q.T, -1).copy()
                     q.done = tdone
+                    if self.keep_results:
+                        m = self.pool.models[q.n][0].m
+                        q.result = unpack_outputs(q.out.cpu().numpy(), q.n, m, q.T)
+                        q.result["u"] = q.u
                     done += 1
                     if q.warm_of >= 0:
                         prior = byid[q.warm_of]

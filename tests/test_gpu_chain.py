@@ -141,7 +141,7 @@ def test_chain_host_and_static_entry_points():
     compare({k: v.double().numpy() for k, v in out_h.items()}, ref, FP32_TOL)
     P = lqt.Problem.from_inputs(prob)
     out = P.allocate_outputs()
-    lqt.lqt_solve_static(P, out, None, None)
+    assert lqt.lqt_solve_static(P, out, None, None) == lqt.LQT_OK
     torch.cuda.synchronize()
     compare({k: v.double().cpu().numpy() for k, v in out.items()}, ref, FP32_TOL)
 
