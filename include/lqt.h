@@ -234,6 +234,42 @@ size_t lqt_batch_workspace_bytes(const lqt_batch_item *items, int32_t count);
 lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *workspace,
                              size_t workspace_bytes, void *stream);
 
+/* Warm solves: problems whose S_k and K_k are already known.
+ *
+ * S_k and K_k depend on the matrices F, L, U, H, X and the terminal H_T, X_T
+ * only: the Riccati recursion of Sec. II-B never reads r, c or x_0.  A
+ * problem over steps [s, s + T) of a model that an earlier solve covered over
+ * [0, s + T) with the same terminal weights (a receding horizon, as in model
+ * predictive control) therefore has S_k = S'_{s+k} and K_k = K'_{s+k} of the
+ * earlier solve, whatever its own references, offsets and initial state.
+ * This call takes them as given and computes the rest by the vector
+ * recursions of Sec. II-B with the closed loop Ft_k = F_k - L_k K_k:
+ *   v_T = H_T^T X_T r_T,  v_k = Ft_k^T (v_{k+1} - S_{k+1} c_k) + H_k^T X_k r_k,
+ *   d_k = (L_k^T S_{k+1} L_k + U_k)^{-1} L_k^T (v_{k+1} - S_{k+1} c_k),
+ *   u*_k = -K_k x*_k + d_k,  x*_{k+1} = F_k x*_k + c_k + L_k u*_k,
+ * each scanned over chunks of steps as an affine recursion (Sec. IV-C),
+ * which costs one n x n product and one m x m solve per step instead of the
+ * full solve's element folds and Riccati steps.
+ *   items: HOST array of `count` problems (any mix of dtype FP32 / FP64 and
+ *          of the sizes (n, m) in {(4,2), (8,4), (16,8), (32,16)}; p, pT <=
+ *          2n), with the layouts of lqt_problem and lqt_solution.  On entry
+ *          solution.S ((T+1) x n x n) and solution.K (T x m x n) must hold
+ *          the known S_k and K_k; they are read, never written, so they may
+ *          point into an earlier solve's outputs at step offset s.  v, x, u
+ *          are written.  The array may be reused when the call returns.
+ *   workspace: device buffer of at least lqt_warm_workspace_bytes(items,
+ *          count) bytes (0: an invalid or unsupported item), 256-byte
+ *          aligned; its first word is the status word of
+ *          lqt_workspace_status() (LQT_ENOTSPD when some
+ *          L_k^T S_{k+1} L_k + U_k is not positive definite).
+ * Asynchronous on `stream`; returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM
+ * or LQT_ECUDA on argument or launch errors.  The result equals that of a
+ * full solve of the same problem up to rounding when the given S and K are
+ * that problem's. */
+size_t lqt_warm_workspace_bytes(const lqt_batch_item *items, int32_t count);
+lqt_status lqt_solve_warm(const lqt_batch_item *items, int32_t count, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
 /* Solve without any caller-provided workspace.
  *
  * There is no counterpart to this entry point in the paper.  It exists for

@@ -27,7 +27,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
 SOURCES = ["lqt_api.cu", "lqt_inst_f32_small.cu", "lqt_inst_f32_n4.cu", "lqt_inst_f64.cu",
            "lqt_static.cu", "lqt_batch.cu", "lqt_chain.cu", "lqt_chain_n4.cu", "lqt_chain_n8.cu",
            "lqt_chain_n16.cu", "lqt_chain_n32.cu", "lqt_cross.cu",
-           "lqt_nonlinear.cu", "lqt_condense.cu"]
+           "lqt_nonlinear.cu", "lqt_condense.cu", "lqt_warm.cu"]
 
 
 def nvcc() -> str:

@@ -192,4 +192,56 @@ lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int co
     return v->run(call, s, nullptr);
 }
 
+bool chain_warm_supported(int dtype, int n, int m) {
+    return find_chain(dtype, n, m, false) != nullptr;
+}
+
+namespace {
+
+// Chunk geometry of a warm call: one problem as lqt_solve cuts it, a batch as
+// lqt_solve_batched does.
+lqt_status warm_geometry(const ChainVariant& v, const lqt_batch_item* items, const int* idx,
+                         int count, std::vector<ChainProblem>* probs) {
+    if (count == 1) {
+        const lqt_batch_item& it = items[idx[0]];
+        int nc = 1;
+        long long b = 1;
+        const lqt_status st = geometry(v, &it.problem, false, &nc, &b);
+        if (st != LQT_OK) return st;
+        probs->assign(1, ChainProblem{&it.problem, &it.solution, nc, b});
+        return LQT_OK;
+    }
+    return batch_geometry(v, items, idx, count, probs);
+}
+
+}  // namespace
+
+lqt_status chain_warm_workspace(const lqt_batch_item* items, const int* idx, int count,
+                                size_t* bytes) {
+    *bytes = 0;
+    if (count <= 0) return LQT_OK;
+    const lqt_problem& P0 = items[idx[0]].problem;
+    const ChainVariant* v = find_chain(P0.dtype, P0.n, P0.m, false);
+    if (!v) return LQT_EUNSUPPORTED;
+    std::vector<ChainProblem> probs;
+    const lqt_status st = warm_geometry(*v, items, idx, count, &probs);
+    if (st != LQT_OK) return st;
+    *bytes = v->workspace(probs.data(), count, false, false, false);
+    return LQT_OK;
+}
+
+lqt_status chain_warm_solve(const lqt_batch_item* items, const int* idx, int count, void* ws,
+                            size_t ws_bytes, int* status, cudaStream_t s) {
+    if (count <= 0) return LQT_OK;
+    const lqt_problem& P0 = items[idx[0]].problem;
+    const ChainVariant* v = find_chain(P0.dtype, P0.n, P0.m, false);
+    if (!v) return LQT_EUNSUPPORTED;
+    std::vector<ChainProblem> probs;
+    const lqt_status st = warm_geometry(*v, items, idx, count, &probs);
+    if (st != LQT_OK) return st;
+    ChainCall call{probs.data(), count, false, false, false, false, ws, ws_bytes, status};
+    call.warm = true;
+    return v->run(call, s, nullptr);
+}
+
 }  // namespace lqt

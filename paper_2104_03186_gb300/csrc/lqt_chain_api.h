@@ -30,6 +30,9 @@ struct ChainCall {
     void* ws;
     size_t ws_bytes;
     int* status;  // device status word (nullptr: the first word of ws)
+    // warm solve (lqt_warm.cuh): S and K of every problem are given in its
+    // solution; only v, the feedforward, x* and u* are computed
+    bool warm = false;
 };
 
 struct ChainVariant {
@@ -104,5 +107,11 @@ lqt_status chain_batch_workspace(const lqt_batch_item* items, const int* idx, in
                                  size_t* bytes);
 lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int count, void* ws,
                              size_t ws_bytes, int* status, cudaStream_t s);
+// Warm solves (S and K known): the sizes with a chain variant, FP32 or FP64.
+bool chain_warm_supported(int dtype, int n, int m);
+lqt_status chain_warm_workspace(const lqt_batch_item* items, const int* idx, int count,
+                                size_t* bytes);
+lqt_status chain_warm_solve(const lqt_batch_item* items, const int* idx, int count, void* ws,
+                            size_t ws_bytes, int* status, cudaStream_t s);
 
 }  // namespace lqt

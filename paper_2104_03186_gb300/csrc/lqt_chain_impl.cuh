@@ -11,10 +11,42 @@
 
 #include "lqt_chain.cuh"
 #include "lqt_chain_api.h"
+#include "lqt_warm.cuh"
 #include "lqt_launch.cuh"
 
 namespace lqt {
 namespace chain {
+
+// Per host thread and device: the stream on which Method 2's forward element
+// scan runs beside the backward scan, and the fork and join events.  Created
+// on first use and never destroyed (a thread_local destructor can run after
+// the CUDA runtime has shut down at process exit).
+struct ForkAux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static ForkAux* fork_aux() {
+    thread_local ForkAux aux[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    ForkAux& a = aux[dev];
+    if (!a.s) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
+            if (e1) cudaEventDestroy(e1);
+            cudaStreamDestroy(s);
+            return nullptr;
+        }
+        a.s = s;
+        a.fork = e1;
+        a.join = e2;
+    }
+    return &a;
+}
 
 template <typename Kernel>
 static cudaError_t chain_allow_smem(Kernel k, std::atomic<bool>* done, size_t bytes) {
@@ -56,6 +88,8 @@ struct Launcher {
     static constexpr int NG_RESID = groups_for<N>(RESID_B);
     static constexpr int M2_B = gstride<N>(M2Smem<N, M>::SIZE) * (int)sizeof(R);
     static constexpr int NG_M2 = groups_for<N>(M2_B);
+    static constexpr int WARM_B = gstride<N>(WarmSmem<N, M>::SIZE) * (int)sizeof(R);
+    static constexpr int NG_WARM = groups_for<N>(WARM_B);
 
     static cudaError_t prepare() {
         static std::atomic<bool> d_fold[64], d_refold[64], d_up[64], d_down[64], d_fup[64], d_fdown[64],
@@ -99,6 +133,17 @@ struct Launcher {
                                   (size_t)NG_NEWTON * NEWTON_B)) != cudaSuccess)
             return e;
         return chain_allow_smem(k_croll<R, RT, N, M, NG_ROLL>, d_roll, (size_t)NG_ROLL * ROLL_B);
+    }
+
+    static cudaError_t prepare_warm() {
+        static std::atomic<bool> d_wfold[64], d_wrefold[64];
+        cudaError_t e;
+        if ((e = prepare()) != cudaSuccess) return e;
+        if ((e = chain_allow_smem(k_wfold<R, RT, N, M, NG_WARM>, d_wfold,
+                                  (size_t)NG_WARM * WARM_B)) != cudaSuccess)
+            return e;
+        return chain_allow_smem(k_wrefold<R, RT, N, M, NG_WARM>, d_wrefold,
+                                (size_t)NG_WARM * WARM_B);
     }
 
     static int blocks(long long items, int ng) { return (int)((items + ng - 1) / ng); }
@@ -202,20 +247,55 @@ struct Launcher {
         return names[kind][phase];
     }
 
+    // Method 2's forward element scan: up-sweep of the chunk totals E2, the
+    // seed (0, x_0, 0, 0, 0) and the down-sweep into the prefixes Pref.  It
+    // needs only the chunk totals, so it can run beside the backward scan.
+    static void m2_scan(const Args<R, RT>& a, const long long* active, int levels, RT* E2,
+                        RT* Pref, cudaStream_t s) {
+        for (int l = 0; l < levels; ++l) {
+            const int h = 1 << l;
+            k_m2up<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
+                                   (size_t)NG_UP * UP_B, s>>>(E2, active[l], h, a.status);
+        }
+        k_m2seed<R, RT, N><<<a.count, N, 0, s>>>(a.items, Pref);
+        for (int l = levels - 1; l >= 0; --l) {
+            const int h = 1 << l;
+            k_m2down<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
+                                     (size_t)NG_UP * UP_B, s>>>(E2, Pref, active[l], h,
+                                                                a.status);
+        }
+    }
+
     // One pass: backward scan, re-fold, then (unless backward_only) the forward
-    // scan and the rollout.
+    // scan and the rollout.  With Method 2 (E2 given) the forward element scan
+    // runs on a second stream, forked after the chunk fold and joined before
+    // the Method 2 rollout, so that it overlaps the backward scan (Lemma
+    // LQT_trajectory_method2 needs no backward result for it); with kernel
+    // timing on, it runs in line so that the events stay in launch order.
     static void pass(const Args<R, RT>& a, const long long* active, int levels, bool sequential,
                      int kind, bool backward_only, cudaStream_t s, Prof* prof, RT* E2 = nullptr,
                      RT* Pref = nullptr) {
         const long long C = a.C;
         const bool m2 = E2 != nullptr && !backward_only;
+        ForkAux* fa = (m2 && !(prof && prof->enabled)) ? fork_aux() : nullptr;
+        bool forked = false, scanned = false;
         if (!sequential) {
             prof_mark(prof, s, pname(kind, 0));
             k_cfold<R, RT, N, M, NG_FOLD>
                 <<<blocks(C, NG_FOLD), NG_FOLD * N, (size_t)NG_FOLD * FOLD_B, s>>>(a);
-            if (m2)  // the chunk totals, before the backward up-sweep overwrites them
+            if (m2) {  // the chunk totals, before the backward up-sweep overwrites them
                 cudaMemcpyAsync(E2, a.E, (size_t)C * LElem<N>::SIZE * sizeof(RT),
                                 cudaMemcpyDeviceToDevice, s);
+                if (fa && cudaEventRecord(fa->fork, s) == cudaSuccess &&
+                    cudaStreamWaitEvent(fa->s, fa->fork, 0) == cudaSuccess) {
+                    m2_scan(a, active, levels, E2, Pref, fa->s);
+                    scanned = true;
+                    if (cudaEventRecord(fa->join, fa->s) == cudaSuccess)
+                        forked = true;
+                    else
+                        cudaStreamSynchronize(fa->s);  // join without the event
+                }
+            }
             if (levels > 0) prof_mark(prof, s, pname(kind, 1));
             for (int l = 0; l < levels; ++l) {
                 const int h = 1 << l;
@@ -237,18 +317,11 @@ struct Launcher {
         if (backward_only) return;
         if (m2) {
             // Method 2: prefix scan of the elements from (0, x_0, 0, 0, 0)
-            prof_mark(prof, s, kind == 1 ? "chain_m2scan.refine" : "chain_m2scan");
-            for (int l = 0; l < levels; ++l) {
-                const int h = 1 << l;
-                k_m2up<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
-                                       (size_t)NG_UP * UP_B, s>>>(E2, active[l], h, a.status);
-            }
-            k_m2seed<R, RT, N><<<a.count, N, 0, s>>>(a.items, Pref);
-            for (int l = levels - 1; l >= 0; --l) {
-                const int h = 1 << l;
-                k_m2down<RT, N, NG_UP><<<blocks(active[l] / (2 * h), NG_UP), NG_UP * N,
-                                         (size_t)NG_UP * UP_B, s>>>(E2, Pref, active[l], h,
-                                                                    a.status);
+            if (forked) {
+                cudaStreamWaitEvent(s, fa->join, 0);
+            } else if (!scanned) {
+                prof_mark(prof, s, kind == 1 ? "chain_m2scan.refine" : "chain_m2scan");
+                m2_scan(a, active, levels, E2, Pref, s);
             }
             prof_mark(prof, s, kind == 1 ? "chain_m2roll.refine" : "chain_m2roll");
             k_m2roll<R, RT, N, M, NG_M2>
@@ -274,7 +347,94 @@ struct Launcher {
             <<<blocks(C, NG_ROLL), NG_ROLL * N, (size_t)NG_ROLL * ROLL_B, s>>>(a);
     }
 
+    // Forward affine scan of the maps FE from the seeds in each problem's top
+    // slot of X: afterwards X[c] is the state at the start of chunk c.
+    static void affine_scan(RT* FE, RT* X, const long long* active, int levels, cudaStream_t s) {
+        for (int l = 0; l < levels; ++l) {
+            const int h = 1 << l;
+            k_cfup<RT, N, NG_FUP><<<blocks(active[l] / (2 * h), NG_FUP), NG_FUP * N,
+                                    (size_t)NG_FUP * FUP_B, s>>>(FE, active[l], h);
+        }
+        for (int l = levels - 1; l >= 0; --l) {
+            const int h = 1 << l;
+            k_cfdown<RT, N, NG_FDOWN><<<blocks(active[l] / (2 * h), NG_FDOWN), NG_FDOWN * N,
+                                        (size_t)NG_FDOWN * FDOWN_B, s>>>(FE, X, active[l], h);
+        }
+    }
+
+    // Warm solve (lqt_warm.cuh): the value vector scanned from v_T over the
+    // chunks' mirrored maps, the per-chunk v_k and d_k with the chunk maps of
+    // the trajectory, the trajectory scanned from x_0, then the rollout.
+    static lqt_status run_warm(const ChainCall& call, cudaStream_t s, Prof* prof) {
+        if (prepare_warm() != cudaSuccess) return LQT_ECUDA;
+        const int count = call.count;
+        if (count <= 0) return LQT_OK;
+        const Layout L = layout(call.probs, count, false, false, false);
+        if (call.ws_bytes < L.total) return LQT_ENOMEM;
+        char* base = static_cast<char*>(call.ws);
+        std::vector<Item<R>> it1((size_t)count);
+        long long c0 = 0;
+        int maxNC = 1;
+        for (int i = 0; i < count; ++i) {
+            const ChainProblem& cp = call.probs[i];
+            Item<R>& a = it1[(size_t)i];
+            memset(&a, 0, sizeof(a));
+            a.D = make_desc<R>(cp.problem, cp.solution);
+            a.B = cp.B;
+            a.c0 = c0;
+            a.NC = cp.NC;
+            c0 += cp.NC;
+            if (cp.NC > maxNC) maxNC = cp.NC;
+        }
+        int levels = 0;
+        while ((1 << levels) < maxNC) ++levels;
+        std::vector<long long> active((size_t)levels + 1, 0);
+        for (int l = 0; l < levels; ++l)
+            for (int i = 0; i < count; ++i)
+                if (call.probs[i].NC >= (2 << l)) active[(size_t)l] += call.probs[i].NC;
+        Item<R>* d1 = reinterpret_cast<Item<R>*>(base + L.items1);
+        if (count == 1) {
+            k_set_items<R><<<1, 1, 0, s>>>(d1, it1[0], nullptr, it1[0]);
+        } else if (cudaMemcpyAsync(d1, it1.data(), it1.size() * sizeof(Item<R>),
+                                   cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            return LQT_ECUDA;
+        }
+        Args<R, RT> a;
+        a.items = d1;
+        a.count = count;
+        a.C = L.C;
+        a.E = reinterpret_cast<RT*>(base + L.E);
+        a.V = reinterpret_cast<RT*>(base + L.V);
+        a.FE = reinterpret_cast<RT*>(base + L.FE);
+        a.X = reinterpret_cast<RT*>(base + L.X);
+        a.status = call.status ? call.status : reinterpret_cast<int*>(base);
+        a.out_mask = 0;
+        a.refine_add = 0;
+        // the chunk totals' region holds a copy of each chunk's Psi
+        static_assert(LElem<N>::SIZE >= LAffine<N>::SIZE, "Psi copy fits the element slots");
+        RT* psi = a.E;
+        const long long C = a.C;
+        prof_mark(prof, s, "warm_fold");
+        k_wfold<R, RT, N, M, NG_WARM>
+            <<<blocks(C, NG_WARM), NG_WARM * N, (size_t)NG_WARM * WARM_B, s>>>(a, psi);
+        prof_mark(prof, s, "warm_vscan");
+        k_wterm<R, RT, N><<<count, N, 0, s>>>(a);
+        affine_scan(a.FE, a.X, active.data(), levels, s);
+        prof_mark(prof, s, "warm_refold");
+        k_wrefold<R, RT, N, M, NG_WARM>
+            <<<blocks(C, NG_WARM), NG_WARM * N, (size_t)NG_WARM * WARM_B, s>>>(a, psi);
+        prof_mark(prof, s, "warm_fwd");
+        k_wseed<R, RT, N><<<count, N, 0, s>>>(a);
+        affine_scan(a.FE, a.X, active.data(), levels, s);
+        prof_mark(prof, s, "warm_roll");
+        k_croll<R, RT, N, M, NG_ROLL>
+            <<<blocks(C, NG_ROLL), NG_ROLL * N, (size_t)NG_ROLL * ROLL_B, s>>>(a);
+        prof_end(prof, s);
+        return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    }
+
     static lqt_status run(const ChainCall& call, cudaStream_t s, Prof* prof) {
+        if (call.warm) return run_warm(call, s, prof);
         if (prepare() != cudaSuccess) return LQT_ECUDA;
         const int count = call.count;
         if (count <= 0) return LQT_OK;

@@ -116,6 +116,8 @@ def _load() -> ctypes.CDLL:
         "lqt_solve_static": (st, [P, S, O, vp]),
         "lqt_batch_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
         "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
+        "lqt_warm_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
+        "lqt_solve_warm": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
         "lqt_cross_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_cross), O]),
         "lqt_solve_cross": (st, [P, ctypes.POINTER(lqt_cross), S, O, vp, sz, vp]),
         "lqt_nonlinear_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_nonlinear), O]),
@@ -411,6 +413,60 @@ def lqt_solve_batched_array(items: np.ndarray, workspace, stream=None) -> None:
                                 _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
     if st != LQT_OK:
         raise LQTError(st, "lqt_solve_batched")
+
+
+def lqt_warm_workspace_bytes_array(items: np.ndarray) -> int:
+    """lqt_warm_workspace_bytes over a C-contiguous numpy array of BATCH_ITEM."""
+    return int(_lib.lqt_warm_workspace_bytes(
+        items.ctypes.data_as(ctypes.POINTER(lqt_batch_item)), len(items)))
+
+
+def lqt_solve_warm_array(items: np.ndarray, workspace, stream=None) -> None:
+    """lqt_solve_warm over a C-contiguous numpy array of BATCH_ITEM (each
+    solution's S and K hold the known S_k, K_k on entry)."""
+    if items.dtype != BATCH_ITEM or not items.flags.c_contiguous:
+        raise LQTError(LQT_EINVAL, "items must be a contiguous BATCH_ITEM array")
+    st = _lib.lqt_solve_warm(items.ctypes.data_as(ctypes.POINTER(lqt_batch_item)), len(items),
+                             _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_warm")
+
+
+def lqt_warm_workspace_bytes(problems, outputs) -> int:
+    return int(_lib.lqt_warm_workspace_bytes(_items(problems, outputs), len(problems)))
+
+
+def lqt_solve_warm(problems, outputs, workspace, stream=None) -> None:
+    """Warm solves: outputs[i]["S"] and ["K"] hold the known S_k and K_k of
+    problems[i] on entry (they are only read); v, x, u are written.
+    Asynchronous; read the device status with lqt_workspace_status."""
+    st = _lib.lqt_solve_warm(_items(problems, outputs), len(problems), _ptr(workspace),
+                             _nbytes(workspace), _stream_handle(stream))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_solve_warm")
+
+
+def solve_warm(problems, known, stream=None, check: bool = True):
+    """Allocate v, x, u with torch and run lqt_solve_warm; known[i] is a dict
+    with the device tensors "S" ((T+1) x n x n) and "K" (T x m x n) of
+    problems[i], used in place."""
+    import torch
+
+    outs = []
+    for P, kn in zip(problems, known):
+        o = P.allocate_outputs()
+        o["S"], o["K"] = kn["S"], kn["K"]
+        outs.append(o)
+    nbytes = lqt_warm_workspace_bytes(problems, outs)
+    if nbytes == 0:
+        raise LQTError(LQT_EUNSUPPORTED, "lqt_warm_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lqt_solve_warm(problems, outs, ws, stream)
+    if check:
+        st = lqt_workspace_status(ws, stream)
+        if st != LQT_OK:
+            raise LQTError(st, "device status")
+    return outs
 
 
 def solve_batched(problems, stream=None, check: bool = True):

@@ -9,8 +9,15 @@ predicted state x*_s.
 
 The loop admits arrived requests while their device memory fits the budget,
 groups whatever has been admitted into a batch as soon as a stream is free,
-and solves the batch with one lqt_solve_batched call (per state size present,
-one persistent launch for n = 4 and one chunked pipeline for n >= 8).  Batches on different streams run concurrently, so
+and solves the batch's cold requests with one lqt_solve_batched call (per
+state size present, one persistent launch for n = 4 and one chunked pipeline
+for n >= 8).  A warm request's S_k and K_k are those of the request it
+continues, shifted by s steps (same model, same terminal weights; they do not
+depend on the reference or the initial state), so with reuse_warm (the
+default) the batch's warm requests go to one lqt_solve_warm call that reads
+them in place from the device-resident outputs of the cold request that
+computed them, and computes only v, x* and u*.  Batches on different streams
+run concurrently, so
 requests that arrive while others are on the GPU start without waiting for
 them.  Per batch the references and initial states go up in one host-to-device
 copy and the optimal controls u* come back in one device-to-host copy.
@@ -46,6 +53,8 @@ class Request:
     out: Optional[Dict[str, object]] = None
     result: Optional[Dict[str, np.ndarray]] = None  # S, v, K, x, u (keep_results only)
     refs: int = 0           # warm requests still pointing at this one's outputs
+    owner: int = -1         # request whose outputs hold this one's S_k, K_k
+    skoff: int = 0          # step of this request's S_0, K_0 in the owner's arrays
 
 
 class ModelPool:
@@ -100,6 +109,11 @@ def out_bytes(n: int, m: int, T: int) -> int:
     """Device bytes a request holds while admitted: S, v, K and x (its u goes to
     the stream's staging buffer)."""
     return 4 * ((T + 1) * n * n + (T + 1) * n + T * m * n + (T + 1) * n)
+
+
+def warm_out_bytes(n: int, T: int) -> int:
+    """Device bytes of a warm request solved from its owner's S and K: v, x."""
+    return 4 * 2 * (T + 1) * n
 
 
 def make_requests(count: int, rate: float, seed: int = 0, sizes=(4, 8, 16, 32),
@@ -163,18 +177,25 @@ class _Slot:
         if not hasattr(self, "ws"):
             self.ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
 
-    def ensure_ws(self, nbytes: int):
+    def ensure_ws(self, nbytes: int, warm: bool = False):
+        """The batch workspace (or, warm=True, the warm solves' own one: both
+        run on the stream one after the other, each with its status word)."""
         import torch
 
-        if nbytes > self.ws.numel():
-            self.ws = torch.empty(max(nbytes, 2 * self.ws.numel()), dtype=torch.uint8,
-                                  device="cuda")
+        name = "ws_warm" if warm else "ws"
+        cur = getattr(self, name, None)
+        if cur is None or nbytes > cur.numel():
+            size = max(nbytes, 2 * cur.numel() if cur is not None else 1 << 20)
+            setattr(self, name, torch.empty(size, dtype=torch.uint8, device="cuda"))
 
 
 class Server:
     def __init__(self, pool: ModelPool, memory_budget: int = 4 << 30, streams: int = 4,
-                 max_batch: int = 1024, keep_results: bool = False):
+                 max_batch: int = 1024, keep_results: bool = False, reuse_warm: bool = True):
         self.pool = pool
+        # reuse_warm: warm requests take S_k, K_k from the request that computed
+        # them (lqt_solve_warm); off, they are solved in full like cold ones
+        self.reuse_warm = reuse_warm
         # keep_results: copy every request's S, v, K, x* and u* to the host as it
         # completes (Request.result), before its device outputs are released
         self.keep_results = keep_results
@@ -186,11 +207,27 @@ class Server:
         self.batches = 0
         self.launches = 0
 
+    def _reused(self, req: Request) -> bool:
+        """Solved from its owner's S and K (its own buffer holds v, x)."""
+        return req.owner != req.rid
+
+    def _bytes(self, req: Request) -> int:
+        if self._reused(req):
+            return warm_out_bytes(req.n, req.T)
+        return out_bytes(req.n, self.pool.models[req.n][0].m, req.T)
+
+    def _x_offset(self, req: Request) -> int:
+        """Element offset of x in the request's own buffer."""
+        n, T = req.n, req.T
+        if self._reused(req):
+            return (T + 1) * n
+        m = self.pool.models[n][0].m
+        return (T + 1) * n * n + (T + 1) * n + T * m * n
+
     def _alloc(self, req: Request):
         import torch
 
-        m = self.pool.models[req.n][0].m
-        nb = out_bytes(req.n, m, req.T)
+        nb = self._bytes(req)
         req.out = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
         self.mem += nb
         self.peak_mem = max(self.peak_mem, self.mem)
@@ -198,19 +235,40 @@ class Server:
     def _release(self, req: Request):
         """Free a finished request's outputs once no warm request still needs them."""
         if req.out is not None and req.refs == 0 and not math.isnan(req.done):
-            self.mem -= out_bytes(req.n, self.pool.models[req.n][0].m, req.T)
+            self.mem -= self._bytes(req)
             req.out = None
+
+    def _results(self, q: Request, byid) -> Dict[str, np.ndarray]:
+        """Host copies of a completed request's S, v, K, x* (u* is q.u)."""
+        n, T = q.n, q.T
+        m = self.pool.models[n][0].m
+        if not self._reused(q):
+            return unpack_outputs(q.out.cpu().numpy(), n, m, T)
+        own = byid[q.owner]
+        full = unpack_outputs(own.out.cpu().numpy(), n, m, own.T)
+        buf = q.out.cpu().numpy()
+        return {"S": full["S"][q.skoff: q.skoff + T + 1].copy(),
+                "K": full["K"][q.skoff: q.skoff + T].copy(),
+                "v": buf[: (T + 1) * n].reshape(T + 1, n),
+                "x": buf[(T + 1) * n:].reshape(T + 1, n)}
 
     def run(self, reqs: List[Request], realtime: bool = True):
         """Serve the stream; returns per-request latencies (s) and summary."""
         import torch
 
         byid = {r.rid: r for r in reqs}
-        for q in reqs:  # warm requests that will read each request's outputs
+        for q in sorted(reqs, key=lambda r: r.rid):  # predecessors come first
             q.refs = 0
-        for q in reqs:
+            if q.warm_of < 0 or not self.reuse_warm:
+                q.owner, q.skoff = q.rid, 0
+            else:
+                prior = byid[q.warm_of]
+                q.owner, q.skoff = prior.owner, prior.skoff + q.shift
+        for q in reqs:  # warm requests that will read each request's outputs
             if q.warm_of >= 0:
-                byid[q.warm_of].refs += 1
+                byid[q.warm_of].refs += 1         # its x*_s
+                if q.owner not in (q.rid, q.warm_of):
+                    byid[q.owner].refs += 1       # its S_k, K_k
         queue = deque(sorted(reqs, key=lambda r: r.arrival))
         ready: deque = deque()    # warm requests whose predecessor has finished
         parked: Dict[int, List[Request]] = {}  # predecessor rid -> warm requests
@@ -231,7 +289,7 @@ class Server:
                     src.popleft()
                     parked.setdefault(q.warm_of, []).append(q)
                     continue
-                need = out_bytes(q.n, self.pool.models[q.n][0].m, q.T)
+                need = self._bytes(q)
                 if self.mem + need > self.budget and (admitted or inflight):
                     blocked = True
                     break
@@ -256,14 +314,17 @@ class Server:
                     q.u = hu[off: off + mt].reshape(q.T, -1).copy()
                     q.done = tdone
                     if self.keep_results:
-                        m = self.pool.models[q.n][0].m
-                        q.result = unpack_outputs(q.out.cpu().numpy(), q.n, m, q.T)
+                        q.result = self._results(q, byid)
                         q.result["u"] = q.u
                     done += 1
                     if q.warm_of >= 0:
                         prior = byid[q.warm_of]
                         prior.refs -= 1
                         self._release(prior)
+                        if q.owner not in (q.rid, q.warm_of):
+                            own = byid[q.owner]
+                            own.refs -= 1
+                            self._release(own)
                     self._release(q)  # kept while warm requests still need it
                     if q.rid in parked:
                         ready.extend(parked.pop(q.rid))
@@ -282,6 +343,7 @@ class Server:
                      "mean_ms": float(lat.mean() * 1e3), "peak_device_bytes": self.peak_mem,
                      "time_steps": int(sum(q.T for q in reqs)),
                      "warm_requests": int(sum(q.warm_of >= 0 for q in reqs)),
+                     "warm_reused": int(sum(self._reused(q) for q in reqs)),
                      "batches": self.batches, "mean_batch": len(reqs) / max(self.batches, 1)}
 
     def _launch(self, batch: List[Request], slot: _Slot, byid):
@@ -301,22 +363,57 @@ class Server:
             hv[a: a + q.r.size] = q.r.ravel()
             if q.warm_of < 0:
                 hv[a + q.r.size: a + q.r.size + q.n] = q.x0
-        # descriptors, column by column
-        ns = np.fromiter((q.n for q in batch), np.int64, k)
-        Ts = np.fromiter((q.T for q in batch), np.int64, k)
-        offs = np.fromiter((q.offset for q in batch), np.int64, k)
-        outp = np.fromiter((q.out.data_ptr() for q in batch), np.uint64, k)
-        x0p = np.empty(k, np.uint64)
         din = np.uint64(slot.d_in.data_ptr())
-        for i, q in enumerate(batch):
+        dup = np.uint64(slot.d_u.data_ptr())
+        cold = [i for i, q in enumerate(batch) if not self._reused(q)]
+        warm = [i for i, q in enumerate(batch) if self._reused(q)]
+        st = slot.stream
+        with torch.cuda.stream(st):
+            slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
+            if cold:
+                it = self._items(slot.items[: len(cold)], [batch[i] for i in cold],
+                                 in_off[cold], u_off[cold], din, dup, byid)
+                nbytes = lqt.lqt_batch_workspace_bytes_array(it)
+                if nbytes == 0:
+                    raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "batch workspace")
+                slot.ensure_ws(nbytes)
+                lqt.lqt_solve_batched_array(it, slot.ws, st)
+            if warm:
+                it = self._items(slot.items[len(cold): k], [batch[i] for i in warm],
+                                 in_off[warm], u_off[warm], din, dup, byid)
+                nbytes = lqt.lqt_warm_workspace_bytes_array(it)
+                if nbytes == 0:
+                    raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "warm workspace")
+                slot.ensure_ws(nbytes, warm=True)
+                lqt.lqt_solve_warm_array(it, slot.ws_warm, st)
+            nu_el = int(u_off[-1])
+            slot.h_u[:nu_el].copy_(slot.d_u[:nu_el], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        self.batches += 1
+        ns = [q.n for q in batch]
+        self.launches += len(set(ns[i] for i in cold)) + len(set(ns[i] for i in warm))
+        return (slot, ev, batch, [int(a) for a in u_off[:-1]])
+
+    def _items(self, it, reqs: List[Request], in_off, u_off, din, dup, byid):
+        """Descriptors of `reqs` in the BATCH_ITEM array `it`, column by column:
+        model windows from the pool, references and cold initial states from
+        the packed input copy, warm initial states from the predecessor's x*,
+        outputs in each request's buffer (S and K of a reused warm request in
+        its owner's), u* in the stream's staging buffer."""
+        pool = self.pool
+        k = len(reqs)
+        ns = np.fromiter((q.n for q in reqs), np.int64, k)
+        Ts = np.fromiter((q.T for q in reqs), np.int64, k)
+        offs = np.fromiter((q.offset for q in reqs), np.int64, k)
+        x0p = np.empty(k, np.uint64)
+        for i, q in enumerate(reqs):
             if q.warm_of < 0:
                 x0p[i] = din + np.uint64(4 * (int(in_off[i]) + q.r.size))
             else:
                 prior = byid[q.warm_of]
-                m0 = pool.models[prior.n][0].m
-                xbase = 4 * ((prior.T + 1) * prior.n * prior.n + (prior.T + 1) * prior.n
-                             + prior.T * m0 * prior.n)
-                x0p[i] = np.uint64(prior.out.data_ptr() + xbase + 4 * q.shift * q.n)
+                x0p[i] = np.uint64(prior.out.data_ptr() +
+                                   4 * (self._x_offset(prior) + q.shift * q.n))
         ms = np.empty(k, np.int64)
         base = {f: np.empty(k, np.uint64) for f in ("F", "L", "U", "H", "X", "HT", "XT")}
         for n, (pr, dev) in pool.models.items():
@@ -326,7 +423,6 @@ class Server:
             ms[sel] = pr.m
             for f in base:
                 base[f][sel] = dev[f].data_ptr()
-        it = slot.items[:k]
         P, S = it["problem"], it["solution"]
         P["n"], P["m"], P["p"], P["pT"], P["T"], P["dtype"] = ns, ms, ns, ns, Ts, lqt.LQT_F32
         n2 = (ns * ns).astype(np.uint64)
@@ -338,29 +434,28 @@ class Server:
         P["U"]["ptr"], P["U"]["step_stride"] = base["U"], 0
         P["H"]["ptr"], P["H"]["step_stride"] = base["H"], 0
         P["c"]["ptr"], P["c"]["step_stride"] = 0, 0
-        rp = din + in_off[:-1].astype(np.uint64) * np.uint64(4)
+        rp = din + np.asarray(in_off, np.int64).astype(np.uint64) * np.uint64(4)
         P["r"]["ptr"], P["r"]["step_stride"] = rp, ns
         P["HT"], P["XT"] = base["HT"], base["XT"]
         P["rT"] = rp + Ts.astype(np.uint64) * ns.astype(np.uint64) * np.uint64(4)
         P["x0"] = x0p
         Tu, nu = Ts.astype(np.uint64), ns.astype(np.uint64)
-        S["S"] = outp
-        S["v"] = outp + np.uint64(4) * (Tu + 1) * nu * nu
-        S["K"] = S["v"] + np.uint64(4) * (Tu + 1) * nu
-        S["x"] = S["K"] + np.uint64(4) * Tu * nm
-        S["u"] = np.uint64(slot.d_u.data_ptr()) + u_off[:-1].astype(np.uint64) * np.uint64(4)
-        st = slot.stream
-        nbytes = lqt.lqt_batch_workspace_bytes_array(it)
-        if nbytes == 0:
-            raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "batch workspace")
-        slot.ensure_ws(nbytes)
-        with torch.cuda.stream(st):
-            slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
-            lqt.lqt_solve_batched_array(it, slot.ws, st)
-            nu_el = int(u_off[-1])
-            slot.h_u[:nu_el].copy_(slot.d_u[:nu_el], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(st)
-        self.batches += 1
-        self.launches += len(set(ns.tolist()))
-        return (slot, ev, batch, [int(a) for a in u_off[:-1]])
+        for i, q in enumerate(reqs):
+            outp = np.uint64(q.out.data_ptr())
+            if self._reused(q):
+                own = byid[q.owner]
+                obase = np.uint64(own.out.data_ptr())
+                To = np.uint64(own.T)
+                S["S"][i] = obase + np.uint64(4 * q.skoff * q.n * q.n)
+                S["K"][i] = obase + np.uint64(4) * ((To + np.uint64(1)) * nu[i] * nu[i] +
+                                                    (To + np.uint64(1)) * nu[i]) + \
+                    np.uint64(4 * q.skoff * int(nm[i]))
+                S["v"][i] = outp
+                S["x"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i]
+            else:
+                S["S"][i] = outp
+                S["v"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i] * nu[i]
+                S["K"][i] = S["v"][i] + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i]
+                S["x"][i] = S["K"][i] + np.uint64(4) * Tu[i] * nm[i]
+        S["u"] = dup + np.asarray(u_off, np.int64).astype(np.uint64) * np.uint64(4)
+        return it

@@ -171,3 +171,20 @@ def test_nonlinear_arguments_rejected_before_any_device_work(lib):
     small.n, small.m = 2, 1
     assert call(nl, small) == lib.LQT_EINVAL
     assert so.lqt_nonlinear_workspace_bytes(ctypes.byref(small), ctypes.byref(nl), None) == 0
+
+
+def test_warm_arguments_rejected_before_any_device_work(lib):
+    """lqt_solve_warm and its workspace query check every item on the host."""
+    assert lib._lib.lqt_warm_workspace_bytes(None, -1) == 0
+    items = (lib.lqt_batch_item * 1)()
+    p = items[0].problem
+    p.n, p.m, p.p, p.pT, p.T, p.dtype = 5, 2, 5, 5, 10, lib.LQT_F32   # no (5, 2) variant
+    assert lib._lib.lqt_warm_workspace_bytes(items, 1) == 0
+    ws = ctypes.c_void_p(256)  # never dereferenced: the item check fails first
+    assert lib._lib.lqt_solve_warm(items, 1, ws, 1 << 20, None) == lib.LQT_EUNSUPPORTED
+    p.n, p.m = 8, 4
+    p.dtype = 7
+    assert lib._lib.lqt_solve_warm(items, 1, ws, 1 << 20, None) == lib.LQT_EINVAL
+    p.dtype = lib.LQT_F32
+    p.x0 = None  # no initial state
+    assert lib._lib.lqt_solve_warm(items, 1, ws, 1 << 20, None) == lib.LQT_EINVAL

@@ -27,7 +27,11 @@ def _request_problem(pool, q, x0):
         T=q.T)
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("reuse_warm", [True, False])
+def test_results_alone_equal_results_in_the_mix(reuse_warm):
+    """With reuse_warm, warm requests are solved from their owner's S and K
+    (lqt_solve_warm); the request alone is a full solve, so the two agree to
+    rounding, not bit for bit."""
     import torch
 
     import oracle
@@ -36,10 +40,11 @@ def test_results_alone_equal_results_in_the_mix():
     pool = serve.ModelPool((4, 8, 16, 32), steps=1024, seed=3)
     reqs = serve.make_requests(120, rate=20000.0, seed=5, t_lo=16, t_hi=512, pool_steps=1024)
     srv = serve.Server(pool, memory_budget=256 << 20, streams=3, max_batch=16,
-                       keep_results=True)
+                       keep_results=True, reuse_warm=reuse_warm)
     lat, summary = srv.run(reqs)
     assert summary["requests"] == 120 and np.all(np.isfinite(lat)) and np.all(lat >= 0)
     assert summary["warm_requests"] > 0
+    assert summary["warm_reused"] == (summary["warm_requests"] if reuse_warm else 0)
     assert summary["batches"] > 1
     byid = {q.rid: q for q in reqs}
     bitwise = 0
