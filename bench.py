@@ -647,17 +647,66 @@ def run_serving(args):
     serve.Server(pool, memory_budget=8 << 30).run(warm)  # warm-up
     out = []
     for rate in (2000, 5000, 10000, 20000, 50000):
-        reqs = serve.make_requests(args.serve_requests, rate=float(rate), seed=rate)
-        _, summ = serve.Server(pool, memory_budget=8 << 30, streams=4).run(reqs)
-        summ["arrival_rate_per_s"] = rate
-        summ["time_steps_per_s"] = summ["time_steps"] / (args.serve_requests / rate) \
-            if summ["solves_per_s"] >= rate * 0.98 else None
-        out.append(summ)
+        for reuse in ((True, False) if rate >= 20000 else (True,)):
+            reqs = serve.make_requests(args.serve_requests, rate=float(rate), seed=rate)
+            _, summ = serve.Server(pool, memory_budget=8 << 30, streams=4,
+                                   reuse_warm=reuse).run(reqs)
+            summ["arrival_rate_per_s"] = rate
+            summ["reuse_warm"] = reuse
+            summ["time_steps_per_s"] = summ["time_steps"] / (args.serve_requests / rate) \
+                if summ["solves_per_s"] >= rate * 0.98 else None
+            out.append(summ)
     return {"workload": "Poisson stream of %d LQT requests per rate; n in {4,8,16,32}, m=n/2, "
                         "T log-uniform in [32,2048], time-varying device-resident models "
                         "(diag tracking), fresh reference and x0 per request, 30%% warm starts "
-                        "with shifted horizon; 8 GiB admission budget; FP32" % args.serve_requests,
-            "rates": out}
+                        "with shifted horizon; 8 GiB admission budget; FP32; reuse_warm: warm "
+                        "requests solved from the S, K of the request that computed them "
+                        "(lqt_solve_warm), else in full" % args.serve_requests,
+            "rates": out, "warm_vs_cold_solve": run_warm_vs_cold()}
+
+
+def run_warm_vs_cold():
+    """Device time of one warm solve (S, K known: lqt_solve_warm) against a full
+    solve of the same problem (lqt_solve_batched with one item, the path the
+    server takes for cold requests), per state size, on a horizon of 2048
+    steps shifted by 256 from a 2304-step model."""
+    import torch
+
+    from paper_2104_03186_gb300 import inputs, lqt
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    res = []
+    for n in (4, 8, 16, 32):
+        prob = inputs.diag_tracking(n, T=2304, seed=n).astype(np.float32)
+        Pp = lqt.Problem.from_inputs(prob)
+        prior = lqt.solve_batched([Pp])[0]
+        warm = inputs.diag_tracking(n, T=2304, seed=n).astype(np.float32)
+        for f in ("F", "L", "X", "r"):
+            setattr(warm, f, np.ascontiguousarray(getattr(warm, f)[256:]))
+        warm.T = 2048
+        P = lqt.Problem.from_inputs(warm)
+        cold_out = P.allocate_outputs()
+        ws_c = torch.empty(lqt.lqt_batch_workspace_bytes([P], [cold_out]), dtype=torch.uint8,
+                           device="cuda")
+        wo = P.allocate_outputs()
+        wo["S"], wo["K"] = prior["S"][256:].contiguous(), prior["K"][256:].contiguous()
+        ws_w = torch.empty(lqt.lqt_warm_workspace_bytes([P], [wo]), dtype=torch.uint8,
+                           device="cuda")
+        cold = lambda: lqt.lqt_solve_batched([P], [cold_out], ws_c, stream)  # noqa: E731
+        hot = lambda: lqt.lqt_solve_warm([P], [wo], ws_w, stream)  # noqa: E731
+        for f in (cold, hot):
+            for _ in range(3):
+                f()
+        tc = _time_solves(cold, 20, flush, stream)
+        tw = _time_solves(hot, 20, flush, stream)
+        err = {k: accuracy.rel_fro(wo[k].double().cpu().numpy(),
+                                   cold_out[k].double().cpu().numpy()) for k in ("v", "x", "u")}
+        res.append({"n": n, "T": 2048, "full_solve_ms": float(np.median(tc)),
+                    "warm_solve_ms": float(np.median(tw)),
+                    "speedup": float(np.median(tc) / np.median(tw)),
+                    "warm_vs_full_rel_error": err})
+    return res
 
 
 def measured_compute_peaks():

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "lqt_lanes.cuh"
+#include "lqt_mma.cuh"
 #include "lqt_tma.cuh"
 
 namespace lqt {
@@ -247,6 +248,86 @@ constexpr int kd_ld() {
     return lds(N + 1);
 }
 
+// Groups of 32 lanes in FP32 (n = 32) run their dense products on the tensor
+// cores (lqt_mma.cuh, 3xTF32 with FP32 accumulation); the solves and the
+// vector terms stay on the CUDA cores.
+template <typename R, int N>
+constexpr bool use_tensor_cores() {
+    return N == 32 && sizeof(R) == 4;
+}
+
+// riccati (below) for a 32-lane FP32 group: the same formulas and shared-memory
+// layout, with S L, S F, U + L^T S L, L^T S F, F - L K, S F - S L K and
+// Q + F^T (S Ft) as warp-wide tensor-core products.
+template <int N, int M>
+__device__ bool riccati_tc(float* val, const float* sb, float* Kd, float* Ft, float* scr,
+                           const Group<N>& g) {
+    using SLay = StepLayout<N, M>;
+    using E = LElem<N>;
+    using V = LValue<N>;
+    using A = LAffine<N>;
+    constexpr int LD = SLay::LD, LM = SLay::LM, LK = kd_ld<N>();
+    const float* e = sb + SLay::E;
+    const float* F = e + E::OA;
+    const float* c = e + E::OB;
+    const float* Q = e + E::OJ;
+    const float* q = e + E::OE;
+    const float* L = sb + SLay::L;
+    const float* U = sb + SLay::U;
+    const float* S = val + V::OS;
+    const float* v = val + V::OV;
+    float* SL = scr;            // N x M
+    float* SF = SL + N * LM;    // N x N  (later S Ft)
+    float* G = SF + N * LD;     // M x M
+    float* ev = G + M * LM;     // N
+    float* O = ev + N;          // N x N + N
+    const int r = g.lr;
+    mma_mul<N, N, M, false>(SL, LM, S, LD, L, LM, nullptr, 0, 1.f);
+    mma_mul<N, N, N, false>(SF, LD, S, LD, F, LD, nullptr, 0, 1.f);
+    {
+        float t = v[r];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t -= S[r * LD + k] * c[k];
+        ev[r] = t;
+    }
+    g.sync();
+    // G = U + L^T S L ; [L^T S F | L^T (v - S c)]
+    mma_mul<M, N, M, true>(G, LM, L, LM, SL, LM, U, LM, 1.f);
+    mma_mul<M, N, N, true>(Kd, LK, SL, LM, F, LD, nullptr, 0, 1.f);
+    if (r < M) {
+        float w = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) w += L[k * LM + r] * ev[k];
+        Kd[r * LK + N] = w;
+    }
+    g.sync();
+    const bool ok = solve_spd<N, M, N + 1>(G, LM, Kd, LK, g);
+    // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
+    mma_mul<N, M, N, false>(Ft + A::OF, LD, L, LM, Kd, LK, F, LD, -1.f);
+    mma_mul<N, M, N, false>(SF, LD, SL, LM, Kd, LK, SF, LD, -1.f);
+    {
+        float ct = c[r];
+#pragma unroll
+        for (int a = 0; a < M; ++a) ct += L[r * LM + a] * Kd[a * LK + N];
+        Ft[A::OC + r] = ct;
+    }
+    g.sync();
+    // S <- F^T (S Ft) + Q ; v <- Ft^T (v - S c) + q
+    mma_mul<N, N, N, true>(O, LD, F, LD, SF, LD, Q, LD, 1.f);
+    {
+        float t = q[r];
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) t += Ft[A::OF + k * LD + r] * ev[k];
+        O[N * LD + r] = t;
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = 0.5f * (O[r * LD + j] + O[j * LD + r]);
+    val[V::OV + r] = O[N * LD + r];
+    g.sync();
+    return ok;
+}
+
 // The gains of one Riccati step (Sec. II-B, eq. Control_LQT) at the value
 // (S, v) in val: Kd = [K | d] (M x (N + 1), row stride kd_ld, u = d - K x)
 // from G = U + L^T S L,  G [K | d] = [L^T S F | L^T (v - S c)].  Leaves
@@ -311,6 +392,8 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
 // (LAffine: F - L K, c + L d), and replaces val by (S_k, v_k).
 template <typename R, int N, int M>
 __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N>& g) {
+    if constexpr (use_tensor_cores<R, N>())
+        return riccati_tc<N, M>(val, sb, Kd, Ft, scr, g);
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     using V = LValue<N>;
@@ -391,6 +474,104 @@ constexpr int fold_scratch() {
            M * lds(2 * N + 1) /*rhs*/;
 }
 
+// fold_step (below) for a 32-lane FP32 group: the same formulas and scratch
+// layout, with J2 F, J2 L, A2 F, A2 L, U + L^T J2 L, L^T J2 F, F^T J2 F,
+// A2 F - P2 Zt, C2 + P2 Pt and J1 + F^T J2 F - Z^T Zt as warp-wide
+// tensor-core products.
+template <int N, int M>
+__device__ bool fold_step_tc(float* P, const float* sb, float* scr, const Group<N>& g) {
+    using SLay = StepLayout<N, M>;
+    using E = LElem<N>;
+    constexpr int NR = 2 * N + 1;
+    constexpr int LD = SLay::LD, LM = SLay::LM, LR = lds(NR);
+    const float* e1 = sb + SLay::E;
+    const float* F = e1 + E::OA;
+    const float* c = e1 + E::OB;
+    const float* L = sb + SLay::L;
+    const float* U = sb + SLay::U;
+    float* JF = scr;              // N x N
+    float* A2F = JF + N * LD;     // N x N
+    float* FJF = A2F + N * LD;    // N x N
+    float* P2 = FJF + N * LD;     // N x M
+    float* JL = P2 + N * LM;      // N x M
+    float* Z = JL + N * LM;       // M x N
+    float* w = Z + M * LD;        // N
+    float* A2c = w + N;           // N
+    float* G = A2c + N;           // M x M
+    float* rhs = G + M * LM;      // M x NR
+    float* O = JF;                // staged C and J (2 N x N), after JF and A2F are consumed
+    const int r = g.lr;
+    // 1. J2 F, J2 L, A2 F, A2 L; w = eta2 - J2 c, A2 c
+    mma_mul<N, N, N, false>(JF, LD, P + E::OJ, LD, F, LD, nullptr, 0, 1.f);
+    mma_mul<N, N, M, false>(JL, LM, P + E::OJ, LD, L, LM, nullptr, 0, 1.f);
+    mma_mul<N, N, N, false>(A2F, LD, P + E::OA, LD, F, LD, nullptr, 0, 1.f);
+    mma_mul<N, N, M, false>(P2, LM, P + E::OA, LD, L, LM, nullptr, 0, 1.f);
+    {
+        float t = P[E::OE + r], ac = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) {
+            t -= P[E::OJ + r * LD + k] * c[k];
+            ac += P[E::OA + r * LD + k] * c[k];
+        }
+        w[r] = t;
+        A2c[r] = ac;
+    }
+    g.sync();
+    // P2^T into the right sides
+#pragma unroll 4
+    for (int a = 0; a < M; ++a) rhs[a * LR + N + 1 + r] = P2[r * LM + a];
+    // 2. G = U + L^T JL, Z = L^T JF, L^T w; F^T JF
+    mma_mul<M, N, M, true>(G, LM, L, LM, JL, LM, U, LM, 1.f);
+    mma_mul<M, N, N, true>(Z, LD, L, LM, JF, LD, nullptr, 0, 1.f);
+    mma_mul<N, N, N, true>(FJF, LD, F, LD, JF, LD, nullptr, 0, 1.f);
+    if (r < M) {
+        float t = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) t += L[k * LM + r] * w[k];
+        rhs[r * LR + N] = t;
+    }
+    g.sync();
+    if (r < M) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) rhs[r * LR + j] = Z[r * LD + j];
+    }
+    g.sync();
+    // 3. [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]
+    const bool ok = solve_spd<N, M, NR>(G, LM, rhs, LR, g);
+    // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (A2 is not read again)
+    mma_mul<N, M, N, false>(P + E::OA, LD, P2, LM, rhs, LR, A2F, LD, -1.f);
+    {
+        float t = A2c[r] + P[E::OB + r];
+#pragma unroll
+        for (int a = 0; a < M; ++a) t += P2[r * LM + a] * rhs[a * LR + N];
+        P[E::OB + r] = t;
+        // J1 + F^T J2 F, in place (row r)
+#pragma unroll
+        for (int j = 0; j < N; ++j) FJF[r * LD + j] += e1[E::OJ + r * LD + j];
+    }
+    g.sync();  // A2F and JF consumed: O (over JF, A2F) may be written
+    //    C = C2 + P2 Pt and J = J1 + F^T J2 F - Z^T Zt staged in O
+    mma_mul<N, M, N, false>(O, LD, P2, LM, rhs + N + 1, LR, P + E::OC, LD, 1.f);
+    mma_mul<N, M, N, true>(O + N * LD, LD, Z, LD, rhs, LR, FJF, LD, -1.f);
+    //    eta = eta1 + F^T w - Z^T om
+    {
+        float t = e1[E::OE + r];
+#pragma unroll
+        for (int a = 0; a < M; ++a) t -= Z[a * LD + r] * rhs[a * LR + N];
+#pragma unroll 4
+        for (int k = 0; k < N; ++k) t += F[k * LD + r] * w[k];
+        P[E::OE + r] = t;
+    }
+    g.sync();
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        P[E::OC + r * LD + j] = 0.5f * (O[r * LD + j] + O[j * LD + r]);
+        P[E::OJ + r * LD + j] = 0.5f * (O[N * LD + r * LD + j] + O[N * LD + j * LD + r]);
+    }
+    g.sync();
+    return ok;
+}
+
 // P <- a_k (x) P (eq. lqt_comb, a_k = (F, c, L U^{-1} L^T, H^T X r, H^T X H)
 // from the step buffer).  With C_k = L W L^T, W = U^{-1}, and
 // G = U + L^T J2 L:  (I + C_k J2)^{-1} = I - L G^{-1} L^T J2, and
@@ -402,6 +583,7 @@ constexpr int fold_scratch() {
 // Returns false if G is numerically singular.
 template <typename R, int N, int M>
 __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
+    if constexpr (use_tensor_cores<R, N>()) return fold_step_tc<N, M>(P, sb, scr, g);
     using SLay = StepLayout<N, M>;
     using E = LElem<N>;
     constexpr int NR = 2 * N + 1;

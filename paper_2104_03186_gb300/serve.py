@@ -13,11 +13,14 @@ and solves the batch's cold requests with one lqt_solve_batched call (per
 state size present, one persistent launch for n = 4 and one chunked pipeline
 for n >= 8).  A warm request's S_k and K_k are those of the request it
 continues, shifted by s steps (same model, same terminal weights; they do not
-depend on the reference or the initial state), so with reuse_warm (the
-default) the batch's warm requests go to one lqt_solve_warm call that reads
-them in place from the device-resident outputs of the cold request that
-computed them, and computes only v, x* and u*.  Batches on different streams
-run concurrently, so
+depend on the reference or the initial state).  With reuse_warm (the
+default), the warm requests of a state size n >= 8 that has no full solve in
+the batch go to one lqt_solve_warm call, on a second stream beside the full
+solves: it reads S and K in place from the device-resident outputs of the
+request that computed them and computes only v, x* and u*.  (Where a size has
+full solves anyway, its warm requests join them: a second pipeline of
+launches would cost more host time than it saves on the device.)  Batches on
+different streams run concurrently, so
 requests that arrive while others are on the GPU start without waiting for
 them.  Per batch the references and initial states go up in one host-to-device
 copy and the optimal controls u* come back in one device-to-host copy.
@@ -55,6 +58,8 @@ class Request:
     refs: int = 0           # warm requests still pointing at this one's outputs
     owner: int = -1         # request whose outputs hold this one's S_k, K_k
     skoff: int = 0          # step of this request's S_0, K_0 in the owner's arrays
+    reused: bool = False    # solved from the owner's S, K (lqt_solve_warm)
+    holds: Optional[List[int]] = None  # requests whose outputs this one may read
 
 
 class ModelPool:
@@ -111,10 +116,6 @@ def out_bytes(n: int, m: int, T: int) -> int:
     return 4 * ((T + 1) * n * n + (T + 1) * n + T * m * n + (T + 1) * n)
 
 
-def warm_out_bytes(n: int, T: int) -> int:
-    """Device bytes of a warm request solved from its owner's S and K: v, x."""
-    return 4 * 2 * (T + 1) * n
-
 
 def make_requests(count: int, rate: float, seed: int = 0, sizes=(4, 8, 16, 32),
                   t_lo: int = 32, t_hi: int = 2048, warm_frac: float = 0.3,
@@ -155,6 +156,7 @@ class _Slot:
         import torch
 
         self.stream = torch.cuda.Stream()
+        self.warm_stream = torch.cuda.Stream()  # the batch's warm solves, beside the cold ones
         self.cap_in = self.cap_u = self.cap_items = 0
         self.ensure(1 << 22, 1 << 21, 1024)
 
@@ -208,19 +210,15 @@ class Server:
         self.launches = 0
 
     def _reused(self, req: Request) -> bool:
-        """Solved from its owner's S and K (its own buffer holds v, x)."""
-        return req.owner != req.rid
+        """Solved from its owner's S and K (its own S and K regions unused)."""
+        return req.reused
 
     def _bytes(self, req: Request) -> int:
-        if self._reused(req):
-            return warm_out_bytes(req.n, req.T)
         return out_bytes(req.n, self.pool.models[req.n][0].m, req.T)
 
     def _x_offset(self, req: Request) -> int:
         """Element offset of x in the request's own buffer."""
         n, T = req.n, req.T
-        if self._reused(req):
-            return (T + 1) * n
         m = self.pool.models[n][0].m
         return (T + 1) * n * n + (T + 1) * n + T * m * n
 
@@ -242,33 +240,32 @@ class Server:
         """Host copies of a completed request's S, v, K, x* (u* is q.u)."""
         n, T = q.n, q.T
         m = self.pool.models[n][0].m
-        if not self._reused(q):
-            return unpack_outputs(q.out.cpu().numpy(), n, m, T)
-        own = byid[q.owner]
-        full = unpack_outputs(own.out.cpu().numpy(), n, m, own.T)
-        buf = q.out.cpu().numpy()
-        return {"S": full["S"][q.skoff: q.skoff + T + 1].copy(),
-                "K": full["K"][q.skoff: q.skoff + T].copy(),
-                "v": buf[: (T + 1) * n].reshape(T + 1, n),
-                "x": buf[(T + 1) * n:].reshape(T + 1, n)}
+        res = unpack_outputs(q.out.cpu().numpy(), n, m, T)
+        if self._reused(q):
+            own = byid[q.owner]
+            full = unpack_outputs(own.out.cpu().numpy(), n, m, own.T)
+            res["S"] = full["S"][q.skoff: q.skoff + T + 1].copy()
+            res["K"] = full["K"][q.skoff: q.skoff + T].copy()
+        return res
 
     def run(self, reqs: List[Request], realtime: bool = True):
         """Serve the stream; returns per-request latencies (s) and summary."""
         import torch
 
         byid = {r.rid: r for r in reqs}
-        for q in sorted(reqs, key=lambda r: r.rid):  # predecessors come first
-            q.refs = 0
-            if q.warm_of < 0 or not self.reuse_warm:
-                q.owner, q.skoff = q.rid, 0
-            else:
-                prior = byid[q.warm_of]
-                q.owner, q.skoff = prior.owner, prior.skoff + q.shift
-        for q in reqs:  # warm requests that will read each request's outputs
-            if q.warm_of >= 0:
-                byid[q.warm_of].refs += 1         # its x*_s
-                if q.owner not in (q.rid, q.warm_of):
-                    byid[q.owner].refs += 1       # its S_k, K_k
+        for q in reqs:
+            q.refs, q.reused, q.owner, q.skoff, q.holds = 0, False, q.rid, 0, []
+        # warm requests keep the outputs they may read: the predecessor's x*_s
+        # and, when reusing, S_k and K_k, which sit with the first ancestor that
+        # was solved in full (up the chain of warm requests to a cold one)
+        for q in reqs:
+            a = q.warm_of
+            while a >= 0:
+                byid[a].refs += 1
+                q.holds.append(a)
+                if not self.reuse_warm:
+                    break
+                a = byid[a].warm_of
         queue = deque(sorted(reqs, key=lambda r: r.arrival))
         ready: deque = deque()    # warm requests whose predecessor has finished
         parked: Dict[int, List[Request]] = {}  # predecessor rid -> warm requests
@@ -317,14 +314,9 @@ class Server:
                         q.result = self._results(q, byid)
                         q.result["u"] = q.u
                     done += 1
-                    if q.warm_of >= 0:
-                        prior = byid[q.warm_of]
-                        prior.refs -= 1
-                        self._release(prior)
-                        if q.owner not in (q.rid, q.warm_of):
-                            own = byid[q.owner]
-                            own.refs -= 1
-                            self._release(own)
+                    for a in q.holds:
+                        byid[a].refs -= 1
+                        self._release(byid[a])
                     self._release(q)  # kept while warm requests still need it
                     if q.rid in parked:
                         ready.extend(parked.pop(q.rid))
@@ -337,9 +329,16 @@ class Server:
         torch.cuda.synchronize()
         lat = np.array([q.done - q.arrival for q in reqs])
         span = max(q.done for q in reqs) - min(q.arrival for q in reqs)
+        warm = np.array([q.warm_of >= 0 for q in reqs])
+
+        def pct(sel, p):
+            return float(np.percentile(lat[sel], p) * 1e3) if sel.any() else None
+
         return lat, {"requests": len(reqs), "solves_per_s": len(reqs) / span,
                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                     "cold_p50_ms": pct(~warm, 50), "cold_p99_ms": pct(~warm, 99),
+                     "warm_p50_ms": pct(warm, 50), "warm_p99_ms": pct(warm, 99),
                      "mean_ms": float(lat.mean() * 1e3), "peak_device_bytes": self.peak_mem,
                      "time_steps": int(sum(q.T for q in reqs)),
                      "warm_requests": int(sum(q.warm_of >= 0 for q in reqs)),
@@ -365,11 +364,42 @@ class Server:
                 hv[a + q.r.size: a + q.r.size + q.n] = q.x0
         din = np.uint64(slot.d_in.data_ptr())
         dup = np.uint64(slot.d_u.data_ptr())
+        # A warm request is solved from its owner's S and K when its state size
+        # has no request of the batch that needs a full solve anyway, and
+        # n >= 8: the full solves of a size share their launches, so adding a
+        # separate warm pipeline beside them would add launches (host time) for
+        # little device time, and at n = 4 the full solve is one launch.
+        full_sizes = {q.n for q in batch if q.warm_of < 0 or not self.reuse_warm or q.n < 8}
+        for q in batch:
+            q.reused = False
+            if q.warm_of >= 0 and self.reuse_warm and q.n not in full_sizes:
+                prior = byid[q.warm_of]
+                q.reused = True
+                if prior.reused:
+                    q.owner, q.skoff = prior.owner, prior.skoff + q.shift
+                else:
+                    q.owner, q.skoff = prior.rid, q.shift
         cold = [i for i, q in enumerate(batch) if not self._reused(q)]
         warm = [i for i, q in enumerate(batch) if self._reused(q)]
         st = slot.stream
         with torch.cuda.stream(st):
             slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
+            if warm:
+                # the warm solves run on the slot's second stream, concurrently
+                # with the cold ones, after the input copy; joined before u*
+                # goes back
+                fork = torch.cuda.Event()
+                fork.record(st)
+                slot.warm_stream.wait_event(fork)
+                it = self._items(slot.items[len(cold): k], [batch[i] for i in warm],
+                                 in_off[warm], u_off[warm], din, dup, byid)
+                nbytes = lqt.lqt_warm_workspace_bytes_array(it)
+                if nbytes == 0:
+                    raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "warm workspace")
+                slot.ensure_ws(nbytes, warm=True)
+                lqt.lqt_solve_warm_array(it, slot.ws_warm, slot.warm_stream)
+                join = torch.cuda.Event()
+                join.record(slot.warm_stream)
             if cold:
                 it = self._items(slot.items[: len(cold)], [batch[i] for i in cold],
                                  in_off[cold], u_off[cold], din, dup, byid)
@@ -379,13 +409,7 @@ class Server:
                 slot.ensure_ws(nbytes)
                 lqt.lqt_solve_batched_array(it, slot.ws, st)
             if warm:
-                it = self._items(slot.items[len(cold): k], [batch[i] for i in warm],
-                                 in_off[warm], u_off[warm], din, dup, byid)
-                nbytes = lqt.lqt_warm_workspace_bytes_array(it)
-                if nbytes == 0:
-                    raise lqt.LQTError(lqt.LQT_EUNSUPPORTED, "warm workspace")
-                slot.ensure_ws(nbytes, warm=True)
-                lqt.lqt_solve_warm_array(it, slot.ws_warm, st)
+                st.wait_event(join)
             nu_el = int(u_off[-1])
             slot.h_u[:nu_el].copy_(slot.d_u[:nu_el], non_blocking=True)
             ev = torch.cuda.Event()
@@ -450,8 +474,8 @@ class Server:
                 S["K"][i] = obase + np.uint64(4) * ((To + np.uint64(1)) * nu[i] * nu[i] +
                                                     (To + np.uint64(1)) * nu[i]) + \
                     np.uint64(4 * q.skoff * int(nm[i]))
-                S["v"][i] = outp
-                S["x"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i]
+                S["v"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i] * nu[i]
+                S["x"][i] = outp + np.uint64(4 * self._x_offset(q))
             else:
                 S["S"][i] = outp
                 S["v"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i] * nu[i]

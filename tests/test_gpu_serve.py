@@ -44,7 +44,10 @@ def test_results_alone_equal_results_in_the_mix(reuse_warm):
     lat, summary = srv.run(reqs)
     assert summary["requests"] == 120 and np.all(np.isfinite(lat)) and np.all(lat >= 0)
     assert summary["warm_requests"] > 0
-    assert summary["warm_reused"] == (summary["warm_requests"] if reuse_warm else 0)
+    if reuse_warm:
+        assert 0 < summary["warm_reused"] <= summary["warm_requests"], summary
+    else:
+        assert summary["warm_reused"] == 0
     assert summary["batches"] > 1
     byid = {q.rid: q for q in reqs}
     bitwise = 0
