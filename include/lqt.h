@@ -234,6 +234,27 @@ size_t lqt_batch_workspace_bytes(const lqt_batch_item *items, int32_t count);
 lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *workspace,
                              size_t workspace_bytes, void *stream);
 
+/* Launch plan of lqt_solve_batched for the lane-group sizes (n >= 8; not in
+ * the paper: a property of this implementation).  Each problem's steps are
+ * cut into a power-of-two number of chunks, one lane group per chunk (Sec. V-C
+ * block processing); by default the chunk length is the batch's total steps
+ * over the resident lane groups, clamped to [4, 64].  An entry {n, t_max,
+ * chunk_steps} sets the chunk length of the problems of state size n with
+ * T <= t_max (the first matching entry applies); `persistent` selects one
+ * cooperative launch per state size that runs every tree level with grid
+ * barriers (1, the default) or one launch per tree level (0).  count = 0
+ * clears the table.  The settings are process-wide; calls already launched
+ * are not affected.  Returns LQT_EINVAL for more than 64 entries or a
+ * non-positive n or chunk length.  The Python binding applies the table that
+ * paper_2104_03186_gb300/tune.py measured on this GPU model. */
+typedef struct {
+    int32_t n;
+    int32_t chunk_steps;
+    int64_t t_max;
+} lqt_batch_tune_entry;
+lqt_status lqt_batch_set_tuning(const lqt_batch_tune_entry *entries, int32_t count,
+                                int32_t persistent);
+
 /* Warm solves: problems whose S_k and K_k are already known.
  *
  * S_k and K_k depend on the matrices F, L, U, H, X and the terminal H_T, X_T

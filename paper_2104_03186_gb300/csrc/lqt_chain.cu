@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "lqt_chain_api.h"
@@ -14,6 +16,25 @@ namespace {
 
 // smallest chunk the planner makes, in steps
 constexpr long long kMinChunk = 4;
+
+// Batches of the lane sizes: one persistent launch (default) or one launch
+// per tree level (lqt_batch_set_tuning).
+std::atomic<bool> g_batch_persistent{true};
+
+// Tuned chunk lengths of batches (lqt_batch_set_tuning): entry e applies to
+// problems of state size n = e.n with T <= e.t_max (the first such entry).
+constexpr int kMaxTune = 64;
+std::mutex g_tune_mu;
+lqt_batch_tune_entry g_tune[kMaxTune];
+int g_tune_count = 0;
+
+// The tuned chunk length for a problem, or 0 (none).
+long long tuned_chunk(int n, long long T) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int i = 0; i < g_tune_count; ++i)
+        if (g_tune[i].n == n && T <= g_tune[i].t_max) return g_tune[i].chunk_steps;
+    return 0;
+}
 
 const ChainVariant* find_chain(int dtype, int n, int m, bool mixed) {
     const ChainVariant* (*tables[])(int*) = {&chain_variants_n4, &chain_variants_n8,
@@ -95,8 +116,10 @@ lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, co
     for (int i = 0; i < count; ++i) {
         const lqt_batch_item& it = items[idx[i]];
         const long long T = it.problem.T;
+        const long long tuned = tuned_chunk(it.problem.n, T);
+        const long long Bi = tuned > 0 ? tuned : Bt;
         long long nc = 1;
-        while (nc * 2 * Bt <= T && nc < (1LL << 20)) nc *= 2;
+        while (nc * 2 * Bi <= T && nc < (1LL << 20)) nc *= 2;
         ChainProblem& cp = (*out)[(size_t)i];
         cp.problem = &it.problem;
         cp.solution = &it.solution;
@@ -189,6 +212,7 @@ lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int co
     const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
     if (st != LQT_OK) return st;
     ChainCall call{probs.data(), count, false, false, false, false, ws, ws_bytes, status};
+    call.persistent = g_batch_persistent.load();
     return v->run(call, s, nullptr);
 }
 
@@ -245,3 +269,17 @@ lqt_status chain_warm_solve(const lqt_batch_item* items, const int* idx, int cou
 }
 
 }  // namespace lqt
+
+extern "C" lqt_status lqt_batch_set_tuning(const lqt_batch_tune_entry* entries, int32_t count,
+                                           int32_t persistent) {
+    using namespace lqt;
+    if (count < 0 || count > kMaxTune || (count > 0 && !entries)) return LQT_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (entries[i].n < 1 || entries[i].t_max < 0 || entries[i].chunk_steps < 1)
+            return LQT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int i = 0; i < count; ++i) g_tune[i] = entries[i];
+    g_tune_count = count;
+    g_batch_persistent.store(persistent != 0);
+    return LQT_OK;
+}

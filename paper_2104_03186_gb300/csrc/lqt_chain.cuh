@@ -170,11 +170,12 @@ struct FdownSmem {
 };
 
 template <int N, int M>
-struct RollSmem {  // x, u, then F_k (N x lds(N)), L_k (N x lds(M)), K_k (M x lds(N))
+struct RollSmem {  // x, u, then two buffers of F_k (N x lds(N)), L_k (N x lds(M)), K_k (M x lds(N))
     static constexpr int F = N + M;
     static constexpr int L = F + N * lds(N);
     static constexpr int K = L + N * lds(M);
-    static constexpr int SIZE = K + M * lds(N);
+    static constexpr int BUF = N * lds(N) + N * lds(M) + M * lds(N);  // one step's matrices
+    static constexpr int SIZE = F + 2 * BUF;
 };
 
 // Groups per CTA: at most 256 threads, and at most 112 KB of shared memory so
@@ -207,15 +208,12 @@ __device__ __forceinline__ bool h_is_identity(const DescT<R>& D, const Group<N>&
 
 // ---- chunk totals ----------------------------------------------------------
 template <typename R, typename RT, int N, int M, int NG>
-__global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
+__device__ __forceinline__ void b_cfold(const Args<R, RT>& a, long long c,
+                                        unsigned char* smem_raw, int gi) {
     using S = FoldSmem<N, M>;
     using E = LElem<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sh = reinterpret_cast<R*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
     R* gs = sh + gi * gstride<N>(S::SIZE);
@@ -240,17 +238,23 @@ __global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
     flag(a.status, ok);
 }
 
+template <typename R, typename RT, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_cfold(Args<R, RT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long c = (long long)blockIdx.x * NG + gi;
+    if (c >= a.C) return;
+    b_cfold<R, RT, N, M, NG>(a, c, smem_raw, gi);
+}
+
 // ---- up-sweep level h: E[i] <- E[i] (x) E[i + h], i a multiple of 2h -------
 // (i < active: the chunks of the problems with NC >= 2h)
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cup(RT* E_, long long active, int h, int* status) {
+__device__ __forceinline__ void b_cup(RT* E_, long long active, int h, int* status, long long i,
+                                        unsigned char* smem_raw, int gi) {
     using E = LElem<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
-    if (i >= active) return;
     RT* e1 = sh + gi * gstride<N>(UpSmem<N>::SIZE);
     RT* e2 = e1 + E::SIZE;
     RT* scr = e2 + E::SIZE;
@@ -261,6 +265,15 @@ __global__ void __launch_bounds__(NG* N) k_cup(RT* E_, long long active, int h, 
     RT* out = E_ + i * E::SIZE;
     for (int t = g.lr; t < E::SIZE; t += N) out[t] = e1[t];
     flag(status, ok);
+}
+
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_cup(RT* E_, long long active, int h, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
+    if (i >= active) return;
+    b_cup<RT, N, NG>(E_, active, h, status, i, smem_raw, gi);
 }
 
 // ---- terminal values (one CTA of N threads per problem): V[c0] <- the value
@@ -315,16 +328,13 @@ __global__ void __launch_bounds__(N) k_cterm(Args<R, RT> a) {
 
 // ---- down-sweep level h: V[i + h] <- V[i]; V[i] <- E[i + h] (x) V[i] --------
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, long long active, int h,
-                                                 int* status) {
+__device__ __forceinline__ void b_cdown(const RT* E_, RT* V_, long long active, int h,
+                                                 int* status, long long i,
+                                        unsigned char* smem_raw, int gi) {
     using E = LElem<N>;
     using V = LValue<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
-    if (i >= active) return;
     RT* e = sh + gi * gstride<N>(DownSmem<N>::SIZE);
     RT* val = e + E::SIZE;
     RT* scr = val + V::SIZE;
@@ -337,18 +347,25 @@ __global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, long long
     flag(status, ok);
 }
 
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_cdown(const RT* E_, RT* V_, long long active, int h,
+                                                 int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long i = ((long long)blockIdx.x * NG + gi) * 2 * h;
+    if (i >= active) return;
+    b_cdown<RT, N, NG>(E_, V_, active, h, status, i, smem_raw, gi);
+}
+
 // ---- per-chunk Riccati re-fold with outputs and the chunk affine map -------
 template <typename R, typename RT, int N, int M, int NG>
-__global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
+__device__ __forceinline__ void b_crefold(const Args<R, RT>& a, long long c,
+                                        unsigned char* smem_raw, int gi) {
     using S = RefoldSmem<N, M>;
     using V = LValue<N>;
     using A = LAffine<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sh = reinterpret_cast<R*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
     R* gs = sh + gi * gstride<N>(S::SIZE);
@@ -408,16 +425,22 @@ __global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
     flag(a.status, ok);
 }
 
+template <typename R, typename RT, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_crefold(Args<R, RT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long c = (long long)blockIdx.x * NG + gi;
+    if (c >= a.C) return;
+    b_crefold<R, RT, N, M, NG>(a, c, smem_raw, gi);
+}
+
 // ---- forward up-sweep level h: FE[j] <- FE[j] o FE[j - h], j = 2h q + 2h - 1
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, long long active, int h) {
+__device__ __forceinline__ void b_cfup(RT* FE, long long active, int h, long long j,
+                                        unsigned char* smem_raw, int gi) {
     using A = LAffine<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     RT* sh = reinterpret_cast<RT*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
-    if (j >= active) return;
     RT* f1 = sh + gi * gstride<N>(FupSmem<N>::SIZE);
     RT* f2 = f1 + A::SIZE;
     copy_in(f1, FE + (j - h) * A::SIZE, A::SIZE, g.lr, N);
@@ -427,17 +450,23 @@ __global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, long long active, int h)
     for (int t = g.lr; t < A::SIZE; t += N) FE[j * A::SIZE + t] = f2[t];
 }
 
-// ---- forward down-sweep level h: X[j - h] <- X[j]; X[j] <- FE[j - h](X[j]) -
-// (each problem's top slot X[c0 + NC - 1] holds x_0 from k_cterm)
 template <typename RT, int N, int NG>
-__global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, long long active, int h) {
-    using A = LAffine<N>;
+__global__ void __launch_bounds__(NG* N) k_cfup(RT* FE, long long active, int h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RT* sh = reinterpret_cast<RT*>(smem_raw);
-    const Group<N> g;
     const int gi = threadIdx.x / N;
     const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
     if (j >= active) return;
+    b_cfup<RT, N, NG>(FE, active, h, j, smem_raw, gi);
+}
+
+// ---- forward down-sweep level h: X[j - h] <- X[j]; X[j] <- FE[j - h](X[j]) -
+// (each problem's top slot X[c0 + NC - 1] holds x_0 from k_cterm)
+template <typename RT, int N, int NG>
+__device__ __forceinline__ void b_cfdown(const RT* FE, RT* X, long long active, int h, long long j,
+                                        unsigned char* smem_raw, int gi) {
+    using A = LAffine<N>;
+    RT* sh = reinterpret_cast<RT*>(smem_raw);
+    const Group<N> g;
     RT* f = sh + gi * gstride<N>(FdownSmem<N>::SIZE);
     RT* x = f + A::SIZE;
     const int r = g.lr;
@@ -450,15 +479,21 @@ __global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, long long
     X[j * N + r] = x[r];
 }
 
+template <typename RT, int N, int NG>
+__global__ void __launch_bounds__(NG* N) k_cfdown(const RT* FE, RT* X, long long active, int h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long j = ((long long)blockIdx.x * NG + gi) * 2 * h + 2 * h - 1;
+    if (j >= active) return;
+    b_cfdown<RT, N, NG>(FE, X, active, h, j, smem_raw, gi);
+}
+
 // ---- per-chunk rollout of x*_k and u*_k ------------------------------------
 template <typename R, typename RT, int N, int M, int NG>
-__global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void b_croll(const Args<R, RT>& a, long long c,
+                                        unsigned char* smem_raw, int gi) {
     R* sh = reinterpret_cast<R*>(smem_raw);
     const Group<N> g;
-    const int gi = threadIdx.x / N;
-    const long long c = (long long)blockIdx.x * NG + gi;
-    if (c >= a.C) return;
     const Item<R>& it = a.items[find_chunk(a.items, a.count, c)];
     const DescT<R>& D = it.D;
     R* xc = sh + gi * gstride<N>(RollSmem<N, M>::SIZE);
@@ -470,25 +505,39 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
     const long long e0 = s0 + it.B < T ? s0 + it.B : T;
     xc[r] = lc == 0 ? D.x0[r] : static_cast<R>(a.X[c * N + r]);
     g.sync();
+    using RS = RollSmem<N, M>;
     constexpr int LD = lds(N), LM = lds(M);
-    R* Fs = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::F;
-    R* Ls = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::L;
-    R* Ks = sh + gi * gstride<N>(RollSmem<N, M>::SIZE) + RollSmem<N, M>::K;
-    for (long long k = s0; k < e0; ++k) {
-        // F_k and L_k into shared memory by coalesced asynchronous copies
+    R* base = sh + gi * gstride<N>(RS::SIZE);
+    // F_k, L_k, K_k into shared memory by coalesced asynchronous copies, one
+    // step ahead (two buffers), so each step's loads overlap the step before
+    auto stage = [&](long long k, int b) {
+        R* Fb = base + RS::F + b * RS::BUF;
+        R* Lb = base + RS::L + b * RS::BUF;
+        R* Kb = base + RS::K + b * RS::BUF;
         const R* F = D.F + k * D.sF;
         const R* Lk = D.L + k * D.sL;
 #pragma unroll 8
-        for (int t = r; t < N * N; t += N) cp_async<sizeof(R)>(Fs + (t / N) * LD + t % N, F + t);
+        for (int t = r; t < N * N; t += N) cp_async<sizeof(R)>(Fb + (t / N) * LD + t % N, F + t);
 #pragma unroll 4
-        for (int t = r; t < N * M; t += N) cp_async<sizeof(R)>(Ls + (t / M) * LM + t % M, Lk + t);
+        for (int t = r; t < N * M; t += N) cp_async<sizeof(R)>(Lb + (t / M) * LM + t % M, Lk + t);
 #pragma unroll 4
         for (int t = r; t < M * N; t += N)
-            cp_async<sizeof(R)>(Ks + (t / N) * LD + t % N, D.K + k * M * N + t);
+            cp_async<sizeof(R)>(Kb + (t / N) * LD + t % N, D.K + k * M * N + t);
         cp_async_commit();
+    };
+    if (s0 < e0) stage(s0, 0);
+    for (long long k = s0; k < e0; ++k) {
+        const int b = (int)((k - s0) & 1);
+        const R* Fs = base + RS::F + b * RS::BUF;
+        const R* Ls = base + RS::L + b * RS::BUF;
+        const R* Ks = base + RS::K + b * RS::BUF;
+        if (k + 1 < e0) stage(k + 1, b ^ 1);  // that buffer was last read before step k's syncs
         const R xr = xc[r];
         D.x[k * N + r] = a.refine_add ? D.x[k * N + r] + xr : xr;
-        cp_async_wait<0>();
+        if (k + 1 < e0)
+            cp_async_wait<1>();
+        else
+            cp_async_wait<0>();
         g.sync();
         // u = d - K x (lanes a < M), published through shared memory
         if (r < M) {
@@ -512,6 +561,15 @@ __global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
         g.sync();
         if (k == T - 1) D.x[T * N + r] = a.refine_add ? D.x[T * N + r] + t : t;
     }
+}
+
+template <typename R, typename RT, int N, int M, int NG>
+__global__ void __launch_bounds__(NG* N) k_croll(Args<R, RT> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gi = threadIdx.x / N;
+    const long long c = (long long)blockIdx.x * NG + gi;
+    if (c >= a.C) return;
+    b_croll<R, RT, N, M, NG>(a, c, smem_raw, gi);
 }
 
 // ---- Method 2 (Lemma LQT_trajectory_method2) --------------------------------

@@ -33,6 +33,9 @@ struct ChainCall {
     // warm solve (lqt_warm.cuh): S and K of every problem are given in its
     // solution; only v, the feedforward, x* and u* are computed
     bool warm = false;
+    // one persistent cooperative launch instead of one launch per tree level
+    // (no refinement, Method 1 only)
+    bool persistent = false;
 };
 
 struct ChainVariant {

@@ -11,6 +11,7 @@
 
 #include "lqt_chain.cuh"
 #include "lqt_chain_api.h"
+#include "lqt_persist.cuh"
 #include "lqt_warm.cuh"
 #include "lqt_launch.cuh"
 
@@ -147,11 +148,49 @@ struct Launcher {
     }
 
     static int blocks(long long items, int ng) { return (int)((items + ng - 1) / ng); }
+
+    // The persistent launch (lqt_persist.cuh): groups per CTA from its group
+    // block, as many CTAs as are co-resident (at most one group per chunk).
+    static constexpr int PERSIST_B = persist_group_bytes<R, RT, N, M>();
+    // an even number of groups per CTA (the up-sweep pairs them)
+    static constexpr int NG_PERSIST = groups_for<N>(PERSIST_B) & ~1;
+
+    static lqt_status run_persistent(const Args<R, RT>& a, const long long* active, int levels,
+                                     GridBarrier* bar, cudaStream_t s) {
+        if (levels > kMaxLevels) return LQT_EINVAL;
+        auto kern = k_cpersist<R, RT, N, M, NG_PERSIST>;
+        static std::atomic<bool> done[64];
+        const size_t smem = (size_t)NG_PERSIST * PERSIST_B;
+        if (chain_allow_smem(kern, done, smem) != cudaSuccess) return LQT_ECUDA;
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NG_PERSIST * N, smem) !=
+                cudaSuccess)
+            return LQT_ECUDA;
+        if (per_sm < 1) return LQT_ECUDA;
+        long long grid = (long long)per_sm * sms;
+        const long long need = (a.C + NG_PERSIST - 1) / NG_PERSIST;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        LevelPlan lp;
+        memset(&lp, 0, sizeof(lp));
+        lp.levels = levels;
+        for (int l = 0; l < levels; ++l) lp.active[l] = active[l];
+        if (cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return LQT_ECUDA;
+        Args<R, RT> aa = a;
+        long long limit = 1LL << 22;  // polls of 64 ns sleeps: far above any phase's length
+        void* args[] = {&aa, &lp, &bar, &limit};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3((unsigned)grid),
+                                        dim3(NG_PERSIST * N), args, smem, s) != cudaSuccess)
+            return LQT_ECUDA;
+        return LQT_OK;
+    }
     static char* base_of(const ChainCall& call) { return static_cast<char*>(call.ws); }
 
     // Workspace layout of a call (bytes from the start of the workspace).
     struct Layout {
-        size_t items1, items2, items3, consts, E, V, FE, X, E2, Pref, refine0, total;
+        size_t items1, items2, items3, consts, bar, E, V, FE, X, E2, Pref, refine0, total;
         long long C;
     };
 
@@ -173,6 +212,8 @@ struct Launcher {
         // the linear problem's constant matrices: L = 0 (N x M), U = I (M x M), H = I
         L.consts = off;
         if (newton) off += up((size_t)(N * M + M * M + N * N) * sizeof(R));
+        L.bar = off;  // grid barrier of the persistent launch
+        off += up(sizeof(GridBarrier));
         const size_t nc = (size_t)C;
         L.E = off;
         off += up(nc * LElem<N>::SIZE * sizeof(RT));
@@ -560,6 +601,14 @@ struct Launcher {
         a.status = call.status ? call.status : reinterpret_cast<int*>(base);
         a.out_mask = 7;
         a.refine_add = 0;
+        if (call.persistent && !refine && !method2 && !call.sequential) {
+            // one cooperative launch for the whole pass (batches)
+            const lqt_status st = run_persistent(
+                a, active.data(), levels, reinterpret_cast<GridBarrier*>(base + L.bar), s);
+            prof_end(prof, s);
+            if (st != LQT_OK) return st;
+            return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+        }
         pass(a, active.data(), levels, call.sequential, 0, false, s, prof, E2, Pref);
         if (newton) {
             // Newton correction of S and v, then K from the corrected S and v

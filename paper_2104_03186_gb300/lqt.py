@@ -63,6 +63,10 @@ LQT_REFINE_OFF, LQT_REFINE_ON, LQT_REFINE_AUTO, LQT_REFINE_FULL = 0, 1, 2, 3
 LQT_METHOD_DEFAULT, LQT_METHOD_1, LQT_METHOD_2 = 0, 1, 2
 
 
+class lqt_batch_tune_entry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("chunk_steps", ctypes.c_int32), ("t_max", ctypes.c_int64)]
+
+
 class lqt_options(ctypes.Structure):
     _fields_ = [("refine", ctypes.c_int32), ("method", ctypes.c_int32),
                 ("wait_probe_polls", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
@@ -117,6 +121,8 @@ def _load() -> ctypes.CDLL:
         "lqt_batch_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
         "lqt_solve_batched": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
         "lqt_warm_workspace_bytes": (sz, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32]),
+        "lqt_batch_set_tuning": (st, [ctypes.POINTER(lqt_batch_tune_entry), ctypes.c_int32,
+                                      ctypes.c_int32]),
         "lqt_solve_warm": (st, [ctypes.POINTER(lqt_batch_item), ctypes.c_int32, vp, sz, vp]),
         "lqt_cross_workspace_bytes": (sz, [P, ctypes.POINTER(lqt_cross), O]),
         "lqt_solve_cross": (st, [P, ctypes.POINTER(lqt_cross), S, O, vp, sz, vp]),
@@ -137,6 +143,40 @@ _lib = _load()
 
 def library() -> ctypes.CDLL:
     return _lib
+
+
+# ---------------------------------------------------------------------------
+# batch launch plan (tuned by paper_2104_03186_gb300.tune)
+# ---------------------------------------------------------------------------
+
+TUNED_PLANS = os.path.join(_PKG, "tuned_batch_plans.json")
+
+
+def lqt_batch_set_tuning(entries, persistent: bool = True) -> None:
+    """Set the chunk-length table and the launch mode of lqt_solve_batched for
+    the lane-group sizes: entries are (n, t_max, chunk_steps) triples."""
+    arr = (lqt_batch_tune_entry * max(len(entries), 1))()
+    for i, (n, t_max, b) in enumerate(entries):
+        arr[i].n, arr[i].t_max, arr[i].chunk_steps = int(n), int(t_max), int(b)
+    st = _lib.lqt_batch_set_tuning(arr, len(entries), 1 if persistent else 0)
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_batch_set_tuning")
+
+
+def apply_tuned_plans(path: str = TUNED_PLANS) -> bool:
+    """Apply the tuner's table (if the file exists); returns whether it did."""
+    import json
+
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        plan = json.load(f)
+    lqt_batch_set_tuning([(e["n"], e["t_max"], e["chunk_steps"]) for e in plan["entries"]],
+                         bool(plan.get("persistent", True)))
+    return True
+
+
+apply_tuned_plans()
 
 
 # ---------------------------------------------------------------------------
