@@ -36,10 +36,10 @@ struct Layout {
     // operator scratch
     static constexpr int G_STEP = 0;
     static constexpr int G_SCR = SL::SIZE;
-    static constexpr int SCR = combine_scratch<N>() > riccati_scratch<N, M>() + M * (N + 1) +
+    static constexpr int SCR = combine_scratch<N>() > riccati_scratch<N, M>() + M * kd_ld<N>() +
                                                            LAffine<N>::SIZE
                                    ? combine_scratch<N>()
-                                   : riccati_scratch<N, M>() + M * (N + 1) + LAffine<N>::SIZE;
+                                   : riccati_scratch<N, M>() + M * kd_ld<N>() + LAffine<N>::SIZE;
     static constexpr int G_SIZE = gstride<N>(G_SCR + SCR);
     // CTA: tree of chunk totals, value carries, affine maps, chunk start states
     static constexpr int TREE = 0;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
         Phi[A::OC + r] = 0.f;
         g.sync();
         float* Kd = scr + riccati_scratch<N, M>();
-        float* Ft = Kd + M * (N + 1);
+        float* Ft = Kd + M * kd_ld<N>();
         for (long long k = e - 1; k >= s; --k) {
             load_step<float, N, M, false>(D, k, gs, scr, g, ok);
             ok &= riccati<float, N, M>(val, gs, Kd, Ft, scr, g);
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(NG* N) k_batch(const BatchDesc* __restrict__ i
             D.v[k * N + r] = val[V::OV + r];
             if (r < M) {
 #pragma unroll
-                for (int j = 0; j < N; ++j) D.K[k * M * N + r * N + j] = Kd[r * (N + 1) + j];
-                D.u[k * M + r] = Kd[r * (N + 1) + N];
+                for (int j = 0; j < N; ++j) D.K[k * M * N + r * N + j] = Kd[r * kd_ld<N>() + j];
+                D.u[k * M + r] = Kd[r * kd_ld<N>() + N];
             }
             // chunk map after adding step k: Phi <- Phi Ft, gamma <- gamma + Phi ct
             float pn[N];

@@ -142,7 +142,7 @@ struct RefoldSmem {  // val | Phi | step | scratch (riccati + Kd + Ft) overlappi
     static constexpr int PHI = LValue<N>::SIZE;
     static constexpr int SB = PHI + LAffine<N>::SIZE;
     static constexpr int SCR_OFF = SB + StepLayout<N, M>::Y;
-    static constexpr int RIC = riccati_scratch<N, M>() + M * (N + 1) + LAffine<N>::SIZE;
+    static constexpr int RIC = riccati_scratch<N, M>() + M * kd_ld<N>() + LAffine<N>::SIZE;
     static constexpr int SCR = RIC > StepLayout<N, M>::SIZE - StepLayout<N, M>::Y
                                    ? RIC
                                    : StepLayout<N, M>::SIZE - StepLayout<N, M>::Y;
@@ -374,7 +374,7 @@ __device__ __forceinline__ void b_crefold(const Args<R, RT>& a, long long c,
     R* sb = gs + S::SB;
     R* scr = gs + S::SCR_OFF;
     R* Kd = scr + riccati_scratch<N, M>();
-    R* Ft = Kd + M * (N + 1);
+    R* Ft = Kd + M * kd_ld<N>();
     const int r = g.lr;
     const long long T = D.T;
     const long long lc = c - it.c0;
@@ -399,9 +399,9 @@ __device__ __forceinline__ void b_crefold(const Args<R, RT>& a, long long c,
         if (a.out_mask & 4) D.v[k * N + r] = val[V::OV + r];
         if (a.out_mask & 2) {
 #pragma unroll 8
-            for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = Kd[i * (N + 1) + r];
+            for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = Kd[i * kd_ld<N>() + r];
         }
-        if (r < M) D.u[k * M + r] = Kd[r * (N + 1) + N];  // feedforward d_k, replaced in the rollout
+        if (r < M) D.u[k * M + r] = Kd[r * kd_ld<N>() + N];  // feedforward d_k, replaced in the rollout
         // chunk map after adding step k: Phi <- Phi Ft, gamma <- gamma + Phi ct
         R pn[N];
         R gm = Phi[A::OC + r];
@@ -953,7 +953,7 @@ struct NewtonSmem {  // double: val | step | riccati scratch | Kd | Ft
     static constexpr int SB = LValue<N>::SIZE;
     static constexpr int SCR = SB + StepLayout<N, M>::SIZE;
     static constexpr int KD = SCR + riccati_scratch<N, M>();
-    static constexpr int FT = KD + M * (N + 1);
+    static constexpr int FT = KD + M * kd_ld<N>();
     static constexpr int SIZE = FT + LAffine<N>::SIZE;
 };
 
@@ -1057,7 +1057,7 @@ __global__ void __launch_bounds__(NG* N) k_ngains(const Item<R>* items1, const I
         g.sync();
         ok &= gains<D64, N, M>(val, sb, Kd, scr, g);
 #pragma unroll 8
-        for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = static_cast<R>(Kd[i * (N + 1) + r]);
+        for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = static_cast<R>(Kd[i * kd_ld<N>() + r]);
         g.sync();
     }
     flag(status, ok);

@@ -152,11 +152,18 @@ struct Launcher {
     // The persistent launch (lqt_persist.cuh): groups per CTA from its group
     // block, as many CTAs as are co-resident (at most one group per chunk).
     static constexpr int PERSIST_B = persist_group_bytes<R, RT, N, M>();
-    // an even number of groups per CTA (the up-sweep pairs them)
-    static constexpr int NG_PERSIST = groups_for<N>(PERSIST_B) & ~1;
+    // an even number of groups per CTA (the up-sweep pairs them), at least two
+    static constexpr int NG_PERSIST =
+        (groups_for<N>(PERSIST_B) & ~1) > 2 ? (groups_for<N>(PERSIST_B) & ~1) : 2;
+    // variants whose two groups do not fit one SM (FP64 at n = 32) always take
+    // the per-level launches
+    static constexpr bool kPersistFits = (long long)NG_PERSIST * PERSIST_B <= 227 * 1024;
 
     static lqt_status run_persistent(const Args<R, RT>& a, const long long* active, int levels,
                                      GridBarrier* bar, cudaStream_t s) {
+        if constexpr (!kPersistFits) {
+            return LQT_EUNSUPPORTED;
+        } else {
         if (levels > kMaxLevels) return LQT_EINVAL;
         auto kern = k_cpersist<R, RT, N, M, NG_PERSIST>;
         static std::atomic<bool> done[64];
@@ -185,6 +192,7 @@ struct Launcher {
                                         dim3(NG_PERSIST * N), args, smem, s) != cudaSuccess)
             return LQT_ECUDA;
         return LQT_OK;
+        }
     }
     static char* base_of(const ChainCall& call) { return static_cast<char*>(call.ws); }
 
@@ -601,7 +609,7 @@ struct Launcher {
         a.status = call.status ? call.status : reinterpret_cast<int*>(base);
         a.out_mask = 7;
         a.refine_add = 0;
-        if (call.persistent && !refine && !method2 && !call.sequential) {
+        if (kPersistFits && call.persistent && !refine && !method2 && !call.sequential) {
             // one cooperative launch for the whole pass (batches)
             const lqt_status st = run_persistent(
                 a, active.data(), levels, reinterpret_cast<GridBarrier*>(base + L.bar), s);
