@@ -922,29 +922,40 @@ def run_nonlinear(args, stream, flush):
 
 
 def run_condensed(args, stream, flush, prob, ref, plain_ms):
-    """Partial condensing (Sec. V-C) of the vehicle workload: blocks of B = 2
-    steps (n = 4, stacked m = 4, p = 4, generalised stage cost), solved by
-    lqt_solve_condensed; the same FP32 inputs and refinement as the headline,
-    errors against the same FP64 oracle."""
-    from paper_2104_03186_gb300 import lqt
+    """Partial condensing (Sec. V-C) of the vehicle workload: blocks of B steps
+    (n = 4, stacked m = 2B, p = 2B, generalised stage cost), solved by
+    lqt_solve_condensed (B = 2 as the condensed problem itself, B >= 3 through
+    the rank-reduced blocks), beside the plain solve, at T = 1e5 and the
+    headline's T = 1e6; the same FP32 inputs and refinement as the headline,
+    errors against the FP64 oracle."""
+    import oracle
+    from paper_2104_03186_gb300 import inputs, lqt
 
-    B = 2
     opts = lqt.LQT_REFINE_ON
-    P = lqt.Problem.from_inputs(prob, dtype=np.float32)
-    o = P.allocate_outputs()
-    ws = torch_empty_bytes(lqt.lqt_condensed_workspace_bytes(P, B, opts))
-    call = lambda: lqt.lqt_solve_condensed(P, B, o, ws, stream, opts)  # noqa: E731
-    for _ in range(3):
-        call()
-    st = lqt.lqt_workspace_status(ws, stream)
-    times = _time_solves(call, 10, flush, stream)
-    got = {k: v.double().cpu().numpy() for k, v in o.items()}
-    errs = accuracy.errors(got, ref)
-    med = float(np.median(times))
-    return {"workload": "vehicle T=%d condensed in blocks of B=%d (n=4, m=4, p=4, "
-                        "T/B steps); FP32, refinement ON" % (prob.T, B),
-            "status": int(st), "ms": med, "steps_per_s": prob.T / (med * 1e-3),
-            "plain_solve_ms": plain_ms, "error_vs_fp64_oracle": errs}
+    out = []
+    for T in (100_000, prob.T):
+        pr = prob if T == prob.T else inputs.vehicle(T, seed=0).rounded_to(np.float32)
+        rf = ref if T == prob.T else oracle.riccati(pr, keep_kv_kc=False)
+        P = lqt.Problem.from_inputs(pr, dtype=np.float32)
+        for B in (1, 2, 4, 8, 16):
+            o = P.allocate_outputs()
+            ws = torch_empty_bytes(lqt.lqt_condensed_workspace_bytes(P, B, opts))
+            call = lambda: lqt.lqt_solve_condensed(P, B, o, ws, stream, opts)  # noqa: E731
+            for _ in range(3):
+                call()
+            st = lqt.lqt_workspace_status(ws, stream)
+            times = _time_solves(call, 10, flush, stream)
+            got = {k: v.double().cpu().numpy() for k, v in o.items()}
+            med = float(np.median(times))
+            out.append({"T": T, "B": B, "status": int(st), "ms": med,
+                        "steps_per_s": T / (med * 1e-3),
+                        "error_vs_fp64_oracle": accuracy.errors(got, rf)})
+            del o, ws, got
+        del P
+    return {"workload": "vehicle (n=4, m=2, p=2) condensed in blocks of B steps (stacked "
+                        "controls 2B, outputs 2B, T/B steps; B >= 3 rank-reduced to 4 controls "
+                        "per block); FP32, refinement ON; B = 1 is the plain solve",
+            "plain_solve_ms_headline": plain_ms, "sweep": out}
 
 
 def torch_empty_bytes(nbytes):
@@ -958,7 +969,7 @@ def torch_empty_bytes(nbytes):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
 # (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_BWD_DOWN = 112.0e6
+TRAFFIC_BWD_DOWN = 112.2e6
 
 
 def main(argv=None):

@@ -412,10 +412,19 @@ lqt_status lqt_solve_nonlinear(const lqt_problem *prob, const lqt_nonlinear *nl,
  * lqt_solve_cross solves.  An expansion kernel then re-runs each block's B
  * Riccati steps and its rollout, so `sol` receives S, v, K, x*, u* at every
  * step, as from lqt_solve (a shorter last block is padded with steps that
- * change nothing).  Available where the condensed size (n, B m) is compiled:
- * FP32 (n, m, B) in {(2,1,2), (3,1,2), (4,1,2), (4,1,4), (4,2,2)}, FP64
- * (4,1,2), with p <= 8; B = 1 is lqt_solve itself.  Workspace and return
- * values as for lqt_solve (LQT_EUNSUPPORTED for other sizes and for T = 0). */
+ * change nothing).  Where the condensed size (n, B m) is compiled -- FP32
+ * (n, m, B) in {(2,1,2), (3,1,2), (4,1,2), (4,1,4), (4,2,2)}, FP64 (4,1,2),
+ * with p <= 8 -- the condensed problem is solved as it stands.  Otherwise, for
+ * FP32 (n, m) in {(4,2), (4,1), (2,1), (2,2), (1,1)} with B m <= 32 and
+ * B p <= 32, each block is reduced exactly to n controls: the controls reach
+ * the next block only through w = L_bar u_bar (n values), the best stacked
+ * control for given block start and w is eliminated in FP64, and the reduced
+ * problem (n states, n controls, B p outputs, generalised cost) is solved at
+ * (n, n); the stacked controls are rebuilt from its solution before the
+ * expansion.  A block that cannot move the state in every direction (a last
+ * block of fewer than n / m steps) keeps the directions it can.  B = 1 is
+ * lqt_solve itself.  Workspace and return values as for lqt_solve
+ * (LQT_EUNSUPPORTED for other sizes and for T = 0). */
 size_t lqt_condensed_workspace_bytes(const lqt_problem *prob, int32_t B, const lqt_options *opts);
 lqt_status lqt_solve_condensed(const lqt_problem *prob, int32_t B, const lqt_solution *sol,
                                const lqt_options *opts, void *workspace, size_t workspace_bytes,

@@ -18,6 +18,7 @@
 // x_{jB} with the stacked controls, writing every step's S, v, K, x, u.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "lqt.h"
 #include "lqt_dense.cuh"
@@ -343,6 +344,477 @@ __global__ void __launch_bounds__(kCondThreads) k_expand(CondArgs<R> a) {
     if (!finite) atomicCAS(a.status, 0, (int)LQT_ENONFINITE);
 }
 
+// ---- rank-reduced condensing (any block size with B m <= 32 and B p <= 32) --
+// The condensed block problem of the kernels above has B m stacked controls,
+// more than the compiled solvers take at larger B.  Its state dimension stays
+// n, and the controls reach the next block only through w = L_bar u_bar (n
+// values).  For given block start x (output error y = H_bar x - r_bar) and w,
+// the best u_bar minimises 1/2 u^T U_bar u + y^T M u subject to L_bar u = w;
+// with A = U_bar^{-1} L_bar^T, Z = U_bar^{-1} M^T and the eigenbasis
+// W = L_bar A = V diag(lam) V^T, writing w = V z:
+//   u_bar = P z - Q y,   P = A V diag(1/lam),   Q = Z - P V^T L_bar Z,
+// and the block's cost becomes 1/2 z^T diag(1/lam) z + y^T M_r z
+// + 1/2 y^T X_r y with M_r = M A V diag(1/lam), X_r = X_bar - M Z +
+// M_r (M A V)^T.  So each block is exactly one step of a problem with n
+// controls z: dynamics (F_bar, c_bar, L_r = V), U_r = diag(1/lam), and the
+// generalised cost of Sec. IV-D with H_bar, r_bar, X_r, M_r, which
+// lqt_solve_cross solves at (n, n).  A direction with lam = 0 (a block that
+// cannot move the state that way, such as a last block of fewer than n / m
+// steps) gets a zero column of L_r and a unit weight, so its control stays 0.
+// The stacked controls are then rebuilt per block from (x, z) and expanded as
+// before.  The reduction runs in FP64.
+constexpr int kRedMax = 32;      // largest B m and B p
+constexpr int kRedThreads = 128;
+
+template <typename R>
+struct RedArgs {
+    long long T, Tb;
+    int m, p, B;
+    int inv;  // time-invariant model and T a multiple of B: one copy of the block matrices
+    const R *F, *c, *L, *U, *H, *r, *X;
+    long long sF, sc, sL, sU, sH, sr, sX;
+    // reduced problem: per block (inv: one copy), except r_bar (per block)
+    R *Fb, *cb, *Lb, *Ub, *Hb, *rb, *Xb, *Mb;
+    // rebuilding the stacked controls: P (B m x n), Q (B m x B p)
+    R *Pb, *Qb;
+    double* HD;  // inv: H del_i, i < B (B x p), for r_bar of every block
+    // reduced solution, stacked controls
+    const R *xb, *wb;
+    R* ub;
+    int* status;
+};
+
+template <int N>
+struct RedSmem {  // doubles; MB = B m, PB = B p, both <= kRedMax
+    static constexpr int X = kRedMax;
+    static constexpr int PHI = 0, DEL = PHI + N * N, GAM = DEL + N, TP = GAM + N * X,
+                         TD = TP + N * N, TG = TD + N, HBAR = TG + N * X, G = HBAR + X * N,
+                         UB = G + X * X, MM = UB + X * X, XBAR = MM + X * X, RBAR = XBAR + X * X,
+                         RHS = RBAR + X, W = RHS + X * (N + X), WI = W + N * N, MA = WI + N * N,
+                         MR = MA + X * N, XR = MR + X * N, PP = XR + X * X, LZ = PP + X * N,
+                         SIZE = LZ + N * X;
+};
+
+template <typename R, int N, int M>
+__global__ void __launch_bounds__(kRedThreads) k_cond_reduce(RedArgs<R> a) {
+    using S = RedSmem<N>;
+    extern __shared__ __align__(16) double rs[];
+    double* Phi = rs + S::PHI;
+    double* del = rs + S::DEL;
+    double* Gam = rs + S::GAM;   // N x MB
+    double* tP = rs + S::TP;
+    double* td = rs + S::TD;
+    double* tG = rs + S::TG;
+    double* Hbar = rs + S::HBAR;  // PB x N
+    double* G = rs + S::G;        // PB x MB
+    double* Ub = rs + S::UB;      // MB x MB
+    double* Mm = rs + S::MM;      // PB x MB
+    double* Xbar = rs + S::XBAR;  // PB x PB
+    double* rbar = rs + S::RBAR;  // PB
+    double* RHS = rs + S::RHS;    // MB x (N + PB)
+    double* W = rs + S::W;
+    double* Wi = rs + S::WI;
+    double* MA = rs + S::MA;      // PB x N
+    double* Mr = rs + S::MR;      // PB x N
+    double* Xr = rs + S::XR;      // PB x PB
+    double* Pm = rs + S::PP;      // MB x N
+    double* LZ = rs + S::LZ;      // N x PB
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int m = a.m, p = a.p, B = a.B, MB = B * m, PB = B * p, NR = N + PB;
+    const long long j = blockIdx.x;
+    const long long k0 = j * B;
+    const int b = (int)(a.T - k0 < B ? a.T - k0 : B);
+    for (int e = tid; e < S::SIZE; e += nt) rs[e] = 0.0;
+    __syncthreads();
+    for (int e = tid; e < N; e += nt) Phi[e * N + e] = 1.0;
+    __syncthreads();
+    // 1. the block's stages: rows H Phi_i, H Gam_i, r - H del_i, X_bar, U_bar
+    for (int i = 0; i < B; ++i) {
+        const bool live = i < b;
+        const long long k = k0 + i;
+        const R* F = a.F + a.sF * k;
+        const R* L = a.L + a.sL * k;
+        const R* U = a.U + a.sU * k;
+        const R* c = at(a.c, a.sc, k);
+        const R* H = at(a.H, a.sH, k);
+        const R* r = at(a.r, a.sr, k);
+        const R* X = at(a.X, a.sX, k);
+        if (live) {
+            for (int e = tid; e < p * N; e += nt) {
+                const int q = e / N, l = e % N;
+                double t = 0.0;
+                for (int s = 0; s < N; ++s) t += (double)H[q * N + s] * Phi[s * N + l];
+                Hbar[(i * p + q) * N + l] = t;
+            }
+            for (int e = tid; e < p * MB; e += nt) {
+                const int q = e / MB, l = e % MB;
+                double t = 0.0;
+                for (int s = 0; s < N; ++s) t += (double)H[q * N + s] * Gam[s * MB + l];
+                G[(i * p + q) * MB + l] = t;
+            }
+            for (int q = tid; q < p; q += nt) {
+                double hd = 0.0;
+                for (int s = 0; s < N; ++s) hd += (double)H[q * N + s] * del[s];
+                rbar[i * p + q] = (r ? (double)r[q] : 0.0) - hd;
+                if (a.inv && a.HD) a.HD[i * p + q] = hd;
+            }
+            for (int e = tid; e < p * p; e += nt)
+                Xbar[(i * p + e / p) * PB + i * p + e % p] = (double)X[e];
+            for (int e = tid; e < m * m; e += nt)
+                Ub[(i * m + e / m) * MB + i * m + e % m] += (double)U[e];
+        } else {
+            // padding past T: no cost rows, identity weight on its (zero) controls
+            for (int e = tid; e < m; e += nt) Ub[(i * m + e) * MB + i * m + e] += 1.0;
+            if (a.inv && a.HD)
+                for (int q = tid; q < p; q += nt) a.HD[i * p + q] = 0.0;
+        }
+        __syncthreads();
+        if (live) {
+            for (int e = tid; e < N * N; e += nt) {
+                const int s = e / N, l = e % N;
+                double t = 0.0;
+                for (int q = 0; q < N; ++q) t += (double)F[s * N + q] * Phi[q * N + l];
+                tP[e] = t;
+            }
+            for (int e = tid; e < N * MB; e += nt) {
+                const int s = e / MB, l = e % MB;
+                double t = 0.0;
+                for (int q = 0; q < N; ++q) t += (double)F[s * N + q] * Gam[q * MB + l];
+                if (l >= i * m && l < i * m + m) t += (double)L[s * m + (l - i * m)];
+                tG[e] = t;
+            }
+            for (int s = tid; s < N; s += nt) {
+                double t = c ? (double)c[s] : 0.0;
+                for (int q = 0; q < N; ++q) t += (double)F[s * N + q] * del[q];
+                td[s] = t;
+            }
+            __syncthreads();
+            for (int e = tid; e < N * N; e += nt) Phi[e] = tP[e];
+            for (int e = tid; e < N * MB; e += nt) Gam[e] = tG[e];
+            for (int s = tid; s < N; s += nt) del[s] = td[s];
+            __syncthreads();
+        }
+    }
+    // 2. M = X_bar G, U_bar += G^T M
+    for (int e = tid; e < PB * MB; e += nt) {
+        const int q = e / MB, l = e % MB;
+        double t = 0.0;
+        for (int s = 0; s < PB; ++s) t += Xbar[q * PB + s] * G[s * MB + l];
+        Mm[e] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < MB * MB; e += nt) {
+        const int c1 = e / MB, c2 = e % MB;
+        double t = 0.0;
+        for (int q = 0; q < PB; ++q) t += G[q * MB + c1] * Mm[q * MB + c2];
+        Ub[e] += t;
+    }
+    __syncthreads();
+    // 3. Cholesky U_bar = R R^T (lower, in place), then [A | Z] = U_bar^{-1} [L_bar^T | M^T]
+    __shared__ int s_ok;
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    for (int kk = 0; kk < MB; ++kk) {
+        if (tid == 0) {
+            const double d = Ub[kk * MB + kk];
+            if (!(d > 0.0) || !isfinite(d)) s_ok = 0;
+            Ub[kk * MB + kk] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double piv = Ub[kk * MB + kk];
+        for (int i = kk + 1 + tid; i < MB; i += nt) Ub[i * MB + kk] /= piv;
+        __syncthreads();
+        const int rest = MB - kk - 1;
+        for (int e = tid; e < rest * rest; e += nt) {
+            const int i = kk + 1 + e / rest, jj = kk + 1 + e % rest;
+            if (jj <= i) Ub[i * MB + jj] -= Ub[i * MB + kk] * Ub[jj * MB + kk];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < MB * NR; e += nt) {
+        const int i = e / NR, cc = e % NR;
+        RHS[e] = cc < N ? Gam[cc * MB + i] : Mm[(cc - N) * MB + i];
+    }
+    __syncthreads();
+    for (int cc = tid; cc < NR; cc += nt) {
+        for (int i = 0; i < MB; ++i) {  // R y = rhs
+            double t = RHS[i * NR + cc];
+            for (int l = 0; l < i; ++l) t -= Ub[i * MB + l] * RHS[l * NR + cc];
+            RHS[i * NR + cc] = t / Ub[i * MB + i];
+        }
+        for (int i = MB - 1; i >= 0; --i) {  // R^T x = y
+            double t = RHS[i * NR + cc];
+            for (int l = i + 1; l < MB; ++l) t -= Ub[l * MB + i] * RHS[l * NR + cc];
+            RHS[i * NR + cc] = t / Ub[i * MB + i];
+        }
+    }
+    __syncthreads();
+    // 4. W = L_bar A = V diag(lam) V^T; M A; M_r = M A V / lam; P = A V / lam;
+    //    X_r = X_bar - M Z + sum_i (M A v_i)(M A v_i)^T / lam_i (live directions)
+    for (int e = tid; e < N * N; e += nt) {
+        const int r0 = e / N, cc = e % N;
+        double t = 0.0;
+        for (int i = 0; i < MB; ++i) t += Gam[r0 * MB + i] * RHS[i * NR + cc];
+        W[e] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // cyclic Jacobi rotations on the symmetric W; V (in Wi) collects them
+        double Aw[N][N], V[N][N];
+        for (int i = 0; i < N; ++i)
+            for (int l = 0; l < N; ++l) {
+                Aw[i][l] = 0.5 * (W[i * N + l] + W[l * N + i]);
+                V[i][l] = i == l ? 1.0 : 0.0;
+            }
+        for (int sweep = 0; sweep < 32; ++sweep) {
+            double off = 0.0;
+            for (int i = 0; i < N; ++i)
+                for (int l = i + 1; l < N; ++l) off += Aw[i][l] * Aw[i][l];
+            if (!(off > 1e-60)) break;
+            for (int pp = 0; pp < N; ++pp)
+                for (int qq = pp + 1; qq < N; ++qq) {
+                    if (Aw[pp][qq] == 0.0) continue;
+                    const double th = 0.5 * (Aw[qq][qq] - Aw[pp][pp]) / Aw[pp][qq];
+                    const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                    for (int l = 0; l < N; ++l) {  // columns p, q
+                        const double ap = Aw[l][pp], aq = Aw[l][qq];
+                        Aw[l][pp] = cs * ap - sn * aq;
+                        Aw[l][qq] = sn * ap + cs * aq;
+                    }
+                    for (int l = 0; l < N; ++l) {  // rows p, q
+                        const double ap = Aw[pp][l], aq = Aw[qq][l];
+                        Aw[pp][l] = cs * ap - sn * aq;
+                        Aw[qq][l] = sn * ap + cs * aq;
+                    }
+                    for (int l = 0; l < N; ++l) {
+                        const double vp = V[l][pp], vq = V[l][qq];
+                        V[l][pp] = cs * vp - sn * vq;
+                        V[l][qq] = sn * vp + cs * vq;
+                    }
+                }
+        }
+        double lmax = 0.0;
+        for (int i = 0; i < N; ++i) lmax = fmax(lmax, Aw[i][i]);
+        if (!(lmax > 0.0) || !isfinite(lmax)) s_ok = 0;
+        for (int i = 0; i < N; ++i) {
+            const double lam = Aw[i][i];
+            // W[i] now holds 1 / lam_i for a live direction, 0 for a null one
+            W[i] = lam > 1e-12 * lmax ? 1.0 / lam : 0.0;
+            for (int l = 0; l < N; ++l) Wi[l * N + i] = V[l][i];
+        }
+    }
+    __syncthreads();
+    const double* ilam = W;  // N entries
+    const double* Vm = Wi;   // N x N, column i = eigenvector i
+    for (int e = tid; e < PB * N; e += nt) {  // (M A) V
+        const int q = e / N, cc = e % N;
+        double t = 0.0;
+        for (int l = 0; l < MB; ++l) {
+            double av = 0.0;
+            for (int d = 0; d < N; ++d) av += RHS[l * NR + d] * Vm[d * N + cc];
+            t += Mm[q * MB + l] * av;
+        }
+        MA[e] = t;
+    }
+    for (int e = tid; e < MB * N; e += nt) {  // P = A V / lam
+        const int l = e / N, cc = e % N;
+        double av = 0.0;
+        for (int d = 0; d < N; ++d) av += RHS[l * NR + d] * Vm[d * N + cc];
+        Pm[e] = av * ilam[cc];
+    }
+    for (int e = tid; e < N * PB; e += nt) {  // V^T L_bar Z
+        const int cc = e / PB, s = e % PB;
+        double t = 0.0;
+        for (int d = 0; d < N; ++d) {
+            double lz = 0.0;
+            for (int l = 0; l < MB; ++l) lz += Gam[d * MB + l] * RHS[l * NR + N + s];
+            t += Vm[d * N + cc] * lz;
+        }
+        LZ[e] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < PB * N; e += nt) Mr[e] = MA[e] * ilam[e % N];
+    __syncthreads();
+    for (int e = tid; e < PB * PB; e += nt) {
+        const int q = e / PB, s = e % PB;
+        double t = Xbar[e];
+        for (int l = 0; l < MB; ++l) t -= Mm[q * MB + l] * RHS[l * NR + N + s];
+        for (int cc = 0; cc < N; ++cc) t += Mr[q * N + cc] * MA[s * N + cc];
+        Xr[e] = t;
+    }
+    __syncthreads();
+    // 5. outputs (one copy of the matrices when the model is time-invariant)
+    const bool mats = !a.inv || j == 0;
+    const long long jm = a.inv ? 0 : j;
+    if (mats) {
+        R* Fb = a.Fb + jm * N * N;
+        R* cb = a.cb + jm * N;
+        R* Lrb = a.Lb + jm * N * N;
+        R* Urb = a.Ub + jm * N * N;
+        R* Hb = a.Hb + jm * (long long)PB * N;
+        R* Xb = a.Xb + jm * (long long)PB * PB;
+        R* Mb = a.Mb + jm * (long long)PB * N;
+        R* Pb = a.Pb + jm * (long long)MB * N;
+        R* Qb = a.Qb + jm * (long long)MB * PB;
+        for (int e = tid; e < N * N; e += nt) {
+            const int r0 = e / N, cc = e % N;
+            const bool live = W[cc] > 0.0;  // 1 / lam of direction cc, 0 when null
+            Fb[e] = static_cast<R>(Phi[e]);
+            // L_r = V (null directions: zero column), U_r = diag(1 / lam) (null: 1)
+            Lrb[e] = static_cast<R>(live ? Wi[r0 * N + cc] : 0.0);
+            Urb[e] = static_cast<R>(r0 == cc ? (live ? W[cc] : 1.0) : 0.0);
+        }
+        for (int s = tid; s < N; s += nt) cb[s] = static_cast<R>(del[s]);
+        for (int e = tid; e < PB * N; e += nt) {
+            Hb[e] = static_cast<R>(Hbar[e]);
+            Mb[e] = static_cast<R>(Mr[e]);
+        }
+        for (int e = tid; e < PB * PB; e += nt) {
+            const int q = e / PB, s = e % PB;
+            Xb[e] = static_cast<R>(0.5 * (Xr[e] + Xr[s * PB + q]));
+        }
+        for (int e = tid; e < MB * N; e += nt) Pb[e] = static_cast<R>(Pm[e]);
+        for (int e = tid; e < MB * PB; e += nt) {  // Q = Z - P V^T L_bar Z
+            const int l = e / PB, s = e % PB;
+            double t = RHS[l * NR + N + s];
+            for (int cc = 0; cc < N; ++cc) t -= Pm[l * N + cc] * LZ[cc * PB + s];
+            Qb[e] = static_cast<R>(t);
+        }
+    }
+    if (!a.inv)
+        for (int q = tid; q < PB; q += nt) a.rb[j * PB + q] = static_cast<R>(rbar[q]);
+    if (tid == 0 && !s_ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
+}
+
+// r_bar of every block of a time-invariant model (one thread per block):
+// r_{jB+i} - H del_i, del_i from the reduction of block 0.
+template <typename R>
+__global__ void __launch_bounds__(kCondThreads) k_cond_rbar(RedArgs<R> a) {
+    const long long j = (long long)blockIdx.x * kCondThreads + threadIdx.x;
+    if (j >= a.Tb) return;
+    const int p = a.p, B = a.B;
+    const long long k0 = j * B;
+    for (int i = 0; i < B; ++i) {
+        const long long k = k0 + i;
+        const R* r = at(a.r, a.sr, k);
+        for (int q = 0; q < p; ++q)
+            a.rb[j * (long long)B * p + i * p + q] =
+                k < a.T ? static_cast<R>((r ? (double)r[q] : 0.0) - a.HD[i * p + q]) : R(0);
+    }
+}
+
+// The stacked controls of every block from the reduced solution (one thread
+// per block): u_bar_j = P w_j - Q (H_bar x_j - r_bar_j).
+template <typename R, int N>
+__global__ void __launch_bounds__(kCondThreads) k_cond_unreduce(RedArgs<R> a) {
+    const long long j = (long long)blockIdx.x * kCondThreads + threadIdx.x;
+    if (j >= a.Tb) return;
+    const int MB = a.B * a.m, PB = a.B * a.p;
+    const long long jm = a.inv ? 0 : j;
+    const R* Hb = a.Hb + jm * (long long)PB * N;
+    const R* Pb = a.Pb + jm * (long long)MB * N;
+    const R* Qb = a.Qb + jm * (long long)MB * PB;
+    const R* rb = a.rb + j * PB;
+    R x[N], w[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        x[s] = a.xb[j * N + s];
+        w[s] = a.wb[j * N + s];
+    }
+    R y[kRedMax];
+    for (int q = 0; q < PB; ++q) {
+        R t = -rb[q];
+#pragma unroll
+        for (int s = 0; s < N; ++s) t += Hb[q * N + s] * x[s];
+        y[q] = t;
+    }
+    for (int l = 0; l < MB; ++l) {
+        R t = R(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) t += Pb[l * N + s] * w[s];
+        for (int q = 0; q < PB; ++q) t -= Qb[l * PB + q] * y[q];
+        a.ub[j * MB + l] = t;
+    }
+}
+
+// Expansion with a run-time block size (the block loop of k_expand).
+template <typename R, int N, int M>
+__global__ void __launch_bounds__(kCondThreads) k_expand_rt(CondArgs<R> a, int B) {
+    const long long j = (long long)blockIdx.x * kCondThreads + threadIdx.x;
+    if (j >= a.Tb) return;
+    const long long k0 = j * B;
+    const int b = (int)(a.T - k0 < B ? a.T - k0 : B);
+    R S[Dims<N>::SYM], v[N];
+    const R* Se = a.Sb + (j + 1) * N * N;
+    const R* ve = a.vb + (j + 1) * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int l = i; l < N; ++l) S[sym<N>(i, l)] = Se[i * N + l];
+        v[i] = ve[i];
+    }
+    if (j == a.Tb - 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int l = 0; l < N; ++l) a.S[a.T * N * N + i * N + l] = Se[i * N + l];
+            a.v[a.T * N + i] = ve[i];
+        }
+    }
+    bool ok = true, finite = true;
+    for (int i = b - 1; i >= 0; --i) {
+        const long long k = k0 + i;
+        Step<R, N, M> st;
+        cond_step<R, N, M>(a, k, st);
+        R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
+        ok &= riccati_step<R, N, M>(st, a.c != nullptr, S, v, K, d, Ft, ct, Rc, Rinv);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+#pragma unroll
+            for (int l = 0; l < N; ++l) a.S[k * N * N + s * N + l] = S[sym<N>(s, l)];
+            a.v[k * N + s] = v[s];
+            finite = finite && isfinite(v[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < M; ++s)
+#pragma unroll
+            for (int l = 0; l < N; ++l) a.K[(k * M + s) * N + l] = K[s][l];
+    }
+    R x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = a.xb[j * N + i];
+    const R* ub = a.ub + j * (long long)B * M;
+    for (int i = 0; i < b; ++i) {
+        const long long k = k0 + i;
+        const R* F = a.F + a.sF * k;
+        const R* L = a.L + a.sL * k;
+        const R* c = at(a.c, a.sc, k);
+#pragma unroll
+        for (int s = 0; s < N; ++s) a.x[k * N + s] = x[s];
+#pragma unroll
+        for (int s = 0; s < M; ++s) a.u[k * M + s] = ub[i * M + s];
+        R xn[N];
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            R t = c ? c[s] : R(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) t += F[s * N + l] * x[l];
+#pragma unroll
+            for (int l = 0; l < M; ++l) t += L[s * M + l] * ub[i * M + l];
+            xn[s] = t;
+        }
+#pragma unroll
+        for (int s = 0; s < N; ++s) x[s] = xn[s];
+    }
+    if (j == a.Tb - 1) {
+#pragma unroll
+        for (int s = 0; s < N; ++s) a.x[a.T * N + s] = a.xb[a.Tb * N + s];
+    }
+    if (!ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
+    if (!finite) atomicCAS(a.status, 0, (int)LQT_ENONFINITE);
+}
+
 // Compiled (dtype, n, m, B): the condensed size (n, B m) has a solver.
 struct CondVariant {
     int dtype, n, m, B;
@@ -510,10 +982,246 @@ CondArgs<R> cond_args(const lqt_problem* P, const lqt_solution* sol, const CondP
     return a;
 }
 
+// Rank-reduced variants: the original (n, m) of the expansion; the reduced
+// problem is solved at (n, n).
+struct RedVariant {
+    int n, m;
+    void (*reduce)(const void* args, unsigned grid, size_t smem, cudaStream_t s);
+    void (*unreduce)(const void* args, long long blocks, cudaStream_t s);
+    void (*expand)(const void* args, int B, long long blocks, cudaStream_t s);
+};
+
+template <typename R, int N, int M>
+void run_reduce(const void* args, unsigned grid, size_t smem, cudaStream_t s) {
+    static bool attr = false;  // a benign race: every caller sets the same value
+    if (!attr) {
+        cudaFuncSetAttribute(k_cond_reduce<R, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    const RedArgs<R>& a = *static_cast<const RedArgs<R>*>(args);
+    k_cond_reduce<R, N, M><<<grid, kRedThreads, smem, s>>>(a);
+    if (a.inv) {
+        const long long blocks = (a.Tb + kCondThreads - 1) / kCondThreads;
+        k_cond_rbar<R><<<(unsigned)blocks, kCondThreads, 0, s>>>(a);
+    }
+}
+template <typename R, int N>
+void run_unreduce(const void* args, long long blocks, cudaStream_t s) {
+    k_cond_unreduce<R, N><<<(unsigned)blocks, kCondThreads, 0, s>>>(
+        *static_cast<const RedArgs<R>*>(args));
+}
+template <typename R, int N, int M>
+void run_expand_rt(const void* args, int B, long long blocks, cudaStream_t s) {
+    k_expand_rt<R, N, M><<<(unsigned)blocks, kCondThreads, 0, s>>>(
+        *static_cast<const CondArgs<R>*>(args), B);
+}
+
+#define LQT_RED(N, M) \
+    RedVariant { N, M, &run_reduce<float, N, M>, &run_unreduce<float, N>, &run_expand_rt<float, N, M> }
+const RedVariant kRedVariants[] = {LQT_RED(4, 2), LQT_RED(4, 1), LQT_RED(2, 1), LQT_RED(2, 2),
+                                   LQT_RED(1, 1)};
+
+const RedVariant* find_red(int dtype, int n, int m) {
+    if (dtype != LQT_F32) return nullptr;
+    for (const RedVariant& v : kRedVariants)
+        if (v.n == n && v.m == m) return &v;
+    return nullptr;
+}
+
+struct RedPlan {
+    lqt_problem Pc;   // reduced problem: n states, n controls, B p outputs, T/B steps
+    lqt_cross cross;  // its cross weights M_r
+    lqt_solution sc;  // its solution (w in sc.u)
+    size_t cross_ws, Fb, cb, Lb, Ub, Hb, rb, Xb, Mb, Pb, Qb, HD, Sb, vb, Kb, xb, wb, ub, total;
+    long long Tb;
+    bool inv;
+};
+
+lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* base, RedPlan* rp) {
+    if (!P || B < 2) return LQT_EINVAL;
+    if (P->n < 1 || P->m < 1 || P->p < 0 || P->pT < 0 || P->T < 0 || !P->x0) return LQT_EINVAL;
+    if (!find_red(P->dtype, P->n, P->m)) return LQT_EUNSUPPORTED;
+    const int64_t n = P->n, m = P->m, p = P->p;
+    if (m * B > kRedMax || p * B > kRedMax) return LQT_EUNSUPPORTED;
+    const size_t es = 4;
+    if (!ok_in(P->F, n * n, es, true, P->T) || !ok_in(P->L, n * m, es, true, P->T) ||
+        !ok_in(P->U, m * m, es, true, P->T) || !ok_in(P->c, n, es, false, P->T) ||
+        !ok_in(P->H, p * n, es, p > 0, P->T) || !ok_in(P->r, p, es, false, P->T) ||
+        !ok_in(P->X, p * p, es, p > 0, P->T))
+        return LQT_EINVAL;
+    const long long Tb = (P->T + B - 1) / B;
+    const int64_t mb = m * B, pb = p * B;
+    rp->Tb = Tb;
+    auto fixed = [](const lqt_in& in) { return !in.ptr || in.step_stride == 0; };
+    rp->inv = P->T % B == 0 && fixed(P->F) && fixed(P->L) && fixed(P->U) && fixed(P->c) &&
+              fixed(P->H) && fixed(P->X);
+    const long long Tm = rp->inv ? 1 : Tb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at0 = off;
+        off += up_p(bytes > 0 ? bytes : 1);
+        return at0;
+    };
+    const size_t Fb = take(Tm * n * n * es), cb = take(Tm * n * es), Lb = take(Tm * n * n * es),
+                 Ub = take(Tm * n * n * es), Hb = take(Tm * pb * n * es), rb = take(Tb * pb * es),
+                 Xb = take(Tm * pb * pb * es), Mb = take(Tm * pb * n * es),
+                 Pb = take(Tm * mb * n * es), Qb = take(Tm * mb * pb * es),
+                 HD = take((size_t)B * p * sizeof(double)), Sb = take((Tb + 1) * n * n * es),
+                 vb = take((Tb + 1) * n * es), Kb = take(Tb * n * n * es),
+                 xb = take((Tb + 1) * n * es), wb = take(Tb * n * es), ub = take(Tb * mb * es);
+    const size_t tail = off;
+    char* bb = base ? base : reinterpret_cast<char*>(size_t(1) << 20);
+    auto point = [&](size_t at0) {
+        lqt_problem& Q = rp->Pc;
+        Q = *P;
+        Q.m = (int32_t)n;
+        Q.p = (int32_t)pb;
+        Q.T = Tb;
+        const int64_t v = rp->inv ? 0 : 1;
+        Q.F = lqt_in{bb + at0 + Fb, v * n * n};
+        Q.c = lqt_in{bb + at0 + cb, v * n};
+        Q.L = lqt_in{bb + at0 + Lb, v * n * n};
+        Q.U = lqt_in{bb + at0 + Ub, v * n * n};
+        Q.H = lqt_in{pb > 0 ? bb + at0 + Hb : nullptr, v * pb * n};
+        Q.r = lqt_in{pb > 0 ? bb + at0 + rb : nullptr, pb};
+        Q.X = lqt_in{pb > 0 ? bb + at0 + Xb : nullptr, v * pb * pb};
+        rp->cross.M = lqt_in{pb > 0 ? bb + at0 + Mb : nullptr, v * pb * n};
+        rp->cross.s = lqt_in{nullptr, 0};
+        rp->sc.S = bb + at0 + Sb;
+        rp->sc.v = bb + at0 + vb;
+        rp->sc.K = bb + at0 + Kb;
+        rp->sc.x = bb + at0 + xb;
+        rp->sc.u = bb + at0 + wb;
+    };
+    point(kAlignP);
+    const size_t cross_ws = lqt_cross_workspace_bytes(&rp->Pc, &rp->cross, o);
+    if (cross_ws == 0) return LQT_EUNSUPPORTED;
+    rp->cross_ws = up_p(cross_ws);
+    point(rp->cross_ws);
+    const size_t o0 = rp->cross_ws;
+    rp->Fb = o0 + Fb;
+    rp->cb = o0 + cb;
+    rp->Lb = o0 + Lb;
+    rp->Ub = o0 + Ub;
+    rp->Hb = o0 + Hb;
+    rp->rb = o0 + rb;
+    rp->Xb = o0 + Xb;
+    rp->Mb = o0 + Mb;
+    rp->Pb = o0 + Pb;
+    rp->Qb = o0 + Qb;
+    rp->HD = o0 + HD;
+    rp->Sb = o0 + Sb;
+    rp->vb = o0 + vb;
+    rp->Kb = o0 + Kb;
+    rp->xb = o0 + xb;
+    rp->wb = o0 + wb;
+    rp->ub = o0 + ub;
+    rp->total = o0 + tail;
+    return LQT_OK;
+}
+
+RedArgs<float> red_args(const lqt_problem* P, int B, const RedPlan& rp, char* base) {
+    RedArgs<float> a;
+    a.T = P->T;
+    a.Tb = rp.Tb;
+    a.m = P->m;
+    a.p = P->p;
+    a.B = B;
+    a.inv = rp.inv ? 1 : 0;
+    auto in = [](const lqt_in& i, const float** ptr, long long* s) {
+        *ptr = static_cast<const float*>(i.ptr);
+        *s = i.step_stride;
+    };
+    in(P->F, &a.F, &a.sF);
+    in(P->c, &a.c, &a.sc);
+    in(P->L, &a.L, &a.sL);
+    in(P->U, &a.U, &a.sU);
+    in(P->H, &a.H, &a.sH);
+    in(P->r, &a.r, &a.sr);
+    in(P->X, &a.X, &a.sX);
+    a.Fb = reinterpret_cast<float*>(base + rp.Fb);
+    a.cb = reinterpret_cast<float*>(base + rp.cb);
+    a.Lb = reinterpret_cast<float*>(base + rp.Lb);
+    a.Ub = reinterpret_cast<float*>(base + rp.Ub);
+    a.Hb = reinterpret_cast<float*>(base + rp.Hb);
+    a.rb = reinterpret_cast<float*>(base + rp.rb);
+    a.Xb = reinterpret_cast<float*>(base + rp.Xb);
+    a.Mb = reinterpret_cast<float*>(base + rp.Mb);
+    a.Pb = reinterpret_cast<float*>(base + rp.Pb);
+    a.Qb = reinterpret_cast<float*>(base + rp.Qb);
+    a.HD = reinterpret_cast<double*>(base + rp.HD);
+    a.xb = reinterpret_cast<const float*>(base + rp.xb);
+    a.wb = reinterpret_cast<const float*>(base + rp.wb);
+    a.ub = reinterpret_cast<float*>(base + rp.ub);
+    a.status = reinterpret_cast<int*>(base);
+    return a;
+}
+
+// The expansion's arguments from the reduced plan (the CondArgs of the small path).
+CondArgs<float> red_expand_args(const lqt_problem* P, const lqt_solution* sol, const RedPlan& rp,
+                                char* base) {
+    CondArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    a.T = P->T;
+    a.Tb = rp.Tb;
+    a.p = P->p;
+    a.inv = rp.inv ? 1 : 0;
+    auto in = [](const lqt_in& i, const float** ptr, long long* s) {
+        *ptr = static_cast<const float*>(i.ptr);
+        *s = i.step_stride;
+    };
+    in(P->F, &a.F, &a.sF);
+    in(P->c, &a.c, &a.sc);
+    in(P->L, &a.L, &a.sL);
+    in(P->U, &a.U, &a.sU);
+    in(P->H, &a.H, &a.sH);
+    in(P->r, &a.r, &a.sr);
+    in(P->X, &a.X, &a.sX);
+    a.Sb = reinterpret_cast<const float*>(base + rp.Sb);
+    a.vb = reinterpret_cast<const float*>(base + rp.vb);
+    a.xb = reinterpret_cast<const float*>(base + rp.xb);
+    a.ub = reinterpret_cast<const float*>(base + rp.ub);
+    a.S = static_cast<float*>(sol->S);
+    a.v = static_cast<float*>(sol->v);
+    a.K = static_cast<float*>(sol->K);
+    a.x = static_cast<float*>(sol->x);
+    a.u = static_cast<float*>(sol->u);
+    a.status = reinterpret_cast<int*>(base);
+    return a;
+}
+
 }  // namespace
 }  // namespace lqt
 
 using namespace lqt;
+
+static lqt_status solve_reduced(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
+                                const lqt_options* opts, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+    char* base = static_cast<char*>(workspace);
+    RedPlan rp;
+    lqt_status st = plan_red(prob, B, opts, base, &rp);
+    if (st != LQT_OK) return st;
+    if (workspace_bytes < rp.total) return LQT_ENOMEM;
+    st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, workspace, 0, stream);
+    if (st != LQT_ENOMEM) return st == LQT_OK ? LQT_EINVAL : st;
+    const RedVariant* var = find_red(prob->dtype, prob->n, prob->m);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long blocks = (rp.Tb + kCondThreads - 1) / kCondThreads;
+    if (blocks > INT32_MAX || rp.Tb > INT32_MAX) return LQT_EINVAL;
+    const size_t smem = (size_t)RedSmem<4>::SIZE * sizeof(double);
+    const RedArgs<float> a = red_args(prob, B, rp, base);
+    var->reduce(&a, rp.inv ? 1u : (unsigned)rp.Tb, smem, s);
+    if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
+    if ((st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, workspace, rp.cross_ws, stream)) !=
+        LQT_OK)
+        return st;
+    var->unreduce(&a, blocks, s);
+    const CondArgs<float> e = red_expand_args(prob, sol, rp, base);
+    var->expand(&e, B, blocks, s);
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+}
 
 extern "C" {
 
@@ -521,8 +1229,10 @@ size_t lqt_condensed_workspace_bytes(const lqt_problem* prob, int32_t B,
                                      const lqt_options* opts) {
     if (prob && B == 1) return lqt_workspace_bytes(prob, opts);
     CondPlan cp;
-    if (plan_cond(prob, B, opts, nullptr, &cp) != LQT_OK) return 0;
-    return cp.total;
+    if (plan_cond(prob, B, opts, nullptr, &cp) == LQT_OK) return cp.total;
+    RedPlan rp;
+    if (plan_red(prob, B, opts, nullptr, &rp) == LQT_OK) return rp.total;
+    return 0;
 }
 
 lqt_status lqt_solve_condensed(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
@@ -534,6 +1244,14 @@ lqt_status lqt_solve_condensed(const lqt_problem* prob, int32_t B, const lqt_sol
     char* base = static_cast<char*>(workspace);
     CondPlan cp;
     lqt_status st = plan_cond(prob, B, opts, base, &cp);
+    if (st == LQT_EUNSUPPORTED) {
+        // no register kernel for (n, B m): the rank-reduced path
+        if (prob->T == 0) return LQT_EUNSUPPORTED;
+        const void* outs[] = {sol->S, sol->v, sol->K, sol->x, sol->u};
+        for (const void* q : outs)
+            if (!q || reinterpret_cast<uintptr_t>(q) % 16) return LQT_EINVAL;
+        return solve_reduced(prob, B, sol, opts, workspace, workspace_bytes, stream);
+    }
     if (st != LQT_OK) return st;
     if (workspace_bytes < cp.total) return LQT_ENOMEM;
     if (prob->T == 0) return LQT_EUNSUPPORTED;  // nothing to condense: use lqt_solve

@@ -55,3 +55,31 @@ def test_condensed_unsupported_and_passthrough():
     assert lqt.lqt_condensed_workspace_bytes(P, 2) == 0
     prob = inputs.random_problem(4, 2, T=300, seed=2).rounded_to(np.float32)
     compare(_solve(prob, 1), oracle_solve(prob), FP32_TOL)
+
+
+@pytest.mark.parametrize("B", [3, 4, 8, 16])
+@pytest.mark.parametrize("T", [1000, 4096, 1001])
+def test_rank_reduced_condensing_vehicle(B, T):
+    """Block sizes past the register kernels (B m > 4) go through the
+    rank-reduced condensed problem (n controls per block, solved at (4, 4));
+    T = 4096 with B | T takes the time-invariant block matrices, the others
+    a padded last block."""
+    prob = inputs.vehicle(T, seed=B).rounded_to(np.float32)
+    compare(_solve(prob, B), oracle_solve(prob), FP32_TOL)
+
+
+@pytest.mark.parametrize("B", [3, 8, 16])
+def test_rank_reduced_condensing_time_varying(B):
+    """Time-varying dynamics, costs, offsets c_k and control weights."""
+    prob = inputs.random_problem(4, 2, p=2, T=777, seed=30 + B, pT=4).rounded_to(np.float32)
+    compare(_solve(prob, B), oracle_solve(prob), FP32_TOL)
+
+
+def test_rank_reduced_limits():
+    from paper_2104_03186_gb300 import lqt
+
+    # B p > 32: no plan
+    P = lqt.Problem.from_inputs(inputs.random_problem(4, 2, p=4, T=100, seed=1).rounded_to(
+        np.float32))
+    assert lqt.lqt_condensed_workspace_bytes(P, 16) == 0
+    assert lqt.lqt_condensed_workspace_bytes(P, 8) > 0
