@@ -240,7 +240,10 @@ lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *w
  * block processing); by default the chunk length is the batch's total steps
  * over the resident lane groups, clamped to [4, 64].  An entry {n, t_max,
  * chunk_steps} sets the chunk length of the problems of state size n with
- * T <= t_max (the first matching entry applies); `persistent` selects one
+ * T <= t_max (the first matching entry applies), capped at the batch's total
+ * steps over the resident lane groups (at least 4), so that a batch too small
+ * to fill the device with chunks of that length still spreads over every
+ * resident group; `persistent` selects one
  * cooperative launch per state size that runs every tree level with grid
  * barriers (1, the default) or one launch per tree level (0).  count = 0
  * clears the table.  The settings are process-wide; calls already launched

@@ -97,9 +97,11 @@ int levels(int NC) {
 
 // Chunk geometry of a batch of one variant: a chunk length B* from the
 // total work over the resident fold groups, clamped to [kMinChunk,
-// kMaxBatchChunk] so that no problem's latency grows with the batch; each
-// problem takes the largest power-of-two chunk count with chunks of at least
-// B* steps.  Problems sorted by decreasing chunk count.
+// kMaxBatchChunk] so that no problem's latency grows with the batch, or the
+// tuned length of the problem's (n, T) where it is shorter than the unclamped
+// fill length; each problem takes the largest power-of-two chunk count with
+// chunks of at least that many steps.  Problems sorted by decreasing chunk
+// count.
 constexpr long long kMaxBatchChunk = 64;
 
 lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, const int* idx,
@@ -109,15 +111,17 @@ lqt_status batch_geometry(const ChainVariant& v, const lqt_batch_item* items, co
     if (st != LQT_OK) return st;
     long long total = 0;
     for (int i = 0; i < count; ++i) total += items[idx[i]].problem.T;
-    long long Bt = (total + slots - 1) / (slots > 0 ? slots : 1);
-    if (Bt < kMinChunk) Bt = kMinChunk;
-    if (Bt > kMaxBatchChunk) Bt = kMaxBatchChunk;
+    long long fill = (total + slots - 1) / (slots > 0 ? slots : 1);
+    if (fill < kMinChunk) fill = kMinChunk;
+    const long long Bt = fill < kMaxBatchChunk ? fill : kMaxBatchChunk;
     out->resize((size_t)count);
     for (int i = 0; i < count; ++i) {
         const lqt_batch_item& it = items[idx[i]];
         const long long T = it.problem.T;
+        // a tuned length applies up to the one that fills the device: a batch
+        // with less work than that keeps every resident group busy instead
         const long long tuned = tuned_chunk(it.problem.n, T);
-        const long long Bi = tuned > 0 ? tuned : Bt;
+        const long long Bi = tuned > 0 ? (tuned < fill ? tuned : fill) : Bt;
         long long nc = 1;
         while (nc * 2 * Bi <= T && nc < (1LL << 20)) nc *= 2;
         ChainProblem& cp = (*out)[(size_t)i];

@@ -9,7 +9,9 @@ is.  The tuner times lqt_solve_batched on this GPU on a synthetic batch shaped
 like the benchmark's ragged batch (diagonal tracking, m = n / 2), choosing the
 chunk length of each (n, T-bucket) in turn with the others fixed, then times
 the two launch modes (one persistent launch per size, or one launch per tree
-level) with that table and keeps the faster.
+level) with that table and keeps the faster.  The library applies a tuned
+length only up to the batch's total steps over the resident lane groups, so
+the small batches of a server keep their short chunks.
 
     python -m paper_2104_03186_gb300.tune [--out FILE] [--problems K]
 
