@@ -997,12 +997,14 @@ def main(argv=None):
     ap.add_argument("--T", type=int, default=T_HEADLINE, help="horizon of --profile-solves")
     ap.add_argument("--refine", type=int, default=1, help="refinement in --profile-solves")
     ap.add_argument("--profile-workload",
-                    choices=("vehicle", "precision", "cross", "nonlinear", "batch"),
+                    choices=("vehicle", "precision", "cross", "nonlinear", "batch", "condensed"),
                     default="vehicle",
                     help="workload of --profile-solves: the vehicle (n = 4), the n = 32 "
                          "precision study, the vehicle with cross weights and offsets "
                          "(lqt_solve_cross), the unicycle (lqt_solve_nonlinear, 10 passes), or "
-                         "the ragged batch (lqt_solve_batched, --batch-count problems)")
+                         "the ragged batch (lqt_solve_batched, --batch-count problems), or the "
+                         "vehicle condensed in blocks of --block steps (lqt_solve_condensed)")
+    ap.add_argument("--block", type=int, default=2, help="block size of the condensed profile")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -1042,6 +1044,9 @@ def run_profile_solves(args):
         C = lqt.Cross.from_inputs(inputs.cross_terms(pr, seed=1, scale=0.5).rounded_to(np.float32))
         ws = torch_empty_bytes(lqt.lqt_cross_workspace_bytes(P, C, args.refine))
         call = lambda: lqt.lqt_solve_cross(P, C, out, ws, None, args.refine)  # noqa: E731
+    elif args.profile_workload == "condensed":
+        ws = torch_empty_bytes(lqt.lqt_condensed_workspace_bytes(P, args.block, args.refine))
+        call = lambda: lqt.lqt_solve_condensed(P, args.block, out, ws, None, args.refine)  # noqa: E731
     elif args.profile_workload == "nonlinear":
         nl = lqt.nonlinear(10, 0.1)
         ws = torch_empty_bytes(lqt.lqt_nonlinear_workspace_bytes(P, nl, args.refine))

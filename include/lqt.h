@@ -426,8 +426,15 @@ lqt_status lqt_solve_nonlinear(const lqt_problem *prob, const lqt_nonlinear *nl,
  * (n, n); the stacked controls are rebuilt from its solution before the
  * expansion.  A block that cannot move the state in every direction (a last
  * block of fewer than n / m steps) keeps the directions it can.  B = 1 is
- * lqt_solve itself.  Workspace and return values as for lqt_solve
- * (LQT_EUNSUPPORTED for other sizes and for T = 0). */
+ * lqt_solve itself.  Refinement (opts->refine; AUTO = ON for FP32): the
+ * expansion rebuilds u from block starts and references of order one, so
+ * with LQT_REFINE_ON or FULL the whole condensed solve runs twice, the second
+ * time on the problem shifted by the first trajectory x^ (the shift of
+ * lqt_options.refine for n <= 4, formed in compensated arithmetic), whose
+ * controls are u* and whose states are added to x^; S, v, K are the first
+ * solve's.  The condensed problem itself is solved without refinement.
+ * Workspace and return values as for lqt_solve (LQT_EUNSUPPORTED for other
+ * sizes and for T = 0). */
 size_t lqt_condensed_workspace_bytes(const lqt_problem *prob, int32_t B, const lqt_options *opts);
 lqt_status lqt_solve_condensed(const lqt_problem *prob, int32_t B, const lqt_solution *sol,
                                const lqt_options *opts, void *workspace, size_t workspace_bytes,

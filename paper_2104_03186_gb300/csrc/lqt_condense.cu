@@ -22,6 +22,7 @@
 
 #include "lqt.h"
 #include "lqt_dense.cuh"
+#include "lqt_refine.cuh"
 
 namespace lqt {
 namespace {
@@ -45,12 +46,58 @@ struct CondArgs {
     const R *Sb, *vb, *xb, *ub;
     // original solution
     R *S, *v, *K, *x, *u;
+    // second pass of the refinement: only the forward rollout, adding xi to x
+    int shift_add;
     int* status;
+    const int* pre_status;  // status of the kernels before the condensed solve
 };
 
 template <typename R>
 __device__ __forceinline__ const R* at(const R* a, long long s, long long k) {
     return a ? a + s * k : nullptr;
+}
+
+// The vectors of block j of the condensed problem: del_0 = 0,
+// del_{i+1} = F_k del_i + c_k, r_bar_i = r_k - H_k del_i (k = jB + i; zero
+// rows past T) into rb (B p values), and c_bar_j = del_B into cb (N values).
+template <typename R, int N>
+__device__ __forceinline__ void block_vectors(const R* F0, long long sF, const R* c0, long long sc,
+                                              const R* H0, long long sH, const R* r0,
+                                              long long sr, int p, int B, long long T,
+                                              long long j, R* rb, R* cb) {
+    const long long k0 = j * B;
+    R del[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) del[s] = R(0);
+    for (int i = 0; i < B; ++i) {
+        const long long k = k0 + i;
+        if (k >= T) {
+            for (int q = 0; q < p; ++q) rb[i * p + q] = R(0);
+            continue;
+        }
+        const R* F = F0 + sF * k;
+        const R* H = at(H0, sH, k);
+        const R* r = at(r0, sr, k);
+        const R* c = at(c0, sc, k);
+        for (int q = 0; q < p; ++q) {
+            R t = r ? r[q] : R(0);
+#pragma unroll
+            for (int s = 0; s < N; ++s) t -= H[q * N + s] * del[s];
+            rb[i * p + q] = t;
+        }
+        R dn[N];
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            R t = c ? c[s] : R(0);
+#pragma unroll
+            for (int l = 0; l < N; ++l) t += F[s * N + l] * del[l];
+            dn[s] = t;
+        }
+#pragma unroll
+        for (int s = 0; s < N; ++s) del[s] = dn[s];
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s) cb[s] = del[s];
 }
 
 template <typename R, int N, int M, int B>
@@ -190,10 +237,16 @@ __global__ void __launch_bounds__(kCondThreads) k_condense(CondArgs<R> a) {
             for (int c1 = 0; c1 < M; ++c1) UG[i * M + c1][i * M + c1] += R(1);
         }
     }
+    // c_bar: one per block unless the model and its offsets are time-invariant
+    const bool cvar = !a.inv || (a.c && a.sc != 0);
+    if (cvar || j == 0) {
+        R* cb = a.cb + (cvar ? j : 0) * N;
+#pragma unroll
+        for (int s = 0; s < N; ++s) cb[s] = del[s];
+    }
     if (!mats) return;
     R* Fb = a.Fb + jm * N * N;
     R* Lb = a.Lb + jm * N * MB;
-    R* cb = a.cb + jm * N;
     R* Ub = a.Ub + jm * MB * MB;
 #pragma unroll
     for (int s = 0; s < N; ++s) {
@@ -201,7 +254,6 @@ __global__ void __launch_bounds__(kCondThreads) k_condense(CondArgs<R> a) {
         for (int l = 0; l < N; ++l) Fb[s * N + l] = Phi[s][l];
 #pragma unroll
         for (int l = 0; l < MB; ++l) Lb[s * MB + l] = Gam[s][l];
-        cb[s] = del[s];
     }
 #pragma unroll
     for (int c1 = 0; c1 < MB; ++c1)
@@ -257,6 +309,16 @@ __device__ __forceinline__ void cond_step(const CondArgs<R>& a, long long k, Ste
     }
 }
 
+// Status of an expansion: a failure recorded before the condensed solve (whose
+// start clears the status word) is the root cause and wins.
+template <typename R>
+__device__ __forceinline__ void expand_status(const CondArgs<R>& a, long long j, bool ok,
+                                              bool finite) {
+    if (j == 0 && a.pre_status && *a.pre_status != 0) atomicExch(a.status, *a.pre_status);
+    if (!ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
+    if (!finite) atomicCAS(a.status, 0, (int)LQT_ENONFINITE);
+}
+
 template <typename R, int N, int M, int B>
 __global__ void __launch_bounds__(kCondThreads) k_expand(CondArgs<R> a) {
     constexpr int MB = M * B;
@@ -264,45 +326,47 @@ __global__ void __launch_bounds__(kCondThreads) k_expand(CondArgs<R> a) {
     if (j >= a.Tb) return;
     const long long k0 = j * B;
     const int b = (int)(a.T - k0 < B ? a.T - k0 : B);
-    // backward: the block's Riccati steps from the value at its end
-    R S[Dims<N>::SYM], v[N];
-    const R* Se = a.Sb + (j + 1) * N * N;
-    const R* ve = a.vb + (j + 1) * N;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int l = i; l < N; ++l) S[sym<N>(i, l)] = Se[i * N + l];
-        v[i] = ve[i];
-    }
-    if (j == a.Tb - 1) {
-        // terminal value S_T, v_T
+    bool ok = true, finite = true;
+    if (!a.shift_add) {
+        // backward: the block's Riccati steps from the value at its end
+        R S[Dims<N>::SYM], v[N];
+        const R* Se = a.Sb + (j + 1) * N * N;
+        const R* ve = a.vb + (j + 1) * N;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) a.S[a.T * N * N + i * N + l] = Se[i * N + l];
-            a.v[a.T * N + i] = ve[i];
+            for (int l = i; l < N; ++l) S[sym<N>(i, l)] = Se[i * N + l];
+            v[i] = ve[i];
         }
-    }
-    bool ok = true, finite = true;
+        if (j == a.Tb - 1) {
+            // terminal value S_T, v_T
 #pragma unroll
-    for (int i = B - 1; i >= 0; --i) {
-        if (i < b) {
-            const long long k = k0 + i;
-            Step<R, N, M> st;
-            cond_step<R, N, M>(a, k, st);
-            R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
-            ok &= riccati_step<R, N, M>(st, a.c != nullptr, S, v, K, d, Ft, ct, Rc, Rinv);
+            for (int i = 0; i < N; ++i) {
 #pragma unroll
-            for (int s = 0; s < N; ++s) {
-#pragma unroll
-                for (int l = 0; l < N; ++l) a.S[k * N * N + s * N + l] = S[sym<N>(s, l)];
-                a.v[k * N + s] = v[s];
-                finite = finite && isfinite(v[s]);
+                for (int l = 0; l < N; ++l) a.S[a.T * N * N + i * N + l] = Se[i * N + l];
+                a.v[a.T * N + i] = ve[i];
             }
+        }
 #pragma unroll
-            for (int s = 0; s < M; ++s)
+        for (int i = B - 1; i >= 0; --i) {
+            if (i < b) {
+                const long long k = k0 + i;
+                Step<R, N, M> st;
+                cond_step<R, N, M>(a, k, st);
+                R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
+                ok &= riccati_step<R, N, M>(st, a.c != nullptr, S, v, K, d, Ft, ct, Rc, Rinv);
 #pragma unroll
-                for (int l = 0; l < N; ++l) a.K[(k * M + s) * N + l] = K[s][l];
+                for (int s = 0; s < N; ++s) {
+#pragma unroll
+                    for (int l = 0; l < N; ++l) a.S[k * N * N + s * N + l] = S[sym<N>(s, l)];
+                    a.v[k * N + s] = v[s];
+                    finite = finite && isfinite(v[s]);
+                }
+#pragma unroll
+                for (int s = 0; s < M; ++s)
+#pragma unroll
+                    for (int l = 0; l < N; ++l) a.K[(k * M + s) * N + l] = K[s][l];
+            }
         }
     }
     // forward: the rollout from x_{jB} with the block's stacked controls
@@ -318,7 +382,11 @@ __global__ void __launch_bounds__(kCondThreads) k_expand(CondArgs<R> a) {
             const R* L = a.L + a.sL * k;
             const R* c = at(a.c, a.sc, k);
 #pragma unroll
-            for (int s = 0; s < N; ++s) a.x[k * N + s] = x[s];
+            for (int s = 0; s < N; ++s) {
+                const R xo = a.shift_add ? a.x[k * N + s] + x[s] : x[s];
+                a.x[k * N + s] = xo;
+                finite = finite && isfinite(xo);
+            }
 #pragma unroll
             for (int s = 0; s < M; ++s) a.u[k * M + s] = ub[i * M + s];
             R xn[N];
@@ -338,10 +406,11 @@ __global__ void __launch_bounds__(kCondThreads) k_expand(CondArgs<R> a) {
     if (j == a.Tb - 1) {
         // x_T: the condensed solve's last state (the block rollout agrees to rounding)
 #pragma unroll
-        for (int s = 0; s < N; ++s) a.x[a.T * N + s] = a.xb[a.Tb * N + s];
+        for (int s = 0; s < N; ++s)
+            a.x[a.T * N + s] = a.shift_add ? a.x[a.T * N + s] + a.xb[a.Tb * N + s]
+                                           : a.xb[a.Tb * N + s];
     }
-    if (!ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
-    if (!finite) atomicCAS(a.status, 0, (int)LQT_ENONFINITE);
+    expand_status(a, j, ok, finite);
 }
 
 // ---- rank-reduced condensing (any block size with B m <= 32 and B p <= 32) --
@@ -381,7 +450,7 @@ struct RedArgs {
     // reduced solution, stacked controls
     const R *xb, *wb;
     R* ub;
-    int* status;
+    int* status;  // the reduction's failures, merged by the expansion
 };
 
 template <int N>
@@ -495,18 +564,23 @@ __global__ void __launch_bounds__(kRedThreads) k_cond_reduce(RedArgs<R> a) {
             __syncthreads();
         }
     }
-    // 2. M = X_bar G, U_bar += G^T M
+    // 2. M = X_bar G, U_bar += G^T M.  X_bar is block diagonal (stage i's X),
+    // and the rows of stage i of G (and of M) vanish in the columns of stages
+    // i and later (a control acts on the outputs of the following stages), so
+    // both products run over the stages that contribute only.
     for (int e = tid; e < PB * MB; e += nt) {
-        const int q = e / MB, l = e % MB;
+        const int q = e / MB, l = e % MB, i0 = q / p;
         double t = 0.0;
-        for (int s = 0; s < PB; ++s) t += Xbar[q * PB + s] * G[s * MB + l];
+        if (l < i0 * m)
+            for (int s = i0 * p; s < i0 * p + p; ++s) t += Xbar[q * PB + s] * G[s * MB + l];
         Mm[e] = t;
     }
     __syncthreads();
     for (int e = tid; e < MB * MB; e += nt) {
         const int c1 = e / MB, c2 = e % MB;
+        const int s1 = c1 / m, s2 = c2 / m;
         double t = 0.0;
-        for (int q = 0; q < PB; ++q) t += G[q * MB + c1] * Mm[q * MB + c2];
+        for (int q = ((s1 > s2 ? s1 : s2) + 1) * p; q < PB; ++q) t += G[q * MB + c1] * Mm[q * MB + c2];
         Ub[e] += t;
     }
     __syncthreads();
@@ -639,7 +713,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cond_reduce(RedArgs<R> a) {
     for (int e = tid; e < PB * PB; e += nt) {
         const int q = e / PB, s = e % PB;
         double t = Xbar[e];
-        for (int l = 0; l < MB; ++l) t -= Mm[q * MB + l] * RHS[l * NR + N + s];
+        for (int l = 0, le = (q / p) * m; l < le; ++l) t -= Mm[q * MB + l] * RHS[l * NR + N + s];
         for (int cc = 0; cc < N; ++cc) t += Mr[q * N + cc] * MA[s * N + cc];
         Xr[e] = t;
     }
@@ -665,7 +739,8 @@ __global__ void __launch_bounds__(kRedThreads) k_cond_reduce(RedArgs<R> a) {
             Lrb[e] = static_cast<R>(live ? Wi[r0 * N + cc] : 0.0);
             Urb[e] = static_cast<R>(r0 == cc ? (live ? W[cc] : 1.0) : 0.0);
         }
-        for (int s = tid; s < N; s += nt) cb[s] = static_cast<R>(del[s]);
+        if (!a.inv || !a.c || a.sc == 0)  // else k_cond_rbar writes every block's
+            for (int s = tid; s < N; s += nt) cb[s] = static_cast<R>(del[s]);
         for (int e = tid; e < PB * N; e += nt) {
             Hb[e] = static_cast<R>(Hbar[e]);
             Mb[e] = static_cast<R>(Mr[e]);
@@ -687,21 +762,30 @@ __global__ void __launch_bounds__(kRedThreads) k_cond_reduce(RedArgs<R> a) {
     if (tid == 0 && !s_ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
 }
 
-// r_bar of every block of a time-invariant model (one thread per block):
-// r_{jB+i} - H del_i, del_i from the reduction of block 0.
-template <typename R>
+// r_bar of every block of a time-invariant model (one thread per block).
+// Offsets c fixed (or none): r_{jB+i} - H del_i with del_i from the reduction
+// of block 0.  Offsets c_k that vary (matrices still time-invariant): each
+// block's own del_i (del_0 = 0, del_{i+1} = F del_i + c_{jB+i}) and
+// c_bar_j = del_B.
+template <typename R, int N>
 __global__ void __launch_bounds__(kCondThreads) k_cond_rbar(RedArgs<R> a) {
     const long long j = (long long)blockIdx.x * kCondThreads + threadIdx.x;
     if (j >= a.Tb) return;
     const int p = a.p, B = a.B;
     const long long k0 = j * B;
-    for (int i = 0; i < B; ++i) {
-        const long long k = k0 + i;
-        const R* r = at(a.r, a.sr, k);
-        for (int q = 0; q < p; ++q)
-            a.rb[j * (long long)B * p + i * p + q] =
-                k < a.T ? static_cast<R>((r ? (double)r[q] : 0.0) - a.HD[i * p + q]) : R(0);
+    R* rb = a.rb + j * (long long)B * p;
+    if (!a.c || a.sc == 0) {
+        for (int i = 0; i < B; ++i) {
+            const long long k = k0 + i;
+            const R* r = at(a.r, a.sr, k);
+            for (int q = 0; q < p; ++q)
+                rb[i * p + q] =
+                    k < a.T ? static_cast<R>((r ? (double)r[q] : 0.0) - a.HD[i * p + q]) : R(0);
+        }
+        return;
     }
+    block_vectors<R, N>(a.F, a.sF, a.c, a.sc, a.H, a.sH, a.r, a.sr, p, B, a.T, j, rb,
+                        a.cb + j * N);
 }
 
 // The stacked controls of every block from the reduced solution (one thread
@@ -745,41 +829,43 @@ __global__ void __launch_bounds__(kCondThreads) k_expand_rt(CondArgs<R> a, int B
     if (j >= a.Tb) return;
     const long long k0 = j * B;
     const int b = (int)(a.T - k0 < B ? a.T - k0 : B);
-    R S[Dims<N>::SYM], v[N];
-    const R* Se = a.Sb + (j + 1) * N * N;
-    const R* ve = a.vb + (j + 1) * N;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int l = i; l < N; ++l) S[sym<N>(i, l)] = Se[i * N + l];
-        v[i] = ve[i];
-    }
-    if (j == a.Tb - 1) {
+    bool ok = true, finite = true;
+    if (!a.shift_add) {
+        R S[Dims<N>::SYM], v[N];
+        const R* Se = a.Sb + (j + 1) * N * N;
+        const R* ve = a.vb + (j + 1) * N;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) a.S[a.T * N * N + i * N + l] = Se[i * N + l];
-            a.v[a.T * N + i] = ve[i];
+            for (int l = i; l < N; ++l) S[sym<N>(i, l)] = Se[i * N + l];
+            v[i] = ve[i];
         }
-    }
-    bool ok = true, finite = true;
-    for (int i = b - 1; i >= 0; --i) {
-        const long long k = k0 + i;
-        Step<R, N, M> st;
-        cond_step<R, N, M>(a, k, st);
-        R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
-        ok &= riccati_step<R, N, M>(st, a.c != nullptr, S, v, K, d, Ft, ct, Rc, Rinv);
+        if (j == a.Tb - 1) {
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
+            for (int i = 0; i < N; ++i) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) a.S[k * N * N + s * N + l] = S[sym<N>(s, l)];
-            a.v[k * N + s] = v[s];
-            finite = finite && isfinite(v[s]);
+                for (int l = 0; l < N; ++l) a.S[a.T * N * N + i * N + l] = Se[i * N + l];
+                a.v[a.T * N + i] = ve[i];
+            }
         }
+        for (int i = b - 1; i >= 0; --i) {
+            const long long k = k0 + i;
+            Step<R, N, M> st;
+            cond_step<R, N, M>(a, k, st);
+            R K[M][N], d[M], Ft[N][N], ct[N], Rc[M][M], Rinv[M];
+            ok &= riccati_step<R, N, M>(st, a.c != nullptr, S, v, K, d, Ft, ct, Rc, Rinv);
 #pragma unroll
-        for (int s = 0; s < M; ++s)
+            for (int s = 0; s < N; ++s) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) a.K[(k * M + s) * N + l] = K[s][l];
+                for (int l = 0; l < N; ++l) a.S[k * N * N + s * N + l] = S[sym<N>(s, l)];
+                a.v[k * N + s] = v[s];
+                finite = finite && isfinite(v[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < M; ++s)
+#pragma unroll
+                for (int l = 0; l < N; ++l) a.K[(k * M + s) * N + l] = K[s][l];
+        }
     }
     R x[N];
 #pragma unroll
@@ -791,7 +877,11 @@ __global__ void __launch_bounds__(kCondThreads) k_expand_rt(CondArgs<R> a, int B
         const R* L = a.L + a.sL * k;
         const R* c = at(a.c, a.sc, k);
 #pragma unroll
-        for (int s = 0; s < N; ++s) a.x[k * N + s] = x[s];
+        for (int s = 0; s < N; ++s) {
+            const R xo = a.shift_add ? a.x[k * N + s] + x[s] : x[s];
+            a.x[k * N + s] = xo;
+            finite = finite && isfinite(xo);
+        }
 #pragma unroll
         for (int s = 0; s < M; ++s) a.u[k * M + s] = ub[i * M + s];
         R xn[N];
@@ -809,10 +899,61 @@ __global__ void __launch_bounds__(kCondThreads) k_expand_rt(CondArgs<R> a, int B
     }
     if (j == a.Tb - 1) {
 #pragma unroll
-        for (int s = 0; s < N; ++s) a.x[a.T * N + s] = a.xb[a.Tb * N + s];
+        for (int s = 0; s < N; ++s)
+            a.x[a.T * N + s] = a.shift_add ? a.x[a.T * N + s] + a.xb[a.Tb * N + s]
+                                           : a.xb[a.Tb * N + s];
     }
-    if (!ok) atomicCAS(a.status, 0, (int)LQT_ENOTSPD);
-    if (!finite) atomicCAS(a.status, 0, (int)LQT_ENONFINITE);
+    expand_status(a, j, ok, finite);
+}
+
+// The vectors of the condensed problem alone (block_vectors, one thread per
+// block), for a second solve whose matrices (F, L, U, H, X) are those of the
+// first.
+template <typename R>
+struct VecArgs {
+    long long T, Tb;
+    int p, B;
+    const R *F, *c, *H, *r;
+    long long sF, sc, sH, sr;
+    R *rb, *cb;
+};
+
+template <typename R, int N>
+__global__ void __launch_bounds__(kCondThreads) k_cond_vec(VecArgs<R> a) {
+    const long long j = (long long)blockIdx.x * kCondThreads + threadIdx.x;
+    if (j >= a.Tb) return;
+    block_vectors<R, N>(a.F, a.sF, a.c, a.sc, a.H, a.sH, a.r, a.sr, a.p, a.B, a.T, j,
+                        a.rb + j * (long long)a.B * a.p, a.cb + j * N);
+}
+
+template <typename R>
+lqt_status launch_vec(const lqt_problem* P, int B, long long Tb, char* rb, char* cb,
+                      cudaStream_t s) {
+    VecArgs<R> a;
+    a.T = P->T;
+    a.Tb = Tb;
+    a.p = P->p;
+    a.B = B;
+    auto in = [](const lqt_in& i, const R** ptr, long long* st) {
+        *ptr = static_cast<const R*>(i.ptr);
+        *st = i.step_stride;
+    };
+    in(P->F, &a.F, &a.sF);
+    in(P->c, &a.c, &a.sc);
+    in(P->H, &a.H, &a.sH);
+    in(P->r, &a.r, &a.sr);
+    a.rb = reinterpret_cast<R*>(rb);
+    a.cb = reinterpret_cast<R*>(cb);
+    const long long blocks = (Tb + kCondThreads - 1) / kCondThreads;
+    if (blocks > INT32_MAX) return LQT_EINVAL;
+    switch (P->n) {
+        case 1: k_cond_vec<R, 1><<<(unsigned)blocks, kCondThreads, 0, s>>>(a); break;
+        case 2: k_cond_vec<R, 2><<<(unsigned)blocks, kCondThreads, 0, s>>>(a); break;
+        case 3: k_cond_vec<R, 3><<<(unsigned)blocks, kCondThreads, 0, s>>>(a); break;
+        case 4: k_cond_vec<R, 4><<<(unsigned)blocks, kCondThreads, 0, s>>>(a); break;
+        default: return LQT_EUNSUPPORTED;
+    }
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
 }
 
 // Compiled (dtype, n, m, B): the condensed size (n, B m) has a solver.
@@ -863,8 +1004,10 @@ bool ok_in(const lqt_in& in, int64_t size, size_t es, bool required, int64_t T) 
     return in.step_stride == 0 || in.step_stride >= size;
 }
 
+// cross_min: the condensed solve's workspace is at least this large, so that
+// the two solves of a refinement share one layout.
 lqt_status plan_cond(const lqt_problem* P, int B, const lqt_options* o, char* base,
-                     CondPlan* cp) {
+                     CondPlan* cp, size_t cross_min = 0) {
     if (!P || B < 1) return LQT_EINVAL;
     if (P->dtype != LQT_F32 && P->dtype != LQT_F64) return LQT_EINVAL;
     if (P->n < 1 || P->m < 1 || P->p < 0 || P->pT < 0 || P->T < 0 || !P->x0) return LQT_EINVAL;
@@ -881,16 +1024,18 @@ lqt_status plan_cond(const lqt_problem* P, int B, const lqt_options* o, char* ba
     const int64_t mb = m * B, pb = p * B;
     cp->Tb = Tb;
     auto fixed = [](const lqt_in& in) { return !in.ptr || in.step_stride == 0; };
-    cp->inv = P->T % B == 0 && fixed(P->F) && fixed(P->L) && fixed(P->U) && fixed(P->c) &&
-              fixed(P->H) && fixed(P->X);
+    // offsets c_k may vary: they enter only c_bar and r_bar, which are per block
+    cp->inv = P->T % B == 0 && fixed(P->F) && fixed(P->L) && fixed(P->U) && fixed(P->H) &&
+              fixed(P->X);
     const long long Tm = cp->inv ? 1 : Tb;  // rows of the block matrices
+    const long long Tc = cp->inv && fixed(P->c) ? 1 : Tb;  // rows of c_bar
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
         off += up_p(bytes > 0 ? bytes : 1);
         return at;
     };
-    const size_t Fb = take(Tm * n * n * es), Lb = take(Tm * n * mb * es), cb = take(Tm * n * es),
+    const size_t Fb = take(Tm * n * n * es), Lb = take(Tm * n * mb * es), cb = take(Tb * n * es),
                  Ub = take(Tm * mb * mb * es), Hb = take(Tm * pb * n * es),
                  rb = take(Tb * pb * es), Xb = take(Tm * pb * pb * es),
                  Mb = take(Tm * pb * mb * es), Sb = take((Tb + 1) * n * n * es),
@@ -907,7 +1052,7 @@ lqt_status plan_cond(const lqt_problem* P, int B, const lqt_options* o, char* ba
         const int64_t v = cp->inv ? 0 : 1;  // step strides of the block matrices
         Q.F = lqt_in{bb + at0 + Fb, v * n * n};
         Q.L = lqt_in{bb + at0 + Lb, v * n * mb};
-        Q.c = lqt_in{bb + at0 + cb, v * n};
+        Q.c = lqt_in{bb + at0 + cb, Tc > 1 ? n : 0};
         Q.U = lqt_in{bb + at0 + Ub, v * mb * mb};
         Q.H = lqt_in{pb > 0 ? bb + at0 + Hb : nullptr, v * pb * n};
         Q.r = lqt_in{pb > 0 ? bb + at0 + rb : nullptr, pb};
@@ -923,7 +1068,7 @@ lqt_status plan_cond(const lqt_problem* P, int B, const lqt_options* o, char* ba
     point(kAlignP);
     const size_t cross_ws = lqt_cross_workspace_bytes(&cp->Pc, &cp->cross, o);
     if (cross_ws == 0) return LQT_EUNSUPPORTED;
-    cp->cross_ws = up_p(cross_ws);
+    cp->cross_ws = up_p(cross_ws > cross_min ? cross_ws : cross_min);
     point(cp->cross_ws);
     cp->Fb = cp->cross_ws + Fb;
     cp->Lb = cp->cross_ws + Lb;
@@ -944,7 +1089,7 @@ lqt_status plan_cond(const lqt_problem* P, int B, const lqt_options* o, char* ba
 
 template <typename R>
 CondArgs<R> cond_args(const lqt_problem* P, const lqt_solution* sol, const CondPlan& cp,
-                      char* base) {
+                      char* base, const int* pre, bool shift_add) {
     CondArgs<R> a;
     a.T = P->T;
     a.Tb = cp.Tb;
@@ -979,6 +1124,8 @@ CondArgs<R> cond_args(const lqt_problem* P, const lqt_solution* sol, const CondP
     a.x = static_cast<R*>(sol->x);
     a.u = static_cast<R*>(sol->u);
     a.status = reinterpret_cast<int*>(base);
+    a.pre_status = pre;
+    a.shift_add = shift_add ? 1 : 0;
     return a;
 }
 
@@ -1003,7 +1150,7 @@ void run_reduce(const void* args, unsigned grid, size_t smem, cudaStream_t s) {
     k_cond_reduce<R, N, M><<<grid, kRedThreads, smem, s>>>(a);
     if (a.inv) {
         const long long blocks = (a.Tb + kCondThreads - 1) / kCondThreads;
-        k_cond_rbar<R><<<(unsigned)blocks, kCondThreads, 0, s>>>(a);
+        k_cond_rbar<R, N><<<(unsigned)blocks, kCondThreads, 0, s>>>(a);
     }
 }
 template <typename R, int N>
@@ -1038,7 +1185,8 @@ struct RedPlan {
     bool inv;
 };
 
-lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* base, RedPlan* rp) {
+lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* base, RedPlan* rp,
+                    size_t cross_min = 0) {
     if (!P || B < 2) return LQT_EINVAL;
     if (P->n < 1 || P->m < 1 || P->p < 0 || P->pT < 0 || P->T < 0 || !P->x0) return LQT_EINVAL;
     if (!find_red(P->dtype, P->n, P->m)) return LQT_EUNSUPPORTED;
@@ -1054,16 +1202,17 @@ lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* bas
     const int64_t mb = m * B, pb = p * B;
     rp->Tb = Tb;
     auto fixed = [](const lqt_in& in) { return !in.ptr || in.step_stride == 0; };
-    rp->inv = P->T % B == 0 && fixed(P->F) && fixed(P->L) && fixed(P->U) && fixed(P->c) &&
-              fixed(P->H) && fixed(P->X);
+    rp->inv = P->T % B == 0 && fixed(P->F) && fixed(P->L) && fixed(P->U) && fixed(P->H) &&
+              fixed(P->X);
     const long long Tm = rp->inv ? 1 : Tb;
+    const long long Tc = rp->inv && fixed(P->c) ? 1 : Tb;  // rows of c_bar
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at0 = off;
         off += up_p(bytes > 0 ? bytes : 1);
         return at0;
     };
-    const size_t Fb = take(Tm * n * n * es), cb = take(Tm * n * es), Lb = take(Tm * n * n * es),
+    const size_t Fb = take(Tm * n * n * es), cb = take(Tb * n * es), Lb = take(Tm * n * n * es),
                  Ub = take(Tm * n * n * es), Hb = take(Tm * pb * n * es), rb = take(Tb * pb * es),
                  Xb = take(Tm * pb * pb * es), Mb = take(Tm * pb * n * es),
                  Pb = take(Tm * mb * n * es), Qb = take(Tm * mb * pb * es),
@@ -1080,7 +1229,7 @@ lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* bas
         Q.T = Tb;
         const int64_t v = rp->inv ? 0 : 1;
         Q.F = lqt_in{bb + at0 + Fb, v * n * n};
-        Q.c = lqt_in{bb + at0 + cb, v * n};
+        Q.c = lqt_in{bb + at0 + cb, Tc > 1 ? n : 0};
         Q.L = lqt_in{bb + at0 + Lb, v * n * n};
         Q.U = lqt_in{bb + at0 + Ub, v * n * n};
         Q.H = lqt_in{pb > 0 ? bb + at0 + Hb : nullptr, v * pb * n};
@@ -1097,7 +1246,7 @@ lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* bas
     point(kAlignP);
     const size_t cross_ws = lqt_cross_workspace_bytes(&rp->Pc, &rp->cross, o);
     if (cross_ws == 0) return LQT_EUNSUPPORTED;
-    rp->cross_ws = up_p(cross_ws);
+    rp->cross_ws = up_p(cross_ws > cross_min ? cross_ws : cross_min);
     point(rp->cross_ws);
     const size_t o0 = rp->cross_ws;
     rp->Fb = o0 + Fb;
@@ -1121,7 +1270,7 @@ lqt_status plan_red(const lqt_problem* P, int B, const lqt_options* o, char* bas
     return LQT_OK;
 }
 
-RedArgs<float> red_args(const lqt_problem* P, int B, const RedPlan& rp, char* base) {
+RedArgs<float> red_args(const lqt_problem* P, int B, const RedPlan& rp, char* base, int* pre) {
     RedArgs<float> a;
     a.T = P->T;
     a.Tb = rp.Tb;
@@ -1154,13 +1303,13 @@ RedArgs<float> red_args(const lqt_problem* P, int B, const RedPlan& rp, char* ba
     a.xb = reinterpret_cast<const float*>(base + rp.xb);
     a.wb = reinterpret_cast<const float*>(base + rp.wb);
     a.ub = reinterpret_cast<float*>(base + rp.ub);
-    a.status = reinterpret_cast<int*>(base);
+    a.status = pre;
     return a;
 }
 
 // The expansion's arguments from the reduced plan (the CondArgs of the small path).
 CondArgs<float> red_expand_args(const lqt_problem* P, const lqt_solution* sol, const RedPlan& rp,
-                                char* base) {
+                                char* base, const int* pre, bool shift_add) {
     CondArgs<float> a;
     memset(&a, 0, sizeof(a));
     a.T = P->T;
@@ -1188,7 +1337,269 @@ CondArgs<float> red_expand_args(const lqt_problem* P, const lqt_solution* sol, c
     a.x = static_cast<float*>(sol->x);
     a.u = static_cast<float*>(sol->u);
     a.status = reinterpret_cast<int*>(base);
+    a.pre_status = pre;
+    a.shift_add = shift_add ? 1 : 0;
     return a;
+}
+
+// ---- refinement of the condensed solve --------------------------------------
+// The expansion rebuilds u_bar = P z - Q (H_bar x - r_bar) (or the condensed
+// solver's u_bar) from block starts and references of order one, a small
+// difference of large terms when the tracking error is small; the error of
+// u grows with B.  As lqt_solve does for n <= 4, the whole condensed solve
+// runs twice: on the problem, giving x^, then on the problem shifted by x^
+// (x = x^ + xi: r'_k = r_k - H_k x^_k, c'_k = F_k x^_k + c_k - x^_{k+1},
+// r'_T = r_T - H_T x^_T, x'_0 = 0; the same matrices, so S, K are those of
+// the first solve), whose controls are u* and whose states are xi.  The
+// shifted data are compensated dot products; every term of the second
+// solve is of the size of u.  S, v, K are the first solve's.
+
+template <typename R>
+struct ShiftArgs {
+    long long T;
+    int n, p, pT;
+    const R *F, *c, *H, *r, *HT, *rT;
+    long long sF, sc, sH, sr;
+    const R* x;  // x^ (T + 1 states)
+    R *rp, *cp, *rTp, *x0p;
+    const int* status;  // the first solve's status
+    int* pre_status;    // carried into the second solve's
+};
+
+// One thread per step k < T (r'_k, c'_k); thread T writes r'_T and x'_0 and
+// carries the first solve's status.
+template <typename R>
+__global__ void __launch_bounds__(kCondThreads) k_cond_shift(ShiftArgs<R> a) {
+    const long long k = (long long)blockIdx.x * kCondThreads + threadIdx.x;
+    if (k > a.T) return;
+    const int n = a.n;
+    const R* x = a.x + k * n;
+    if (k == a.T) {
+        for (int q = 0; q < a.pT; ++q) {
+            Dot2<R> acc(a.rT ? a.rT[q] : R(0));
+            for (int s = 0; s < n; ++s) acc.add_prod(-a.HT[q * n + s], x[s]);
+            a.rTp[q] = acc.value();
+        }
+        for (int s = 0; s < n; ++s) a.x0p[s] = R(0);
+        if (*a.status != 0) atomicCAS(a.pre_status, 0, *a.status);
+        return;
+    }
+    const R* F = a.F + a.sF * k;
+    const R* c = at(a.c, a.sc, k);
+    const R* H = at(a.H, a.sH, k);
+    const R* r = at(a.r, a.sr, k);
+    for (int q = 0; q < a.p; ++q) {
+        Dot2<R> acc(r ? r[q] : R(0));
+        for (int s = 0; s < n; ++s) acc.add_prod(-H[q * n + s], x[s]);
+        a.rp[k * a.p + q] = acc.value();
+    }
+    for (int i = 0; i < n; ++i) {
+        Dot2<R> acc(c ? c[i] : R(0));
+        for (int s = 0; s < n; ++s) acc.add_prod(F[i * n + s], x[s]);
+        acc.add(-x[n + i]);
+        a.cp[k * n + i] = acc.value();
+    }
+}
+
+// Workspace after the condensed solve's own: the status word of the kernels
+// before the condensed solve, then (refined) the shifted data.
+struct Tail {
+    size_t cross;  // workspace of the condensed solve (the same for both solves)
+    size_t pre, rp, cp, rTp, x0p, total;
+};
+
+Tail tail_layout(const lqt_problem* P, size_t core, bool refine) {
+    const size_t es = P->dtype == LQT_F64 ? 8 : 4;
+    Tail t;
+    size_t off = core;
+    auto take = [&](size_t bytes) {
+        const size_t at0 = off;
+        off += up_p(bytes > 0 ? bytes : 1);
+        return at0;
+    };
+    t.pre = take(sizeof(int));
+    t.rp = t.cp = t.rTp = t.x0p = 0;
+    if (refine) {
+        t.rp = take((size_t)P->T * P->p * es);
+        t.cp = take((size_t)P->T * P->n * es);
+        t.rTp = take((size_t)P->pT * es);
+        t.x0p = take((size_t)P->n * es);
+    }
+    t.total = off;
+    return t;
+}
+
+// The shifted problem: the same matrices, r', c', r'_T, x'_0 at `base` + the
+// tail's offsets (any base with the workspace's alignment, for sizing).
+lqt_problem shifted(const lqt_problem* P, char* base, const Tail& t) {
+    lqt_problem Q = *P;
+    Q.r = lqt_in{P->p > 0 ? base + t.rp : nullptr, P->p};
+    Q.c = lqt_in{base + t.cp, P->n};
+    Q.rT = P->pT > 0 ? base + t.rTp : nullptr;
+    Q.x0 = base + t.x0p;
+    return Q;
+}
+
+// Workspace of one condensed solve of P (either path) and of its condensed
+// solve within it, or the error.
+lqt_status core_bytes(const lqt_problem* P, int B, const lqt_options* o, size_t cross_min,
+                      size_t* bytes, size_t* cross) {
+    CondPlan cp;
+    lqt_status st = plan_cond(P, B, o, nullptr, &cp, cross_min);
+    if (st == LQT_OK) {
+        *bytes = cp.total;
+        *cross = cp.cross_ws;
+        return st;
+    }
+    if (st != LQT_EUNSUPPORTED) return st;
+    RedPlan rp;
+    if ((st = plan_red(P, B, o, nullptr, &rp, cross_min)) == LQT_OK) {
+        *bytes = rp.total;
+        *cross = rp.cross_ws;
+    }
+    return st;
+}
+
+// Refinement of a condensed solve: two solves (see above) for LQT_REFINE_ON
+// and LQT_REFINE_FULL (and AUTO on FP32); the condensed problem itself is
+// solved without refinement either way.
+lqt_status condensed_options(const lqt_problem* P, const lqt_options* o, bool* twice,
+                             lqt_options* inner) {
+    lqt_options d;
+    memset(&d, 0, sizeof(d));
+    d.refine = LQT_REFINE_AUTO;
+    if (o) d = *o;
+    const int r = d.refine;
+    if (r != LQT_REFINE_OFF && r != LQT_REFINE_ON && r != LQT_REFINE_AUTO && r != LQT_REFINE_FULL)
+        return LQT_EINVAL;
+    *twice = r == LQT_REFINE_ON || r == LQT_REFINE_FULL || (r == LQT_REFINE_AUTO && P->dtype == LQT_F32);
+    *inner = d;
+    inner->refine = LQT_REFINE_OFF;
+    return LQT_OK;
+}
+
+lqt_status sizes(const lqt_problem* P, int B, const lqt_options* o, bool* twice,
+                 lqt_options* inner, Tail* t) {
+    lqt_status st = condensed_options(P, o, twice, inner);
+    if (st != LQT_OK) return st;
+    size_t core = 0, cross = 0;
+    if ((st = core_bytes(P, B, inner, 0, &core, &cross)) != LQT_OK) return st;
+    if (*twice) {
+        // the second solve keeps the first's block matrices: one layout for both
+        const Tail t0 = tail_layout(P, 0, true);
+        const lqt_problem P2 = shifted(P, reinterpret_cast<char*>(size_t(1) << 20), t0);
+        size_t core2 = 0, cross2 = 0;
+        if ((st = core_bytes(&P2, B, inner, cross, &core2, &cross2)) != LQT_OK) return st;
+        if (cross2 > cross &&
+            (st = core_bytes(P, B, inner, cross2, &core, &cross)) != LQT_OK)
+            return st;
+        if (core2 > core) core = core2;
+    }
+    *t = tail_layout(P, up_p(core), *twice);
+    t->cross = cross;
+    return LQT_OK;
+}
+
+lqt_status solve_reduced(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
+                         const lqt_options* opts, char* base, int* pre, bool shift_add,
+                         size_t cross, cudaStream_t s) {
+    RedPlan rp;
+    lqt_status st = plan_red(prob, B, opts, base, &rp, cross);
+    if (st != LQT_OK) return st;
+    st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, base, 0, s);
+    if (st != LQT_ENOMEM) return st == LQT_OK ? LQT_EINVAL : st;
+    const RedVariant* var = find_red(prob->dtype, prob->n, prob->m);
+    const long long blocks = (rp.Tb + kCondThreads - 1) / kCondThreads;
+    if (blocks > INT32_MAX || rp.Tb > INT32_MAX) return LQT_EINVAL;
+    const size_t smem = (size_t)RedSmem<4>::SIZE * sizeof(double);
+    const RedArgs<float> a = red_args(prob, B, rp, base, pre);
+    if (shift_add) {
+        // the second solve of the refinement: the first's reduction stands
+        if ((st = launch_vec<float>(prob, B, rp.Tb, base + rp.rb, base + rp.cb, s)) != LQT_OK)
+            return st;
+    } else {
+        var->reduce(&a, rp.inv ? 1u : (unsigned)rp.Tb, smem, s);
+        if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
+    }
+    if ((st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, base, rp.cross_ws, s)) != LQT_OK)
+        return st;
+    var->unreduce(&a, blocks, s);
+    const CondArgs<float> e = red_expand_args(prob, sol, rp, base, pre, shift_add);
+    var->expand(&e, B, blocks, s);
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+}
+
+// One condensed solve of prob into sol (shift_add: the second solve of the
+// refinement, which adds its states to sol->x and writes sol->u only).
+lqt_status solve_once(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
+                      const lqt_options* opts, char* base, int* pre, bool shift_add,
+                      size_t cross, cudaStream_t s) {
+    CondPlan cp;
+    lqt_status st = plan_cond(prob, B, opts, base, &cp, cross);
+    if (st == LQT_EUNSUPPORTED)
+        return solve_reduced(prob, B, sol, opts, base, pre, shift_add, cross, s);
+    if (st != LQT_OK) return st;
+    // argument check of the condensed solve before anything is launched
+    st = lqt_solve_cross(&cp.Pc, &cp.cross, &cp.sc, opts, base, 0, s);
+    if (st != LQT_ENOMEM) return st == LQT_OK ? LQT_EINVAL : st;
+    const CondVariant* var = find_cond(prob->dtype, prob->n, prob->m, B);
+    const long long blocks = (cp.Tb + kCondThreads - 1) / kCondThreads;
+    if (blocks > INT32_MAX) return LQT_EINVAL;
+    if (shift_add) {
+        // the second solve of the refinement: the first's block matrices stand
+        st = prob->dtype == LQT_F64
+                 ? launch_vec<double>(prob, B, cp.Tb, base + cp.rb, base + cp.cb, s)
+                 : launch_vec<float>(prob, B, cp.Tb, base + cp.rb, base + cp.cb, s);
+        if (st != LQT_OK) return st;
+    } else if (prob->dtype == LQT_F64) {
+        const CondArgs<double> a = cond_args<double>(prob, sol, cp, base, pre, shift_add);
+        var->condense(&a, blocks, s);
+    } else {
+        const CondArgs<float> a = cond_args<float>(prob, sol, cp, base, pre, shift_add);
+        var->condense(&a, blocks, s);
+    }
+    if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
+    if ((st = lqt_solve_cross(&cp.Pc, &cp.cross, &cp.sc, opts, base, cp.cross_ws, s)) != LQT_OK)
+        return st;
+    if (prob->dtype == LQT_F64) {
+        const CondArgs<double> a = cond_args<double>(prob, sol, cp, base, pre, shift_add);
+        var->expand(&a, blocks, s);
+    } else {
+        const CondArgs<float> a = cond_args<float>(prob, sol, cp, base, pre, shift_add);
+        var->expand(&a, blocks, s);
+    }
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+}
+
+template <typename R>
+lqt_status launch_shift(const lqt_problem* P, const lqt_solution* sol, char* base,
+                        const Tail& t, cudaStream_t s) {
+    ShiftArgs<R> a;
+    a.T = P->T;
+    a.n = P->n;
+    a.p = P->p;
+    a.pT = P->pT;
+    auto in = [](const lqt_in& i, const R** ptr, long long* st) {
+        *ptr = static_cast<const R*>(i.ptr);
+        *st = i.step_stride;
+    };
+    in(P->F, &a.F, &a.sF);
+    in(P->c, &a.c, &a.sc);
+    in(P->H, &a.H, &a.sH);
+    in(P->r, &a.r, &a.sr);
+    a.HT = static_cast<const R*>(P->HT);
+    a.rT = static_cast<const R*>(P->rT);
+    a.x = static_cast<const R*>(sol->x);
+    a.rp = reinterpret_cast<R*>(base + t.rp);
+    a.cp = reinterpret_cast<R*>(base + t.cp);
+    a.rTp = reinterpret_cast<R*>(base + t.rTp);
+    a.x0p = reinterpret_cast<R*>(base + t.x0p);
+    a.status = reinterpret_cast<const int*>(base);
+    a.pre_status = reinterpret_cast<int*>(base + t.pre);
+    const long long blocks = (P->T + 1 + kCondThreads - 1) / kCondThreads;
+    if (blocks > INT32_MAX) return LQT_EINVAL;
+    k_cond_shift<R><<<(unsigned)blocks, kCondThreads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
 }
 
 }  // namespace
@@ -1196,43 +1607,16 @@ CondArgs<float> red_expand_args(const lqt_problem* P, const lqt_solution* sol, c
 
 using namespace lqt;
 
-static lqt_status solve_reduced(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
-                                const lqt_options* opts, void* workspace, size_t workspace_bytes,
-                                void* stream) {
-    char* base = static_cast<char*>(workspace);
-    RedPlan rp;
-    lqt_status st = plan_red(prob, B, opts, base, &rp);
-    if (st != LQT_OK) return st;
-    if (workspace_bytes < rp.total) return LQT_ENOMEM;
-    st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, workspace, 0, stream);
-    if (st != LQT_ENOMEM) return st == LQT_OK ? LQT_EINVAL : st;
-    const RedVariant* var = find_red(prob->dtype, prob->n, prob->m);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long long blocks = (rp.Tb + kCondThreads - 1) / kCondThreads;
-    if (blocks > INT32_MAX || rp.Tb > INT32_MAX) return LQT_EINVAL;
-    const size_t smem = (size_t)RedSmem<4>::SIZE * sizeof(double);
-    const RedArgs<float> a = red_args(prob, B, rp, base);
-    var->reduce(&a, rp.inv ? 1u : (unsigned)rp.Tb, smem, s);
-    if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
-    if ((st = lqt_solve_cross(&rp.Pc, &rp.cross, &rp.sc, opts, workspace, rp.cross_ws, stream)) !=
-        LQT_OK)
-        return st;
-    var->unreduce(&a, blocks, s);
-    const CondArgs<float> e = red_expand_args(prob, sol, rp, base);
-    var->expand(&e, B, blocks, s);
-    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
-}
-
 extern "C" {
 
 size_t lqt_condensed_workspace_bytes(const lqt_problem* prob, int32_t B,
                                      const lqt_options* opts) {
     if (prob && B == 1) return lqt_workspace_bytes(prob, opts);
-    CondPlan cp;
-    if (plan_cond(prob, B, opts, nullptr, &cp) == LQT_OK) return cp.total;
-    RedPlan rp;
-    if (plan_red(prob, B, opts, nullptr, &rp) == LQT_OK) return rp.total;
-    return 0;
+    if (!prob) return 0;
+    bool twice = false;
+    lqt_options inner;
+    Tail t;
+    return sizes(prob, B, opts, &twice, &inner, &t) == LQT_OK ? t.total : 0;
 }
 
 lqt_status lqt_solve_condensed(const lqt_problem* prob, int32_t B, const lqt_solution* sol,
@@ -1242,48 +1626,27 @@ lqt_status lqt_solve_condensed(const lqt_problem* prob, int32_t B, const lqt_sol
     if (B == 1) return lqt_solve(prob, sol, opts, workspace, workspace_bytes, stream);
     if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlignP) return LQT_EINVAL;
     char* base = static_cast<char*>(workspace);
-    CondPlan cp;
-    lqt_status st = plan_cond(prob, B, opts, base, &cp);
-    if (st == LQT_EUNSUPPORTED) {
-        // no register kernel for (n, B m): the rank-reduced path
-        if (prob->T == 0) return LQT_EUNSUPPORTED;
-        const void* outs[] = {sol->S, sol->v, sol->K, sol->x, sol->u};
-        for (const void* q : outs)
-            if (!q || reinterpret_cast<uintptr_t>(q) % 16) return LQT_EINVAL;
-        return solve_reduced(prob, B, sol, opts, workspace, workspace_bytes, stream);
-    }
+    bool twice = false;
+    lqt_options inner;
+    Tail t;
+    lqt_status st = sizes(prob, B, opts, &twice, &inner, &t);
     if (st != LQT_OK) return st;
-    if (workspace_bytes < cp.total) return LQT_ENOMEM;
+    if (workspace_bytes < t.total) return LQT_ENOMEM;
     if (prob->T == 0) return LQT_EUNSUPPORTED;  // nothing to condense: use lqt_solve
     const void* outs[] = {sol->S, sol->v, sol->K, sol->x, sol->u};
     for (const void* q : outs)
         if (!q || reinterpret_cast<uintptr_t>(q) % 16) return LQT_EINVAL;
-    // argument check of the condensed solve before anything is launched
-    st = lqt_solve_cross(&cp.Pc, &cp.cross, &cp.sc, opts, workspace, 0, stream);
-    if (st != LQT_ENOMEM) return st == LQT_OK ? LQT_EINVAL : st;
-    const CondVariant* var = find_cond(prob->dtype, prob->n, prob->m, B);
+    if (prob->pT > 0 && !prob->HT) return LQT_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const long long blocks = (cp.Tb + kCondThreads - 1) / kCondThreads;
-    if (blocks > INT32_MAX) return LQT_EINVAL;
-    if (prob->dtype == LQT_F64) {
-        const CondArgs<double> a = cond_args<double>(prob, sol, cp, base);
-        var->condense(&a, blocks, s);
-    } else {
-        const CondArgs<float> a = cond_args<float>(prob, sol, cp, base);
-        var->condense(&a, blocks, s);
-    }
-    if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
-    if ((st = lqt_solve_cross(&cp.Pc, &cp.cross, &cp.sc, opts, workspace, cp.cross_ws, stream)) !=
-        LQT_OK)
+    int* pre = reinterpret_cast<int*>(base + t.pre);
+    if (cudaMemsetAsync(pre, 0, sizeof(int), s) != cudaSuccess) return LQT_ECUDA;
+    if ((st = solve_once(prob, B, sol, &inner, base, pre, false, t.cross, s)) != LQT_OK || !twice)
         return st;
-    if (prob->dtype == LQT_F64) {
-        const CondArgs<double> a = cond_args<double>(prob, sol, cp, base);
-        var->expand(&a, blocks, s);
-    } else {
-        const CondArgs<float> a = cond_args<float>(prob, sol, cp, base);
-        var->expand(&a, blocks, s);
-    }
-    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    st = prob->dtype == LQT_F64 ? launch_shift<double>(prob, sol, base, t, s)
+                                : launch_shift<float>(prob, sol, base, t, s);
+    if (st != LQT_OK) return st;
+    const lqt_problem P2 = shifted(prob, base, t);
+    return solve_once(&P2, B, sol, &inner, base, pre, true, t.cross, s);
 }
 
 }  // extern "C"

@@ -31,6 +31,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kPreThreads = 128;
+constexpr int kVecMaxM = 32;  // largest m of k_cross_vec
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -42,6 +43,7 @@ struct CrossPre {
     const R *F, *c, *L, *U, *H, *r, *X, *M, *s;
     long long sF, sc, sL, sU, sH, sr, sX, sM, ss;
     R *Ft, *ct, *Xt, *WH, *g;           // outputs (null: not needed)
+    R* Wm;                              // W of step 0 (m x p), for k_cross_vec (null: none)
     long long oF, oc, oX, oW, og;       // output step strides (0: time-invariant)
     int* status;                        // transform status word
 };
@@ -115,6 +117,8 @@ __global__ void __launch_bounds__(kPreThreads) k_cross_pre(CrossPre<R> a) {
 
     // (W H)_k and g_k = W_k r_k + s_k
     const bool first = k == 0;
+    if (M && a.Wm && first)
+        for (int e = lane; e < m * p; e += G) a.Wm[e] = Ws[(e / p) * ldw + e % p];
     for (int e = lane; e < m * n; e += G) {
         const int i = e / n, l = e % n;
         R acc = R(0);
@@ -287,6 +291,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_cross_pre_small(CrossPre<R> a
         }
     }
     // outputs, each packed to its run-time size in this thread's stage row
+    if (M && a.Wm && first)
+#pragma unroll
+        for (int i = 0; i < MX; ++i)
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if (i < m && j < p) a.Wm[i * p + j] = W[i][j];
     R* row = stage + threadIdx.x * LDS;
     if (a.WH) {
 #pragma unroll
@@ -347,6 +357,39 @@ __global__ void __launch_bounds__(kSmallThreads) k_cross_pre_small(CrossPre<R> a
                 }
         stage_flush(stage, LDS, p * p, a.Xt, a.oX, k0, nvalid, first);
     }
+}
+
+// The vectors of the transform where its matrices do not vary with k (U, M,
+// H, F, L, X time-invariant) but r_k, s_k or c_k do: W, W H, F~ and X~ come
+// from the pre-transform of step 0 alone, and one thread per step forms
+// g_k = W r_k + s_k and c~_k = c_k + L g_k.
+template <typename R, int MX>
+__global__ void __launch_bounds__(kPreThreads) k_cross_vec(CrossPre<R> a, long long T) {
+    const long long k = (long long)blockIdx.x * kPreThreads + threadIdx.x;
+    if (k >= T) return;
+    const int n = a.n, m = a.m, p = a.p;
+    const R* r = a.r ? a.r + a.sr * k : nullptr;
+    const R* s = a.s ? a.s + a.ss * k : nullptr;
+    const R* c = a.c ? a.c + a.sc * k : nullptr;
+    const R* L = a.L + a.sL * k;
+    R g[MX];
+#pragma unroll
+    for (int i = 0; i < MX; ++i) {
+        if (i >= m) continue;
+        R acc = s ? s[i] : R(0);
+        if (r)
+            for (int j = 0; j < p; ++j) acc += a.Wm[i * p + j] * r[j];
+        g[i] = acc;
+        if (a.og) a.g[a.og * k + i] = acc;
+    }
+    if (a.oc)
+        for (int l = 0; l < n; ++l) {
+            R acc = c ? c[l] : R(0);
+#pragma unroll
+            for (int i = 0; i < MX; ++i)
+                if (i < m) acc += L[l * m + i] * g[i];
+            a.ct[a.oc * k + l] = acc;
+        }
 }
 
 // Small sizes: a block per 256 steps.  K += W H as one contiguous run of the
@@ -413,7 +456,8 @@ bool tv(const lqt_in& in) { return in.ptr && in.step_stride != 0; }
 // Workspace layout and the transformed problem.
 struct CrossPlan {
     lqt_problem P2;  // pointers into the workspace are offsets from `base`
-    size_t solver, pre_status, Ft, ct, Xt, WH, g, total;
+    size_t solver, pre_status, Ft, ct, Xt, WH, g, Wm, total;
+    bool split;  // matrices from step 0 alone, vectors by k_cross_vec
     long long oF, oc, oX, oW, og;
     bool hasF, hasX;
     long long rows;
@@ -463,7 +507,8 @@ lqt_status plan_cross(const lqt_problem* P, const lqt_cross* X, const lqt_option
     cp->oc = tvc ? n : 0;
     cp->oX = tvX ? (long long)p * p : 0;
     const bool any_tv = tvWH || tvg || tvF || tvc || tvX;
-    cp->rows = T == 0 ? 0 : (any_tv ? T : 1);
+    cp->split = hasM && !tvW && !tvWH && !tvF && !tvX && (tvg || tvc) && m <= kVecMaxM;
+    cp->rows = T == 0 ? 0 : (any_tv && !cp->split ? T : 1);
     const long long rW = cp->oW ? T : 1, rg = cp->og ? T : 1, rF = cp->oF ? T : 1,
                     rc = cp->oc ? T : 1, rX = cp->oX ? T : 1;
 
@@ -484,6 +529,7 @@ lqt_status plan_cross(const lqt_problem* P, const lqt_cross* X, const lqt_option
     const size_t Xt = cp->hasX ? take(rX * p * p * es) : 0;
     const size_t WH = take(rW * m * n * es);
     const size_t g = take(rg * m * es);
+    const size_t Wm = cp->split ? take((size_t)m * p * es) : 0;
     const size_t tail = off;
     // the solver's workspace comes first (its status word at offset 0); its
     // size depends on the problem's sizes and options only
@@ -503,6 +549,7 @@ lqt_status plan_cross(const lqt_problem* P, const lqt_cross* X, const lqt_option
     cp->Xt = cp->solver + Xt;
     cp->WH = cp->solver + WH;
     cp->g = cp->solver + g;
+    cp->Wm = cp->solver + Wm;
     cp->total = cp->solver + tail;
     if (T == 0) P2 = *P;
     return LQT_OK;
@@ -580,12 +627,23 @@ lqt_status launch_pre(const lqt_problem* P, const lqt_cross* X, const CrossPlan&
     a.oX = cp.oX;
     a.oW = cp.oW;
     a.og = cp.og;
+    a.Wm = cp.split ? reinterpret_cast<R*>(base + cp.Wm) : nullptr;
     a.status = reinterpret_cast<int*>(base + cp.pre_status);
+    auto vectors = [&]() -> lqt_status {
+        if (cudaGetLastError() != cudaSuccess) return LQT_ECUDA;
+        if (!cp.split) return LQT_OK;
+        const long long vb = (P->T + kPreThreads - 1) / kPreThreads;
+        if (vb > INT32_MAX) return LQT_EINVAL;
+        if (a.m <= 8)
+            k_cross_vec<R, 8><<<(unsigned)vb, kPreThreads, 0, s>>>(a, P->T);
+        else
+            k_cross_vec<R, kVecMaxM><<<(unsigned)vb, kPreThreads, 0, s>>>(a, P->T);
+        return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    };
     if (a.p <= 8) {
         const long long blocks = (cp.rows + kSmallThreads - 1) / kSmallThreads;
         if (blocks > INT32_MAX) return LQT_EINVAL;
-        if (launch_pre_small(a, (unsigned)blocks, s))
-            return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+        if (launch_pre_small(a, (unsigned)blocks, s)) return vectors();
     }
     constexpr int groups = kPreThreads / G;
     const size_t smem = (size_t)groups * a.group_elems * sizeof(R);
@@ -597,7 +655,7 @@ lqt_status launch_pre(const lqt_problem* P, const lqt_cross* X, const CrossPlan&
     const long long blocks = (cp.rows + groups - 1) / groups;
     if (blocks > INT32_MAX) return LQT_EINVAL;
     k_cross_pre<R, G><<<(unsigned)blocks, kPreThreads, smem, s>>>(a);
-    return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    return vectors();
 }
 
 template <typename R>

@@ -83,3 +83,43 @@ def test_rank_reduced_limits():
         np.float32))
     assert lqt.lqt_condensed_workspace_bytes(P, 16) == 0
     assert lqt.lqt_condensed_workspace_bytes(P, 8) > 0
+
+
+@pytest.mark.parametrize("B", [2, 16])
+def test_condensed_refinement_restores_u(B):
+    """The expansion rebuilds u from block starts and references of order one;
+    the second (shifted) solve makes every term of the size of u, so all
+    outputs stay near FP32 rounding at any B.  Unrefined, u carries the
+    cancellation of the FP32 solve (about 1e-5 here, as for lqt_solve)."""
+    from paper_2104_03186_gb300 import lqt
+
+    prob = inputs.vehicle(100_000, seed=40 + B).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    errs = compare(_solve(prob, B), ref, FP32_TOL)
+    assert max(errs.values()) <= 1e-6, errs
+    off = compare(_solve(prob, B, refine=lqt.options(refine=lqt.LQT_REFINE_OFF)), ref, 1e-4,
+                  step_tol=1e-2)
+    assert errs["u"] < off["u"], (errs, off)
+
+
+def test_condensed_refinement_with_offsets_and_terminal_reference():
+    """The shifted data cover c_k, r_k and r_T; time-varying model, B = 8
+    (rank-reduced) and B = 2 (register kernels)."""
+    prob = inputs.random_problem(4, 2, p=2, T=1500, seed=77, pT=4).rounded_to(np.float32)
+    ref = oracle_solve(prob)
+    for B in (2, 8):
+        compare(_solve(prob, B), ref, FP32_TOL)
+
+
+@pytest.mark.parametrize("B", [2, 8])
+def test_condensed_reports_indefinite_U(B):
+    """A negative control weight: the failure recorded before the condensed
+    solve (the reduction's factorisation at B = 8) or by it (B = 2) reaches
+    the workspace status through both solves of the refinement."""
+    from paper_2104_03186_gb300 import lqt
+
+    prob = inputs.vehicle(400, seed=1).rounded_to(np.float32)
+    prob.U = -prob.U
+    with pytest.raises(lqt.LQTError) as e:
+        _solve(prob, B)
+    assert e.value.status == lqt.LQT_ENOTSPD

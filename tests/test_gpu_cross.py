@@ -139,3 +139,23 @@ def test_cross_reports_indefinite_U():
     with pytest.raises(lqt.LQTError) as e:
         lqt.solve_cross(P, C)
     assert e.value.status == lqt.LQT_ENOTSPD
+
+
+@pytest.mark.parametrize("n,m", [(4, 2), (2, 1), (8, 4)])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_cross_invariant_matrices_varying_vectors(n, m, dtype):
+    """Time-invariant F, L, U, H, X and M with r_k, c_k and s_k varying: the
+    transform's matrices come from step 0 alone and a per-step kernel forms
+    g_k = W r_k + s_k and c~_k = c_k + L g_k.  F is scaled to spectral radius
+    0.98: a fixed F with an unstable mode (1.04 here) grows by 1.04^T over
+    the scan's spans, which no FP32 scan resolves to the tolerance."""
+    prob = inputs.random_problem(n, m, T=1500, seed=41 + n, time_varying=False)
+    prob.F = prob.F * (0.98 / np.abs(np.linalg.eigvals(prob.F[0])).max())
+    ct = inputs.cross_terms(prob, seed=42, scale=0.5, time_varying=False)
+    rng = np.random.default_rng(43)
+    ct = inputs.CrossTerms(M=ct.M, s=rng.standard_normal((prob.T, m)))
+    prob.c = rng.normal(0.0, 0.1, (prob.T, n))
+    tol = FP64_TOL
+    if dtype == np.float32:
+        prob, ct, tol = prob.rounded_to(np.float32), ct.rounded_to(np.float32), FP32_TOL
+    compare(_solve(prob, ct, dtype=dtype), _oracle(prob, ct), tol)
