@@ -169,6 +169,19 @@ size_t lqt_workspace_bytes(const lqt_problem *prob, const lqt_options *opts);
 lqt_status lqt_solve(const lqt_problem *prob, const lqt_solution *sol, const lqt_options *opts,
                      void *workspace, size_t workspace_bytes, void *stream);
 
+/* Single-tile solves (n <= 4 thread-per-chunk path; a property of this
+ * implementation, not of the paper).  Each thread of a tile folds a chunk of
+ * consecutive steps (Sec. V-C block processing) and a tile's W chunks are
+ * scanned in shared memory (Alg. 1).  A problem with 0 < T <= W x
+ * max_chunk_steps (W = 512 threads in FP32, 256 in FP64) runs in a single CTA:
+ * each pass (two when refining) is one launch that keeps the in-tile trees in
+ * shared memory, where a longer problem takes five launches per pass over
+ * many tiles.  0 turns single-tile solves off.  Default 2 (T <= 1024 in
+ * FP32).  The setting is process-wide; solves already launched are not
+ * affected.  *previous (may be NULL) receives the old value.  Returns
+ * LQT_EINVAL for a negative value. */
+lqt_status lqt_set_single_tile_chunk(int32_t max_chunk_steps, int32_t *previous);
+
 /* Sequential Riccati recursion of Sec. II-B followed by the forward pass of
  * eq. optimal_trajectory, run on the GPU by one thread per problem (the
  * sequential baseline).  Same problem, options, outputs and workspace rules

@@ -157,10 +157,29 @@ lqt_status resolve_refine(const lqt_problem* P, const lqt_options* o, bool* refi
     return LQT_OK;
 }
 
+// A problem whose steps fit one tile with chunks of at most this many steps
+// (0 < T <= W x this) runs in one CTA, each pass one launch of k_solo; 0
+// turns that off.  lqt_set_single_tile_chunk sets it.
+constexpr int kSingleTileChunkDefault = 2;
+std::atomic<int> g_single_tile_chunk{kSingleTileChunkDefault};
+
 lqt_status make_plan(const lqt_problem* P, const Variant& var, Plan* plan) {
     const int sms = sm_count_current();
     if (sms <= 0) return LQT_ECUDA;
     const int64_t W = var.W;
+    plan->solo = 0;
+    if (P->T > 0 && P->T <= W * (int64_t)g_single_tile_chunk.load()) {
+        // one tile: chunks of ceil(T / W) steps, every pass one launch
+        const int64_t B = (P->T + W - 1) / W;
+        if (B <= INT32_MAX) {
+            plan->B = (int)B;
+            plan->W = (int)W;
+            plan->tiles = 1;
+            plan->TP = var.TP;
+            plan->solo = 1;
+            return LQT_OK;
+        }
+    }
     const int64_t target = (int64_t)sms * W;
     int64_t B = (P->T + target - 1) / target;
     if (B < 1) B = 1;
@@ -374,7 +393,7 @@ lqt_status lqt_plan(const lqt_problem* prob, const lqt_options* opts, int32_t* c
     if (chunk_steps) *chunk_steps = plan.B;
     if (tile_threads_out) *tile_threads_out = plan.W;
     if (tiles) *tiles = plan.tiles;
-    const int per_pass = plan.tiles > 0 ? 5 : 2;
+    const int per_pass = plan.solo ? 1 : (plan.tiles > 0 ? 5 : 2);
     if (kernels) *kernels = (refine && prob->T > 0) ? 2 * per_pass : per_pass;
     return LQT_OK;
 }
@@ -513,6 +532,13 @@ extern "C" {
 lqt_status lqt_solve(const lqt_problem* prob, const lqt_solution* sol, const lqt_options* opts,
                      void* workspace, size_t workspace_bytes, void* stream) {
     return solve_common(prob, sol, opts, workspace, workspace_bytes, stream, false);
+}
+
+lqt_status lqt_set_single_tile_chunk(int32_t max_chunk_steps, int32_t* previous) {
+    if (max_chunk_steps < 0) return LQT_EINVAL;
+    const int old = lqt::g_single_tile_chunk.exchange(max_chunk_steps);
+    if (previous) *previous = old;
+    return LQT_OK;
 }
 
 lqt_status lqt_riccati_sequential(const lqt_problem* prob, const lqt_solution* sol,

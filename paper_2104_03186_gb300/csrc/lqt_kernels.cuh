@@ -436,19 +436,17 @@ constexpr int tile_threads() {
 // keeps the total of [i + 2^d, i + 2^{d+1}) for the down-sweep).  Only the
 // chunks that hold steps are swept (the rest are neutral).
 // ===========================================================================
-template <typename R, int N, int M, int W>
-__global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
-    griddep_launch_dependents();
-    griddep_wait();
+// The body of each per-tile kernel is a device function over one tile, so
+// that the single-tile solve (k_solo) runs the same code back to back with
+// its trees left in shared memory.  SOLO: the only tile of the problem; the
+// tree is not stored for another kernel.  The model area `sm` is filled.
+template <typename R, int N, int M, int W, bool SOLO>
+__device__ __forceinline__ void bwd_up_body(const Params<R>& P, unsigned tile, R* tree,
+                                            const R* sm) {
     using SM = Smem<R, N, M, W>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][WS]
-    R* sm = tree + SM::UP_BIG + SM::RBUF;
     constexpr int WS = SM::WS;
-    model_prologue<R, N, M>(P, sm);
-
     const int tid = threadIdx.x;
-    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    const TileGeo geo{P.T, (long long)tile * W, P.B};
     const int Weff = next_pow2(geo.live(W));
     long long s, e;
     geo.chunk(tid, s, e);
@@ -472,11 +470,25 @@ __global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
                                       ElemView<R, N>{tree + tslot<R>(i), WS});
         __syncthreads();
     }
-    if (tid < Dims<N>::ELEM) P.tile_agg[(size_t)blockIdx.x * Dims<N>::ELEM + tid] = tree[tid * WS];
-    cta_bulk_store(P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS, tree,
-                   (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)));
+    if (!SOLO) {
+        if (tid < Dims<N>::ELEM) P.tile_agg[(size_t)tile * Dims<N>::ELEM + tid] = tree[tid * WS];
+        cta_bulk_store(P.tree + (size_t)tile * Dims<N>::ELEM * WS, tree,
+                       (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)));
+    }
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!ok2) set_status(P.status, ST_SINGULAR);
+}
+
+template <typename R, int N, int M, int W>
+__global__ void __launch_bounds__(W, 1) k_bwd_up(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
+    using SM = Smem<R, N, M, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* tree = reinterpret_cast<R*>(smem_raw + kSmemHead);  // [ELEM][WS]
+    R* sm = tree + SM::UP_BIG + SM::RBUF;
+    model_prologue<R, N, M>(P, sm);
+    bwd_up_body<R, N, M, W, false>(P, blockIdx.x, tree, sm);
 }
 
 // Terminal value S_T = H_T^T X_T H_T, v_T = H_T^T X_T r_T.
@@ -694,27 +706,41 @@ __global__ void __launch_bounds__(TP, 1) k_bwd_top(const Params<R> P) {
 // bwd_down: in-tile down-sweep of values, Riccati re-fold per chunk with the
 // gains fused, and the forward affine up-sweep (right-anchored).
 // ===========================================================================
-template <typename R, int N, int M, int W>
-__global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
-    griddep_launch_dependents();
-    griddep_wait();
+// S_T and v_T of the terminal value z, as the pass's out_mask asks.
+template <typename R, int N>
+__device__ __forceinline__ void terminal_outputs(const Params<R>& P, const Value<R, N>& z) {
+    R* ST = P.S + (size_t)P.T * N * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (P.out_mask & OUT_S) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) ST[i * N + j] = z.S[sym<N>(i, j)];
+        }
+        if (P.out_mask & OUT_V) P.v[(size_t)P.T * N + i] = z.v[i];
+    }
+}
+
+// bwd_down over one tile.  rbuf: this thread's r buffers (slot-major, stride
+// W); sm: the model area, filled here unless SOLO (the caller filled it).
+// SOLO: the up-sweep's tree is already in `big`, and the value carried into
+// the tile is the terminal value (Lemma LQT_assoc), formed here.
+template <typename R, int N, int M, int W, bool SOLO>
+__device__ __forceinline__ void bwd_down_body(const Params<R>& P, unsigned tile,
+                                              unsigned char* smem_raw, R* rbuf, R* sm) {
     using SM = Smem<R, N, M, W>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* probe_bar = bar + 1;  // second word of the head: the diagnostic wait
     R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
     constexpr int WS = SM::WS;
     R* tree = big;                                       // [ELEM][WS]
     R* carry = big + (size_t)Dims<N>::ELEM * WS;         // [VALUE][WS]
-    R* rbuf = big + SM::DOWN_BIG + threadIdx.x;  // slot-major, stride W
-    R* sm = big + SM::DOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(bar, 1);
+        if (!SOLO) mbar_init(bar, 1);
         if (P.wait_probe > 0) mbar_init(probe_bar, 1);
     }
     long long s, e;
-    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    const TileGeo geo{P.T, (long long)tile * W, P.B};
     geo.chunk(tid, s, e);
     {
         long long lo;
@@ -722,19 +748,33 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
         bwd_group(s, e, 0, lo, cnt);
         r_prefetch(P, rbuf, lo, cnt, W);
     }
-    model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
+    if (SOLO)
+        __syncthreads();  // the barrier is initialised before anyone waits on it
+    else
+        model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
 
-    uint32_t phase = 0;
-    bool ok_load = cta_bulk_load(tree, P.tree + (size_t)blockIdx.x * Dims<N>::ELEM * WS,
-                                 (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)), bar, phase,
-                                 P.wait_limit);
+    bool ok_load = true;
+    if (!SOLO) {
+        uint32_t phase = 0;
+        ok_load = cta_bulk_load(tree, P.tree + (size_t)tile * Dims<N>::ELEM * WS,
+                                (uint32_t)(Dims<N>::ELEM * WS * sizeof(R)), bar, phase,
+                                P.wait_limit);
+    }
     // Diagnostic: a wait on a barrier that no copy and no thread completes runs
     // out after P.wait_probe polls, as a lost bulk copy would; the kernel then
     // flags the timeout and carries on like after any other timed-out wait.
     if (P.wait_probe > 0 && !mbar_wait(probe_bar, 0, P.wait_probe)) ok_load = false;
     const int Weff = next_pow2(geo.live(W));
-    if (tid < Dims<N>::VALUE)
-        carry[tid * WS] = P.tile_carry[(size_t)blockIdx.x * Dims<N>::VALUE + tid];
+    if (SOLO) {
+        if (tid == W - 1) {
+            Value<R, N> z;
+            terminal_value<R, N>(P, z);
+            store_value(z, ValueView<R, N>{carry, WS});
+            terminal_outputs<R, N>(P, z);
+        }
+    } else if (tid < Dims<N>::VALUE) {
+        carry[tid * WS] = P.tile_carry[(size_t)tile * Dims<N>::VALUE + tid];
+    }
     __syncthreads();
     bool ok_sing = true;
 #pragma unroll 1
@@ -861,15 +901,28 @@ __global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
                                       AffineView<R, N>{ftree + tslot<R>(j), WS});
         __syncthreads();
     }
-    if (tid < Dims<N>::AFFINE)
-        P.ftile_agg[(size_t)blockIdx.x * Dims<N>::AFFINE + tid] =
-            ftree[tid * WS + tslot<R>(Weff - 1)];
-    cta_bulk_store(P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * WS, ftree,
-                   (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)));
+    if (!SOLO) {
+        if (tid < Dims<N>::AFFINE)
+            P.ftile_agg[(size_t)tile * Dims<N>::AFFINE + tid] =
+                ftree[tid * WS + tslot<R>(Weff - 1)];
+        cta_bulk_store(P.ftree + (size_t)tile * Dims<N>::AFFINE * WS, ftree,
+                       (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)));
+    }
     if (!ok) set_status(P.status, ST_NOTSPD);
     if (!finite) set_status(P.status, ST_NONFINITE);
     if (!ok_sing) set_status(P.status, ST_SINGULAR);
     if (!ok_load) set_status(P.status, ST_TIMEOUT);
+}
+
+template <typename R, int N, int M, int W>
+__global__ void __launch_bounds__(W, 1) k_bwd_down(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
+    using SM = Smem<R, N, M, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
+    bwd_down_body<R, N, M, W, false>(P, blockIdx.x, smem_raw, big + SM::DOWN_BIG + threadIdx.x,
+                                     big + SM::DOWN_BIG + SM::RBUF);
 }
 
 // ===========================================================================
@@ -953,30 +1006,40 @@ __global__ void __launch_bounds__(TP, 1) k_fwd_top(const Params<R> P) {
 // First refined pass: also r'_k = r_k - H_k x^_k, c'_k = F_k x^_k + c_k - x^_{k+1}
 // (compensated), r'_T and x'_0.  Second pass: x*_{k+1} = x^_{k+1} + xi_{k+1}.
 // ===========================================================================
-template <typename R, int N, int M, int W>
-__global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
-    griddep_launch_dependents();
-    griddep_wait();
+// fwd_down over one tile; sm: the model area, filled here unless SOLO.
+// SOLO: the forward tree is already in `big` and the tile starts at x_0
+// (Lemma lqt_fwd_init).
+template <typename R, int N, int M, int W, bool SOLO>
+__device__ __forceinline__ void fwd_down_body(const Params<R>& P, unsigned tile,
+                                              unsigned char* smem_raw, R* sm) {
     using SM = Smem<R, N, M, W>;
     using ML = ModelLayout<N, M>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
     constexpr int WS = SM::WS;
     R* ftree = big;                                      // [AFFINE][WS]
     R* xs = big + (size_t)Dims<N>::AFFINE * WS;          // [N][WS]
-    R* sm = big + SM::FDOWN_BIG + SM::RBUF;
     const int tid = threadIdx.x;
-    if (tid == 0) mbar_init(bar, 1);
-    model_prologue<R, N, M>(P, sm);
-
-    uint32_t phase = 0;
-    const bool ok_load = cta_bulk_load(ftree, P.ftree + (size_t)blockIdx.x * Dims<N>::AFFINE * WS,
-                                       (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)), bar, phase,
-                                       P.wait_limit);
-    const TileGeo geo{P.T, (long long)blockIdx.x * W, P.B};
+    bool ok_load = true;
+    if (!SOLO) {
+        if (tid == 0) mbar_init(bar, 1);
+        model_prologue<R, N, M>(P, sm);
+        uint32_t phase = 0;
+        ok_load = cta_bulk_load(ftree, P.ftree + (size_t)tile * Dims<N>::AFFINE * WS,
+                                (uint32_t)(Dims<N>::AFFINE * WS * sizeof(R)), bar, phase,
+                                P.wait_limit);
+    }
+    const TileGeo geo{P.T, (long long)tile * W, P.B};
     const int Weff = next_pow2(geo.live(W));
-    if (tid < N) xs[tid * WS + tslot<R>(Weff - 1)] = P.ftile_x[(size_t)blockIdx.x * N + tid];
+    if (tid < N) {
+        if (SOLO) {
+            const R x0 = P.x0[tid];
+            xs[tid * WS + tslot<R>(Weff - 1)] = x0;
+            if (!P.refine_add) P.x[tid] = x0;  // second pass: x*_0 = x^_0 + 0 stays
+        } else {
+            xs[tid * WS + tslot<R>(Weff - 1)] = P.ftile_x[(size_t)tile * N + tid];
+        }
+    }
     __syncthreads();
 #pragma unroll 1
     for (int h = Weff / 2; h >= 1; h >>= 1) {
@@ -1003,9 +1066,9 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
         x[i] = xs[i * WS + tslot<R>(tid)];
         xnext[i] = tid + 1 < W ? xs[i * WS + tslot<R>(tid + 1)] : R(0);
     }
-    if (tid == W - 1 && blockIdx.x + 1 < (unsigned)P.tiles) {
+    if (!SOLO && tid == W - 1 && tile + 1 < (unsigned)P.tiles) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) xnext[i] = P.ftile_x[(size_t)(blockIdx.x + 1) * N + i];
+        for (int i = 0; i < N; ++i) xnext[i] = P.ftile_x[(size_t)(tile + 1) * N + i];
     }
     __syncthreads();  // the big area becomes the warp staging rows
 
@@ -1166,8 +1229,50 @@ __global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
         }
         __syncwarp();
     }
-    if (P.refine_emit && blockIdx.x == 0 && tid < N) P.x0p[tid] = R(0);
+    if (P.refine_emit && tile == 0 && tid < N) P.x0p[tid] = R(0);
     if (!ok_load) set_status(P.status, ST_TIMEOUT);
+}
+
+template <typename R, int N, int M, int W>
+__global__ void __launch_bounds__(W, 1) k_fwd_down(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
+    using SM = Smem<R, N, M, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
+    fwd_down_body<R, N, M, W, false>(P, blockIdx.x, smem_raw, big + SM::FDOWN_BIG + SM::RBUF);
+}
+
+// ===========================================================================
+// solo: a problem of one tile in one CTA -- the pass's up-sweep, value
+// down-sweep with the Riccati re-folds, forward up-sweep and rollout back to
+// back (the bodies above with SOLO), the trees kept in shared memory between
+// them.  The top-level scans reduce to the terminal value and x_0, so a pass
+// is one launch instead of five.
+// ===========================================================================
+template <typename R, int N, int M, int W>
+struct SoloSmem {
+    using SM = Smem<R, N, M, W>;
+    static constexpr int BIG = SM::DOWN_BIG > SM::FDOWN_BIG ? SM::DOWN_BIG : SM::FDOWN_BIG;
+    static_assert(SM::UP_BIG <= BIG, "the up-sweep's tree fits the common area");
+    static size_t bytes(int p) { return SM::bytes(BIG, p); }
+};
+
+template <typename R, int N, int M, int W>
+__global__ void __launch_bounds__(W, 1) k_solo(const Params<R> P) {
+    griddep_launch_dependents();
+    griddep_wait();
+    using SM = Smem<R, N, M, W>;
+    constexpr int BIG = SoloSmem<R, N, M, W>::BIG;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* big = reinterpret_cast<R*>(smem_raw + kSmemHead);
+    R* sm = big + BIG + SM::RBUF;
+    model_prologue<R, N, M>(P, sm);  // ends with __syncthreads
+    bwd_up_body<R, N, M, W, true>(P, 0, big, sm);
+    __syncthreads();
+    bwd_down_body<R, N, M, W, true>(P, 0, smem_raw, big + BIG + threadIdx.x, sm);
+    __syncthreads();
+    fwd_down_body<R, N, M, W, true>(P, 0, smem_raw, sm);
 }
 
 // ===========================================================================

@@ -19,6 +19,7 @@ struct Plan {
     int W;      // chunks per tile (one CTA)
     int tiles;  // CTAs of the per-tile kernels
     int TP;     // threads of the top-level scans
+    int solo;   // 1: a single tile, each pass one launch of k_solo
 };
 
 // Kernel timing (lqt_profile_enable); owned by the C ABI.

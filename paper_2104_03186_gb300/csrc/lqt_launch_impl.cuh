@@ -56,7 +56,18 @@ lqt_status launch_solve(const Params<R>& P, const Plan& plan, cudaStream_t strea
     constexpr int TP = top_threads();
     using SM = Smem<R, N, M, W>;
     static std::atomic<bool> done_up[64], done_top[64], done_top1[64], done_top2[64], done_down[64],
-        done_ftop[64], done_fdown[64];
+        done_ftop[64], done_fdown[64], done_solo[64];
+    if (plan.solo) {
+        // one tile: the whole pass in one CTA
+        const size_t smem = SoloSmem<R, N, M, W>::bytes(P.p);
+        if (plan.tiles != 1 || allow_smem(k_solo<R, N, M, W>, done_solo, smem) != cudaSuccess)
+            return plan.tiles != 1 ? LQT_EINVAL : LQT_ECUDA;
+        prof_mark(prof, stream, P.refine_add ? "solo.refine" : "solo");
+        if (launch_pdl<R>(k_solo<R, N, M, W>, 1, W, smem, stream, P, true) != cudaSuccess)
+            return LQT_ECUDA;
+        if (bwd_done && cudaEventRecord(bwd_done, stream) != cudaSuccess) return LQT_ECUDA;
+        return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+    }
     const size_t smem_up = SM::bytes(SM::UP_BIG, P.p);
     constexpr long long kTopReplay =
         top_smem_bytes(Dims<N>::ELEM, Dims<N>::VALUE, N, TP, (int)sizeof(R), true);

@@ -130,6 +130,7 @@ def _load() -> ctypes.CDLL:
         "lqt_condensed_workspace_bytes": (sz, [P, ctypes.c_int32, O]),
         "lqt_solve_condensed": (st, [P, ctypes.c_int32, S, O, vp, sz, vp]),
         "lqt_solve_nonlinear": (st, [P, ctypes.POINTER(lqt_nonlinear), S, O, vp, sz, vp]),
+        "lqt_set_single_tile_chunk": (st, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -143,6 +144,16 @@ _lib = _load()
 
 def library() -> ctypes.CDLL:
     return _lib
+
+
+def lqt_set_single_tile_chunk(max_chunk_steps: int) -> int:
+    """Problems of at most max_chunk_steps steps per thread of one tile run in
+    one CTA per pass (0: never); returns the previous setting."""
+    prev = ctypes.c_int32(0)
+    st = _lib.lqt_set_single_tile_chunk(int(max_chunk_steps), ctypes.byref(prev))
+    if st != LQT_OK:
+        raise LQTError(st, "lqt_set_single_tile_chunk")
+    return int(prev.value)
 
 
 # ---------------------------------------------------------------------------

@@ -24,3 +24,14 @@ def rel_fro(a, b):
     from paper_2104_03186_gb300.accuracy import rel_fro as _rel_fro
 
     return _rel_fro(a, b)
+
+
+@pytest.fixture
+def single_tile():
+    """Sets the single-tile threshold (lqt_set_single_tile_chunk, default 2)
+    for one test and restores it afterwards; yields the setter."""
+    from paper_2104_03186_gb300 import lqt
+
+    prev = lqt.lqt_set_single_tile_chunk(2)
+    yield lqt.lqt_set_single_tile_chunk
+    lqt.lqt_set_single_tile_chunk(prev)

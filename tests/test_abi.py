@@ -188,3 +188,15 @@ def test_warm_arguments_rejected_before_any_device_work(lib):
     p.dtype = lib.LQT_F32
     p.x0 = None  # no initial state
     assert lib._lib.lqt_solve_warm(items, 1, ws, 1 << 20, None) == lib.LQT_EINVAL
+
+
+def test_single_tile_setting_round_trip(lib):
+    """lqt_set_single_tile_chunk needs no device: a negative value is
+    rejected, a valid one returns the previous setting."""
+    so = lib.library()
+    prev = ctypes.c_int32(-7)
+    assert so.lqt_set_single_tile_chunk(-1, ctypes.byref(prev)) == lib.LQT_EINVAL
+    assert prev.value == -7  # untouched on error
+    old = lib.lqt_set_single_tile_chunk(5)
+    assert lib.lqt_set_single_tile_chunk(old) == 5
+    assert so.lqt_set_single_tile_chunk(old, None) == lib.LQT_OK

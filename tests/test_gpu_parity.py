@@ -286,11 +286,13 @@ def test_refined_fp64_on_request():
                                    ("f64", 1, 1), ("f64", 2, 1)],
                          ids=lambda v: "%s_n%d_m%d" % v)
 @pytest.mark.parametrize("T", [700, 150001])
-def test_refined_second_pass_replays_top_scan(dt_nm, T):
+def test_refined_second_pass_replays_top_scan(dt_nm, T, single_tile):
     """The refinement pass runs its top-level backward scan from the maps the
     first pass recorded (FP32 at every n <= 4, FP64 at n <= 2, where they fit
-    the CTA's shared memory): a few tiles (one or two levels) and about 150
-    tiles (eight levels), time-varying random data."""
+    the CTA's shared memory): a few tiles (one or two levels; single-tile
+    solves off, which would take T = 700 in one CTA) and about 150 tiles
+    (eight levels), time-varying random data."""
+    single_tile(0)
     dt, n, m = dt_nm
     prob = inputs.random_problem(n, m, min(n, 2), T=T, seed=300 + n + m)
     if dt == "f32":
