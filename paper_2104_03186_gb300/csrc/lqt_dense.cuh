@@ -58,11 +58,14 @@ struct Step {
     R q[N];             // H^T X r
 };
 
+// Correctly rounded reciprocal (the same value as R(1) / x, without the
+// general division code).
 template <typename R>
 __device__ __forceinline__ R rcp_(R x) { return R(1) / x; }
-
-template <typename R>
-__device__ __forceinline__ R sqrt_(R x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double rcp_(double x) { return __drcp_rn(x); }
 
 template <typename R>
 __device__ __forceinline__ R abs_(R x) { return fabs(x); }
@@ -123,7 +126,7 @@ __device__ __forceinline__ bool riccati_step(const Step<R, N, M>& st, bool has_c
 #pragma unroll
         for (int k = 0; k < a; ++k) g -= Rc[a][k] * Rc[a][k];
         ok = ok && (g > R(0));
-        const R r = sqrt_(g);
+        const R r = sqrt(g);
         Rc[a][a] = r;
         Rinv[a] = rcp_(r);
 #pragma unroll

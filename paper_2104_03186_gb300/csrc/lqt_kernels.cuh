@@ -97,12 +97,16 @@ __host__ __device__ inline int next_pow2(int x) {
 
 // Shared-memory model area (floats of R), same layout in every kernel:
 //   F[N*N] L[N*M] U[M*M] c[N] Q[SYM] HX[p*N] H[p*N]
+// Each part starts on a multiple of 4 elements (16 bytes in FP32), and the
+// area itself is 16-byte aligned in every kernel, so that load_step reads the
+// parts with vector loads.
 template <int N, int M>
 struct ModelLayout {
-    static constexpr int OF = 0, OL = N * N, OU = OL + N * M, OC = OU + M * M,
-                         OQ = OC + N, OHX = OQ + Dims<N>::SYM;
-    __host__ __device__ static constexpr int OH(int p) { return OHX + p * N; }
-    __host__ __device__ static constexpr int size(int p) { return OHX + 2 * p * N; }
+    static constexpr int OF = 0, OL = round4(N * N), OU = round4(OL + N * M),
+                         OC = round4(OU + M * M), OQ = round4(OC + N),
+                         OHX = round4(OQ + Dims<N>::SYM);
+    __host__ __device__ static constexpr int OH(int p) { return round4(OHX + p * N); }
+    __host__ __device__ static constexpr int size(int p) { return round4(OH(p) + p * N); }
 };
 
 // Fill the model area from the time-invariant inputs (each part only when its
@@ -138,96 +142,6 @@ __device__ __forceinline__ void model_prologue(const Params<R>& P, R* sm) {
         }
     }
     __syncthreads();
-}
-
-// Step k of the model: F, c, L, U and the cost element Q = H^T X H, q = H^T X r,
-// from the shared model area where the input is time-invariant.
-template <typename R, int N, int M>
-__device__ __forceinline__ void load_step(const Params<R>& P, long long k, const R* sm,
-                                          const R* r_staged, Step<R, N, M>& st,
-                                          int r_stride = 1) {
-    using ML = ModelLayout<N, M>;
-    if (P.dyn_invariant) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) st.F[i][j] = sm[ML::OF + i * N + j];
-#pragma unroll
-            for (int a = 0; a < M; ++a) st.L[i][a] = sm[ML::OL + i * M + a];
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int b = 0; b < M; ++b) st.U[a][b] = sm[ML::OU + a * M + b];
-    } else {
-        const R* F = P.F + k * P.sF;
-        const R* L = P.L + k * P.sL;
-        const R* U = P.U + k * P.sU;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) st.F[i][j] = __ldg(F + i * N + j);
-#pragma unroll
-            for (int a = 0; a < M; ++a) st.L[i][a] = __ldg(L + i * M + a);
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int b = 0; b < M; ++b) st.U[a][b] = __ldg(U + a * M + b);
-    }
-    if (P.c_invariant) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) st.c[i] = sm[ML::OC + i];
-    } else {
-        const R* c = P.c + k * P.sc;
-#pragma unroll
-        for (int i = 0; i < N; ++i) st.c[i] = __ldg(c + i);
-    }
-    const int p = P.p;
-    const R* r = P.r ? P.r + k * P.sr : nullptr;
-    if (P.cost_invariant) {
-        const R* sHX = sm + ML::OHX;
-#pragma unroll
-        for (int k2 = 0; k2 < Dims<N>::SYM; ++k2) st.Q[k2] = sm[ML::OQ + k2];
-#pragma unroll
-        for (int i = 0; i < N; ++i) st.q[i] = R(0);
-        if (r) {
-            for (int a = 0; a < p; ++a) {
-                const R ra = r_staged ? r_staged[a * r_stride] : __ldg(r + a);
-#pragma unroll
-                for (int i = 0; i < N; ++i) st.q[i] += sHX[a * N + i] * ra;
-            }
-        }
-    } else {
-        // Q = sum_a H_a^T y_a with y_a = (X H)_a ; q = sum_a H_a^T (X r)_a
-        const R* H = P.H + k * P.sH;
-        const R* X = P.X + k * P.sX;
-#pragma unroll
-        for (int k2 = 0; k2 < Dims<N>::SYM; ++k2) st.Q[k2] = R(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) st.q[i] = R(0);
-        for (int a = 0; a < p; ++a) {
-            R y[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) y[j] = R(0);
-            R xr = R(0);
-            for (int b = 0; b < p; ++b) {
-                const R xab = __ldg(X + a * p + b);
-#pragma unroll
-                for (int j = 0; j < N; ++j) y[j] += xab * __ldg(H + b * N + j);
-                if (r) xr += xab * __ldg(r + b);
-            }
-            R h[N];
-#pragma unroll
-            for (int i = 0; i < N; ++i) h[i] = __ldg(H + a * N + i);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                st.q[i] += h[i] * xr;
-#pragma unroll
-                for (int j = i; j < N; ++j) st.Q[sym<N>(i, j)] += h[i] * y[j];
-            }
-        }
-    }
 }
 
 // Vector stores of COUNT consecutive values when 16-byte aligned per item.
@@ -277,6 +191,88 @@ __device__ __forceinline__ void load_row(const R* src, R* vals) {
     } else {
 #pragma unroll
         for (int i = 0; i < COUNT; ++i) vals[i] = src[i];
+    }
+}
+
+// Step k of the model: F, c, L, U and the cost element Q = H^T X H, q = H^T X r,
+// from the shared model area where the input is time-invariant.
+template <typename R, int N, int M>
+__device__ __forceinline__ void load_step(const Params<R>& P, long long k, const R* sm,
+                                          const R* r_staged, Step<R, N, M>& st,
+                                          int r_stride = 1) {
+    using ML = ModelLayout<N, M>;
+    if (P.dyn_invariant) {
+        load_row<R, N * N>(sm + ML::OF, &st.F[0][0]);
+        load_row<R, N * M>(sm + ML::OL, &st.L[0][0]);
+        load_row<R, M * M>(sm + ML::OU, &st.U[0][0]);
+    } else {
+        const R* F = P.F + k * P.sF;
+        const R* L = P.L + k * P.sL;
+        const R* U = P.U + k * P.sU;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) st.F[i][j] = __ldg(F + i * N + j);
+#pragma unroll
+            for (int a = 0; a < M; ++a) st.L[i][a] = __ldg(L + i * M + a);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b) st.U[a][b] = __ldg(U + a * M + b);
+    }
+    if (P.c_invariant) {
+        load_row<R, N>(sm + ML::OC, st.c);
+    } else {
+        const R* c = P.c + k * P.sc;
+#pragma unroll
+        for (int i = 0; i < N; ++i) st.c[i] = __ldg(c + i);
+    }
+    const int p = P.p;
+    const R* r = P.r ? P.r + k * P.sr : nullptr;
+    if (P.cost_invariant) {
+        const R* sHX = sm + ML::OHX;
+        load_row<R, Dims<N>::SYM>(sm + ML::OQ, st.Q);
+#pragma unroll
+        for (int i = 0; i < N; ++i) st.q[i] = R(0);
+        if (r) {
+            for (int a = 0; a < p; ++a) {
+                const R ra = r_staged ? r_staged[a * r_stride] : __ldg(r + a);
+                R hx[N];
+                load_row<R, N>(sHX + a * N, hx);
+#pragma unroll
+                for (int i = 0; i < N; ++i) st.q[i] += hx[i] * ra;
+            }
+        }
+    } else {
+        // Q = sum_a H_a^T y_a with y_a = (X H)_a ; q = sum_a H_a^T (X r)_a
+        const R* H = P.H + k * P.sH;
+        const R* X = P.X + k * P.sX;
+#pragma unroll
+        for (int k2 = 0; k2 < Dims<N>::SYM; ++k2) st.Q[k2] = R(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) st.q[i] = R(0);
+        for (int a = 0; a < p; ++a) {
+            R y[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) y[j] = R(0);
+            R xr = R(0);
+            for (int b = 0; b < p; ++b) {
+                const R xab = __ldg(X + a * p + b);
+#pragma unroll
+                for (int j = 0; j < N; ++j) y[j] += xab * __ldg(H + b * N + j);
+                if (r) xr += xab * __ldg(r + b);
+            }
+            R h[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) h[i] = __ldg(H + a * N + i);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                st.q[i] += h[i] * xr;
+#pragma unroll
+                for (int j = i; j < N; ++j) st.Q[sym<N>(i, j)] += h[i] * y[j];
+            }
+        }
     }
 }
 
