@@ -256,13 +256,22 @@ lqt_status lqt_solve_batched(const lqt_batch_item *items, int32_t count, void *w
  * T <= t_max (the first matching entry applies), capped at the batch's total
  * steps over the resident lane groups (at least 4), so that a batch too small
  * to fill the device with chunks of that length still spreads over every
- * resident group; `persistent` selects one
- * cooperative launch per state size that runs every tree level with grid
- * barriers (1, the default) or one launch per tree level (0).  count = 0
+ * resident group; `persistent` selects the launch mode: one launch per tree
+ * level (LQT_BATCH_PER_LEVEL), one cooperative launch per state size that
+ * runs every tree level with grid barriers (LQT_BATCH_PERSISTENT), or
+ * (LQT_BATCH_AUTO, the default) the cooperative launch when its grid (one lane
+ * group per chunk) needs at most half of the CTAs the device holds at once,
+ * per-level launches otherwise.  The persistent launch saves the launch gaps
+ * that dominate small batches; a larger cooperative launch waits until its
+ * whole grid is resident, which serialises it with the work of other
+ * streams, and with many waves of chunks the per-level kernels, whose blocks
+ * are sized per phase, keep more groups busy.  count = 0
  * clears the table.  The settings are process-wide; calls already launched
- * are not affected.  Returns LQT_EINVAL for more than 64 entries or a
- * non-positive n or chunk length.  The Python binding applies the table that
- * paper_2104_03186_gb300/tune.py measured on this GPU model. */
+ * are not affected.  Returns LQT_EINVAL for more than 64 entries, a
+ * non-positive n or chunk length, or another launch mode.  The Python binding
+ * applies the table that paper_2104_03186_gb300/tune.py measured on this GPU
+ * model. */
+enum { LQT_BATCH_PER_LEVEL = 0, LQT_BATCH_PERSISTENT = 1, LQT_BATCH_AUTO = 2 };
 typedef struct {
     int32_t n;
     int32_t chunk_steps;

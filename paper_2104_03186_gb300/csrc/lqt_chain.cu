@@ -17,9 +17,19 @@ namespace {
 // smallest chunk the planner makes, in steps
 constexpr long long kMinChunk = 4;
 
-// Batches of the lane sizes: one persistent launch (default) or one launch
-// per tree level (lqt_batch_set_tuning).
-std::atomic<bool> g_batch_persistent{true};
+// Batches of the lane sizes: one launch per tree level, one persistent
+// launch, or (the default) the persistent launch where its grid needs at most
+// half of the CTAs the device holds at once, per-level launches otherwise
+// (lqt_batch_set_tuning).  Measured on one GB300 (time-varying random
+// problems, p = n, chunk lengths as planned): the persistent launch took
+// 5-20% off single problems and batches of 16 at n = 8, 16, 32 and
+// T = 128..2048, and lost where its chunks were many waves of the device's
+// groups (n = 32, 16 problems of T = 2048 in 4-step chunks: 7.5 against
+// 6.1 ms; the 4096-problem benchmark batch: 47.3 against 45.8 ms).  A server
+// running batches on several streams at once lost twice its latency at
+// 20 000 requests/s when every batch took a cooperative launch: a launch whose
+// grid covers the device waits for the other streams' kernels to leave.
+std::atomic<int> g_batch_mode{LQT_BATCH_AUTO};
 
 // Tuned chunk lengths of batches (lqt_batch_set_tuning): entry e applies to
 // problems of state size n = e.n with T <= e.t_max (the first such entry).
@@ -216,7 +226,9 @@ lqt_status chain_batch_solve(const lqt_batch_item* items, const int* idx, int co
     const lqt_status st = batch_geometry(*v, items, idx, count, &probs);
     if (st != LQT_OK) return st;
     ChainCall call{probs.data(), count, false, false, false, false, ws, ws_bytes, status};
-    call.persistent = g_batch_persistent.load();
+    const int mode = g_batch_mode.load();
+    call.persistent = mode != LQT_BATCH_PER_LEVEL;
+    call.persistent_if_small = mode == LQT_BATCH_AUTO;
     return v->run(call, s, nullptr);
 }
 
@@ -278,12 +290,13 @@ extern "C" lqt_status lqt_batch_set_tuning(const lqt_batch_tune_entry* entries, 
                                            int32_t persistent) {
     using namespace lqt;
     if (count < 0 || count > kMaxTune || (count > 0 && !entries)) return LQT_EINVAL;
+    if (persistent < LQT_BATCH_PER_LEVEL || persistent > LQT_BATCH_AUTO) return LQT_EINVAL;
     for (int i = 0; i < count; ++i)
         if (entries[i].n < 1 || entries[i].t_max < 0 || entries[i].chunk_steps < 1)
             return LQT_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (int i = 0; i < count; ++i) g_tune[i] = entries[i];
     g_tune_count = count;
-    g_batch_persistent.store(persistent != 0);
+    g_batch_mode.store(persistent);
     return LQT_OK;
 }

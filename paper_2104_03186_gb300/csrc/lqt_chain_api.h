@@ -36,6 +36,9 @@ struct ChainCall {
     // one persistent cooperative launch instead of one launch per tree level
     // (no refinement, Method 1 only)
     bool persistent = false;
+    // ... but only when its grid needs at most half of the CTAs the device
+    // holds at once; larger launches take the per-level path
+    bool persistent_if_small = false;
 };
 
 struct ChainVariant {

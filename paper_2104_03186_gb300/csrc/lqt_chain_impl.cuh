@@ -159,8 +159,13 @@ struct Launcher {
     // the per-level launches
     static constexpr bool kPersistFits = (long long)NG_PERSIST * PERSIST_B <= 227 * 1024;
 
+    // only_if_small: launch nothing and return LQT_EUNSUPPORTED when the grid
+    // would need more than half of the co-resident CTAs.  A cooperative launch
+    // waits until its whole grid is resident, so a grid that covers the device
+    // serialises it with the work of other streams (a server's concurrent
+    // batches), where per-level kernels run beside them.
     static lqt_status run_persistent(const Args<R, RT>& a, const long long* active, int levels,
-                                     GridBarrier* bar, cudaStream_t s) {
+                                     GridBarrier* bar, cudaStream_t s, bool only_if_small) {
         if constexpr (!kPersistFits) {
             return LQT_EUNSUPPORTED;
         } else {
@@ -178,6 +183,7 @@ struct Launcher {
         if (per_sm < 1) return LQT_ECUDA;
         long long grid = (long long)per_sm * sms;
         const long long need = (a.C + NG_PERSIST - 1) / NG_PERSIST;
+        if (only_if_small && 2 * need > grid) return LQT_EUNSUPPORTED;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;
         LevelPlan lp;
@@ -611,11 +617,16 @@ struct Launcher {
         a.refine_add = 0;
         if (kPersistFits && call.persistent && !refine && !method2 && !call.sequential) {
             // one cooperative launch for the whole pass (batches)
-            const lqt_status st = run_persistent(
-                a, active.data(), levels, reinterpret_cast<GridBarrier*>(base + L.bar), s);
-            prof_end(prof, s);
-            if (st != LQT_OK) return st;
-            return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+            const lqt_status st =
+                run_persistent(a, active.data(), levels,
+                               reinterpret_cast<GridBarrier*>(base + L.bar), s,
+                               call.persistent_if_small);
+            if (st != LQT_EUNSUPPORTED || !call.persistent_if_small) {
+                prof_end(prof, s);
+                if (st != LQT_OK) return st;
+                return cudaGetLastError() == cudaSuccess ? LQT_OK : LQT_ECUDA;
+            }
+            // too large for the automatic choice: the per-level launches below
         }
         pass(a, active.data(), levels, call.sequential, 0, false, s, prof, E2, Pref);
         if (newton) {

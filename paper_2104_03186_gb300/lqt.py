@@ -163,13 +163,24 @@ def lqt_set_single_tile_chunk(max_chunk_steps: int) -> int:
 TUNED_PLANS = os.path.join(_PKG, "tuned_batch_plans.json")
 
 
-def lqt_batch_set_tuning(entries, persistent: bool = True) -> None:
+LQT_BATCH_PER_LEVEL, LQT_BATCH_PERSISTENT, LQT_BATCH_AUTO = 0, 1, 2
+BATCH_MODES = {"per_level": LQT_BATCH_PER_LEVEL, "persistent": LQT_BATCH_PERSISTENT,
+               "auto": LQT_BATCH_AUTO}
+
+
+def lqt_batch_set_tuning(entries, mode="auto") -> None:
     """Set the chunk-length table and the launch mode of lqt_solve_batched for
-    the lane-group sizes: entries are (n, t_max, chunk_steps) triples."""
+    the lane-group sizes: entries are (n, t_max, chunk_steps) triples; mode is
+    "per_level", "persistent" or "auto" (True / False: persistent /
+    per_level)."""
+    if isinstance(mode, bool):
+        code = LQT_BATCH_PERSISTENT if mode else LQT_BATCH_PER_LEVEL
+    else:
+        code = BATCH_MODES[mode]
     arr = (lqt_batch_tune_entry * max(len(entries), 1))()
     for i, (n, t_max, b) in enumerate(entries):
         arr[i].n, arr[i].t_max, arr[i].chunk_steps = int(n), int(t_max), int(b)
-    st = _lib.lqt_batch_set_tuning(arr, len(entries), 1 if persistent else 0)
+    st = _lib.lqt_batch_set_tuning(arr, len(entries), code)
     if st != LQT_OK:
         raise LQTError(st, "lqt_batch_set_tuning")
 
@@ -182,8 +193,12 @@ def apply_tuned_plans(path: str = TUNED_PLANS) -> bool:
         return False
     with open(path) as f:
         plan = json.load(f)
+    if "launch_mode" in plan:
+        mode = plan["launch_mode"]
+    else:  # a plan that only says whether the persistent launch won
+        mode = bool(plan.get("persistent", True))
     lqt_batch_set_tuning([(e["n"], e["t_max"], e["chunk_steps"]) for e in plan["entries"]],
-                         bool(plan.get("persistent", True)))
+                         mode)
     return True
 
 

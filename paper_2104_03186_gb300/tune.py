@@ -8,16 +8,20 @@ levels; long chunks the reverse, and which wins depends on how full the GPU
 is.  The tuner times lqt_solve_batched on this GPU on a synthetic batch shaped
 like the benchmark's ragged batch (diagonal tracking, m = n / 2), choosing the
 chunk length of each (n, T-bucket) in turn with the others fixed, then times
-the two launch modes (one persistent launch per size, or one launch per tree
-level) with that table and keeps the faster.  The library applies a tuned
+the three launch modes (one launch per tree level, one persistent launch per
+size, or the library's automatic choice between them by the number of chunk
+waves) with that table on the whole batch and on a small batch of the size a
+server forms, and keeps the mode that is fastest on the small batch among
+those within 1% of the best on the whole batch.  The library applies a tuned
 length only up to the batch's total steps over the resident lane groups, so
 the small batches of a server keep their short chunks.
 
-    python -m paper_2104_03186_gb300.tune [--out FILE] [--problems K]
+    python -m paper_2104_03186_gb300.tune [--out FILE] [--problems K] [--modes-only]
 
 writes the table as JSON (default: tuned_batch_plans.json beside this file),
-which the Python binding applies when it loads the library.  The selection
-and file logic below needs no GPU.
+which the Python binding applies when it loads the library; --modes-only keeps
+the committed chunk lengths and re-times the launch modes alone.  The
+selection and file logic below needs no GPU.
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ from typing import Dict, List, Sequence, Tuple
 import numpy as np
 
 SIZES = (8, 16)
+MODES = ("per_level", "persistent", "auto")  # lqt_batch_set_tuning's launch modes
+SMALL_BATCH = 16  # problems in the small batch the launch modes are also timed on
 BUCKETS = ((64, 512), (513, 2048), (2049, 4096))  # T ranges (inclusive)
 CANDIDATES = (8, 16, 32, 64, 128, 256)
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_batch_plans.json")
@@ -47,6 +53,23 @@ def choose(timings: Dict[Tuple[int, int], Dict[int, float]]) -> List[dict]:
         out.append({"n": int(n), "t_max": int(t_max), "chunk_steps": int(best),
                     "ms": {str(b): float(ms) for b, ms in sorted(per_b.items())}})
     return out
+
+
+def choose_mode(mix_ms: Dict[str, float], small_ms: Dict[str, float],
+                rel: float = 0.01) -> str:
+    """The launch mode to keep: among the modes within `rel` of the fastest on
+    the whole batch, the fastest on the small batch (ties in MODES order)."""
+    best = min(mix_ms.values())
+    near = [m for m in MODES if m in mix_ms and mix_ms[m] <= best * (1.0 + rel)]
+    return min(near, key=lambda m: (small_ms.get(m, float("inf")), MODES.index(m)))
+
+
+def plan_mode(plan: dict) -> str:
+    """A plan's launch mode; plans written before there were three modes say
+    only whether the persistent launch won."""
+    if "launch_mode" in plan:
+        return plan["launch_mode"]
+    return "persistent" if plan.get("persistent", True) else "per_level"
 
 
 def entries_for(plan: dict) -> List[Tuple[int, int, int]]:
@@ -69,6 +92,8 @@ def load(path: str = DEFAULT_OUT) -> dict:
     for e in plan["entries"]:
         if not (e["n"] >= 1 and e["t_max"] >= 0 and e["chunk_steps"] >= 1):
             raise ValueError("bad tuning entry %r" % (e,))
+    if plan_mode(plan) not in MODES:
+        raise ValueError("bad launch mode %r" % (plan_mode(plan),))
     return plan
 
 
@@ -121,14 +146,17 @@ def _workspace(Ps, outs):
 
 
 def measure(problems: int = 4096, reps: int = 3, sizes: Sequence[int] = SIZES,
-            buckets=BUCKETS, candidates: Sequence[int] = CANDIDATES, seed: int = 11) -> dict:
+            buckets=BUCKETS, candidates: Sequence[int] = CANDIDATES, seed: int = 11,
+            fixed_entries: Sequence[Tuple[int, int, int]] = ()) -> dict:
     """Tune on this GPU and return the plan.  The best chunk length of a
     bucket depends on what else the batch holds (a batch that fills the GPU
     favours longer chunks than a small one), so every candidate is timed on
     the whole mixed batch (the benchmark's distribution, another draw: n
     uniform in {4, 8, 16}, T uniform in [64, 4096]): one pass of coordinate descent over
-    the (n, T-bucket) entries from the untuned chunk length (64), then the two
-    launch modes with the resulting table."""
+    the (n, T-bucket) entries from the untuned chunk length (64), then the
+    launch modes with the resulting table, on the whole batch and on its first
+    SMALL_BATCH problems.  fixed_entries: keep these (n, t_max, chunk_steps)
+    and time the launch modes alone."""
     import torch
 
     from . import inputs, lqt
@@ -149,30 +177,38 @@ def measure(problems: int = 4096, reps: int = 3, sizes: Sequence[int] = SIZES,
     del mix
     table = {(n, t_hi): 64 for n in sizes for (_, t_hi) in buckets}
 
-    def run(tab, persistent=False):
-        lqt.lqt_batch_set_tuning([(n, t, b) for (n, t), b in sorted(tab.items())], persistent)
+    def run(tab, mode="per_level", Ps=Ps, outs=outs):
+        lqt.lqt_batch_set_tuning([(n, t, b) for (n, t), b in sorted(tab.items())], mode)
         ws = _workspace(Ps, outs)
         ms = _time_batch(Ps, outs, ws, reps)
         del ws
         return ms
 
-    base_ms = run(table)
-    timings: Dict[Tuple[int, int], Dict[int, float]] = {}
-    for key in sorted(table):
-        per_b = {}
-        for b in candidates:
-            if b > key[1]:
-                continue
-            trial = dict(table)
-            trial[key] = b
-            per_b[b] = run(trial)
-        timings[key] = per_b
-        table[key] = min(per_b.items(), key=lambda kv: (kv[1], -kv[0]))[0]
-    entries = choose(timings)
-    modes = {"per_level": run(table, False), "persistent": run(table, True)}
-    persistent = modes["persistent"] <= modes["per_level"]
-    lqt.lqt_batch_set_tuning([(n, t, b) for (n, t), b in sorted(table.items())], persistent)
-    return {"entries": entries, "persistent": persistent, "mix_ms": modes,
+    if fixed_entries:
+        table = {(n, t): b for n, t, b in fixed_entries}
+        base_ms, entries = None, [{"n": n, "t_max": t, "chunk_steps": b}
+                                  for n, t, b in fixed_entries]
+    else:
+        base_ms = run(table)
+        timings: Dict[Tuple[int, int], Dict[int, float]] = {}
+        for key in sorted(table):
+            per_b = {}
+            for b in candidates:
+                if b > key[1]:
+                    continue
+                trial = dict(table)
+                trial[key] = b
+                per_b[b] = run(trial)
+            timings[key] = per_b
+            table[key] = min(per_b.items(), key=lambda kv: (kv[1], -kv[0]))[0]
+        entries = choose(timings)
+    mix_ms = {m: run(table, m) for m in MODES}
+    small = slice(0, min(SMALL_BATCH, len(Ps)))
+    small_ms = {m: run(table, m, Ps[small], outs[small]) for m in MODES}
+    mode = choose_mode(mix_ms, small_ms)
+    lqt.lqt_batch_set_tuning([(n, t, b) for (n, t), b in sorted(table.items())], mode)
+    return {"entries": entries, "launch_mode": mode, "mix_ms": mix_ms,
+            "small_batch_ms": small_ms, "small_batch": SMALL_BATCH,
             "untuned_ms": base_ms, "gpu": torch.cuda.get_device_name(0),
             "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
             "problems": problems, "candidates": list(candidates),
@@ -184,12 +220,20 @@ def main(argv=None) -> int:
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--problems", type=int, default=4096)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--modes-only", action="store_true",
+                    help="keep the committed chunk lengths, time the launch modes")
     args = ap.parse_args(argv)
-    plan = measure(args.problems, args.reps)
+    old = load(args.out) if args.modes_only else None
+    plan = measure(args.problems, args.reps,
+                   fixed_entries=entries_for(old) if old else ())
+    if old:
+        # the chunk-length timings of the full tuning run stay with their entries
+        plan["entries"], plan["untuned_ms"] = old["entries"], old.get("untuned_ms")
+        plan["candidates"], plan["buckets"] = old["candidates"], old["buckets"]
     save(plan, args.out)
-    print(json.dumps({"out": args.out, "persistent": plan["persistent"],
+    print(json.dumps({"out": args.out, "launch_mode": plan["launch_mode"],
                       "entries": [(e["n"], e["t_max"], e["chunk_steps"]) for e in plan["entries"]],
-                      "mix_ms": plan["mix_ms"]}))
+                      "mix_ms": plan["mix_ms"], "small_batch_ms": plan["small_batch_ms"]}))
     return 0
 
 

@@ -200,3 +200,21 @@ def test_single_tile_setting_round_trip(lib):
     old = lib.lqt_set_single_tile_chunk(5)
     assert lib.lqt_set_single_tile_chunk(old) == 5
     assert so.lqt_set_single_tile_chunk(old, None) == lib.LQT_OK
+
+
+def test_batch_launch_modes(lib):
+    """lqt_batch_set_tuning needs no device: the three launch modes are
+    accepted, any other value is rejected; the committed plan is restored."""
+    so = lib.library()
+    entry = (lib.lqt_batch_tune_entry * 1)()
+    entry[0].n, entry[0].t_max, entry[0].chunk_steps = 8, 512, 16
+    try:
+        for mode in (lib.LQT_BATCH_PER_LEVEL, lib.LQT_BATCH_PERSISTENT, lib.LQT_BATCH_AUTO):
+            assert so.lqt_batch_set_tuning(entry, 1, mode) == lib.LQT_OK
+        for bad in (-1, 3, 7):
+            assert so.lqt_batch_set_tuning(entry, 1, bad) == lib.LQT_EINVAL
+        for name in ("per_level", "persistent", "auto", True, False):
+            lib.lqt_batch_set_tuning([(8, 512, 16)], name)
+    finally:
+        lib.lqt_batch_set_tuning([], "auto")
+        lib.apply_tuned_plans()

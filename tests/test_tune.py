@@ -43,3 +43,25 @@ def test_committed_plan_if_present_is_valid():
     plan = tune.load(tune.DEFAULT_OUT)
     assert {e["n"] for e in plan["entries"]} <= {8, 16, 32}
     assert all(e["chunk_steps"] in plan["candidates"] for e in plan["entries"])
+
+
+def test_choose_mode_prefers_the_small_batch_among_the_near_fastest():
+    # auto within 1% of the best on the whole batch and fastest on the small one
+    assert tune.choose_mode({"per_level": 45.8, "persistent": 47.3, "auto": 46.1},
+                            {"per_level": 0.50, "persistent": 0.42, "auto": 0.42}) == "auto"
+    # persistent is fastest on the small batch but too slow on the whole batch
+    assert tune.choose_mode({"per_level": 45.8, "persistent": 47.3, "auto": 47.0},
+                            {"per_level": 0.50, "persistent": 0.40, "auto": 0.41}) == "per_level"
+    # ties go in MODES order
+    assert tune.choose_mode({"per_level": 1.0, "persistent": 1.0, "auto": 1.0},
+                            {"per_level": 2.0, "persistent": 2.0, "auto": 2.0}) == "per_level"
+
+
+def test_plan_mode_reads_old_and_new_plans(tmp_path):
+    assert tune.plan_mode({"entries": [], "launch_mode": "auto"}) == "auto"
+    assert tune.plan_mode({"entries": [], "persistent": False}) == "per_level"
+    assert tune.plan_mode({"entries": [], "persistent": True}) == "persistent"
+    path = tmp_path / "bad_mode.json"
+    path.write_text(json.dumps({"entries": [], "launch_mode": "sometimes"}))
+    with pytest.raises(ValueError):
+        tune.load(str(path))
