@@ -969,7 +969,7 @@ def torch_empty_bytes(nbytes):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_bwd_down launch
 # (first pass, vehicle T = 1e6) from an ncu capture of the current kernel;
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_BWD_DOWN = 112.2e6
+TRAFFIC_BWD_DOWN = 112.59e6
 
 
 def main(argv=None):
