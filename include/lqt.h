@@ -236,8 +236,12 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
  *          aligned; its first bytes hold the status word read by
  *          lqt_workspace_status().  The size depends on the problems' n and T.
  * No refinement is applied (problems whose controls cancel, see lqt_options,
- * should use lqt_solve).  Asynchronous on `stream`; returns LQT_EINVAL,
- * LQT_EUNSUPPORTED, LQT_ENOMEM or LQT_ECUDA on argument or launch errors. */
+ * should use lqt_solve).  Asynchronous on `stream`: the descriptors built from
+ * `items` reach the workspace as kernel parameters, so the call never waits
+ * for the stream, and it may be captured in a CUDA graph (the graph keeps the
+ * descriptors; replays solve the same problems, reading whatever their input
+ * buffers hold then).  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
+ * LQT_ECUDA on argument or launch errors. */
 typedef struct {
     lqt_problem problem;
     lqt_solution solution;

@@ -12,6 +12,7 @@
 #include "lqt.h"
 #include "lqt_batch_launch.cuh"
 #include "lqt_chain_api.h"
+#include "lqt_upload.cuh"
 
 namespace lqt {
 namespace {
@@ -170,9 +171,10 @@ extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t cou
         return LQT_ECUDA;
     if (count == 0) return LQT_OK;
     if (!descs.empty()) {
-        // pageable source: the runtime stages the copy before the call returns
-        if (cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(BatchDesc),
-                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+        // through kernel parameters (lqt_upload.cuh): a pageable copy would
+        // first wait for the stream, and could not be captured in a graph
+        if (param_upload(d_desc, descs.data(), descs.size() * sizeof(BatchDesc), s) !=
+            cudaSuccess)
             return LQT_ECUDA;
         for (int v = 0; v < kNumBatchVariants; ++v) {
             const int c = offset[v + 1] - offset[v];

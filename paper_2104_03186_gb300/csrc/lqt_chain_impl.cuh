@@ -14,6 +14,7 @@
 #include "lqt_persist.cuh"
 #include "lqt_warm.cuh"
 #include "lqt_launch.cuh"
+#include "lqt_upload.cuh"
 
 namespace lqt {
 namespace chain {
@@ -450,8 +451,8 @@ struct Launcher {
         Item<R>* d1 = reinterpret_cast<Item<R>*>(base + L.items1);
         if (count == 1) {
             k_set_items<R><<<1, 1, 0, s>>>(d1, it1[0], nullptr, it1[0]);
-        } else if (cudaMemcpyAsync(d1, it1.data(), it1.size() * sizeof(Item<R>),
-                                   cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        } else if (param_upload(d1, it1.data(), it1.size() * sizeof(Item<R>), s) !=
+                   cudaSuccess) {
             return LQT_ECUDA;
         }
         Args<R, RT> a;
@@ -593,14 +594,15 @@ struct Launcher {
                                            refine ? it2[0] : it1[0]);
             if (newton) k_set_items<R><<<1, 1, 0, s>>>(d3, it3[0], nullptr, it3[0]);
         } else {
-            if (cudaMemcpyAsync(d1, it1.data(), it1.size() * sizeof(Item<R>),
-                                cudaMemcpyHostToDevice, s) != cudaSuccess)
+            // descriptors through kernel parameters (lqt_upload.cuh): no stream
+            // synchronisation, capturable in a graph
+            if (param_upload(d1, it1.data(), it1.size() * sizeof(Item<R>), s) != cudaSuccess)
                 return LQT_ECUDA;
-            if (refine && cudaMemcpyAsync(d2, it2.data(), it2.size() * sizeof(Item<R>),
-                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+            if (refine && param_upload(d2, it2.data(), it2.size() * sizeof(Item<R>), s) !=
+                              cudaSuccess)
                 return LQT_ECUDA;
-            if (newton && cudaMemcpyAsync(d3, it3.data(), it3.size() * sizeof(Item<R>),
-                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+            if (newton && param_upload(d3, it3.data(), it3.size() * sizeof(Item<R>), s) !=
+                              cudaSuccess)
                 return LQT_ECUDA;
         }
         if (newton) k_consts<R, N, M><<<1, N, 0, s>>>(cL, cU, cH);
