@@ -125,14 +125,15 @@ __global__ void k_set_items(Item<R>* d1, Item<R> a, Item<R>* d2, Item<R> b) {
 }
 
 // ---- shared-memory sizes per group (elements of the kernel's arithmetic type)
-template <int N, int M>
+template <int N, int M, typename R>
 struct FoldSmem {  // P | step (E, L, U) | scratch overlapping the step's Y
     static constexpr int P = 0;
     static constexpr int SB = LElem<N>::SIZE;
     static constexpr int SCR_OFF = SB + StepLayout<N, M>::Y;
-    static constexpr int SCR = fold_scratch<N, M>() > StepLayout<N, M>::SIZE - StepLayout<N, M>::Y
-                                   ? fold_scratch<N, M>()
-                                   : StepLayout<N, M>::SIZE - StepLayout<N, M>::Y;
+    static constexpr int SCR =
+        fold_scratch<N, M, R>() > StepLayout<N, M>::SIZE - StepLayout<N, M>::Y
+            ? fold_scratch<N, M, R>()
+            : StepLayout<N, M>::SIZE - StepLayout<N, M>::Y;
     static constexpr int SIZE = SCR_OFF + SCR;
 };
 
@@ -210,7 +211,7 @@ __device__ __forceinline__ bool h_is_identity(const DescT<R>& D, const Group<N>&
 template <typename R, typename RT, int N, int M, int NG>
 __device__ __forceinline__ void b_cfold(const Args<R, RT>& a, long long c,
                                         unsigned char* smem_raw, int gi) {
-    using S = FoldSmem<N, M>;
+    using S = FoldSmem<N, M, R>;
     using E = LElem<N>;
     R* sh = reinterpret_cast<R*>(smem_raw);
     const Group<N> g;

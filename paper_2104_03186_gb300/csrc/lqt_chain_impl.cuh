@@ -64,7 +64,7 @@ static cudaError_t chain_allow_smem(Kernel k, std::atomic<bool>* done, size_t by
 
 template <typename R, typename RT, int N, int M>
 struct Launcher {
-    static constexpr int FOLD_B = gstride<N>(FoldSmem<N, M>::SIZE) * (int)sizeof(R);
+    static constexpr int FOLD_B = gstride<N>(FoldSmem<N, M, R>::SIZE) * (int)sizeof(R);
     static constexpr int REFOLD_B = gstride<N>(RefoldSmem<N, M>::SIZE) * (int)sizeof(R);
     static constexpr int UP_B = gstride<N>(UpSmem<N>::SIZE) * (int)sizeof(RT);
     static constexpr int DOWN_B = gstride<N>(DownSmem<N>::SIZE) * (int)sizeof(RT);

@@ -87,7 +87,9 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
     const RI* X = D.X + k * D.sX;
     const RI* rk = D.r ? D.r + k * D.sr : nullptr;
     const int lp = p | 1;
-    const bool staged = COST && stage && p * lp + p * LD + p <= stage_cap;
+    // staged X_k, H_k (none when H_k = I) and r_k
+    const int hs = h_identity ? 0 : p * LD;
+    const bool staged = COST && stage && p * lp + hs + p <= stage_cap;
     if constexpr (sizeof(R) == sizeof(RI)) {
         // every copy of the step in flight at once (cp.async, consecutive lanes
         // on consecutive elements), one wait
@@ -102,7 +104,7 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         if (staged) {
             R* Xs = stage;
             R* Hs = Xs + p * lp;
-            R* rs = Hs + p * LD;
+            R* rs = Hs + hs;
             for (int a = 0; a < p; ++a)
                 for (int b = r; b < p; b += N) cp_async<sizeof(R)>(Xs + a * lp + b, X + a * p + b);
             if (!h_identity)
@@ -125,7 +127,7 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         if (staged) {
             R* Xs = stage;
             R* Hs = Xs + p * lp;
-            R* rs = Hs + p * LD;
+            R* rs = Hs + hs;
             for (int a = 0; a < p; ++a)
                 for (int b = r; b < p; b += N) Xs[a * lp + b] = R(__ldg(X + a * p + b));
             if (!h_identity)
@@ -141,7 +143,7 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         // H = I (p = N): J = X, eta = X r
         g.sync();
         const R* Xs = stage;
-        const R* rs = stage + p * lp + p * LD;
+        const R* rs = stage + p * lp;  // no staged H
         R t = R(0);
 #pragma unroll 8
         for (int j = 0; j < N; ++j) {
@@ -466,12 +468,19 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
     return ok;
 }
 
-// Scratch of fold_step (elements of R).
-template <int N, int M>
+// Scratch of fold_step (elements of R).  The tensor-core form (32-lane FP32
+// groups) keeps every product in shared memory; the lane form keeps in
+// registers the rows that only their own lane reads again (A2 F, A2 L,
+// F^T J2 F), and symmetrises C and J in place, which keeps a lane group's
+// shared memory, and so the groups per SM, in check.
+template <int N, int M, typename R = float>
 constexpr int fold_scratch() {
-    return 2 * N * lds(N) /*JF | A2F, later the staged C and J*/ + N * lds(N) /*F^T J2 F*/ +
-           2 * N * lds(M) /*P2, JL*/ + M * lds(N) /*Z*/ + 2 * N /*w, A2 c*/ + M * lds(M) /*G*/ +
-           M * lds(2 * N + 1) /*rhs*/;
+    if (use_tensor_cores<R, N>())
+        return 2 * N * lds(N) /*JF | A2F, later the staged C and J*/ + N * lds(N) /*F^T J2 F*/ +
+               2 * N * lds(M) /*P2, JL*/ + M * lds(N) /*Z*/ + 2 * N /*w, A2 c*/ +
+               M * lds(M) /*G*/ + M * lds(2 * N + 1) /*rhs*/;
+    return N * lds(N) /*JF*/ + N * lds(M) /*JL*/ + M * lds(N) /*Z*/ + 2 * N /*w, A2 c*/ +
+           M * lds(M) /*G*/ + M * lds(2 * N + 1) /*rhs*/;
 }
 
 // fold_step (below) for a 32-lane FP32 group: the same formulas and scratch
@@ -594,16 +603,12 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
     const R* L = sb + SLay::L;
     const R* U = sb + SLay::U;
     R* JF = scr;              // N x N
-    R* A2F = JF + N * LD;     // N x N
-    R* FJF = A2F + N * LD;    // N x N
-    R* P2 = FJF + N * LD;     // N x M
-    R* JL = P2 + N * LM;      // N x M
+    R* JL = JF + N * LD;      // N x M
     R* Z = JL + N * LM;       // M x N
     R* w = Z + M * LD;        // N
     R* A2c = w + N;           // N
     R* G = A2c + N;           // M x M
     R* rhs = G + M * LM;      // M x NR
-    R* O = JF;                // staged C and J (2 N x N), after JF and A2F are consumed
     const int r = g.lr;
     // 1. JF = J2 F, JL = J2 L, w = eta2 - J2 c (row r of J2)
     {
@@ -628,9 +633,10 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         for (int a = 0; a < M; ++a) JL[r * LM + a] = jl[a];
         w[r] = t;
     }
-    //    A2F = A2 F, P2 = A2 L (also into the right sides, transposed), A2 c
+    //    row r of A2 F and P2 = A2 L kept in registers (P2 also into the right
+    //    sides, transposed), A2 c
+    R af[N], pl[M];
     {
-        R af[N], pl[M];
         R t = R(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) af[j] = R(0);
@@ -645,17 +651,13 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
             for (int a = 0; a < M; ++a) pl[a] += ak * L[k * LM + a];
             t += ak * c[k];
         }
-#pragma unroll
-        for (int j = 0; j < N; ++j) A2F[r * LD + j] = af[j];
 #pragma unroll 4
-        for (int a = 0; a < M; ++a) {
-            P2[r * LM + a] = pl[a];
-            rhs[a * LR + N + 1 + r] = pl[a];
-        }
+        for (int a = 0; a < M; ++a) rhs[a * LR + N + 1 + r] = pl[a];
         A2c[r] = t;
     }
     g.sync();
-    // 2. G = U + L^T JL, Z = L^T JF, L^T w (lanes a < M); F^T JF (all lanes)
+    // 2. G = U + L^T JL, Z = L^T JF, L^T w (lanes a < M); row r of F^T JF in
+    //    registers (all lanes)
     if (r < M) {
         R gg[M], zz[N];
         R t = R(0);
@@ -681,60 +683,50 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
         }
         rhs[r * LR + N] = t;
     }
+    R fjf[N];
     {
-        R acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = R(0);
+        for (int j = 0; j < N; ++j) fjf[j] = R(0);
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
             const R fk = F[k * LD + r];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += fk * JF[k * LD + j];
+            for (int j = 0; j < N; ++j) fjf[j] += fk * JF[k * LD + j];
         }
-#pragma unroll
-        for (int j = 0; j < N; ++j) FJF[r * LD + j] = acc[j];
     }
     g.sync();
     // 3. [Zt | om | Pt] = G^{-1} [Z | L^T w | P2^T]
     const bool ok = solve_spd<N, M, NR>(G, LM, rhs, LR, g);
-    // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (in place: A2 is not read again)
+    // 4. A = A2F - P2 Zt, b = A2 c + P2 om + b2 (in place: row r of A2 is read
+    //    by lane r alone)
     {
-        R aa[N];
         R t = A2c[r] + P[E::OB + r];
-#pragma unroll
-        for (int j = 0; j < N; ++j) aa[j] = A2F[r * LD + j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
-            const R pa = P2[r * LM + a];
+            const R pa = pl[a];
 #pragma unroll
-            for (int j = 0; j < N; ++j) aa[j] -= pa * rhs[a * LR + j];
+            for (int j = 0; j < N; ++j) af[j] -= pa * rhs[a * LR + j];
             t += pa * rhs[a * LR + N];
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) P[E::OA + r * LD + j] = aa[j];
+        for (int j = 0; j < N; ++j) P[E::OA + r * LD + j] = af[j];
         P[E::OB + r] = t;
     }
-    g.sync();
-    //    C = C2 + P2 Pt and J = J1 + F^T J2 F - Z^T Zt staged in O;
-    //    eta = eta1 + F^T w - Z^T om in place
+    //    C = C2 + P2 Pt and J = J1 + F^T J2 F - Z^T Zt, row r of each in place
+    //    (row r of C2 is read by lane r alone); eta = eta1 + F^T w - Z^T om
     {
-        R cc[N];
+        R cc[N], jj[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) cc[j] = P[E::OC + r * LD + j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
-            const R pa = P2[r * LM + a];
+            const R pa = pl[a];
 #pragma unroll
             for (int j = 0; j < N; ++j) cc[j] += pa * rhs[a * LR + N + 1 + j];
         }
-#pragma unroll
-        for (int j = 0; j < N; ++j) O[r * LD + j] = cc[j];
-    }
-    {
-        R jj[N];
         R t = e1[E::OE + r];
 #pragma unroll
-        for (int j = 0; j < N; ++j) jj[j] = e1[E::OJ + r * LD + j] + FJF[r * LD + j];
+        for (int j = 0; j < N; ++j) jj[j] = e1[E::OJ + r * LD + j] + fjf[j];
 #pragma unroll 4
         for (int a = 0; a < M; ++a) {
             const R za = Z[a * LD + r];
@@ -745,14 +737,27 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
 #pragma unroll 4
         for (int k = 0; k < N; ++k) t += F[k * LD + r] * w[k];
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[N * LD + r * LD + j] = jj[j];
+        for (int j = 0; j < N; ++j) {
+            P[E::OC + r * LD + j] = cc[j];
+            P[E::OJ + r * LD + j] = jj[j];
+        }
         P[E::OE + r] = t;
     }
     g.sync();
+    // symmetrise C and J: row r becomes the mean of row r and column r
+    {
+        R cs[N], js[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        P[E::OC + r * LD + j] = R(0.5) * (O[r * LD + j] + O[j * LD + r]);
-        P[E::OJ + r * LD + j] = R(0.5) * (O[N * LD + r * LD + j] + O[N * LD + j * LD + r]);
+        for (int j = 0; j < N; ++j) {
+            cs[j] = R(0.5) * (P[E::OC + r * LD + j] + P[E::OC + j * LD + r]);
+            js[j] = R(0.5) * (P[E::OJ + r * LD + j] + P[E::OJ + j * LD + r]);
+        }
+        g.sync();
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            P[E::OC + r * LD + j] = cs[j];
+            P[E::OJ + r * LD + j] = js[j];
+        }
     }
     g.sync();
     return ok;

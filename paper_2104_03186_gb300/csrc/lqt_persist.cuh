@@ -146,7 +146,7 @@ __device__ __forceinline__ void b_cterm_group(const Args<R, RT>& a, int q, RT* Y
 // the up-sweep, which takes two blocks.
 template <typename R, typename RT, int N, int M>
 constexpr int persist_group_bytes() {
-    constexpr int sizes[] = {gstride<N>(FoldSmem<N, M>::SIZE) * (int)sizeof(R),
+    constexpr int sizes[] = {gstride<N>(FoldSmem<N, M, R>::SIZE) * (int)sizeof(R),
                              gstride<N>(RefoldSmem<N, M>::SIZE) * (int)sizeof(R),
                              gstride<N>(RollSmem<N, M>::SIZE) * (int)sizeof(R),
                              gstride<N>(DownSmem<N>::SIZE) * (int)sizeof(RT),

@@ -99,12 +99,12 @@ static void group_checks(int size) {
 int main() {
     for (int W : {128, 256, 512}) tree_checks<float>(W);
     for (int W : {128, 256}) tree_checks<double>(W);  // FP64 tiles are at most 256 wide
-    group_checks<4>(FoldSmem<4, 2>::SIZE);
+    group_checks<4>(FoldSmem<4, 2, float>::SIZE);
     group_checks<4>(UpSmem<4>::SIZE);
-    group_checks<8>(FoldSmem<8, 4>::SIZE);
+    group_checks<8>(FoldSmem<8, 4, float>::SIZE);
     group_checks<8>(RefoldSmem<8, 4>::SIZE);
     group_checks<8>(UpSmem<8>::SIZE);
-    group_checks<16>(FoldSmem<16, 8>::SIZE);
+    group_checks<16>(FoldSmem<16, 8, float>::SIZE);
     group_checks<16>(RefoldSmem<16, 8>::SIZE);
     group_checks<16>(DownSmem<16>::SIZE);
     // the replayed top scan fits one CTA for every FP32 size (the headline path)
