@@ -238,10 +238,12 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
     g.sync();
 }
 
-// Scratch of gains / riccati (elements of R), excluding the caller's Kd and Ft.
+// Scratch of gains / riccati (elements of R), excluding the caller's Kd and Ft:
+// S L, S F, G, v - S c, and for 32-lane groups (the tensor-core form in FP32)
+// a block O that stages the new S and v; the lane form symmetrises S in place.
 template <int N, int M>
 constexpr int riccati_scratch() {
-    return N * lds(M) + N * lds(N) + M * lds(M) + N + N * lds(N) + N;
+    return N * lds(M) + N * lds(N) + M * lds(M) + N + (N == 32 ? N * lds(N) + N : 0);
 }
 
 // Row stride of Kd = [K | d] (M x (N + 1)).
@@ -411,7 +413,6 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
     R* SF = SL + N * LM;     // N x N  (later S Ft)
     R* G = SF + N * LD;      // M x M
     R* ev = G + M * LM;      // N
-    R* O = ev + N;           // N x N + N
     const int r = g.lr;
     const bool ok = gains<R, N, M>(val, sb, Kd, scr, g);
     // Ft = F - L K ; ct = c + L d ; S Ft = SF - SL K
@@ -456,14 +457,22 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
             for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * LD + j];
             t += Ft[A::OF + k * LD + r] * ev[k];
         }
+        // nothing in this phase reads val: the new rows go there directly
 #pragma unroll
-        for (int j = 0; j < N; ++j) O[r * LD + j] = acc[j];
-        O[N * LD + r] = t;
+        for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = acc[j];
+        val[V::OV + r] = t;
     }
     g.sync();
+    // symmetrise S: row r becomes the mean of row r and column r
+    {
+        R ss[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = R(0.5) * (O[r * LD + j] + O[j * LD + r]);
-    val[V::OV + r] = O[N * LD + r];
+        for (int j = 0; j < N; ++j)
+            ss[j] = R(0.5) * (val[V::OS + r * LD + j] + val[V::OS + j * LD + r]);
+        g.sync();
+#pragma unroll
+        for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = ss[j];
+    }
     g.sync();
     return ok;
 }
