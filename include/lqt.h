@@ -240,7 +240,11 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
  * `items` reach the workspace as kernel parameters, so the call never waits
  * for the stream, and it may be captured in a CUDA graph (the graph keeps the
  * descriptors; replays solve the same problems, reading whatever their input
- * buffers hold then).  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
+ * buffers hold then).  A batch of at least 2^20 steps in all runs its lane
+ * sizes side by side on streams of the calling host thread (created on its
+ * first such call on a device and kept until the process exits), forked from
+ * and joined back to `stream` with events; the outputs are those of one
+ * stream, bit for bit.  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
  * LQT_ECUDA on argument or launch errors. */
 typedef struct {
     lqt_problem problem;

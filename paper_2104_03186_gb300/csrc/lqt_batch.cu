@@ -128,17 +128,65 @@ static size_t head_bytes(int32_t count) {
     return up(256) + up(64 * sizeof(int)) + up((size_t)count * sizeof(BatchDesc));
 }
 
+// The lane sizes of a batch with at least kForkSteps steps run side by side,
+// each on an auxiliary stream forked from the caller's stream after the
+// workspace head is cleared and joined back to it (events; a CUDA graph
+// captures them as parallel branches), beside the n = 4 launch on the caller's
+// stream: the sizes are independent, and one size's tree levels and last wave
+// leave most SMs idle.  Smaller batches (a server's) keep the caller's stream:
+// the auxiliary streams belong to the host thread, so a thread's small batches
+// on several streams would otherwise queue on them.
+constexpr long long kForkSteps = 1LL << 20;
+constexpr int kMaxAux = 4;
+
+struct BatchAux {
+    cudaStream_t s[kMaxAux] = {};
+    cudaEvent_t fork = nullptr, join[kMaxAux] = {};
+    bool ready = false;
+};
+
+// This host thread's auxiliary streams and events on the current device,
+// created on its first large batch there and kept until the process exits;
+// nullptr if they cannot be created (the batch then runs on one stream).
+static BatchAux* batch_aux() {
+    thread_local BatchAux aux[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    BatchAux& a = aux[dev];
+    if (!a.ready) {
+        if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess)
+            return nullptr;
+        for (int i = 0; i < kMaxAux; ++i)
+            if (cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess)
+                return nullptr;
+        a.ready = true;
+    }
+    return &a;
+}
+
+// Workspace bytes of each lane group (its own region, so that the groups may
+// run at once); false if a group is invalid.
+static bool lane_bytes_of(const lqt_batch_item* items, const std::vector<std::vector<int>>& groups,
+                          std::vector<size_t>* bytes) {
+    bytes->clear();
+    for (const std::vector<int>& g : groups) {
+        size_t b = 0;
+        if (chain_batch_workspace(items, g.data(), (int)g.size(), &b) != LQT_OK) return false;
+        bytes->push_back(up(b));
+    }
+    return true;
+}
+
 extern "C" size_t lqt_batch_workspace_bytes(const lqt_batch_item* items, int32_t count) {
     if (count < 0 || (count > 0 && !items)) return 0;
-    size_t lane = 0;
     for (int i = 0; i < count; ++i)
         if (check_item(items[i]) != LQT_OK) return 0;
-    for (const std::vector<int>& g : lane_groups(items, count)) {
-        size_t b = 0;
-        if (chain_batch_workspace(items, g.data(), (int)g.size(), &b) != LQT_OK) return 0;
-        lane = std::max(lane, b);  // the groups run one after another on the stream
-    }
-    return head_bytes(count) + up(lane);
+    std::vector<size_t> bytes;
+    if (!lane_bytes_of(items, lane_groups(items, count), &bytes)) return 0;
+    size_t lane = 0;
+    for (size_t b : bytes) lane += b;
+    return head_bytes(count) + lane;
 }
 
 extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t count,
@@ -170,6 +218,17 @@ extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t cou
     if (cudaMemsetAsync(base, 0, up(256) + up(64 * sizeof(int)), s) != cudaSuccess)
         return LQT_ECUDA;
     if (count == 0) return LQT_OK;
+    const std::vector<std::vector<int>> groups = lane_groups(items, count);
+    std::vector<size_t> group_bytes;
+    if (!lane_bytes_of(items, groups, &group_bytes)) return LQT_EINVAL;
+    long long total_steps = 0;
+    for (int i = 0; i < count; ++i) total_steps += items[i].problem.T;
+    const int lanes_running = (int)groups.size();
+    BatchAux* aux = nullptr;
+    if (lanes_running >= 1 && lanes_running <= kMaxAux &&
+        lanes_running + (descs.empty() ? 0 : 1) >= 2 && total_steps >= kForkSteps)
+        aux = batch_aux();
+    if (aux && cudaEventRecord(aux->fork, s) != cudaSuccess) return LQT_ECUDA;
     if (!descs.empty()) {
         // through kernel parameters (lqt_upload.cuh): a pageable copy would
         // first wait for the stream, and could not be captured in a graph
@@ -185,11 +244,20 @@ extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t cou
         }
     }
     char* lane_ws = base + head_bytes(count);
-    const size_t lane_bytes = workspace_bytes - head_bytes(count);
-    for (const std::vector<int>& g : lane_groups(items, count)) {
-        const lqt_status st =
-            chain_batch_solve(items, g.data(), (int)g.size(), lane_ws, lane_bytes, status, s);
+    for (size_t i = 0; i < groups.size(); ++i) {
+        const std::vector<int>& g = groups[i];
+        cudaStream_t gs = s;
+        if (aux) {
+            gs = aux->s[i];
+            if (cudaStreamWaitEvent(gs, aux->fork, 0) != cudaSuccess) return LQT_ECUDA;
+        }
+        const lqt_status st = chain_batch_solve(items, g.data(), (int)g.size(), lane_ws,
+                                                group_bytes[i], status, gs);
         if (st != LQT_OK) return st;
+        if (aux && (cudaEventRecord(aux->join[i], gs) != cudaSuccess ||
+                    cudaStreamWaitEvent(s, aux->join[i], 0) != cudaSuccess))
+            return LQT_ECUDA;
+        lane_ws += group_bytes[i];
     }
     return LQT_OK;
 }
