@@ -312,6 +312,24 @@ def solve_graph(launch):
     return g.replay, g
 
 
+def graph_timed(launch, reps, flush, stream):
+    """Device times (ms) of one call, launch(s), captured once in a CUDA graph and
+    replayed (the headline's method; the host launch work stays out of the
+    timed region), or of eager calls on `stream` if the call cannot be
+    captured.  The call must have run once before.  Returns (times, how)."""
+    import torch
+
+    try:
+        replay, graph = solve_graph(launch)
+    except Exception:  # not capturable: time the eager calls instead
+        torch.cuda.synchronize()
+        return _time_solves(lambda: launch(stream), reps, flush, stream), "eager calls"
+    replay()
+    times = _time_solves(replay, reps, flush, stream)
+    del graph
+    return times, "CUDA graph replay"
+
+
 def _time_solves(fn, reps, flush, stream):
     """Per-call device time (ms) with CUDA events on `stream`, L2 flushed before each."""
     import torch
@@ -818,12 +836,13 @@ def run_precision(args, stream, flush, fp32_peak=None, fp64_peak=None):
         if name.endswith("method2"):  # trajectory by Method 2 (forward element scan)
             refine = lqt.options(refine, lqt.LQT_METHOD_2)
         ws = lqt.workspace_for(P, opts=refine)
-        call = (lambda: lqt.lqt_riccati_sequential(P, o, ws, stream, refine)) if seq else \
-            (lambda: lqt.lqt_solve(P, o, ws, stream, refine))
+        launch = (lambda s: lqt.lqt_riccati_sequential(P, o, ws, s, refine)) if seq else \
+            (lambda s: lqt.lqt_solve(P, o, ws, s, refine))
+        call = lambda: launch(stream)  # noqa: E731
         call()
-        st = lqt.lqt_workspace_status(ws, stream)
         reps = 1 if seq else 5
-        times = _time_solves(call, reps, flush, stream)
+        times, how = graph_timed(launch, reps, flush, stream)
+        st = lqt.lqt_workspace_status(ws, stream)
         lqt.lqt_profile_enable(1)
         call()
         kms = {}
@@ -833,7 +852,7 @@ def run_precision(args, stream, flush, fp32_peak=None, fp64_peak=None):
         got = {k: v.double().cpu().numpy() for k, v in o.items()}
         errs = accuracy.errors(got, ref)
         med = float(np.median(times))
-        e = {"status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3),
+        e = {"status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3), "timing": how,
              "error_vs_fp64_oracle": errs, "plan": lqt.lqt_plan(P, refine) if not seq else None,
              "kernels_ms": kms}
         if not seq and not refine:
@@ -870,17 +889,17 @@ def run_cross(args, stream, flush):
     C = lqt.Cross.from_inputs(ct, dtype=np.float32)
     o = P.allocate_outputs()
     ws = torch_empty_bytes(lqt.lqt_cross_workspace_bytes(P, C, opts))
-    call = lambda: lqt.lqt_solve_cross(P, C, o, ws, stream, opts)  # noqa: E731
+    launch = lambda s: lqt.lqt_solve_cross(P, C, o, ws, s, opts)  # noqa: E731
     for _ in range(3):
-        call()
+        launch(stream)
+    times, how = graph_timed(launch, 10, flush, stream)
     st = lqt.lqt_workspace_status(ws, stream)
-    times = _time_solves(call, 10, flush, stream)
     got = {k: v.double().cpu().numpy() for k, v in o.items()}
     ws_plain = lqt.workspace_for(P, opts=opts)
-    plain = lambda: lqt.lqt_solve(P, o, ws_plain, stream, opts)  # noqa: E731
+    plain = lambda s: lqt.lqt_solve(P, o, ws_plain, s, opts)  # noqa: E731
     for _ in range(3):
-        plain()
-    tplain = _time_solves(plain, 10, flush, stream)
+        plain(stream)
+    tplain, _ = graph_timed(plain, 10, flush, stream)
     t0 = time.perf_counter()
     ref = ocross.riccati_cross(prob, ct.M, ct.s)
     oracle_s = time.perf_counter() - t0
@@ -888,7 +907,7 @@ def run_cross(args, stream, flush):
     med, medp = float(np.median(times)), float(np.median(tplain))
     return {"workload": "vehicle T=%d with time-varying cross weights M_k (2x2) and control "
                         "offsets s_k; inputs rounded to FP32; refinement ON" % T,
-            "status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3),
+            "status": int(st), "ms": med, "steps_per_s": T / (med * 1e-3), "timing": how,
             "plain_solve_ms": medp, "transform_overhead_ms": med - medp,
             "error_vs_fp64_oracle": errs, "oracle_s": oracle_s}
 
@@ -915,15 +934,15 @@ def run_nonlinear(args, stream, flush):
     for name, (opts, seq) in forms.items():
         nl = lqt.nonlinear(iters, 0.1, seq)
         ws = torch_empty_bytes(lqt.lqt_nonlinear_workspace_bytes(P, nl, opts))
-        call = lambda: lqt.lqt_solve_nonlinear(P, nl, o, ws, stream, opts)  # noqa: E731
-        call()
+        launch = lambda s: lqt.lqt_solve_nonlinear(P, nl, o, ws, s, opts)  # noqa: E731
+        launch(stream)
+        times, how = graph_timed(launch, 1 if seq else 5, flush, stream)
         st = lqt.lqt_workspace_status(ws, stream)
-        times = _time_solves(call, 1 if seq else 5, flush, stream)
         got = {k: v.double().cpu().numpy() for k, v in o.items()}
         errs = accuracy.errors(got, ref)
         med = float(np.median(times))
         res[name] = {"status": int(st), "ms": med, "steps_per_s": iters * T / (med * 1e-3),
-                     "error_vs_fp64_oracle": errs}
+                     "timing": how, "error_vs_fp64_oracle": errs}
         del ws
     for name in ("method1", "method2"):
         res[name]["speedup_vs_sequential"] = res["sequential"]["ms"] / res[name]["ms"]
@@ -952,14 +971,14 @@ def run_condensed(args, stream, flush, prob, ref, plain_ms):
         for B in (1, 2, 4, 8, 16):
             o = P.allocate_outputs()
             ws = torch_empty_bytes(lqt.lqt_condensed_workspace_bytes(P, B, opts))
-            call = lambda: lqt.lqt_solve_condensed(P, B, o, ws, stream, opts)  # noqa: E731
+            launch = lambda s: lqt.lqt_solve_condensed(P, B, o, ws, s, opts)  # noqa: E731
             for _ in range(3):
-                call()
+                launch(stream)
+            times, how = graph_timed(launch, 10, flush, stream)
             st = lqt.lqt_workspace_status(ws, stream)
-            times = _time_solves(call, 10, flush, stream)
             got = {k: v.double().cpu().numpy() for k, v in o.items()}
             med = float(np.median(times))
-            out.append({"T": T, "B": B, "status": int(st), "ms": med,
+            out.append({"T": T, "B": B, "status": int(st), "ms": med, "timing": how,
                         "steps_per_s": T / (med * 1e-3),
                         "error_vs_fp64_oracle": accuracy.errors(got, rf)})
             del o, ws, got
