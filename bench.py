@@ -518,12 +518,14 @@ def run_ours(args):
             torch.cuda.synchronize()
             par, graph = solve_graph(lambda s: lqt.lqt_solve(Pq, o2, w2, s, opts))
             seq = lambda: lqt.lqt_riccati_sequential(Pq, o2, w2, stream, opts)  # noqa: E731
-            for _ in range(3):
+            # 20 warm-ups; 200 timed replays below T = 1e6, 20 at 1e6
+            for _ in range(20):
                 par()
-            tp = _time_solves(par, 20 if Ts < T_HEADLINE else 10, flush, stream)
+            tp = _time_solves(par, 200 if Ts < T_HEADLINE else 20, flush, stream)
             seq()
             ts = _time_solves(seq, 3 if Ts <= 100_000 else 1, flush, stream)
-            sweep.append({"T": Ts, "parallel_steps_per_s": Ts / (np.median(tp) * 1e-3),
+            sweep.append({"T": Ts, "reps": len(tp),
+                          "parallel_steps_per_s": Ts / (np.median(tp) * 1e-3),
                           "parallel_p50_ms": percentile(tp, 50), "parallel_p99_ms": percentile(tp, 99),
                           "sequential_steps_per_s": Ts / (np.median(ts) * 1e-3),
                           "sequential_ms": float(np.median(ts)),
@@ -1007,7 +1009,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-sweep", action="store_true", help="skip the T sweep")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
