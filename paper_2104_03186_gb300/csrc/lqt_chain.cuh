@@ -403,21 +403,34 @@ __device__ __forceinline__ void b_crefold(const Args<R, RT>& a, long long c,
             for (int i = 0; i < M; ++i) D.K[k * M * N + i * N + r] = Kd[i * kd_ld<N>() + r];
         }
         if (r < M) D.u[k * M + r] = Kd[r * kd_ld<N>() + N];  // feedforward d_k, replaced in the rollout
-        // chunk map after adding step k: Phi <- Phi Ft, gamma <- gamma + Phi ct
-        R pn[N];
+        // chunk map after adding step k: Phi <- Phi Ft (two rows per lane pair
+        // over half the columns each, as in row_mul_pair), gamma <- gamma + Phi ct
+        constexpr int H = N / 2;
+        const int r0 = r & ~1, c0 = (r & 1) * H;
+        R p0[H], p1[H];
         R gm = Phi[A::OC + r];
 #pragma unroll
-        for (int j = 0; j < N; ++j) pn[j] = R(0);
+        for (int j = 0; j < H; ++j) {
+            p0[j] = R(0);
+            p1[j] = R(0);
+        }
 #pragma unroll 4
         for (int l = 0; l < N; ++l) {
-            const R pl = Phi[A::OF + r * A::LD + l];
+            const R x0 = Phi[A::OF + r0 * A::LD + l], x1 = Phi[A::OF + (r0 + 1) * A::LD + l];
 #pragma unroll
-            for (int j = 0; j < N; ++j) pn[j] += pl * Ft[A::OF + l * A::LD + j];
-            gm += pl * Ft[A::OC + l];
+            for (int j = 0; j < H; ++j) {
+                const R y = Ft[A::OF + l * A::LD + c0 + j];
+                p0[j] += x0 * y;
+                p1[j] += x1 * y;
+            }
+            gm += (r & 1 ? x1 : x0) * Ft[A::OC + l];
         }
         g.sync();
 #pragma unroll
-        for (int j = 0; j < N; ++j) Phi[A::OF + r * A::LD + j] = pn[j];
+        for (int j = 0; j < H; ++j) {
+            Phi[A::OF + r0 * A::LD + c0 + j] = p0[j];
+            Phi[A::OF + (r0 + 1) * A::LD + c0 + j] = p1[j];
+        }
         Phi[A::OC + r] = gm;
         g.sync();
     }

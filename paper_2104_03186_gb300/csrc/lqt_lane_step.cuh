@@ -354,8 +354,8 @@ __device__ bool gains(const R* val, const R* sb, R* Kd, R* scr, const Group<N>& 
     R* G = SF + N * LD;      // M x M
     R* ev = G + M * LM;      // N
     const int r = g.lr;
-    row_mul<N, N, M>(SL, LM, S, LD, L, LM, r);
-    row_mul<N, N, N>(SF, LD, S, LD, F, LD, r);
+    row_mul_pair<N, N, M>(SL, LM, S, LD, L, LM, r);
+    row_mul_pair<N, N, N>(SF, LD, S, LD, F, LD, r);
     {
         R t = v[r];
 #pragma unroll
@@ -444,22 +444,35 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
         Ft[A::OC + r] = ct;
     }
     g.sync();
-    // S <- F^T (S Ft) + Q ; v <- Ft^T (v - S c) + q
+    // S <- F^T (S Ft) + Q, two rows per lane pair over half the columns each
+    // (as in row_mul_pair); v <- Ft^T (v - S c) + q, row r per lane
     {
-        R acc[N];
+        constexpr int H = N / 2;
+        const int r0 = r & ~1, c0 = (r & 1) * H;
+        R a0[H], a1[H];
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = Q[r * LD + j];
+        for (int c = 0; c < H; ++c) {
+            a0[c] = Q[r0 * LD + c0 + c];
+            a1[c] = Q[(r0 + 1) * LD + c0 + c];
+        }
         R t = q[r];
 #pragma unroll 4
         for (int k = 0; k < N; ++k) {
-            const R fk = F[k * LD + r];
+            const R f0 = F[k * LD + r0], f1 = F[k * LD + r0 + 1];
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] += fk * SF[k * LD + j];
+            for (int c = 0; c < H; ++c) {
+                const R y = SF[k * LD + c0 + c];
+                a0[c] += f0 * y;
+                a1[c] += f1 * y;
+            }
             t += Ft[A::OF + k * LD + r] * ev[k];
         }
         // nothing in this phase reads val: the new rows go there directly
 #pragma unroll
-        for (int j = 0; j < N; ++j) val[V::OS + r * LD + j] = acc[j];
+        for (int c = 0; c < H; ++c) {
+            val[V::OS + r0 * LD + c0 + c] = a0[c];
+            val[V::OS + (r0 + 1) * LD + c0 + c] = a1[c];
+        }
         val[V::OV + r] = t;
     }
     g.sync();

@@ -67,6 +67,42 @@ __device__ __forceinline__ void row_mul(R* out, int ldo, const R* X, int ldx, co
     for (int c = 0; c < C; ++c) out[lr * ldo + c] = acc[c];
 }
 
+// The same product with two output rows per lane pair: lanes 2i and 2i + 1
+// both compute rows 2i and 2i + 1, lane 2i the first C/2 columns and lane
+// 2i + 1 the rest.  Each step of k reads two left entries and C/2 right
+// entries per lane (row_mul: one and C), so the right factor's broadcast
+// reads per FMA halve; each output element is summed in the same order as in
+// row_mul.  ROWS and C even; lanes lr < ROWS take part.
+template <int ROWS, int K, int C, typename R>
+__device__ __forceinline__ void row_mul_pair(R* out, int ldo, const R* X, int ldx, const R* Y,
+                                             int ldy, int lr) {
+    static_assert(ROWS % 2 == 0 && C % 2 == 0, "pairs of rows, halves of columns");
+    constexpr int H = C / 2;
+    if (lr >= ROWS) return;
+    const int r0 = lr & ~1, c0 = (lr & 1) * H;
+    R a0[H], a1[H];
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+        a0[c] = R(0);
+        a1[c] = R(0);
+    }
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const R x0 = X[r0 * ldx + k], x1 = X[(r0 + 1) * ldx + k];
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+            const R y = Y[k * ldy + c0 + c];
+            a0[c] += x0 * y;
+            a1[c] += x1 * y;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+        out[r0 * ldo + c0 + c] = a0[c];
+        out[(r0 + 1) * ldo + c0 + c] = a1[c];
+    }
+}
+
 // out[lr][0..C) = X[0..K)[lr]^T-row, i.e. (X^T Y)[lr], X stored K x ROWS
 template <int ROWS, int K, int C, typename R>
 __device__ __forceinline__ void row_mul_tn(R* out, int ldo, const R* X, int ldx, const R* Y,
