@@ -233,7 +233,7 @@ __device__ void load_step(const DescT<RI>& D, long long k, R* sb, R* scr, const 
         }
         g.sync();
         ok &= solve_spd<N, M, N>(U, LM, Z, LD, g);
-        row_mul<N, M, N>(e + E::OC, LD, L, LM, Z, LD, r);
+        row_mul_pair<N, M, N>(e + E::OC, LD, L, LM, Z, LD, r);
     }
     g.sync();
 }

@@ -49,30 +49,13 @@ constexpr int gstride(int size) {
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
-// out[lr][0..C) = X[lr][0..K) * Y (K x C), for rows lr < ROWS
-template <int ROWS, int K, int C, typename R>
-__device__ __forceinline__ void row_mul(R* out, int ldo, const R* X, int ldx, const R* Y, int ldy,
-                                        int lr) {
-    if (lr >= ROWS) return;
-    R acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = R(0);
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const R xk = X[lr * ldx + k];
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] += xk * Y[k * ldy + c];
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) out[lr * ldo + c] = acc[c];
-}
-
-// The same product with two output rows per lane pair: lanes 2i and 2i + 1
-// both compute rows 2i and 2i + 1, lane 2i the first C/2 columns and lane
-// 2i + 1 the rest.  Each step of k reads two left entries and C/2 right
-// entries per lane (row_mul: one and C), so the right factor's broadcast
-// reads per FMA halve; each output element is summed in the same order as in
-// row_mul.  ROWS and C even; lanes lr < ROWS take part.
+// out = X Y for rows 0..ROWS of X (ROWS x K) and Y (K x C), with two output
+// rows per lane pair: lanes 2i and 2i + 1 both compute rows 2i and 2i + 1,
+// lane 2i the first C/2 columns and lane 2i + 1 the rest.  Each step of k
+// reads two left entries and C/2 right entries per lane, where a lane that
+// owned one whole row would read one and C: the right factor's broadcast
+// reads per FMA halve.  Each output element is one accumulator summed over k
+// in order.  ROWS and C even; lanes lr < ROWS take part.
 template <int ROWS, int K, int C, typename R>
 __device__ __forceinline__ void row_mul_pair(R* out, int ldo, const R* X, int ldx, const R* Y,
                                              int ldy, int lr) {
@@ -316,7 +299,7 @@ __device__ bool combine(const R* e1, const R* e2, R* out, R* scr, const Group<LG
         for (int k = 0; k < N; ++k) t += Bx[k * LB + r] * w[k];
         O[E::OE + r] = t;
     }
-    row_mul<N, N, N>(T, LD, e2 + E::OJ, LD, Bx, LB, r);
+    row_mul_pair<N, N, N>(T, LD, e2 + E::OJ, LD, Bx, LB, r);
     g.sync();
     // J = A1^T JX + J1
     {
@@ -420,7 +403,7 @@ __device__ bool value_apply(const R* P, R* val, R* scr, const Group<LG>& g) {
     g.sync();
     const bool ok = solve_gj<LG, N, N>(Mx, LD, X, LD, g);
     // T = S X1 ; v' = X1^T e + eta
-    row_mul<N, N, N>(T, LD, val + V::OS, LD, X, LD, r);
+    row_mul_pair<N, N, N>(T, LD, val + V::OS, LD, X, LD, r);
     {
         R t = P[E::OE + r];
 #pragma unroll
