@@ -632,27 +632,14 @@ __device__ bool fold_step(R* P, const R* sb, R* scr, const Group<N>& g) {
     R* G = A2c + N;           // M x M
     R* rhs = G + M * LM;      // M x NR
     const int r = g.lr;
-    // 1. JF = J2 F, JL = J2 L, w = eta2 - J2 c (row r of J2)
+    // 1. JF = J2 F and JL = J2 L (lane pairs, into shared memory);
+    //    w = eta2 - J2 c (row r of J2)
+    row_mul_pair<N, N, N>(JF, LD, P + E::OJ, LD, F, LD, r);
+    row_mul_pair<N, N, M>(JL, LM, P + E::OJ, LD, L, LM, r);
     {
-        R jf[N], jl[M];
         R t = P[E::OE + r];
-#pragma unroll
-        for (int j = 0; j < N; ++j) jf[j] = R(0);
-#pragma unroll
-        for (int a = 0; a < M; ++a) jl[a] = R(0);
 #pragma unroll 4
-        for (int k = 0; k < N; ++k) {
-            const R jk = P[E::OJ + r * LD + k];
-#pragma unroll
-            for (int j = 0; j < N; ++j) jf[j] += jk * F[k * LD + j];
-#pragma unroll
-            for (int a = 0; a < M; ++a) jl[a] += jk * L[k * LM + a];
-            t -= jk * c[k];
-        }
-#pragma unroll
-        for (int j = 0; j < N; ++j) JF[r * LD + j] = jf[j];
-#pragma unroll
-        for (int a = 0; a < M; ++a) JL[r * LM + a] = jl[a];
+        for (int k = 0; k < N; ++k) t -= P[E::OJ + r * LD + k] * c[k];
         w[r] = t;
     }
     //    row r of A2 F and P2 = A2 L kept in registers (P2 also into the right
