@@ -426,10 +426,12 @@ __device__ __forceinline__ void b_crefold(const Args<R, RT>& a, long long c,
             gm += (r & 1 ? x1 : x0) * Ft[A::OC + l];
         }
         g.sync();
+        const bool odd = r & 1;  // stores in reverse order, as in row_mul_pair
 #pragma unroll
         for (int j = 0; j < H; ++j) {
-            Phi[A::OF + r0 * A::LD + c0 + j] = p0[j];
-            Phi[A::OF + (r0 + 1) * A::LD + c0 + j] = p1[j];
+            const int jj = odd ? H - 1 - j : j;
+            Phi[A::OF + r0 * A::LD + c0 + jj] = odd ? p0[H - 1 - j] : p0[j];
+            Phi[A::OF + (r0 + 1) * A::LD + c0 + jj] = odd ? p1[H - 1 - j] : p1[j];
         }
         Phi[A::OC + r] = gm;
         g.sync();

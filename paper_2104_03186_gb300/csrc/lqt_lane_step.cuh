@@ -467,11 +467,14 @@ __device__ bool riccati(R* val, const R* sb, R* Kd, R* Ft, R* scr, const Group<N
             }
             t += Ft[A::OF + k * LD + r] * ev[k];
         }
-        // nothing in this phase reads val: the new rows go there directly
+        // nothing in this phase reads val: the new rows go there directly (the
+        // odd lane in reverse order, as in row_mul_pair)
+        const bool odd = r & 1;
 #pragma unroll
         for (int c = 0; c < H; ++c) {
-            val[V::OS + r0 * LD + c0 + c] = a0[c];
-            val[V::OS + (r0 + 1) * LD + c0 + c] = a1[c];
+            const int cc = odd ? H - 1 - c : c;
+            val[V::OS + r0 * LD + c0 + cc] = odd ? a0[H - 1 - c] : a0[c];
+            val[V::OS + (r0 + 1) * LD + c0 + cc] = odd ? a1[H - 1 - c] : a1[c];
         }
         val[V::OV + r] = t;
     }

@@ -79,10 +79,15 @@ __device__ __forceinline__ void row_mul_pair(R* out, int ldo, const R* X, int ld
             a1[c] += x1 * y;
         }
     }
+    // the odd lane of a pair stores its half in reverse order: with odd row
+    // strides the two halves then fall on banks of opposite parity, so no two
+    // lanes of a warp store to one bank
+    const bool odd = lr & 1;
 #pragma unroll
     for (int c = 0; c < H; ++c) {
-        out[r0 * ldo + c0 + c] = a0[c];
-        out[(r0 + 1) * ldo + c0 + c] = a1[c];
+        const int cc = odd ? H - 1 - c : c;
+        out[r0 * ldo + c0 + cc] = odd ? a0[H - 1 - c] : a0[c];
+        out[(r0 + 1) * ldo + c0 + cc] = odd ? a1[H - 1 - c] : a1[c];
     }
 }
 
