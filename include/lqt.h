@@ -242,9 +242,9 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
  * descriptors; replays solve the same problems, reading whatever their input
  * buffers hold then).  A batch of at least 2^20 steps in all runs its lane
  * sizes side by side on streams of the calling host thread (created on its
- * first such call on a device and kept until the process exits), forked from
- * and joined back to `stream` with events; the outputs are those of one
- * stream, bit for bit.  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
+ * first such call on a device and kept until the process exits: make that
+ * first call before any stream capture), forked from and joined back to
+ * `stream` with events; the outputs are those of one stream, bit for bit.  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
  * LQT_ECUDA on argument or launch errors. */
 typedef struct {
     lqt_problem problem;

@@ -154,11 +154,14 @@ static BatchAux* batch_aux() {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     BatchAux& a = aux[dev];
     if (!a.ready) {
-        if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess)
+        // handles made by an earlier, failed attempt are kept and not made again
+        if (!a.fork && cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess)
             return nullptr;
         for (int i = 0; i < kMaxAux; ++i)
-            if (cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess)
+            if ((!a.s[i] && cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking) !=
+                                cudaSuccess) ||
+                (!a.join[i] &&
+                 cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess))
                 return nullptr;
         a.ready = true;
     }
