@@ -61,6 +61,10 @@ class Request:
     skoff: int = 0          # step of this request's S_0, K_0 in the owner's arrays
     reused: bool = False    # solved from the owner's S, K (lqt_solve_warm)
     holds: Optional[List[int]] = None  # requests whose outputs this one may read
+    m: int = 0              # control size of the request's model
+    nbytes: int = 0         # out_bytes(n, m, T)
+    xoff: int = 0           # element offset of x* in the request's outputs
+    out_ptr: int = 0        # device address of out
 
 
 class ModelPool:
@@ -147,6 +151,69 @@ def make_requests(count: int, rate: float, seed: int = 0, sizes=(4, 8, 16, 32),
     return reqs
 
 
+def pack_inputs(batch: List[Request], out: np.ndarray) -> np.ndarray:
+    """Pack the batch's references and cold initial states into `out` (the
+    host side of the batch's one host-to-device copy), per request r_0 .. r_T
+    then x_0 if the request is cold; returns each request's first element."""
+    parts = []
+    for q in batch:
+        parts.append(q.r.reshape(-1))
+        if q.warm_of < 0:
+            parts.append(q.x0)
+    sizes = np.fromiter((a.size for a in parts), np.int64, len(parts))
+    starts = np.zeros(len(parts) + 1, np.int64)
+    np.cumsum(sizes, out=starts[1:])
+    np.concatenate(parts, out=out[: starts[-1]])
+    nparts = np.fromiter((1 + (q.warm_of < 0) for q in batch), np.int64, len(batch))
+    first = np.zeros(len(batch), np.int64)
+    np.cumsum(nparts[:-1], out=first[1:])
+    return starts[first]
+
+
+class _Arena:
+    """Device blocks for request outputs, by size class.
+
+    A request's block is its element count rounded up to one of eight classes
+    per power of two (at most 12.5% more), taken from that class's free list
+    when one is there, else allocated.  A released block goes back to its
+    list.  torch.empty on the device costs about 10 us of host time per call
+    (a quarter of the serving loop's host time at 50 000 requests/s, under a
+    profiler); a list pop is a fraction of a microsecond.  The free lists are dropped whenever a new
+    block would take the blocks in use plus those cached over `budget`."""
+
+    def __init__(self, budget: int, device: str = "cuda"):
+        self.budget = budget
+        self.device = device
+        self.free: Dict[int, List[object]] = {}
+        self.cached = 0  # bytes in the free lists
+
+    @staticmethod
+    def size_class(nbytes: int) -> int:
+        """Elements of the block that holds `nbytes` bytes of float32."""
+        e = max(8, -(-nbytes // 4))
+        step = 1 << max(0, e.bit_length() - 4)
+        return -(-e // step) * step
+
+    def take(self, nbytes: int, in_use: int):
+        """A block for `nbytes` bytes: (tensor, bytes it holds)."""
+        import torch
+
+        cls = self.size_class(nbytes)
+        lst = self.free.get(cls)
+        if lst:
+            self.cached -= 4 * cls
+            return lst.pop(), 4 * cls
+        if self.cached and in_use + self.cached + 4 * cls > self.budget:
+            self.free.clear()
+            self.cached = 0
+        return torch.empty(cls, dtype=torch.float32, device=self.device), 4 * cls
+
+    def give(self, block):
+        """Return a block taken from take()."""
+        self.free.setdefault(block.numel(), []).append(block)
+        self.cached += 4 * block.numel()
+
+
 class _Slot:
     """One stream with its staging buffers, reused batch after batch: pinned
     host and device buffers for the packed references and initial states, a
@@ -192,6 +259,9 @@ class _Slot:
             setattr(self, name, torch.empty(size, dtype=torch.uint8, device="cuda"))
 
 
+_MODEL_FIELDS = ("F", "L", "U", "H", "X", "HT", "XT")
+
+
 class Server:
     def __init__(self, pool: ModelPool, memory_budget: int = 4 << 30, streams: int = 4,
                  max_batch: int = 1024, keep_results: bool = False, reuse_warm: bool = True):
@@ -205,46 +275,40 @@ class Server:
         self.budget = memory_budget
         self.slots = [_Slot() for _ in range(streams)]
         self.max_batch = max_batch
-        self.mem = 0
+        self.mem = 0          # bytes of the output blocks in use
         self.peak_mem = 0
         self.batches = 0
         self.launches = 0
+        self.arena = _Arena(memory_budget)
+        # per state size: m and the device addresses of the model's arrays
+        self.model_ptrs = {n: (pr.m, {f: dev[f].data_ptr() for f in _MODEL_FIELDS})
+                           for n, (pr, dev) in pool.models.items()}
 
     def _reused(self, req: Request) -> bool:
         """Solved from its owner's S and K (its own S and K regions unused)."""
         return req.reused
 
-    def _bytes(self, req: Request) -> int:
-        return out_bytes(req.n, self.pool.models[req.n][0].m, req.T)
-
-    def _x_offset(self, req: Request) -> int:
-        """Element offset of x in the request's own buffer."""
-        n, T = req.n, req.T
-        m = self.pool.models[n][0].m
-        return (T + 1) * n * n + (T + 1) * n + T * m * n
-
     def _alloc(self, req: Request):
-        import torch
-
-        nb = self._bytes(req)
-        req.out = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
-        self.mem += nb
+        req.out, held = self.arena.take(req.nbytes, self.mem)
+        req.out_ptr = req.out.data_ptr()
+        self.mem += held
         self.peak_mem = max(self.peak_mem, self.mem)
 
     def _release(self, req: Request):
         """Free a finished request's outputs once no warm request still needs them."""
         if req.out is not None and req.refs == 0 and not math.isnan(req.done):
-            self.mem -= self._bytes(req)
+            self.mem -= 4 * req.out.numel()
+            self.arena.give(req.out)
             req.out = None
 
     def _results(self, q: Request, byid) -> Dict[str, np.ndarray]:
         """Host copies of a completed request's S, v, K, x* (u* is q.u)."""
         n, T = q.n, q.T
         m = self.pool.models[n][0].m
-        res = unpack_outputs(q.out.cpu().numpy(), n, m, T)
+        res = unpack_outputs(q.out[: q.nbytes // 4].cpu().numpy(), n, m, T)
         if self._reused(q):
             own = byid[q.owner]
-            full = unpack_outputs(own.out.cpu().numpy(), n, m, own.T)
+            full = unpack_outputs(own.out[: own.nbytes // 4].cpu().numpy(), n, m, own.T)
             res["S"] = full["S"][q.skoff: q.skoff + T + 1].copy()
             res["K"] = full["K"][q.skoff: q.skoff + T].copy()
         return res
@@ -274,6 +338,9 @@ class Server:
         byid = {r.rid: r for r in reqs}
         for q in reqs:
             q.refs, q.reused, q.owner, q.skoff, q.holds = 0, False, q.rid, 0, []
+            q.m = self.model_ptrs[q.n][0]
+            q.nbytes = out_bytes(q.n, q.m, q.T)
+            q.xoff = (q.T + 1) * q.n * q.n + (q.T + 1) * q.n + q.T * q.m * q.n
         # warm requests keep the outputs they may read: the predecessor's x*_s
         # and, when reusing, S_k and K_k, which sit with the first ancestor that
         # was solved in full (up the chain of warm requests to a cold one)
@@ -305,7 +372,7 @@ class Server:
                     src.popleft()
                     parked.setdefault(q.warm_of, []).append(q)
                     continue
-                need = self._bytes(q)
+                need = 4 * _Arena.size_class(q.nbytes)
                 if self.mem + need > self.budget and (admitted or inflight):
                     blocked = True
                     break
@@ -324,10 +391,11 @@ class Server:
                     still.append(item)
                     continue
                 tdone = time.perf_counter() - t0
-                hu = slot.h_u_np
+                # one copy out of the stream's staging buffer per batch; each
+                # request's u* is a view of it
+                hu = slot.h_u_np[: uoff[-1]].copy()
                 for q, off in zip(batch, uoff):
-                    mt = q.T * self.pool.models[q.n][0].m
-                    q.u = hu[off: off + mt].reshape(q.T, -1).copy()
+                    q.u = hu[off: off + q.T * q.m].reshape(q.T, q.m)
                     q.done = tdone
                     if self.keep_results:
                         q.result = self._results(q, byid)
@@ -367,22 +435,15 @@ class Server:
     def _launch(self, batch: List[Request], slot: _Slot, byid):
         import torch
 
-        pool = self.pool
         k = len(batch)
-        # packed layout of the host-to-device copy: per request r_0..r_T then x_0 (cold)
-        in_sizes = [q.r.size + (q.n if q.warm_of < 0 else 0) for q in batch]
-        u_sizes = [q.T * pool.models[q.n][0].m for q in batch]
-        in_off = np.concatenate([[0], np.cumsum(in_sizes)]).astype(np.int64)
-        u_off = np.concatenate([[0], np.cumsum(u_sizes)]).astype(np.int64)
-        slot.ensure(int(in_off[-1]), int(u_off[-1]), k)
-        hv = slot.h_in_np
-        for q, a in zip(batch, in_off[:-1]):
-            a = int(a)
-            hv[a: a + q.r.size] = q.r.ravel()
-            if q.warm_of < 0:
-                hv[a + q.r.size: a + q.r.size + q.n] = q.x0
-        din = np.uint64(slot.d_in.data_ptr())
-        dup = np.uint64(slot.d_u.data_ptr())
+        u_sizes = np.fromiter((q.T * q.m for q in batch), np.int64, k)
+        u_off = np.zeros(k + 1, np.int64)
+        np.cumsum(u_sizes, out=u_off[1:])
+        n_in = sum(q.r.size + (q.n if q.warm_of < 0 else 0) for q in batch)
+        slot.ensure(n_in, int(u_off[-1]), k)
+        in_off = pack_inputs(batch, slot.h_in_np)
+        din = slot.d_in.data_ptr()
+        dup = slot.d_u.data_ptr()
         # A warm request is solved from its owner's S and K when its state size
         # has no request of the batch that needs a full solve anyway, and
         # n >= 8: the full solves of a size share their launches, so adding a
@@ -398,11 +459,11 @@ class Server:
                     q.owner, q.skoff = prior.owner, prior.skoff + q.shift
                 else:
                     q.owner, q.skoff = prior.rid, q.shift
-        cold = [i for i, q in enumerate(batch) if not self._reused(q)]
-        warm = [i for i, q in enumerate(batch) if self._reused(q)]
+        cold = [i for i, q in enumerate(batch) if not q.reused]
+        warm = [i for i, q in enumerate(batch) if q.reused]
         st = slot.stream
         with torch.cuda.stream(st):
-            slot.d_in[: int(in_off[-1])].copy_(slot.h_in[: int(in_off[-1])], non_blocking=True)
+            slot.d_in[:n_in].copy_(slot.h_in[:n_in], non_blocking=True)
             if warm:
                 # the warm solves run on the slot's second stream, concurrently
                 # with the cold ones, after the input copy; joined before u*
@@ -436,69 +497,59 @@ class Server:
         self.batches += 1
         ns = [q.n for q in batch]
         self.launches += len(set(ns[i] for i in cold)) + len(set(ns[i] for i in warm))
-        return (slot, ev, batch, [int(a) for a in u_off[:-1]])
+        return (slot, ev, batch, u_off.tolist())
 
-    def _items(self, it, reqs: List[Request], in_off, u_off, din, dup, byid):
+    def _items(self, it, reqs: List[Request], in_off, u_off, din: int, dup: int, byid):
         """Descriptors of `reqs` in the BATCH_ITEM array `it`, column by column:
         model windows from the pool, references and cold initial states from
-        the packed input copy, warm initial states from the predecessor's x*,
-        outputs in each request's buffer (S and K of a reused warm request in
-        its owner's), u* in the stream's staging buffer."""
-        pool = self.pool
+        the packed input copy (request i's r_0 at element in_off[i], its x_0
+        after r_T), warm initial states from the predecessor's x*, outputs in
+        each request's buffer (S and K of a reused warm request in its
+        owner's), u* in the stream's staging buffer at element u_off[i].
+        Addresses are computed as int64 (device addresses are below 2^63)."""
         k = len(reqs)
-        ns = np.fromiter((q.n for q in reqs), np.int64, k)
-        Ts = np.fromiter((q.T for q in reqs), np.int64, k)
-        offs = np.fromiter((q.offset for q in reqs), np.int64, k)
-        x0p = np.empty(k, np.uint64)
-        for i, q in enumerate(reqs):
-            if q.warm_of < 0:
-                x0p[i] = din + np.uint64(4 * (int(in_off[i]) + q.r.size))
-            else:
-                prior = byid[q.warm_of]
-                x0p[i] = np.uint64(prior.out.data_ptr() +
-                                   4 * (self._x_offset(prior) + q.shift * q.n))
-        ms = np.empty(k, np.int64)
-        base = {f: np.empty(k, np.uint64) for f in ("F", "L", "U", "H", "X", "HT", "XT")}
-        for n, (pr, dev) in pool.models.items():
+        i64 = np.int64
+        ns = np.fromiter((q.n for q in reqs), i64, k)
+        ms = np.fromiter((q.m for q in reqs), i64, k)
+        Ts = np.fromiter((q.T for q in reqs), i64, k)
+        offs = np.fromiter((q.offset for q in reqs), i64, k)
+        in_off = np.asarray(in_off, i64)
+        # x_0: after r_T in the packed copy (cold), else the predecessor's x*_s
+        cold = np.fromiter((q.warm_of < 0 for q in reqs), bool, k)
+        wx = np.fromiter((0 if q.warm_of < 0 else
+                          byid[q.warm_of].out_ptr + 4 * (byid[q.warm_of].xoff + q.shift * q.n)
+                          for q in reqs), i64, k)
+        rp = din + 4 * in_off
+        x0p = np.where(cold, rp + 4 * (Ts + 1) * ns, wx)
+        base = {f: np.empty(k, i64) for f in _MODEL_FIELDS}
+        for n, (m, ptrs) in self.model_ptrs.items():
             sel = ns == n
-            if not sel.any():
-                continue
-            ms[sel] = pr.m
-            for f in base:
-                base[f][sel] = dev[f].data_ptr()
+            if sel.any():
+                for f in base:
+                    base[f][sel] = ptrs[f]
         P, S = it["problem"], it["solution"]
         P["n"], P["m"], P["p"], P["pT"], P["T"], P["dtype"] = ns, ms, ns, ns, Ts, lqt.LQT_F32
-        n2 = (ns * ns).astype(np.uint64)
-        nm = (ns * ms).astype(np.uint64)
-        o = offs.astype(np.uint64)
-        P["F"]["ptr"], P["F"]["step_stride"] = base["F"] + o * n2 * np.uint64(4), ns * ns
-        P["L"]["ptr"], P["L"]["step_stride"] = base["L"] + o * nm * np.uint64(4), ns * ms
-        P["X"]["ptr"], P["X"]["step_stride"] = base["X"] + o * n2 * np.uint64(4), ns * ns
+        P["F"]["ptr"], P["F"]["step_stride"] = base["F"] + 4 * offs * ns * ns, ns * ns
+        P["L"]["ptr"], P["L"]["step_stride"] = base["L"] + 4 * offs * ns * ms, ns * ms
+        P["X"]["ptr"], P["X"]["step_stride"] = base["X"] + 4 * offs * ns * ns, ns * ns
         P["U"]["ptr"], P["U"]["step_stride"] = base["U"], 0
         P["H"]["ptr"], P["H"]["step_stride"] = base["H"], 0
         P["c"]["ptr"], P["c"]["step_stride"] = 0, 0
-        rp = din + np.asarray(in_off, np.int64).astype(np.uint64) * np.uint64(4)
         P["r"]["ptr"], P["r"]["step_stride"] = rp, ns
         P["HT"], P["XT"] = base["HT"], base["XT"]
-        P["rT"] = rp + Ts.astype(np.uint64) * ns.astype(np.uint64) * np.uint64(4)
+        P["rT"] = rp + 4 * Ts * ns
         P["x0"] = x0p
-        Tu, nu = Ts.astype(np.uint64), ns.astype(np.uint64)
-        for i, q in enumerate(reqs):
-            outp = np.uint64(q.out.data_ptr())
-            if self._reused(q):
-                own = byid[q.owner]
-                obase = np.uint64(own.out.data_ptr())
-                To = np.uint64(own.T)
-                S["S"][i] = obase + np.uint64(4 * q.skoff * q.n * q.n)
-                S["K"][i] = obase + np.uint64(4) * ((To + np.uint64(1)) * nu[i] * nu[i] +
-                                                    (To + np.uint64(1)) * nu[i]) + \
-                    np.uint64(4 * q.skoff * int(nm[i]))
-                S["v"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i] * nu[i]
-                S["x"][i] = outp + np.uint64(4 * self._x_offset(q))
-            else:
-                S["S"][i] = outp
-                S["v"][i] = outp + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i] * nu[i]
-                S["K"][i] = S["v"][i] + np.uint64(4) * (Tu[i] + np.uint64(1)) * nu[i]
-                S["x"][i] = S["K"][i] + np.uint64(4) * Tu[i] * nm[i]
-        S["u"] = dup + np.asarray(u_off, np.int64).astype(np.uint64) * np.uint64(4)
+        # outputs, packed S | v | K | x per request; S and K of a reused warm
+        # request are its owner's from step skoff on (owner = itself, skoff =
+        # 0, for every other request)
+        own = [byid[q.owner] for q in reqs]
+        optr = np.fromiter((o.out_ptr for o in own), i64, k)
+        To = np.fromiter((o.T for o in own), i64, k)
+        sk = np.fromiter((q.skoff for q in reqs), i64, k)
+        outp = np.fromiter((q.out_ptr for q in reqs), i64, k)
+        S["S"] = optr + 4 * sk * ns * ns
+        S["K"] = optr + 4 * ((To + 1) * ns * ns + (To + 1) * ns + sk * ns * ms)
+        S["v"] = outp + 4 * (Ts + 1) * ns * ns
+        S["x"] = outp + 4 * ((Ts + 1) * ns * ns + (Ts + 1) * ns + Ts * ns * ms)
+        S["u"] = dup + 4 * np.asarray(u_off, i64)
         return it

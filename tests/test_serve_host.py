@@ -85,3 +85,127 @@ def test_output_packing(n, m, T):
     # the four parts tile the buffer in order, with nothing left over
     parts = np.concatenate([out[k].ravel() for k in ("S", "v", "K", "x")])
     assert np.array_equal(parts, buf)
+
+
+def test_pack_inputs_layout(stream):
+    batch = stream[:300]
+    n_in = sum(q.r.size + (q.n if q.warm_of < 0 else 0) for q in batch)
+    out = np.full(n_in + 7, np.nan, np.float32)
+    in_off = serve.pack_inputs(batch, out)
+    assert in_off.shape == (300,) and in_off[0] == 0
+    for i, q in enumerate(batch):
+        a = int(in_off[i])
+        assert np.array_equal(out[a: a + q.r.size], q.r.ravel())
+        end = a + q.r.size
+        if q.warm_of < 0:
+            assert np.array_equal(out[end: end + q.n], q.x0)
+            end += q.n
+        # the parts follow one another with no gap
+        assert end == (int(in_off[i + 1]) if i + 1 < len(batch) else n_in)
+    assert np.all(np.isnan(out[n_in:]))
+
+
+def test_arena_size_classes():
+    cls = [serve._Arena.size_class(b) for b in range(1, 1 << 16, 3)]
+    for b, c in zip(range(1, 1 << 16, 3), cls):
+        e = -(-b // 4)
+        assert c >= e and c >= 8
+        assert c <= max(8, e * 1.125)  # at most 12.5% over
+    assert cls == sorted(cls)
+    # eight classes per power of two above 64 elements
+    assert len({serve._Arena.size_class(4 * e) for e in range(1025, 2049)}) == 8
+
+
+def test_arena_reuses_and_bounds_its_cache():
+    arena = serve._Arena(budget=1 << 20, device="cpu")
+    a, ha = arena.take(4000, in_use=0)
+    assert ha == 4 * a.numel() == 4 * serve._Arena.size_class(4000)
+    arena.give(a)
+    b, hb = arena.take(3990, in_use=0)  # same class: the same block back
+    assert b is a and hb == ha and arena.cached == 0
+    c, _ = arena.take(100_000, in_use=hb)
+    arena.give(c)
+    assert arena.cached == 4 * c.numel()
+    # a new block that would take in-use + cached over the budget drops the cache
+    d, hd = arena.take(1_000_000, in_use=hb)
+    assert arena.cached == 0 and not arena.free
+    assert hd >= 1_000_000
+
+
+def _cpu_server(sizes, steps):
+    """A Server with models on the host, enough to build descriptors."""
+    import torch
+
+    pool = serve.ModelPool.__new__(serve.ModelPool)
+    pool.steps = steps
+    pool.models = {}
+    for n in sizes:
+        pr = serve.inputs.diag_tracking(n, T=steps, seed=n).astype(np.float32)
+        dev = {f: torch.from_numpy(getattr(pr, f)) for f in serve._MODEL_FIELDS}
+        pool.models[n] = (pr, dev)
+    srv = serve.Server.__new__(serve.Server)
+    srv.pool, srv.reuse_warm = pool, True
+    srv.model_ptrs = {n: (pr.m, {f: dev[f].data_ptr() for f in serve._MODEL_FIELDS})
+                      for n, (pr, dev) in pool.models.items()}
+    return srv
+
+
+def test_descriptors_address_each_request(stream):
+    """The batch descriptors, built array-wise, against the layout written out
+    request by request: model windows, packed references and x_0, warm x_0 at
+    the predecessor's x*_s, and S, K of a reused warm request in its owner's
+    outputs from step skoff on."""
+    from paper_2104_03186_gb300 import lqt
+
+    sizes, steps = (4, 8, 16, 32), 4096
+    srv = _cpu_server(sizes, steps)
+    batch = stream[:400]
+    byid = {q.rid: q for q in stream}
+    base = 0x7F0000000000
+    for q in stream[:400]:
+        q.m = q.n // 2
+        q.nbytes = serve.out_bytes(q.n, q.m, q.T)
+        q.xoff = (q.T + 1) * q.n * q.n + (q.T + 1) * q.n + q.T * q.m * q.n
+        q.out_ptr = base + (q.rid << 24)
+        q.owner, q.skoff, q.reused = q.rid, 0, False
+    # warm requests of n >= 8 whose predecessor is in the batch reuse its S, K
+    for q in batch:
+        if q.warm_of >= 0 and q.n >= 8 and q.warm_of in byid and byid[q.warm_of].out_ptr:
+            prior = byid[q.warm_of]
+            q.reused = True
+            q.owner, q.skoff = ((prior.owner, prior.skoff + q.shift) if prior.reused
+                                else (prior.rid, q.shift))
+    assert sum(q.reused for q in batch) > 20
+    din, dup = 0x7E0000000000, 0x7D0000000000
+    in_off = np.cumsum([0] + [q.r.size + 7 for q in batch])[:-1]
+    u_off = np.cumsum([0] + [q.T * q.m for q in batch])[:-1]
+    it = srv._items(np.zeros(len(batch), lqt.BATCH_ITEM), batch, in_off, u_off, din, dup, byid)
+    for i, q in enumerate(batch):
+        n, m, T = q.n, q.m, q.T
+        P, S = it["problem"][i], it["solution"][i]
+        ptr = srv.model_ptrs[n][1]
+        assert (P["n"], P["m"], P["p"], P["pT"], P["T"]) == (n, m, n, n, T)
+        assert P["F"]["ptr"] == ptr["F"] + 4 * q.offset * n * n and P["F"]["step_stride"] == n * n
+        assert P["L"]["ptr"] == ptr["L"] + 4 * q.offset * n * m and P["L"]["step_stride"] == n * m
+        assert P["X"]["ptr"] == ptr["X"] + 4 * q.offset * n * n
+        assert (P["U"]["ptr"], P["U"]["step_stride"], P["H"]["ptr"]) == (ptr["U"], 0, ptr["H"])
+        assert (P["HT"], P["XT"], P["c"]["ptr"]) == (ptr["HT"], ptr["XT"], 0)
+        r0 = din + 4 * int(in_off[i])
+        assert P["r"]["ptr"] == r0 and P["r"]["step_stride"] == n
+        assert P["rT"] == r0 + 4 * T * n
+        if q.warm_of < 0:
+            assert P["x0"] == r0 + 4 * (T + 1) * n
+        else:
+            prior = byid[q.warm_of]
+            assert P["x0"] == prior.out_ptr + 4 * (prior.xoff + q.shift * n)
+        v = q.out_ptr + 4 * (T + 1) * n * n
+        assert S["v"] == v and S["x"] == q.out_ptr + 4 * q.xoff
+        assert S["u"] == dup + 4 * int(u_off[i])
+        if q.reused:
+            own = byid[q.owner]
+            To = own.T
+            assert S["S"] == own.out_ptr + 4 * q.skoff * n * n
+            assert S["K"] == own.out_ptr + 4 * ((To + 1) * n * n + (To + 1) * n) + 4 * q.skoff * n * m
+        else:
+            assert S["S"] == q.out_ptr
+            assert S["K"] == v + 4 * (T + 1) * n
