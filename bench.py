@@ -695,7 +695,8 @@ def run_serving(args):
     """20000-request Poisson streams at 2k..50k requests/s: n in {4,8,16,32},
     m = n/2, T log-uniform in [32, 2048], 30% warm starts (receding horizon
     from the previous request's device-resident state), admission by a device
-    memory budget of 8 GiB, up to 4 batches in flight."""
+    memory budget of 8 GiB, up to 8 batches of at most 256 requests in
+    flight."""
     from paper_2104_03186_gb300 import serve
 
     pool = serve.ModelPool((4, 8, 16, 32), steps=4096, seed=11)
@@ -705,7 +706,7 @@ def run_serving(args):
     for rate in (2000, 5000, 10000, 20000, 50000):
         for reuse in ((True, False) if rate >= 20000 else (True,)):
             reqs = serve.make_requests(args.serve_requests, rate=float(rate), seed=rate)
-            _, summ = serve.Server(pool, memory_budget=8 << 30, streams=4,
+            _, summ = serve.Server(pool, memory_budget=8 << 30, streams=8, max_batch=256,
                                    reuse_warm=reuse).run(reqs)
             summ["arrival_rate_per_s"] = rate
             summ["reuse_warm"] = reuse
@@ -715,7 +716,8 @@ def run_serving(args):
     return {"workload": "Poisson stream of %d LQT requests per rate; n in {4,8,16,32}, m=n/2, "
                         "T log-uniform in [32,2048], time-varying device-resident models "
                         "(diag tracking), fresh reference and x0 per request, 30%% warm starts "
-                        "with shifted horizon; 8 GiB admission budget; FP32; reuse_warm: warm "
+                        "with shifted horizon; 8 GiB admission budget; up to 8 batches of at "
+                        "most 256 requests in flight; FP32; reuse_warm: warm "
                         "requests solved from the S, K of the request that computed them "
                         "(lqt_solve_warm), else in full" % args.serve_requests,
             "rates": out, "warm_vs_cold_solve": run_warm_vs_cold()}
