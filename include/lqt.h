@@ -226,8 +226,11 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
  *           queue.
  *   n >= 8: the chunked pipeline of lqt_solve with all problems of one size
  *           in each of its launches: every problem's steps are cut into a
- *           power-of-two number of chunks of at most about 128 steps, and
- *           one launch per tree level sweeps the chunk results of all of them.
+ *           power-of-two number of chunks (of the length lqt_batch_set_tuning
+ *           sets, by default at most 64 steps), whose results are swept tree
+ *           level by tree level, by one launch per level or by one
+ *           cooperative launch per size (the launch mode of
+ *           lqt_batch_set_tuning).
  *   items: HOST array of `count` descriptors; each holds device pointers to a
  *          problem's inputs and outputs, with the layouts of lqt_problem and
  *          lqt_solution.  The array may be reused when the call returns.
@@ -244,8 +247,12 @@ lqt_status lqt_solve_host(const lqt_problem *host_prob, const lqt_solution *host
  * sizes side by side on streams of the calling host thread (created on its
  * first such call on a device and kept until the process exits: make that
  * first call before any stream capture), forked from and joined back to
- * `stream` with events; the outputs are those of one stream, bit for bit.  Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or
- * LQT_ECUDA on argument or launch errors. */
+ * `stream` with events; the outputs are those of one stream, bit for bit.
+ * Returns LQT_EINVAL, LQT_EUNSUPPORTED, LQT_ENOMEM or LQT_ECUDA on argument or
+ * launch errors.  Work queued before a launch error stays queued, ordered
+ * before whatever the caller queues next on `stream` (the side streams are
+ * joined back on every return): keep the workspace and outputs until
+ * `stream` has passed that point. */
 typedef struct {
     lqt_problem problem;
     lqt_solution solution;

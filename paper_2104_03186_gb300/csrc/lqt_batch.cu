@@ -247,20 +247,29 @@ extern "C" lqt_status lqt_solve_batched(const lqt_batch_item* items, int32_t cou
         }
     }
     char* lane_ws = base + head_bytes(count);
+    // The auxiliary streams that already hold part of the batch rejoin the
+    // caller's stream on every return, an error included: the work they hold
+    // still uses the workspace, and a capture on `stream` must end joined.
+    int forked = 0;
+    auto rejoin = [&](lqt_status st) {
+        for (int i = 0; i < forked; ++i)
+            if (cudaEventRecord(aux->join[i], aux->s[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, aux->join[i], 0) != cudaSuccess)
+                st = st == LQT_OK ? LQT_ECUDA : st;
+        return st;
+    };
     for (size_t i = 0; i < groups.size(); ++i) {
         const std::vector<int>& g = groups[i];
         cudaStream_t gs = s;
         if (aux) {
             gs = aux->s[i];
-            if (cudaStreamWaitEvent(gs, aux->fork, 0) != cudaSuccess) return LQT_ECUDA;
+            if (cudaStreamWaitEvent(gs, aux->fork, 0) != cudaSuccess) return rejoin(LQT_ECUDA);
+            forked = (int)i + 1;
         }
         const lqt_status st = chain_batch_solve(items, g.data(), (int)g.size(), lane_ws,
                                                 group_bytes[i], status, gs);
-        if (st != LQT_OK) return st;
-        if (aux && (cudaEventRecord(aux->join[i], gs) != cudaSuccess ||
-                    cudaStreamWaitEvent(s, aux->join[i], 0) != cudaSuccess))
-            return LQT_ECUDA;
+        if (st != LQT_OK) return rejoin(st);
         lane_ws += group_bytes[i];
     }
-    return LQT_OK;
+    return rejoin(LQT_OK);
 }
