@@ -7,8 +7,12 @@ continues a previous one: it reuses the previous request's model shifted by s
 steps (a receding horizon) and starts from that request's device-resident
 predicted state x*_s.
 
-The loop admits arrived requests while their device memory fits the budget,
-groups whatever has been admitted into a batch as soon as a stream is free,
+The loop admits arrived requests while their device memory fits the budget
+(the outputs of finished requests that warm requests will still read count
+too; with nothing admitted or in flight the next request is admitted even
+over the budget, so that the stream always moves and those outputs are
+eventually released), groups whatever has been admitted into a batch as soon
+as a stream is free,
 and solves the batch's cold requests with one lqt_solve_batched call (per
 state size present, one persistent launch for n = 4 and one chunked pipeline
 for n >= 8).  A warm request's S_k and K_k are those of the request it
@@ -311,10 +315,12 @@ class Server:
         """Host copies of a completed request's S, v, K, x* (u* is q.u)."""
         n, T = q.n, q.T
         m = self.pool.models[n][0].m
-        res = unpack_outputs(q.out[: q.nbytes // 4].cpu().numpy(), n, m, T)
+        # copies (a block goes back to the arena once released)
+        res = unpack_outputs(q.out[: q.nbytes // 4].to("cpu", copy=True).numpy(), n, m, T)
         if self._reused(q):
             own = byid[q.owner]
-            full = unpack_outputs(own.out[: own.nbytes // 4].cpu().numpy(), n, m, own.T)
+            full = unpack_outputs(own.out[: own.nbytes // 4].to("cpu", copy=True).numpy(),
+                                  n, m, own.T)
             res["S"] = full["S"][q.skoff: q.skoff + T + 1].copy()
             res["K"] = full["K"][q.skoff: q.skoff + T].copy()
         return res

@@ -209,3 +209,169 @@ def test_descriptors_address_each_request(stream):
         else:
             assert S["S"] == q.out_ptr
             assert S["K"] == v + 4 * (T + 1) * n
+
+
+def _fview(ptr, count):
+    """float32 view of host memory at a raw address (the fake solves below)."""
+    import ctypes
+
+    if count == 0:
+        return np.zeros(0, np.float32)
+    return np.ctypeslib.as_array((ctypes.c_float * count).from_address(int(ptr)))
+
+
+def _rollout(x0, r):
+    """x_0 = x0, x_{k+1} = x_k + r_k: a stand-in trajectory that depends on
+    the initial state and every reference."""
+    T = r.shape[0] - 1
+    x = np.empty((T + 1, r.shape[1]), np.float32)
+    x[0] = x0
+    for k in range(T):
+        x[k + 1] = x[k] + r[k]
+    return x
+
+
+def _fake_solve(it, warm):
+    """Reads each descriptor's inputs through its addresses and writes outputs
+    that identify them: S_k[0,0] = F_k[0,0] and K_k[0,0] = L_k[0,0] of the
+    model window (a warm solve instead checks that the S and K it is given
+    are those), x* = _rollout(x_0, r), u*_k = r_k[:m] + x*_k[:m] + K_k[0,0]."""
+    for row in it:
+        P, S = row["problem"], row["solution"]
+        n, m, T = int(P["n"]), int(P["m"]), int(P["T"])
+        F = _fview(P["F"]["ptr"], T * n * n).reshape(T, n, n)
+        L = _fview(P["L"]["ptr"], T * n * m).reshape(T, n, m)
+        r = _fview(P["r"]["ptr"], (T + 1) * n).reshape(T + 1, n)
+        assert int(P["rT"]) == int(P["r"]["ptr"]) + 4 * T * n
+        x0 = _fview(P["x0"], n).copy()
+        Sk = _fview(S["S"], (T + 1) * n * n).reshape(T + 1, n, n)
+        K = _fview(S["K"], T * m * n).reshape(T, m, n)
+        if warm:
+            assert np.array_equal(Sk[:T, 0, 0], F[:, 0, 0])
+            assert np.array_equal(K[:, 0, 0], L[:, 0, 0])
+        else:
+            Sk[:T, 0, 0] = F[:, 0, 0]
+            K[:, 0, 0] = L[:, 0, 0]
+        x = _fview(S["x"], (T + 1) * n).reshape(T + 1, n)
+        x[:] = _rollout(x0, r)
+        _fview(S["u"], T * m).reshape(T, m)[:] = r[:T, :m] + x[:T, :m] + K[:, 0, 0][:, None]
+
+
+class _FakeStream:
+    def wait_event(self, ev):
+        pass
+
+
+class _FakeEvent:
+    """Completes on its second query, so batches stay in flight a while."""
+
+    def __init__(self):
+        self.polls = 0
+
+    def record(self, stream=None):
+        pass
+
+    def query(self):
+        self.polls += 1
+        return self.polls >= 2
+
+
+class _FakeSlot:
+    """A stream slot with its staging buffers in host memory."""
+
+    def __init__(self):
+        self.stream, self.warm_stream = _FakeStream(), _FakeStream()
+        self.cap_in = self.cap_u = self.cap_items = 0
+        self.ws = self.ws_warm = None
+        self.ensure(1 << 12, 1 << 11, 4)
+
+    def ensure(self, in_elems, u_elems, count):
+        import torch
+
+        from paper_2104_03186_gb300 import lqt
+
+        if in_elems > self.cap_in:
+            self.cap_in = max(in_elems, 2 * self.cap_in)
+            self.h_in, self.d_in = torch.zeros(self.cap_in), torch.zeros(self.cap_in)
+            self.h_in_np = self.h_in.numpy()
+        if u_elems > self.cap_u:
+            self.cap_u = max(u_elems, 2 * self.cap_u)
+            self.h_u, self.d_u = torch.zeros(self.cap_u), torch.zeros(self.cap_u)
+            self.h_u_np = self.h_u.numpy()
+        if count > self.cap_items:
+            self.cap_items = max(count, 2 * self.cap_items)
+            self.items = np.zeros(self.cap_items, dtype=lqt.BATCH_ITEM)
+
+    def ensure_ws(self, nbytes, warm=False):
+        pass
+
+
+def test_serving_loop_plumbing_on_host(monkeypatch):
+    """The serving loop (admission, parking of warm requests, batching, warm
+    reuse, the output arena, release of outputs) run on the host: device
+    buffers and streams replaced by host ones and the solver by _fake_solve,
+    which reads and writes through the descriptors' addresses.  Every
+    request's u*, x* and S must be the ones its own inputs give (its model
+    window, its references, its x_0 or its predecessor's x*_s), read back
+    after the loop has recycled blocks for later requests."""
+    import contextlib
+
+    import torch
+
+    from paper_2104_03186_gb300 import lqt
+
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    monkeypatch.setattr(lqt, "lqt_batch_workspace_bytes_array", lambda it: 1)
+    monkeypatch.setattr(lqt, "lqt_warm_workspace_bytes_array", lambda it: 1)
+    monkeypatch.setattr(lqt, "lqt_solve_batched_array", lambda it, ws, st: _fake_solve(it, False))
+    monkeypatch.setattr(lqt, "lqt_solve_warm_array", lambda it, ws, st: _fake_solve(it, True))
+
+    srv = _cpu_server((4, 8, 16, 32), 1024)
+    pool = srv.pool
+    budget = 6 << 20
+    srv.budget, srv.max_batch, srv.keep_results = budget, 12, True
+    srv.mem = srv.peak_mem = srv.batches = srv.launches = 0
+    srv.slots = [_FakeSlot() for _ in range(3)]
+    srv.arena = serve._Arena(budget, device="cpu")
+    reqs = serve.make_requests(400, rate=1e5, seed=21, t_lo=8, t_hi=256, pool_steps=1024,
+                               warm_frac=0.5)
+    # the budget binds except when nothing is admitted or in flight: every
+    # admission that takes the blocks in use over it must find the loop idle
+    over, pending, inflight = [], [0], set()
+    alloc, launch = srv._alloc, srv._launch
+
+    def checked_alloc(q):
+        before = srv.mem
+        alloc(q)
+        if srv.mem > budget:
+            over.append(before)
+            assert pending[0] == 0 and not any(ev.polls < 2 for ev in inflight)
+        pending[0] += 1
+
+    def counted_launch(batch, slot, byid):
+        pending[0] -= len(batch)
+        item = launch(batch, slot, byid)
+        inflight.add(item[1])
+        return item
+
+    srv._alloc, srv._launch = checked_alloc, counted_launch
+    _, summary = srv.run(reqs, realtime=False)
+
+    assert summary["requests"] == 400 and summary["batches"] > 10
+    assert summary["warm_reused"] > 10, summary
+    assert srv.mem == 0 and all(q.out is None for q in reqs)  # every block released
+    # over the budget only on top of blocks still held for warm requests
+    assert all(0 < before for before in over) and len(over) < 20
+    xs = {}
+    for q in reqs:  # a predecessor precedes its warm successors
+        pr = pool.models[q.n][0]
+        x0 = q.x0 if q.warm_of < 0 else xs[q.warm_of][q.shift]
+        xs[q.rid] = _rollout(x0, q.r)
+        w = slice(q.offset, q.offset + q.T)
+        m = pr.m
+        assert np.array_equal(q.u, q.r[: q.T, :m] + xs[q.rid][: q.T, :m] + pr.L[w, 0, 0][:, None])
+        assert np.array_equal(q.result["x"], xs[q.rid])
+        assert np.array_equal(q.result["S"][: q.T, 0, 0], pr.F[w, 0, 0])
+        assert np.array_equal(q.result["K"][:, 0, 0], pr.L[w, 0, 0])
