@@ -217,6 +217,39 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _check_array(where: str, a, code: int, per_step: Optional[int] = None, steps: int = 0,
+                 numel: Optional[int] = None) -> None:
+    """What a pointer cannot carry through the C ABI, checked on the array
+    itself: C-contiguous storage, the element type of the problem's dtype code
+    (not checked for other codes, which the library rejects), and the extent.
+    per_step: a per-step array of `per_step` elements a step, with one step
+    (stride 0) or at least `steps`; numel: at least that many elements.
+    Raises LQTError(LQT_EINVAL) naming the array."""
+    shape = tuple(a.shape)
+    if isinstance(a, np.ndarray):
+        contiguous = a.flags.c_contiguous
+        want = {LQT_F32: np.float32, LQT_F64: np.float64}.get(code)
+    else:
+        import torch
+
+        contiguous = a.is_contiguous()
+        want = {LQT_F32: torch.float32, LQT_F64: torch.float64}.get(code)
+    if not contiguous:
+        raise LQTError(LQT_EINVAL, "%s: not contiguous" % where)
+    if want is not None and a.dtype != want:
+        raise LQTError(LQT_EINVAL, "%s: element type %s, the problem's is %s" % (where, a.dtype, want))
+    if per_step is not None:
+        got = int(np.prod(shape[1:])) if shape else 0
+        if not shape or got != per_step:
+            raise LQTError(LQT_EINVAL, "%s: %d elements a step, expected %d" % (where, got, per_step))
+        if shape[0] != 1 and shape[0] < steps:
+            raise LQTError(LQT_EINVAL, "%s: %d steps, expected 1 or at least %d"
+                           % (where, shape[0], steps))
+    if numel is not None and int(np.prod(shape)) < numel:
+        raise LQTError(LQT_EINVAL, "%s: %d elements, expected at least %d"
+                       % (where, int(np.prod(shape)), numel))
+
+
 class Problem:
     """An LQT problem whose arrays are torch tensors (device or pinned host) or
     numpy arrays (host), plus the lqt_problem struct that points at them."""
@@ -227,15 +260,20 @@ class Problem:
         self.arrays = arrays
         s = lqt_problem()
         s.n, s.m, s.p, s.pT, s.T, s.dtype = n, m, p, pT, T, dtype
+        step_size = {"F": n * n, "c": n, "L": n * m, "U": m * m, "H": p * n, "r": p, "X": p * p}
         for f in STEP_FIELDS:
             a = arrays.get(f)
             if a is None:
                 setattr(s, f, lqt_in(None, 0))
             else:
-                per_step = int(np.prod(a.shape[1:]))
-                setattr(s, f, lqt_in(_ptr(a), 0 if a.shape[0] == 1 else per_step))
+                _check_array(f, a, dtype, per_step=step_size[f], steps=T)
+                setattr(s, f, lqt_in(_ptr(a), 0 if a.shape[0] == 1 else step_size[f]))
+        terminal_size = {"HT": pT * n, "rT": pT, "XT": pT * pT, "x0": n}
         for f in TERMINAL_FIELDS:
-            setattr(s, f, _ptr(arrays.get(f)))
+            a = arrays.get(f)
+            if a is not None:
+                _check_array(f, a, dtype, numel=terminal_size[f])
+            setattr(s, f, _ptr(a))
         self.struct = s
 
     @classmethod
@@ -301,8 +339,17 @@ def _cross(c):
     return None if c is None else ctypes.byref(c.struct)
 
 
-def solution_struct(out: Dict[str, object]) -> lqt_solution:
+def solution_struct(out: Dict[str, object], prob: Optional["Problem"] = None) -> lqt_solution:
+    """The lqt_solution struct of the output arrays; with `prob`, each array is
+    first checked (contiguous, the problem's element type, at least the
+    elements the solve writes)."""
     s = lqt_solution()
+    if prob is not None:
+        n, m, T = prob.n, prob.m, prob.T
+        size = {"S": (T + 1) * n * n, "v": (T + 1) * n, "K": T * m * n, "x": (T + 1) * n,
+                "u": T * m}
+        for f in OUTPUT_FIELDS:
+            _check_array(f, out[f], prob.dtype, numel=size[f])
     for f in OUTPUT_FIELDS:
         setattr(s, f, _ptr(out[f]) if out[f].numel() > 0 else None)
     return s
@@ -342,7 +389,7 @@ def _nbytes(t) -> int:
 
 
 def lqt_solve(prob: Problem, out: Dict[str, object], workspace, stream=None, opts=None) -> None:
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
                         _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
     if st != LQT_OK:
@@ -351,7 +398,7 @@ def lqt_solve(prob: Problem, out: Dict[str, object], workspace, stream=None, opt
 
 def lqt_riccati_sequential(prob: Problem, out: Dict[str, object], workspace, stream=None,
                            opts=None) -> None:
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_riccati_sequential(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
                                      _ptr(workspace), _nbytes(workspace), _stream_handle(stream))
     if st != LQT_OK:
@@ -366,7 +413,7 @@ def lqt_cross_workspace_bytes(prob: Problem, cross: Optional[Cross], opts=None) 
 def lqt_solve_cross(prob: Problem, cross: Optional[Cross], out: Dict[str, object], workspace,
                     stream=None, opts=None) -> None:
     """Generalised-cost solve (Sec. IV-D); asynchronous like lqt_solve."""
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve_cross(ctypes.byref(prob.struct), _cross(cross), ctypes.byref(sol),
                               _opts(opts), _ptr(workspace), _nbytes(workspace),
                               _stream_handle(stream))
@@ -394,7 +441,7 @@ def lqt_nonlinear_workspace_bytes(prob: Problem, nl: lqt_nonlinear, opts=None) -
 def lqt_solve_nonlinear(prob: Problem, nl: lqt_nonlinear, out: Dict[str, object], workspace,
                         stream=None, opts=None) -> None:
     """Iterated nonlinear LQT (Sec. IV-D); asynchronous like lqt_solve."""
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve_nonlinear(ctypes.byref(prob.struct), ctypes.byref(nl), ctypes.byref(sol),
                                   _opts(opts), _ptr(workspace), _nbytes(workspace),
                                   _stream_handle(stream))
@@ -409,7 +456,7 @@ def lqt_condensed_workspace_bytes(prob: Problem, B: int, opts=None) -> int:
 def lqt_solve_condensed(prob: Problem, B: int, out: Dict[str, object], workspace, stream=None,
                         opts=None) -> None:
     """Partial condensing in blocks of B steps (Sec. V-C); asynchronous like lqt_solve."""
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve_condensed(ctypes.byref(prob.struct), int(B), ctypes.byref(sol),
                                   _opts(opts), _ptr(workspace), _nbytes(workspace),
                                   _stream_handle(stream))
@@ -428,7 +475,7 @@ def lqt_host_solve_bytes(prob: Problem, opts=None) -> int:
 def lqt_solve_host(prob: Problem, out: Dict[str, object], device_buffer, stream=None,
                    opts=None) -> int:
     """Host-pointer solve; returns the device status (raises on launch errors)."""
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve_host(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
                              _ptr(device_buffer), _nbytes(device_buffer), _stream_handle(stream))
     if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):
@@ -441,7 +488,7 @@ def _items(problems, outputs):
     arr = (lqt_batch_item * max(count, 1))()
     for i, (P, out) in enumerate(zip(problems, outputs)):
         arr[i].problem = P.struct
-        arr[i].solution = solution_struct(out)
+        arr[i].solution = solution_struct(out, P)
     return arr
 
 
@@ -561,7 +608,7 @@ def lqt_solve_static(prob: Problem, out: Dict[str, object], stream=None, opts=No
     returns the device status of the solve; raises on argument, size
     (LQT_ENOMEM: the problem needs more than LQT_STATIC_SCRATCH_BYTES) and
     launch errors.  Calls that overlap on the GPU share the array and race."""
-    sol = solution_struct(out)
+    sol = solution_struct(out, prob)
     st = _lib.lqt_solve_static(ctypes.byref(prob.struct), ctypes.byref(sol), _opts(opts),
                                _stream_handle(stream))
     if st in (LQT_EINVAL, LQT_ENOMEM, LQT_EUNSUPPORTED, LQT_ECUDA):

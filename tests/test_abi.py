@@ -218,3 +218,46 @@ def test_batch_launch_modes(lib):
     finally:
         lib.lqt_batch_set_tuning([], "auto")
         lib.apply_tuned_plans()
+
+
+def test_binding_checks_arrays_before_the_call(lib):
+    """The binding rejects what a pointer cannot carry through the C ABI: a
+    non-contiguous array, the wrong element type, too few steps, the wrong
+    per-step size, too small a terminal or output array."""
+    P, arr = _host_problem(lib)
+    T = P.T
+
+    def rejected(**over):
+        a = dict(arr, **over)
+        with pytest.raises(lib.LQTError) as ei:
+            lib.Problem(P.n, P.m, P.p, P.pT, T, lib.LQT_F32, a)
+        assert ei.value.status == lib.LQT_EINVAL
+        return str(ei.value)
+
+    assert "not contiguous" in rejected(r=np.zeros((T, 4), np.float32)[:, ::2])
+    assert "element type" in rejected(F=arr["F"].astype(np.float64))
+    assert "steps" in rejected(r=np.zeros((T - 1, 2), np.float32))
+    assert "elements a step" in rejected(X=np.zeros((T, 3, 3), np.float32))
+    assert "x0" in rejected(x0=np.zeros(3, np.float32))
+    # one step (stride 0), exactly T steps and more than T steps are all valid
+    for r in (np.zeros((1, 2), np.float32), np.zeros((T, 2), np.float32),
+              np.zeros((T + 5, 2), np.float32)):
+        lib.Problem(P.n, P.m, P.p, P.pT, T, lib.LQT_F32, dict(arr, r=r))
+    # outputs: at least the elements the solve writes, the problem's type
+    n, m = P.n, P.m
+    out = {"S": np.zeros((T + 1, n, n), np.float32), "v": np.zeros((T + 1, n), np.float32),
+           "K": np.zeros((T, m, n), np.float32), "x": np.zeros((T + 1, n), np.float32),
+           "u": np.zeros((T, m), np.float32)}
+
+    class _Arr(np.ndarray):  # numpy arrays with a torch-style numel()
+        def numel(self):
+            return self.size
+
+    out = {k: v.view(_Arr) for k, v in out.items()}
+    lib.solution_struct(out, P)
+    for k, bad in (("K", np.zeros((T - 1, m, n), np.float32)),
+                   ("u", np.zeros((T, m), np.float64)),
+                   ("S", np.zeros((T + 1, n, 2 * n), np.float32)[:, :, ::2])):
+        with pytest.raises(lib.LQTError) as ei:
+            lib.solution_struct(dict(out, **{k: bad.view(_Arr)}), P)
+        assert ei.value.status == lib.LQT_EINVAL and k in str(ei.value)
