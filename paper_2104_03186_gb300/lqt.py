@@ -335,8 +335,15 @@ class Cross:
         return cls(cv(ct.M), cv(ct.s))
 
 
-def _cross(c):
-    return None if c is None else ctypes.byref(c.struct)
+def _cross(c, prob: "Problem"):
+    """The lqt_cross struct of `c` (None: no cross terms), its arrays checked
+    against `prob`: M_k is p x m, s_k has m entries, one step or at least T."""
+    if c is None:
+        return None
+    for f, a, size in (("cross M", c.M, prob.p * prob.m), ("cross s", c.s, prob.m)):
+        if a is not None:
+            _check_array(f, a, prob.dtype, per_step=size, steps=prob.T)
+    return ctypes.byref(c.struct)
 
 
 def solution_struct(out: Dict[str, object], prob: Optional["Problem"] = None) -> lqt_solution:
@@ -406,7 +413,7 @@ def lqt_riccati_sequential(prob: Problem, out: Dict[str, object], workspace, str
 
 
 def lqt_cross_workspace_bytes(prob: Problem, cross: Optional[Cross], opts=None) -> int:
-    return int(_lib.lqt_cross_workspace_bytes(ctypes.byref(prob.struct), _cross(cross),
+    return int(_lib.lqt_cross_workspace_bytes(ctypes.byref(prob.struct), _cross(cross, prob),
                                               _opts(opts)))
 
 
@@ -414,7 +421,7 @@ def lqt_solve_cross(prob: Problem, cross: Optional[Cross], out: Dict[str, object
                     stream=None, opts=None) -> None:
     """Generalised-cost solve (Sec. IV-D); asynchronous like lqt_solve."""
     sol = solution_struct(out, prob)
-    st = _lib.lqt_solve_cross(ctypes.byref(prob.struct), _cross(cross), ctypes.byref(sol),
+    st = _lib.lqt_solve_cross(ctypes.byref(prob.struct), _cross(cross, prob), ctypes.byref(sol),
                               _opts(opts), _ptr(workspace), _nbytes(workspace),
                               _stream_handle(stream))
     if st != LQT_OK:

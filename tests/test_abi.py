@@ -261,3 +261,16 @@ def test_binding_checks_arrays_before_the_call(lib):
         with pytest.raises(lib.LQTError) as ei:
             lib.solution_struct(dict(out, **{k: bad.view(_Arr)}), P)
         assert ei.value.status == lib.LQT_EINVAL and k in str(ei.value)
+
+
+def test_binding_checks_cross_arrays(lib):
+    P, _ = _host_problem(lib)
+    T, p, m = P.T, P.p, P.m
+    good = lib.Cross(np.zeros((T, p, m), np.float32), np.zeros((1, m), np.float32))
+    assert lib._cross(good, P) is not None
+    for M, s, what in ((np.zeros((T, p, m + 1), np.float32), None, "elements a step"),
+                       (np.zeros((T - 3, p, m), np.float32), None, "steps"),
+                       (None, np.zeros((T, m), np.float64), "element type")):
+        with pytest.raises(lib.LQTError) as ei:
+            lib._cross(lib.Cross(M, s), P)
+        assert ei.value.status == lib.LQT_EINVAL and what in str(ei.value)
