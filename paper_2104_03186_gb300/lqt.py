@@ -440,6 +440,15 @@ def nonlinear(iterations: int = 10, dt: float = 0.1, sequential: bool = False,
     return nl
 
 
+def _check_nominal(prob: Problem, x_init, u_init) -> None:
+    """A first nominal of the iterated solve: x_init (T+1) x n, u_init T x m,
+    of the problem's element type and contiguous (LQTError(LQT_EINVAL))."""
+    if x_init is not None:
+        _check_array("x_init", x_init, prob.dtype, numel=(prob.T + 1) * prob.n)
+    if u_init is not None:
+        _check_array("u_init", u_init, prob.dtype, numel=prob.T * prob.m)
+
+
 def lqt_nonlinear_workspace_bytes(prob: Problem, nl: lqt_nonlinear, opts=None) -> int:
     return int(_lib.lqt_nonlinear_workspace_bytes(ctypes.byref(prob.struct), ctypes.byref(nl),
                                                   _opts(opts)))
@@ -691,6 +700,7 @@ def solve_nonlinear(prob: Problem, iterations: int = 10, dt: float = 0.1, sequen
     (the unicycle model)."""
     import torch
 
+    _check_nominal(prob, x_init, u_init)
     nl = nonlinear(iterations, dt, sequential, LQT_MODEL_UNICYCLE, x_init, u_init)
     out = prob.allocate_outputs()
     nbytes = lqt_nonlinear_workspace_bytes(prob, nl, opts)

@@ -274,3 +274,16 @@ def test_binding_checks_cross_arrays(lib):
         with pytest.raises(lib.LQTError) as ei:
             lib._cross(lib.Cross(M, s), P)
         assert ei.value.status == lib.LQT_EINVAL and what in str(ei.value)
+
+
+def test_binding_checks_the_first_nominal(lib):
+    P, _ = _host_problem(lib)
+    T, n, m = P.T, P.n, P.m
+    lib._check_nominal(P, np.zeros((T + 1, n), np.float32), np.zeros((T, m), np.float32))
+    lib._check_nominal(P, None, None)
+    for x, u, what in ((np.zeros((T, n), np.float32), None, "x_init"),
+                       (None, np.zeros((T, m), np.float64), "u_init"),
+                       (np.zeros((T + 1, 2 * n), np.float32)[:, ::2], None, "x_init")):
+        with pytest.raises(lib.LQTError) as ei:
+            lib._check_nominal(P, x, u)
+        assert ei.value.status == lib.LQT_EINVAL and what in str(ei.value)
