@@ -288,6 +288,9 @@ class Server:
         self.mem = 0          # bytes of the output blocks in use
         self.peak_mem = 0
         self.batches = 0
+        # per batch, the state sizes of its cold requests plus those of its
+        # reused warm ones: each runs as one pipeline (one launch at n = 4, one
+        # chunked pipeline at n >= 8)
         self.launches = 0
         self.arena = _Arena(memory_budget)
         # per state size: m and the device addresses of the model's arrays
@@ -442,7 +445,8 @@ class Server:
                      "time_steps": int(sum(q.T for q in reqs)),
                      "warm_requests": int(sum(q.warm_of >= 0 for q in reqs)),
                      "warm_reused": int(sum(self._reused(q) for q in reqs)),
-                     "batches": self.batches, "mean_batch": len(reqs) / max(self.batches, 1)}
+                     "batches": self.batches, "mean_batch": len(reqs) / max(self.batches, 1),
+                     "size_groups": self.launches}
 
     def _launch(self, batch: List[Request], slot: _Slot, byid):
         import torch

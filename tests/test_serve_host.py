@@ -360,6 +360,8 @@ def test_serving_loop_plumbing_on_host(monkeypatch):
     _, summary = srv.run(reqs, realtime=False)
 
     assert summary["requests"] == 400 and summary["batches"] > 10
+    # per batch, at least one size group and at most four sizes, cold and warm
+    assert summary["batches"] <= summary["size_groups"] <= 8 * summary["batches"]
     assert summary["warm_reused"] > 10, summary
     assert srv.mem == 0 and all(q.out is None for q in reqs)  # every block released
     # over the budget only on top of blocks still held for warm requests
