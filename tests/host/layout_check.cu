@@ -3,10 +3,12 @@
 //   tslot / tstride: padded slots of the field-major scan trees
 //   gstride:         spacing of the lane groups' shared-memory blocks
 //   top_smem_bytes:  shared memory of the top-level scan's replay
+//   ModelLayout:     the n <= 4 kernels' model area, read with vector loads
 #include <cstdio>
 
 #include "lqt_chain.cuh"
 #include "lqt_kernels.cuh"
+#include "lqt_variants.h"
 
 using namespace lqt;
 using lqt::chain::DownSmem;
@@ -96,6 +98,34 @@ static void group_checks(int size) {
     }
 }
 
+
+// The model area of the n <= 4 scan kernels: each part starts on a multiple of
+// 4 elements and the parts do not overlap (p up to 2N), and the area starts
+// 16 bytes into alignment in every kernel that places it (after the tree or
+// staging area of k_bwd_up, k_bwd_down, k_fwd_down, k_solo), so that
+// load_step's 16-byte vector loads of its parts are aligned.
+template <typename R, int N, int M>
+static void model_layout_checks() {
+    using ML = ModelLayout<N, M>;
+    constexpr int W = tile_threads<R, N, M>();
+    using SM = Smem<R, N, M, W>;
+    const int parts[] = {ML::OF, ML::OL, ML::OU, ML::OC, ML::OQ, ML::OHX};
+    for (int o : parts) CHECK(o % 4 == 0, "N=%d M=%d: part at %d", N, M, o);
+    CHECK(ML::OL >= ML::OF + N * N && ML::OU >= ML::OL + N * M && ML::OC >= ML::OU + M * M &&
+              ML::OQ >= ML::OC + N && ML::OHX >= ML::OQ + Dims<N>::SYM,
+          "N=%d M=%d: overlapping parts", N, M);
+    for (int p = 0; p <= 2 * N; ++p) {
+        CHECK(ML::OH(p) % 4 == 0 && ML::OH(p) >= ML::OHX + p * N, "N=%d p=%d: H part", N, p);
+        CHECK(ML::size(p) % 4 == 0 && ML::size(p) >= ML::OH(p) + p * N, "N=%d p=%d: size", N, p);
+    }
+    const int bases[] = {SM::UP_BIG, SM::DOWN_BIG, SM::FDOWN_BIG, SoloSmem<R, N, M, W>::BIG};
+    for (int b : bases) {
+        const long long at = kSmemHead + (long long)(b + SM::RBUF) * (long long)sizeof(R);
+        CHECK(at % 16 == 0, "N=%d M=%d W=%d: model area at byte %lld", N, M, W, at);
+    }
+}
+#define MODEL_LAYOUT_CHECK(R, N, M) model_layout_checks<R, N, M>();
+
 int main() {
     for (int W : {128, 256, 512}) tree_checks<float>(W);
     for (int W : {128, 256}) tree_checks<double>(W);  // FP64 tiles are at most 256 wide
@@ -112,6 +142,9 @@ int main() {
     CHECK(top_smem_bytes(Dims<2>::ELEM, Dims<2>::VALUE, 2, 256, 4, true) <= kTopSmemMax, "n=2");
     CHECK(top_smem_bytes(Dims<3>::ELEM, Dims<3>::VALUE, 3, 256, 4, true) <= kTopSmemMax, "n=3");
     CHECK(top_smem_bytes(Dims<4>::ELEM, Dims<4>::VALUE, 4, 256, 4, true) <= kTopSmemMax, "n=4");
+    LQT_VARIANTS_F32_SMALL(MODEL_LAYOUT_CHECK)
+    LQT_VARIANTS_F32_N4(MODEL_LAYOUT_CHECK)
+    LQT_VARIANTS_F64(MODEL_LAYOUT_CHECK)
     std::printf("%s (%d failures)\n", fails ? "layout checks FAILED" : "layout checks ok", fails);
     return fails ? 1 : 0;
 }

@@ -1,6 +1,6 @@
 """Host-side checks of the shared-memory layout helpers of the CUDA scan
 kernels (padded tree slots, lane-group block spacing, the replayed top scan's
-shared memory), compiled with nvcc from tests/host/layout_check.cu against the
+shared memory, the alignment of the n <= 4 kernels' model area), compiled with nvcc from tests/host/layout_check.cu against the
 library's own headers and run on the CPU."""
 import os
 import shutil
