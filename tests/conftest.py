@@ -10,6 +10,12 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    # The binding loads liblqt_gb300.so when it is imported, which some test
+    # modules do at collection: compile it first if it is missing or stale
+    # (nvcc cross-compiles without a GPU; an up-to-date build returns at once).
+    from paper_2104_03186_gb300 import build
+
+    build.build()
 
 
 @pytest.fixture(scope="session")
