@@ -287,3 +287,53 @@ def test_binding_checks_the_first_nominal(lib):
         with pytest.raises(lib.LQTError) as ei:
             lib._check_nominal(P, x, u)
         assert ei.value.status == lib.LQT_EINVAL and what in str(ei.value)
+
+
+def test_binding_constants_match_the_header(lib):
+    """Every enumerator and #define of include/lqt.h has the same value in the
+    binding."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lqt.h")).read(), flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, re.S):
+        for name, val in re.findall(r"(LQT_\w+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    for name, expr in re.findall(r"#define[ \t]+(LQT_\w+)[ \t]+(.+)", src):
+        if re.fullmatch(r"\(\(size_t\)\s*\d+\s*<<\s*\d+\)", expr.strip()):
+            a, b = re.findall(r"\d+", expr)
+            consts[name] = int(a) << int(b)
+    assert len(consts) >= 20, consts
+    for name, val in consts.items():
+        assert getattr(lib, name) == val, name
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    """Size and field offsets of every struct of include/lqt.h, from a C program
+    compiled against the header, equal those of the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {name: getattr(lib, name) for name in (
+        "lqt_in", "lqt_problem", "lqt_solution", "lqt_options", "lqt_batch_item",
+        "lqt_batch_tune_entry", "lqt_cross", "lqt_nonlinear")}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lqt.h"', "int main(void) {"]
+    for name, ct in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in ct._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", exe],
+                   check=True, capture_output=True, timeout=120)
+    got = {}
+    for ln in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for name, ct in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(ct), name
+        for f, _ in ct._fields_:
+            assert got[(name, f)] == getattr(ct, f).offset, (name, f)
