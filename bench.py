@@ -316,7 +316,9 @@ def graph_timed(launch, reps, flush, stream):
     """Device times (ms) of one call, launch(s), captured once in a CUDA graph and
     replayed (the headline's method; the host launch work stays out of the
     timed region), or of eager calls on `stream` if the call cannot be
-    captured.  The call must have run once before.  Returns (times, how)."""
+    captured.  The call must have run once before.  `stream` must be the
+    current stream: a graph replays there, and the events are recorded on
+    `stream`.  Returns (times, how)."""
     import torch
 
     try:
